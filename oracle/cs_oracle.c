@@ -1,0 +1,796 @@
+/*
+ * cs_oracle.c -- plain FP64 CPU oracle of the conservative spectral method for
+ * the Boltzmann collision operator (J. R. Haack, "A hybrid OpenMP and MPI
+ * implementation of a conservative spectral method for the Boltzmann
+ * equation", arXiv:1301.4195).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call, link or
+ * execute this file: only tests/, __graft_entry__.smoke() and bench.py's
+ * cpu_baseline / reference leg use it.  It shares no code, header, table or
+ * constant generator with the CUDA library.
+ *
+ * Every routine is written out from the paper's definitions, in the paper's
+ * order, without blocking or fusion.  The one liberty is that the
+ * forward/inverse discrete transforms are evaluated axis by axis (the 3-D
+ * sum of a product of per-axis exponentials factorises exactly).
+ *
+ * Readings of points the paper leaves open (each is also listed in the
+ * design notes):
+ *   - beta = 1 (elastic collisions; the collision law of Sec. 2 gives the
+ *     sinc form of G only for beta = 1).
+ *   - p = beta|zeta|/2 - |xi - beta zeta/2|, q = beta|zeta|/2 + |xi - beta zeta/2|
+ *     in the closed forms of Ghat (Sec. 2.2; p and q are not defined in the
+ *     text; this choice reproduces both printed forms).
+ *   - sinc(x) = sin(x)/x.
+ *   - trapezoid weights omega_m = dzeta^3 on the uniform grid (no endpoint
+ *     halving); likewise dv^3 in the integration matrix C.
+ *   - a term is dropped iff an axis index k - m + N/2 leaves [0, N-1]
+ *     (no periodic wrap, Sec. 3.2).
+ *   - Qtilde is the real part of the inverse transform.
+ *   - the projection is Q = Qt - C^T (C C^T)^{-1} C Qt (the printed sign and
+ *     transpose in Sec. 3.3 are garbled; this is the unique minimiser).
+ *   - r0 = L.
+ *   - transport: see or_transport_rk2 below.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_PI 3.14159265358979323846264338327950288
+
+/* ------------------------------------------------------------------------ */
+/* Grids, Sec. 3.1 ("meshpoints"): v_k = dv (k - N/2), zeta_k = dzeta (k - N/2),
+ * dv = 2L/N, dzeta = pi/L, 0 <= k_j <= N-1.                                  */
+
+double or_dv(int N, double L) { return 2.0 * L / N; }
+double or_dzeta(double L) { return OR_PI / L; }
+
+static int idx3(int N, int i, int j, int k) { return (i * N + j) * N + k; }
+
+/* ------------------------------------------------------------------------ */
+/* Gauss-Legendre nodes and weights on [-1, 1] by Newton's method on the
+ * three-term Legendre recurrence.                                           */
+void or_gauss_legendre(int n, double *x, double *w)
+{
+    for (int i = 0; i < n; ++i) {
+        double z = cos(OR_PI * (i + 0.75) / (n + 0.5));
+        double p0 = 0.0, p1 = 0.0, dp = 0.0;
+        for (int it = 0; it < 200; ++it) {
+            p0 = 1.0;
+            p1 = 0.0;
+            for (int j = 1; j <= n; ++j) {
+                double p2 = p1;
+                p1 = p0;
+                p0 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p2) / j;
+            }
+            dp = n * (z * p0 - p1) / (z * z - 1.0);
+            double step = p0 / dp;
+            z -= step;
+            if (fabs(step) < 1e-16) break;
+        }
+        /* re-evaluate the derivative at the converged node */
+        p0 = 1.0;
+        p1 = 0.0;
+        for (int j = 1; j <= n; ++j) {
+            double p2 = p1;
+            p1 = p0;
+            p0 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p2) / j;
+        }
+        dp = n * (z * p0 - p1) / (z * z - 1.0);
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Forward transform, Sec. 2.2 and 3.2:
+ *   fhat(zeta_k) = (2 pi)^{-3/2} dv^3 sum_j f(v_j) exp(-i zeta_k . v_j).
+ * Per axis zeta_k v_j = (2 pi / N)(k - N/2)(j - N/2), so the phase is taken
+ * from the exact integer residue ((k - N/2)(j - N/2)) mod N.
+ * f: [ncells][N^3] real.  fhat: [ncells][N^3][2] (re, im).                  */
+
+static void twiddle(int N, int k, int j, int sign, double *c, double *s)
+{
+    long r = (long)(k - N / 2) * (long)(j - N / 2);
+    r %= N;
+    if (r < 0) r += N;
+    double ang = 2.0 * OR_PI * (double)r / (double)N;
+    *c = cos(ang);
+    *s = sign * sin(ang);
+}
+
+/* One axis of a separable transform on complex data x[N^3][2], in place.
+ * axis 0,1,2; sign -1 forward, +1 inverse.                                  */
+static void axis_dft(int N, double *x, int axis, int sign)
+{
+    int M = N * N * N;
+    double *y = (double *)calloc((size_t)2 * M, sizeof(double));
+    for (int i1 = 0; i1 < N; ++i1)
+        for (int i2 = 0; i2 < N; ++i2)
+            for (int i3 = 0; i3 < N; ++i3) {
+                int kout[3] = {i1, i2, i3};
+                double re = 0.0, im = 0.0;
+                for (int j = 0; j < N; ++j) {
+                    int jin[3] = {i1, i2, i3};
+                    jin[axis] = j;
+                    double c, s;
+                    twiddle(N, kout[axis], j, sign, &c, &s);
+                    const double *xv = x + 2 * idx3(N, jin[0], jin[1], jin[2]);
+                    re += xv[0] * c - xv[1] * s;
+                    im += xv[0] * s + xv[1] * c;
+                }
+                y[2 * idx3(N, i1, i2, i3)] = re;
+                y[2 * idx3(N, i1, i2, i3) + 1] = im;
+            }
+    memcpy(x, y, sizeof(double) * 2 * M);
+    free(y);
+}
+
+int or_dft_forward(int N, double L, int ncells, const double *f, double *fhat)
+{
+    int M = N * N * N;
+    double dv = or_dv(N, L);
+    double cf = pow(2.0 * OR_PI, -1.5) * dv * dv * dv;
+    for (int c = 0; c < ncells; ++c) {
+        double *x = fhat + (size_t)2 * M * c;
+        for (int j = 0; j < M; ++j) {
+            x[2 * j] = f[(size_t)M * c + j];
+            x[2 * j + 1] = 0.0;
+        }
+        axis_dft(N, x, 2, -1);
+        axis_dft(N, x, 1, -1);
+        axis_dft(N, x, 0, -1);
+        for (int j = 0; j < 2 * M; ++j) x[j] *= cf;
+    }
+    return 0;
+}
+
+/* Inverse transform, Sec. 3.2:
+ *   Qt(v_j) = Re[(2 pi)^{-3/2} dzeta^3 sum_k Qhat(zeta_k) exp(+i zeta_k . v_j)] / eps.
+ * qimag (may be NULL) receives the imaginary part, a diagnostic only.       */
+int or_dft_inverse(int N, double L, int ncells, const double *qhat, double eps,
+                   double *qreal, double *qimag)
+{
+    int M = N * N * N;
+    double dz = or_dzeta(L);
+    double ci = pow(2.0 * OR_PI, -1.5) * dz * dz * dz / eps;
+    double *x = (double *)malloc(sizeof(double) * 2 * M);
+    for (int c = 0; c < ncells; ++c) {
+        memcpy(x, qhat + (size_t)2 * M * c, sizeof(double) * 2 * M);
+        axis_dft(N, x, 2, +1);
+        axis_dft(N, x, 1, +1);
+        axis_dft(N, x, 0, +1);
+        for (int j = 0; j < M; ++j) {
+            qreal[(size_t)M * c + j] = ci * x[2 * j];
+            if (qimag) qimag[(size_t)M * c + j] = ci * x[2 * j + 1];
+        }
+    }
+    free(x);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Convolution weights, Sec. 2.2 ("GHat_calc"), isotropic b = 1/(4 pi), d = 3:
+ *   Ghat(xi, zeta) = sqrt(2/pi) * int_0^{r0} r^{lambda+2}
+ *        [ sinc(r |zeta|/2) sinc(r |xi - zeta/2|) - sinc(r |xi|) ] dr.
+ * With a = |zeta|/2, b = |xi - zeta/2|, c = |xi| the first term is
+ *   (Phi(a - b) - Phi(a + b)) / (2 a b),  Phi(x) = int_0^{r0} r^lambda cos(x r) dr,
+ * and the second is Psi(c),  Psi(x) = int_0^{r0} r^{lambda+2} sinc(x r) dr.
+ * The closed forms printed for lambda = 1 and lambda = 0 are these Phi, Psi.
+ * Removable singularities: a = 0 gives Ghat = 0 exactly (G(u, 0) = 0);
+ * b = 0 gives first term Psi(a); x = 0 limits are the series' first terms.   */
+
+/* Phi by its Taylor series: r0^{l+1} sum_n (-1)^n y^{2n} / ((2n)! (2n+l+1)), y = x r0 */
+static double phi_series(double x, double r0, double lam)
+{
+    double y2 = (x * r0) * (x * r0);
+    double term = 1.0, sum = 0.0; /* term = (-1)^n y^{2n} / (2n)! */
+    for (int n = 0; n < 60; ++n) {
+        double t = term / (2.0 * n + lam + 1.0);
+        sum += t;
+        if (fabs(t) < 1e-18 * fabs(sum) && n > 2) break;
+        term *= -y2 / ((2.0 * n + 1.0) * (2.0 * n + 2.0));
+    }
+    return pow(r0, lam + 1.0) * sum;
+}
+
+/* Psi by its Taylor series: r0^{l+3} sum_n (-1)^n y^{2n} / ((2n+1)! (2n+l+3)) */
+static double psi_series(double x, double r0, double lam)
+{
+    double y2 = (x * r0) * (x * r0);
+    double term = 1.0, sum = 0.0; /* term = (-1)^n y^{2n} / (2n+1)! */
+    for (int n = 0; n < 60; ++n) {
+        double t = term / (2.0 * n + lam + 3.0);
+        sum += t;
+        if (fabs(t) < 1e-18 * fabs(sum) && n > 2) break;
+        term *= -y2 / ((2.0 * n + 2.0) * (2.0 * n + 3.0));
+    }
+    return pow(r0, lam + 3.0) * sum;
+}
+
+/* closed forms (lambda = 0 or 1), Sec. 2.2 */
+static double phi_closed(double x, double r0, int lam)
+{
+    double y = x * r0;
+    if (fabs(y) < 0.5) return phi_series(x, r0, (double)lam);
+    if (lam == 0) return sin(y) / x;
+    return (y * sin(y) + cos(y) - 1.0) / (x * x);
+}
+
+static double psi_closed(double x, double r0, int lam)
+{
+    double y = x * r0;
+    if (fabs(y) < 1.0) return psi_series(x, r0, (double)lam);
+    if (lam == 0) return (sin(y) - y * cos(y)) / (x * x * x);
+    return ((2.0 - y * y) * cos(y) + 2.0 * y * sin(y) - 2.0) / (x * x * x * x);
+}
+
+static double sinc(double x)
+{
+    if (fabs(x) < 1e-4) return 1.0 - x * x / 6.0 + x * x * x * x / 120.0;
+    return sin(x) / x;
+}
+
+/* Radial integral of the bracket by composite Gauss-Legendre; the first panel
+ * is graded geometrically toward r = 0 so that r^{lambda+2} with non-integer
+ * lambda is resolved.  This is the general-lambda route (Sec. 2.2: "a
+ * one-dimensional integral ... numerical quadrature") and, for integer
+ * lambda, an independent check of the closed forms.                        */
+double or_ghat_radial_quad(double a, double b, double c, double r0, double lam,
+                           int npanel, int nodes)
+{
+    double *x = (double *)malloc(sizeof(double) * nodes);
+    double *w = (double *)malloc(sizeof(double) * nodes);
+    or_gauss_legendre(nodes, x, w);
+    double h = r0 / npanel;
+    double total = 0.0;
+    for (int p = 0; p < npanel; ++p) {
+        /* sub-intervals: panel 0 is split as [0,h/2^G],[h/2^G,h/2^{G-1}],...,[h/2,h] */
+        int nsub = (p == 0) ? 12 : 1;
+        for (int sidx = 0; sidx < nsub; ++sidx) {
+            double lo, hi;
+            if (p == 0) {
+                hi = h / pow(2.0, (double)(nsub - 1 - sidx));
+                lo = (sidx == 0) ? 0.0 : h / pow(2.0, (double)(nsub - sidx));
+            } else {
+                lo = p * h;
+                hi = (p + 1) * h;
+            }
+            double mid = 0.5 * (lo + hi), half = 0.5 * (hi - lo);
+            for (int i = 0; i < nodes; ++i) {
+                double r = mid + half * x[i];
+                double g = sinc(a * r) * sinc(b * r) - sinc(c * r);
+                total += half * w[i] * pow(r, lam + 2.0) * g;
+            }
+        }
+    }
+    free(x);
+    free(w);
+    return total;
+}
+
+/* Ghat for grid indices k (zeta) and m (xi), each an int[3] in [0, N-1]. */
+double or_ghat(int N, double L, double lambda, const int *k, const int *m)
+{
+    double dz = or_dzeta(L);
+    double r0 = L;
+    int kp[3], mp[3];
+    long kk = 0, mm = 0, bb = 0;
+    for (int d = 0; d < 3; ++d) {
+        kp[d] = k[d] - N / 2;
+        mp[d] = m[d] - N / 2;
+        kk += (long)kp[d] * kp[d];
+        mm += (long)mp[d] * mp[d];
+        bb += (long)(2 * mp[d] - kp[d]) * (2 * mp[d] - kp[d]);
+    }
+    if (kk == 0) return 0.0; /* G(u, 0) = 0 */
+    double a = 0.5 * dz * sqrt((double)kk);  /* beta |zeta| / 2 */
+    double b = 0.5 * dz * sqrt((double)bb);  /* |xi - beta zeta / 2| */
+    double c = dz * sqrt((double)mm);        /* |xi| */
+    double pref = sqrt(2.0 / OR_PI);         /* 4 pi / (2 pi)^{3/2} */
+    int lam = (int)lambda;
+    if ((double)lam == lambda && (lam == 0 || lam == 1)) {
+        double t1;
+        if (bb == 0)
+            t1 = psi_closed(a, r0, lam);
+        else
+            t1 = (phi_closed(a - b, r0, lam) - phi_closed(a + b, r0, lam)) / (2.0 * a * b);
+        double t2 = psi_closed(c, r0, lam);
+        return pref * (t1 - t2);
+    }
+    /* other lambda: radial quadrature */
+    double fmax = a + b + c;
+    int np = (int)ceil(fmax * r0 / 3.0) + 2;
+    return pref * or_ghat_radial_quad(a, b, c, r0, lambda, np, 24);
+}
+
+/* Same, always through the quadrature route (independent check). */
+double or_ghat_quad(int N, double L, double lambda, const int *k, const int *m,
+                    int nodes)
+{
+    double dz = or_dzeta(L);
+    double zeta[3], xi[3], w[3];
+    for (int d = 0; d < 3; ++d) {
+        zeta[d] = dz * (k[d] - N / 2);
+        xi[d] = dz * (m[d] - N / 2);
+        w[d] = xi[d] - 0.5 * zeta[d];
+    }
+    double a = 0.5 * sqrt(zeta[0] * zeta[0] + zeta[1] * zeta[1] + zeta[2] * zeta[2]);
+    double b = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    double c = sqrt(xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
+    double r0 = L;
+    int np = (int)ceil((a + b + c) * r0 / 3.0) + 2;
+    return sqrt(2.0 / OR_PI) * or_ghat_radial_quad(a, b, c, r0, lambda, np, nodes);
+}
+
+/* Full table Ghat[k][m] for small N (N^6 doubles). */
+int or_ghat_table(int N, double L, double lambda, double *out)
+{
+    int M = N * N * N;
+    for (int kf = 0; kf < M; ++kf) {
+        int k[3] = {kf / (N * N), (kf / N) % N, kf % N};
+        for (int mf = 0; mf < M; ++mf) {
+            int m[3] = {mf / (N * N), (mf / N) % N, mf % N};
+            out[(size_t)kf * M + mf] = or_ghat(N, L, lambda, k, m);
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Weighted convolution, Sec. 3.2:
+ *   Qhat(zeta_k) = sum_m Ghat(xi_m, zeta_k) fhat(xi_m) fhat(zeta_k - xi_m) omega_m,
+ * omega_m = dzeta^3, and fhat(zeta_k - xi_m) = 0 when the index k - m + N/2
+ * leaves [0, N-1] on some axis.  m runs in lexicographic order.  The weight
+ * of each (k, m) is evaluated once and applied to every cell.  OpenMP splits
+ * the zeta_k outputs over threads, as in Sec. 4.1.                          */
+int or_convolve(int N, double L, double lambda, int ncells, const double *fhat,
+                double *qhat, int nthreads)
+{
+    int M = N * N * N;
+    int h = N / 2;
+    double dz = or_dzeta(L);
+    double omega = dz * dz * dz;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel
+    {
+        double *acc = (double *)malloc(sizeof(double) * 2 * (size_t)ncells);
+#pragma omp for schedule(dynamic, 4)
+        for (int kf = 0; kf < M; ++kf) {
+            int k[3] = {kf / (N * N), (kf / N) % N, kf % N};
+            for (int c = 0; c < 2 * ncells; ++c) acc[c] = 0.0;
+            for (int m1 = 0; m1 < N; ++m1) {
+                int s1 = k[0] - m1 + h;
+                if (s1 < 0 || s1 > N - 1) continue;
+                for (int m2 = 0; m2 < N; ++m2) {
+                    int s2 = k[1] - m2 + h;
+                    if (s2 < 0 || s2 > N - 1) continue;
+                    for (int m3 = 0; m3 < N; ++m3) {
+                        int s3 = k[2] - m3 + h;
+                        if (s3 < 0 || s3 > N - 1) continue;
+                        int m[3] = {m1, m2, m3};
+                        double g = or_ghat(N, L, lambda, k, m);
+                        int im = idx3(N, m1, m2, m3), is = idx3(N, s1, s2, s3);
+                        for (int c = 0; c < ncells; ++c) {
+                            const double *F = fhat + (size_t)2 * M * c;
+                            double ar = F[2 * im], ai = F[2 * im + 1];
+                            double br = F[2 * is], bi = F[2 * is + 1];
+                            acc[2 * c] += g * (ar * br - ai * bi);
+                            acc[2 * c + 1] += g * (ar * bi + ai * br);
+                        }
+                    }
+                }
+            }
+            for (int c = 0; c < ncells; ++c) {
+                qhat[(size_t)2 * M * c + 2 * kf] = omega * acc[2 * c];
+                qhat[(size_t)2 * M * c + 2 * kf + 1] = omega * acc[2 * c + 1];
+            }
+        }
+        free(acc);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Moments and conservation, Sec. 2 ("moments") and Sec. 3.3.
+ * Integration matrix C (5 x M): rows dv^3 * (1, v^1, v^2, v^3, |v|^2).      */
+static void c_row(int N, double L, int j, double *row)
+{
+    double dv = or_dv(N, L);
+    double w = dv * dv * dv;
+    double v1 = dv * (j / (N * N) - N / 2);
+    double v2 = dv * ((j / N) % N - N / 2);
+    double v3 = dv * (j % N - N / 2);
+    row[0] = w;
+    row[1] = w * v1;
+    row[2] = w * v2;
+    row[3] = w * v3;
+    row[4] = w * (v1 * v1 + v2 * v2 + v3 * v3);
+}
+
+int or_moments(int N, double L, int ncells, const double *f, double *out)
+{
+    int M = N * N * N;
+    for (int c = 0; c < ncells; ++c) {
+        double s[5] = {0, 0, 0, 0, 0};
+        for (int j = 0; j < M; ++j) {
+            double row[5];
+            c_row(N, L, j, row);
+            for (int i = 0; i < 5; ++i) s[i] += row[i] * f[(size_t)M * c + j];
+        }
+        for (int i = 0; i < 5; ++i) out[5 * c + i] = s[i];
+    }
+    return 0;
+}
+
+/* C C^T, 5 x 5 */
+int or_cct(int N, double L, double *A)
+{
+    int M = N * N * N;
+    for (int i = 0; i < 25; ++i) A[i] = 0.0;
+    for (int j = 0; j < M; ++j) {
+        double row[5];
+        c_row(N, L, j, row);
+        for (int a = 0; a < 5; ++a)
+            for (int b = 0; b < 5; ++b) A[5 * a + b] += row[a] * row[b];
+    }
+    return 0;
+}
+
+/* Solve A y = r for symmetric positive definite 5x5 A by Cholesky. */
+static void chol_solve5(const double *A, const double *r, double *y)
+{
+    double Lm[25] = {0};
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = A[5 * i + j];
+            for (int k = 0; k < j; ++k) s -= Lm[5 * i + k] * Lm[5 * j + k];
+            if (i == j)
+                Lm[5 * i + i] = sqrt(s);
+            else
+                Lm[5 * i + j] = s / Lm[5 * j + j];
+        }
+    double z[5];
+    for (int i = 0; i < 5; ++i) {
+        double s = r[i];
+        for (int k = 0; k < i; ++k) s -= Lm[5 * i + k] * z[k];
+        z[i] = s / Lm[5 * i + i];
+    }
+    for (int i = 4; i >= 0; --i) {
+        double s = z[i];
+        for (int k = i + 1; k < 5; ++k) s -= Lm[5 * k + i] * y[k];
+        y[i] = s / Lm[5 * i + i];
+    }
+}
+
+/* Projection P_N, Sec. 3.3: Q = Qt - C^T (C C^T)^{-1} C Qt, in place. */
+int or_conserve(int N, double L, int ncells, double *Q)
+{
+    int M = N * N * N;
+    double A[25];
+    or_cct(N, L, A);
+    for (int c = 0; c < ncells; ++c) {
+        double *q = Q + (size_t)M * c;
+        double mom[5] = {0, 0, 0, 0, 0}, y[5];
+        for (int j = 0; j < M; ++j) {
+            double row[5];
+            c_row(N, L, j, row);
+            for (int i = 0; i < 5; ++i) mom[i] += row[i] * q[j];
+        }
+        chol_solve5(A, mom, y);
+        for (int j = 0; j < M; ++j) {
+            double row[5];
+            c_row(N, L, j, row);
+            double corr = 0.0;
+            for (int i = 0; i < 5; ++i) corr += row[i] * y[i];
+            q[j] -= corr;
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The whole collision evaluation: forward transform, weighted convolution,
+ * inverse transform (real part, / eps) and, if conserve != 0, the projection. */
+int or_collide(int N, double L, double lambda, int ncells, const double *f,
+               double eps, double *Q, int conserve, int nthreads)
+{
+    int M = N * N * N;
+    double *fh = (double *)malloc(sizeof(double) * 2 * (size_t)M * ncells);
+    double *qh = (double *)malloc(sizeof(double) * 2 * (size_t)M * ncells);
+    or_dft_forward(N, L, ncells, f, fh);
+    or_convolve(N, L, lambda, ncells, fh, qh, nthreads);
+    or_dft_inverse(N, L, ncells, qh, eps, Q, NULL);
+    if (conserve) or_conserve(N, L, ncells, Q);
+    free(fh);
+    free(qh);
+    return 0;
+}
+
+/* Space-homogeneous second-order Runge-Kutta (Heun), Sec. 3.1, on
+ *   d f / dt = P_N Qt(f) / eps.                                               */
+int or_rk2_homogeneous(int N, double L, double lambda, int ncells, double *f,
+                       double dt, int nsteps, double eps, int conserve, int nthreads)
+{
+    size_t n = (size_t)N * N * N * ncells;
+    double *q = (double *)malloc(sizeof(double) * n);
+    double *f1 = (double *)malloc(sizeof(double) * n);
+    for (int s = 0; s < nsteps; ++s) {
+        or_collide(N, L, lambda, ncells, f, eps, q, conserve, nthreads);
+        for (size_t i = 0; i < n; ++i) f1[i] = f[i] + dt * q[i];
+        or_collide(N, L, lambda, ncells, f1, eps, q, conserve, nthreads);
+        for (size_t i = 0; i < n; ++i) f[i] = 0.5 * (f[i] + f1[i] + dt * q[i]);
+    }
+    free(q);
+    free(f1);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Transport, Sec. 3.4, 1-D in x on cells of width dx_j (wall face at x = 0,
+ * cell j spans [sum_{i<j} dx_i, sum_{i<=j} dx_i], centre x_j).
+ *   d f_j / dt = -(F_{j+1/2} - F_{j-1/2}) / dx_j,
+ *   F_{j+1/2} = v1 (f_j + dx_j/2 s_j)          if v1 >= 0,
+ *             = v1 (f_{j+1} - dx_{j+1}/2 s_{j+1}) otherwise,
+ *   s_j = minmod((f_{j+1}-f_j)/(x_{j+1}-x_j), (f_j-f_{j-1})/(x_j-x_{j-1}),
+ *                (f_{j+1}-f_{j-1})/(x_{j+1}-x_{j-1})).
+ * Boundaries (readings):
+ *   wall (left): the ghost f_{-1} is the linear extrapolation of f_0, f_1,
+ *     so s_0 is the one-sided slope; for v1 > 0 the face flux is the diffuse
+ *     reflection v1 sigma_w M_w(v), M_w = (2 pi T_w)^{-3/2}
+ *     exp(-|v - V_w|^2 / (2 T_w)), with sigma_w chosen so the discrete
+ *     incoming flux equals the discrete outgoing flux
+ *     sum_{v1<0} |v1| (f_0 - dx_0/2 s_0) (Sec. 2.1, "BC");
+ *   far end (right): two ghost cells of width dx_{n-1} hold f_far for
+ *     v1 < 0 (the far-field gas) and f_{n-1} for v1 >= 0 (zero gradient).
+ * One call advances dt with Heun's second-order Runge-Kutta (Sec. 3.1).      */
+
+static double minmod3(double a, double b, double c)
+{
+    if (a > 0 && b > 0 && c > 0) return fmin(a, fmin(b, c));
+    if (a < 0 && b < 0 && c < 0) return fmax(a, fmax(b, c));
+    return 0.0;
+}
+
+/* rhs = -(F_{j+1/2} - F_{j-1/2}) / dx_j for all cells */
+static void transport_rhs(int N, double L, int nc, const double *f, const double *dx,
+                          double Tw, const double *Vw, const double *ffar, double *rhs)
+{
+    int M = N * N * N;
+    double dv = or_dv(N, L);
+    double w3 = dv * dv * dv;
+    /* cell centres, with two ghosts on the right and one on the left */
+    double *x = (double *)malloc(sizeof(double) * (nc + 3)); /* x[j+1] = x_j, j=-1..nc+1 */
+    double edge = 0.0;
+    for (int j = 0; j < nc; ++j) {
+        x[j + 1] = edge + 0.5 * dx[j];
+        edge += dx[j];
+    }
+    x[0] = x[1] - dx[0];
+    x[nc + 1] = x[nc] + dx[nc - 1];
+    x[nc + 2] = x[nc + 1] + dx[nc - 1];
+    double *fx = (double *)malloc(sizeof(double) * (nc + 3));
+    double *slope = (double *)malloc(sizeof(double) * (nc + 2)); /* slope[j+1], j=-1..nc */
+    double *face = (double *)malloc(sizeof(double) * (nc + 1));  /* F_{j-1/2}, j=0..nc */
+
+    /* wall: outgoing flux of the reconstructed face values, and the
+     * discrete flux of M_w over v1 > 0                                        */
+    double out_flux = 0.0, mw_flux = 0.0;
+    for (int j = 0; j < M; ++j) {
+        double v1 = dv * (j / (N * N) - N / 2);
+        double v2 = dv * ((j / N) % N - N / 2);
+        double v3 = dv * (j % N - N / 2);
+        if (v1 < 0) {
+            double f0 = f[j], f1 = f[(size_t)M + j];
+            double s0 = (f1 - f0) / (x[2] - x[1]);
+            out_flux += -v1 * (f0 - 0.5 * dx[0] * s0) * w3;
+        } else if (v1 > 0) {
+            double e = (v1 - Vw[0]) * (v1 - Vw[0]) + (v2 - Vw[1]) * (v2 - Vw[1]) +
+                       (v3 - Vw[2]) * (v3 - Vw[2]);
+            double mw = pow(2.0 * OR_PI * Tw, -1.5) * exp(-e / (2.0 * Tw));
+            mw_flux += v1 * mw * w3;
+        }
+    }
+    double sigma_w = out_flux / mw_flux;
+
+    for (int j = 0; j < M; ++j) {
+        double v1 = dv * (j / (N * N) - N / 2);
+        double v2 = dv * ((j / N) % N - N / 2);
+        double v3 = dv * (j % N - N / 2);
+        /* gather the column f_j(v), with ghosts */
+        for (int c = 0; c < nc; ++c) fx[c + 1] = f[(size_t)M * c + j];
+        fx[0] = 0.0; /* the left ghost only enters through s_0 below */
+        double gr = (v1 < 0) ? ffar[j] : fx[nc];
+        fx[nc + 1] = gr;
+        fx[nc + 2] = gr;
+        /* slopes for cells -1 .. nc (index j+1); cell -1 is never used.
+         * With f_{-1} the linear extrapolation of f_0, f_1 all three minmod
+         * arguments of cell 0 equal the one-sided slope, taken directly.     */
+        slope[0] = 0.0;
+        slope[1] = (fx[2] - fx[1]) / (x[2] - x[1]);
+        for (int c = 1; c <= nc; ++c) {
+            int i = c + 1;
+            double a = (fx[i + 1] - fx[i]) / (x[i + 1] - x[i]);
+            double b = (fx[i] - fx[i - 1]) / (x[i] - x[i - 1]);
+            double cc = (fx[i + 1] - fx[i - 1]) / (x[i + 1] - x[i - 1]);
+            slope[i] = minmod3(a, b, cc);
+        }
+        /* faces j - 1/2 for j = 0 .. nc */
+        for (int c = 0; c <= nc; ++c) {
+            double F;
+            if (c == 0) {
+                if (v1 > 0) {
+                    double e = (v1 - Vw[0]) * (v1 - Vw[0]) + (v2 - Vw[1]) * (v2 - Vw[1]) +
+                               (v3 - Vw[2]) * (v3 - Vw[2]);
+                    double mw = pow(2.0 * OR_PI * Tw, -1.5) * exp(-e / (2.0 * Tw));
+                    F = v1 * sigma_w * mw;
+                } else {
+                    F = v1 * (fx[1] - 0.5 * dx[0] * slope[1]);
+                }
+            } else {
+                /* face between cell c-1 (left) and cell c (right) */
+                double dxl = dx[c - 1];
+                double dxr = (c < nc) ? dx[c] : dx[nc - 1];
+                if (v1 >= 0)
+                    F = v1 * (fx[c] + 0.5 * dxl * slope[c]);
+                else
+                    F = v1 * (fx[c + 1] - 0.5 * dxr * slope[c + 1]);
+            }
+            face[c] = F;
+        }
+        for (int c = 0; c < nc; ++c)
+            rhs[(size_t)M * c + j] = -(face[c + 1] - face[c]) / dx[c];
+    }
+    free(x);
+    free(fx);
+    free(slope);
+    free(face);
+}
+
+int or_transport_rk2(int N, double L, int nc, double *f, const double *dx, double Tw,
+                     const double *Vw, const double *ffar, double dt)
+{
+    size_t n = (size_t)N * N * N * nc;
+    double *r = (double *)malloc(sizeof(double) * n);
+    double *f1 = (double *)malloc(sizeof(double) * n);
+    transport_rhs(N, L, nc, f, dx, Tw, Vw, ffar, r);
+    for (size_t i = 0; i < n; ++i) f1[i] = f[i] + dt * r[i];
+    transport_rhs(N, L, nc, f1, dx, Tw, Vw, ffar, r);
+    for (size_t i = 0; i < n; ++i) f[i] = 0.5 * (f[i] + f1[i] + dt * r[i]);
+    free(r);
+    free(f1);
+    return 0;
+}
+
+/* The sign-resolved wall flux used above, exposed for tests:
+ * out[0] = outgoing flux, out[1] = sigma_w.                                 */
+int or_wall_flux(int N, double L, int nc, const double *f, const double *dx, double Tw,
+                 const double *Vw, double *out)
+{
+    int M = N * N * N;
+    double dv = or_dv(N, L), w3 = dv * dv * dv;
+    double x0 = 0.5 * dx[0], x1 = dx[0] + 0.5 * dx[1];
+    double out_flux = 0.0, mw_flux = 0.0;
+    (void)nc;
+    for (int j = 0; j < M; ++j) {
+        double v1 = dv * (j / (N * N) - N / 2);
+        double v2 = dv * ((j / N) % N - N / 2);
+        double v3 = dv * (j % N - N / 2);
+        if (v1 < 0) {
+            double f0 = f[j], f1 = f[(size_t)M + j];
+            double s0 = (f1 - f0) / (x1 - x0);
+            out_flux += -v1 * (f0 - 0.5 * dx[0] * s0) * w3;
+        } else if (v1 > 0) {
+            double e = (v1 - Vw[0]) * (v1 - Vw[0]) + (v2 - Vw[1]) * (v2 - Vw[1]) +
+                       (v3 - Vw[2]) * (v3 - Vw[2]);
+            mw_flux += v1 * pow(2.0 * OR_PI * Tw, -1.5) * exp(-e / (2.0 * Tw)) * w3;
+        }
+    }
+    out[0] = out_flux;
+    out[1] = out_flux / mw_flux;
+    return 0;
+}
+
+/* Strang splitting, Sec. 3.1: transport dt/2, collision dt (Heun on
+ * P_N Qt / eps), transport dt/2.                                            */
+int or_strang_step(int N, double L, double lambda, int nc, double *f, const double *dx,
+                   double Tw, const double *Vw, const double *ffar, double dt,
+                   double eps, int nthreads)
+{
+    or_transport_rk2(N, L, nc, f, dx, Tw, Vw, ffar, 0.5 * dt);
+    or_rk2_homogeneous(N, L, lambda, nc, f, dt, 1, eps, 1, nthreads);
+    or_transport_rk2(N, L, nc, f, dx, Tw, Vw, ffar, 0.5 * dt);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Direct quadrature of the collision integral, Sec. 2 ("Q_general") with
+ * the collision law "velocity_interact", B = |u|^lambda / (4 pi) and the
+ * same cut |u| <= r0 as the weights, for f a sum of Maxwellians
+ * mix[i] = (rho, V1, V2, V3, T).  Written in u = v - v_* = r omega:
+ *   Q(v) = int_0^{r0} r^{2+lambda} dr int_{S^2} d omega int_{S^2} d sigma / (4 pi)
+ *          [f(v') f(v'_*) - f(v) f(v - u)],
+ *   v' = v + (r sigma - u)/2,  v'_* = v - (u + r sigma)/2.
+ * Gauss-Legendre in r (npan panels of nr nodes) and in cos(theta) (nth),
+ * trapezoid in phi (nph), on both spheres.                                  */
+static double maxw_mix(int nmix, const double *mix, const double *v)
+{
+    double s = 0.0;
+    for (int i = 0; i < nmix; ++i) {
+        const double *p = mix + 5 * i;
+        double e = (v[0] - p[1]) * (v[0] - p[1]) + (v[1] - p[2]) * (v[1] - p[2]) +
+                   (v[2] - p[3]) * (v[2] - p[3]);
+        s += p[0] * pow(2.0 * OR_PI * p[4], -1.5) * exp(-e / (2.0 * p[4]));
+    }
+    return s;
+}
+
+int or_q_bruteforce(double lambda, double r0, int nmix, const double *mix, int nv,
+                    const double *vpts, int npan, int nr, int nth, int nph, double *out,
+                    int nthreads)
+{
+    double *xr = (double *)malloc(sizeof(double) * nr), *wr = (double *)malloc(sizeof(double) * nr);
+    double *xt = (double *)malloc(sizeof(double) * nth), *wt = (double *)malloc(sizeof(double) * nth);
+    or_gauss_legendre(nr, xr, wr);
+    or_gauss_legendre(nth, xt, wt);
+    int nsph = nth * nph;
+    double *dir = (double *)malloc(sizeof(double) * 3 * nsph);
+    double *dw = (double *)malloc(sizeof(double) * nsph);
+    for (int a = 0; a < nth; ++a)
+        for (int b = 0; b < nph; ++b) {
+            double mu = xt[a], st = sqrt(1.0 - mu * mu), ph = 2.0 * OR_PI * b / nph;
+            int i = a * nph + b;
+            dir[3 * i] = st * cos(ph);
+            dir[3 * i + 1] = st * sin(ph);
+            dir[3 * i + 2] = mu;
+            dw[i] = wt[a] * 2.0 * OR_PI / nph;
+        }
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int iv = 0; iv < nv; ++iv) {
+        const double *v = vpts + 3 * iv;
+        double fv = maxw_mix(nmix, mix, v);
+        double total = 0.0;
+        double h = r0 / npan;
+        for (int p = 0; p < npan; ++p)
+            for (int ir = 0; ir < nr; ++ir) {
+                double r = p * h + 0.5 * h * (xr[ir] + 1.0);
+                double wrr = 0.5 * h * wr[ir] * pow(r, 2.0 + lambda);
+                for (int io = 0; io < nsph; ++io) {
+                    double u[3] = {r * dir[3 * io], r * dir[3 * io + 1], r * dir[3 * io + 2]};
+                    double vs[3] = {v[0] - u[0], v[1] - u[1], v[2] - u[2]};
+                    double loss = fv * maxw_mix(nmix, mix, vs);
+                    double gain = 0.0;
+                    for (int is = 0; is < nsph; ++is) {
+                        double rs[3] = {r * dir[3 * is], r * dir[3 * is + 1], r * dir[3 * is + 2]};
+                        double vp[3], vps[3];
+                        for (int d = 0; d < 3; ++d) {
+                            vp[d] = v[d] + 0.5 * (rs[d] - u[d]);
+                            vps[d] = v[d] - 0.5 * (u[d] + rs[d]);
+                        }
+                        gain += dw[is] * maxw_mix(nmix, mix, vp) * maxw_mix(nmix, mix, vps);
+                    }
+                    total += wrr * dw[io] * (gain / (4.0 * OR_PI) - loss);
+                }
+            }
+        out[iv] = total;
+    }
+    free(xr); free(wr); free(xt); free(wt); free(dir); free(dw);
+    return 0;
+}
+
+int or_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
