@@ -1,0 +1,185 @@
+/*
+ * cs.h -- C ABI of the GB300 (sm_103a) conservative spectral collision library.
+ *
+ * The library evaluates the Boltzmann collision operator by the conservative
+ * spectral method of Gamba and Tharkabhushanam as described in J. R. Haack,
+ * "A hybrid OpenMP and MPI implementation of a conservative spectral method
+ * for the Boltzmann equation" (arXiv:1301.4195): per spatial cell a forward
+ * transform of f on an N^3 velocity grid, the weighted Fourier convolution
+ * with the precomputed weights Ghat, an inverse transform and the
+ * conservation projection; plus Heun time stepping and a 1-D finite-volume
+ * transport step combined by Strang splitting.
+ *
+ * Conventions shared by every call
+ *   - Velocity grid (Sec. 3.1, "meshpoints"): N even, 4 <= N <= 32, the cube
+ *     [-L, L]^3, v_k = dv (k - N/2), dv = 2L/N, zeta_k = dzeta (k - N/2),
+ *     dzeta = pi/L.  A cell's distribution is N^3 doubles in C order, flat
+ *     index (k1*N + k2)*N + k3.  A batch of cells is [ncells][N^3].
+ *   - Collision kernel B = |u|^lambda / (4 pi) (isotropic, Sec. 2.2),
+ *     0 <= lambda <= 1, weight integral cut at r0 = L, beta = 1.
+ *   - Pointers marked "device" are CUDA device pointers owned by the caller
+ *     (e.g. allocated by PyTorch); "host" pointers are ordinary memory.
+ *     Device arrays must be 8-byte aligned and must not overlap unless a
+ *     call says so.
+ *   - Every call that takes a cudaStream_t is asynchronous on that stream
+ *     (0 = legacy default stream) and returns after enqueueing its work.
+ *   - Every call returns CS_OK (0) or a negative CS_E* code and then leaves
+ *     a message for cs_last_error().  Arguments are checked on the host
+ *     before anything is enqueued; no call traps, asserts or aborts.
+ *   - No call allocates device memory except cs_weights_build (the weight
+ *     table) and cs_reserve / the first call that needs more workspace than
+ *     the handle holds.  Call cs_reserve before capturing a CUDA graph.
+ *   - A handle is not thread-safe: calls on one handle must be serialised by
+ *     the caller (one stream, or external synchronisation).
+ */
+#ifndef CS_H
+#define CS_H
+
+#include <stddef.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CS_OK 0
+#define CS_EINVAL (-1)     /* bad argument: N, L, lambda, pointer, size, alignment */
+#define CS_ENOMEM (-2)     /* device allocation failed */
+#define CS_ENOTSUP (-3)    /* valid request this build does not serve */
+#define CS_ECUDA (-4)      /* a CUDA runtime call failed (message has the CUDA error) */
+#define CS_ETIMEOUT (-5)   /* a bounded device-side wait expired */
+#define CS_ENONFINITE (-6) /* a non-finite value was found where finiteness is checked */
+
+#define CS_FP64 0 /* every step in double precision */
+#define CS_FP32 1 /* transforms and convolution in float (compensated sum over xi),
+                     weights built in double, moments and projection in double */
+
+typedef struct cs_handle_s *cs_handle_t;
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int cs_version(void);
+
+/* Message of the last failing call made by this host thread ("" if none).
+ * The pointer stays valid until the thread's next failing call. */
+const char *cs_last_error(void);
+
+/* Bytes of device memory cs_weights_build will hold for the weight table of
+ * grid size N in the given precision (admission planning).  The table stores
+ * the symmetrised weights Ghat(xi, zeta) + Ghat(zeta - xi, zeta) for the
+ * lexicographically lower half of the valid (xi, zeta) pairs, Sec. 3.2.
+ *   bytes (host, out).  Errors: CS_EINVAL. */
+int cs_weights_bytes(int N, int precision, size_t *bytes);
+
+/* Build the convolution weights of Sec. 2.2 (eq. GHat_calc; closed forms for
+ * lambda = 0 and 1, radial Gauss-Legendre quadrature otherwise), in double on
+ * the device (kept in float for CS_FP32), together with the constants of the
+ * transforms and of the projection (C C^T)^{-1} of Sec. 3.3.
+ *   N        even, 4..32
+ *   L        > 0, half-width of the velocity cube; r0 = L
+ *   lambda   0 <= lambda <= 1
+ *   stream   the build is enqueued here; the handle is usable on any stream
+ *            once the build has completed on this one
+ *   out      (host, out) new handle; *out is untouched on error.
+ * Errors: CS_EINVAL, CS_ENOMEM, CS_ECUDA. */
+int cs_weights_build(int N, double L, double lambda, int precision, cudaStream_t stream,
+                     cs_handle_t *out);
+
+/* Free the handle, its weight table and its workspace.  NULL is a no-op.
+ * The caller must make sure no work using the handle is still in flight. */
+int cs_handle_destroy(cs_handle_t h);
+
+/* Read back the parameters of a handle (any out pointer may be NULL). */
+int cs_handle_info(cs_handle_t h, int *N, double *L, double *lambda, int *precision,
+                   size_t *weight_bytes);
+
+/* Grow the handle's workspace to serve up to ncells cells per call (no-op if
+ * it is already large enough).  Synchronises the device when it reallocates.
+ * Errors: CS_EINVAL, CS_ENOMEM. */
+int cs_reserve(cs_handle_t h, int ncells);
+
+/* Ghat(xi_m, zeta_k) (unsymmetrised, Sec. 2.2) evaluated on the device by the
+ * same function that fills the table, for n index pairs.
+ *   km   (host) [n][6] ints: k1 k2 k3 m1 m2 m3, each in 0..N-1
+ *   out  (host) [n] doubles.  Synchronous.  Errors: CS_EINVAL, CS_ECUDA. */
+int cs_weights_sample(cs_handle_t h, const int *km, int n, double *out);
+
+/* Step a1, the forward transform (Sec. 3.2 with the normalisation of
+ * Sec. 2.2): fhat(zeta_k) = (2 pi)^{-3/2} dv^3 sum_j f(v_j) exp(-i zeta_k.v_j),
+ * in the handle's precision.
+ *   f     (device) [ncells][N^3] doubles
+ *   fhat  (device, out) [ncells][N^3][2] doubles (re, im), widened from float
+ *         in CS_FP32.  Errors: CS_EINVAL, CS_ENOMEM, CS_ECUDA. */
+int cs_transform(cs_handle_t h, const double *f, int ncells, double *fhat, cudaStream_t stream);
+
+/* Step a2, the weighted convolution (Sec. 3.2, trapezoid rule, terms with
+ * zeta_k - xi_m outside the grid dropped):
+ *   Qhat(zeta_k) = dzeta^3 sum_m Ghat(xi_m, zeta_k) fhat(xi_m) fhat(zeta_k - xi_m).
+ *   fhat  (device) [ncells][N^3][2] doubles (rounded to float in CS_FP32)
+ *   qhat  (device, out) [ncells][N^3][2] doubles.
+ * Errors: CS_EINVAL, CS_ENOMEM, CS_ECUDA. */
+int cs_convolve(cs_handle_t h, const double *fhat, int ncells, double *qhat, cudaStream_t stream);
+
+/* Step a3, the inverse transform (Sec. 3.2):
+ *   Qt(v_j) = Re[(2 pi)^{-3/2} dzeta^3 sum_k Qhat(zeta_k) exp(i zeta_k.v_j)] / eps.
+ *   qhat  (device) [ncells][N^3][2] doubles;  Q (device, out) [ncells][N^3].
+ * Errors: CS_EINVAL, CS_ENOMEM, CS_ECUDA. */
+int cs_inverse(cs_handle_t h, const double *qhat, int ncells, double eps, double *Q,
+               cudaStream_t stream);
+
+/* The collision operator (steps a1-a4): Q = P_N Qt(f) / eps if conserve != 0,
+ * else Qt(f) / eps, for every cell.
+ *   f  (device) [ncells][N^3];  Q (device, out) [ncells][N^3]; f and Q must
+ *   not overlap.  eps > 0 is the Knudsen number of eq. (BTE).
+ * Errors: CS_EINVAL, CS_ENOMEM, CS_ECUDA. */
+int cs_collide(cs_handle_t h, const double *f, int ncells, double eps, double *Q, int conserve,
+               cudaStream_t stream);
+
+/* Step a4, the conservation projection of Sec. 3.3, in place, in double:
+ *   Q <- Q - C^T (C C^T)^{-1} C Q,  C = dv^3 (1, v1, v2, v3, |v|^2) (5 x N^3).
+ *   Q        (device, in/out) [ncells][N^3]
+ *   moments  (device, out, may be NULL) [ncells][5]: C Q before the projection.
+ * Errors: CS_EINVAL, CS_ECUDA. */
+int cs_conserve(cs_handle_t h, double *Q, int ncells, double *moments, cudaStream_t stream);
+
+/* The moments of eq. (moments) as the rows of C: per cell
+ * dv^3 sum_j (1, v1, v2, v3, |v|^2)_j f_j  -> out (device) [ncells][5].
+ * Errors: CS_EINVAL, CS_ECUDA. */
+int cs_moments(cs_handle_t h, const double *f, int ncells, double *out, cudaStream_t stream);
+
+/* Step a5: nsteps Heun (second-order Runge-Kutta, Sec. 3.1) steps of the
+ * space-homogeneous problem df/dt = P_N Qt(f) / eps, in place.
+ *   f (device, in/out) [ncells][N^3].  Errors: CS_EINVAL, CS_ENOMEM, CS_ECUDA. */
+int cs_relax(cs_handle_t h, double *f, int ncells, double dt, double eps, int nsteps,
+             cudaStream_t stream);
+
+/* 1-D physical domain of the transport step (Sec. 3.4): cells of width dx_j,
+ * cell 0 touching a diffusely reflecting wall at x = 0 (Sec. 2.1, eq. BC),
+ * the far end open to a given gas. */
+typedef struct {
+    const double *dx;    /* device, [ncells] cell widths > 0 (non-uniform allowed) */
+    const double *f_far; /* device, [N^3] far-field distribution, used for v1 < 0 */
+    double wall_T;       /* wall temperature T_w > 0 */
+    double wall_V[3];    /* wall velocity V_w */
+} cs_domain;
+
+/* One Heun step of length dt of the finite-volume transport of Sec. 3.4
+ * (second-order upwind fluxes, 3-argument minmod slopes), in place.
+ * Boundaries: at the wall the incoming half (v1 > 0) is sigma_w M_w(v) with
+ * sigma_w set from the discrete outgoing flux so the net wall mass flux is
+ * zero; the slope of cell 0 is one-sided (linear extrapolation into the
+ * ghost).  At the far end two ghost cells hold f_far for v1 < 0 and copy the
+ * last cell for v1 >= 0.  ncells >= 2.
+ * Errors: CS_EINVAL, CS_ENOMEM, CS_ECUDA. */
+int cs_transport(cs_handle_t h, double *f, int ncells, const cs_domain *dom, double dt,
+                 cudaStream_t stream);
+
+/* nsteps Strang-split steps (Sec. 3.1): transport dt/2, collision dt (Heun on
+ * P_N Qt / eps), transport dt/2, in place.  f (device, in/out) [ncells][N^3].
+ * Errors: CS_EINVAL, CS_ENOMEM, CS_ECUDA. */
+int cs_step(cs_handle_t h, double *f, int ncells, const cs_domain *dom, double dt, double eps,
+            int nsteps, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CS_H */

@@ -1,0 +1,139 @@
+// K4: the conservation step of Sec. 3.3 in double precision.  With the
+// integration matrix C (rows dv^3 (1, v1, v2, v3, |v|^2)) the constrained
+// least-squares solution is Q = Qt - C^T (C C^T)^{-1} C Qt; (C C^T)^{-1} is a
+// 5x5 constant of the handle.  One block per cell: the five moments are
+// reduced with warp shuffles, the 5x5 product is done by one thread, and the
+// correction is applied together with the Runge-Kutta combination of the
+// caller (out = a x + b y + c Q), so a Heun stage costs no extra pass.
+#include "cs_internal.cuh"
+
+namespace cs {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+struct Proj {
+    double ainv[25];
+};
+
+__device__ __forceinline__ void c_row(const Geom &g, int j, double r[5])
+{
+    const int N = g.N, h = g.h;
+    const double w = g.dv * g.dv * g.dv;
+    const double v1 = g.dv * (j / (N * N) - h);
+    const double v2 = g.dv * ((j / N) % N - h);
+    const double v3 = g.dv * (j % N - h);
+    r[0] = w;
+    r[1] = w * v1;
+    r[2] = w * v2;
+    r[3] = w * v3;
+    r[4] = w * (v1 * v1 + v2 * v2 + v3 * v3);
+}
+
+// block-wide sum of 5 doubles; result valid in every thread
+__device__ void block_sum5(double v[5], double *sh /* [5][kThreads/32] */)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        double x = v[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[i * 32 + wid] = x;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        double x = 0;
+        for (int k = 0; k < nw; ++k) x += sh[i * 32 + k];
+        v[i] = x;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads) conserve_kernel(Geom g, Proj pj, const double *Qt, int project,
+                                                            double a, const double *x, double b,
+                                                            const double *y, double c, double *out,
+                                                            double *moments)
+{
+    __shared__ double sh[5 * 32];
+    __shared__ double ycoef[5];
+    const int cell = blockIdx.x;
+    const size_t base = (size_t)cell * g.M;
+    double mom[5] = {0, 0, 0, 0, 0};
+    if (project || moments) {
+        for (int j = threadIdx.x; j < g.M; j += blockDim.x) {
+            double r[5];
+            c_row(g, j, r);
+            const double q = Qt[base + j];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) mom[i] += r[i] * q;
+        }
+        block_sum5(mom, sh);
+    }
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 5; ++i) {
+            double s = 0;
+            if (project)
+                for (int k = 0; k < 5; ++k) s += pj.ainv[5 * i + k] * mom[k];
+            ycoef[i] = s;
+            if (moments) moments[5 * (size_t)cell + i] = mom[i];
+        }
+    }
+    __syncthreads();
+    double yc[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) yc[i] = ycoef[i];
+    for (int j = threadIdx.x; j < g.M; j += blockDim.x) {
+        double r[5];
+        c_row(g, j, r);
+        double q = Qt[base + j];
+        if (project) q -= r[0] * yc[0] + r[1] * yc[1] + r[2] * yc[2] + r[3] * yc[3] + r[4] * yc[4];
+        double o = c * q;
+        if (x) o += a * x[base + j];
+        if (y) o += b * y[base + j];
+        out[base + j] = o;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) moments_kernel(Geom g, const double *__restrict__ f,
+                                                           double *__restrict__ out)
+{
+    __shared__ double sh[5 * 32];
+    const int cell = blockIdx.x;
+    const size_t base = (size_t)cell * g.M;
+    double mom[5] = {0, 0, 0, 0, 0};
+    for (int j = threadIdx.x; j < g.M; j += blockDim.x) {
+        double r[5];
+        c_row(g, j, r);
+        const double v = f[base + j];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) mom[i] += r[i] * v;
+    }
+    block_sum5(mom, sh);
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 5; ++i) out[5 * (size_t)cell + i] = mom[i];
+}
+
+}  // namespace
+
+int launch_conserve(const Handle &hd, const double *Qt, int ncells, int project, double a, const double *x,
+                    double b, const double *y, double c, double *out, double *moments, cudaStream_t s)
+{
+    Proj pj;
+    for (int i = 0; i < 25; ++i) pj.ainv[i] = hd.cct_inv[i];
+    conserve_kernel<<<ncells, kThreads, 0, s>>>(hd.g, pj, Qt, project, a, x, b, y, c, out, moments);
+    CS_CHECK_LAUNCH("conservation projection");
+    return CS_OK;
+}
+
+int launch_moments(const Handle &hd, const double *f, int ncells, double *out, cudaStream_t s)
+{
+    moments_kernel<<<ncells, kThreads, 0, s>>>(hd.g, f, out);
+    CS_CHECK_LAUNCH("moments");
+    return CS_OK;
+}
+
+}  // namespace cs

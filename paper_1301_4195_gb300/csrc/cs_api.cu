@@ -1,0 +1,481 @@
+// Host side of the C ABI declared in include/cs.h: argument checks, the
+// handle (weights, constants, workspace) and the order of kernel launches for
+// each entry point.  No exception crosses the ABI; every failure returns a
+// CS_E* code and leaves a message for cs_last_error().
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "cs_internal.cuh"
+
+struct cs_handle_s {
+    cs::Handle h;
+};
+
+namespace cs {
+
+namespace {
+thread_local std::string g_last_error;
+
+bool is_finite(double x) { return std::isfinite(x); }
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int check_device_ptr(const void *p, const char *name, bool allow_null = false)
+{
+    if (p == nullptr) {
+        if (allow_null) return CS_OK;
+        return set_error(CS_EINVAL, std::string(name) + " is NULL");
+    }
+    if (((uintptr_t)p & 7u) != 0) return set_error(CS_EINVAL, std::string(name) + " is not 8-byte aligned");
+    cudaPointerAttributes at{};
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(CS_EINVAL, std::string(name) + " is not a CUDA pointer");
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return set_error(CS_EINVAL, std::string(name) + " is not device memory");
+    return CS_OK;
+}
+
+int check_handle(cs_handle_t h)
+{
+    if (h == nullptr) return set_error(CS_EINVAL, "handle is NULL");
+    return CS_OK;
+}
+
+int check_cells(int ncells)
+{
+    if (ncells < 0) return set_error(CS_EINVAL, "ncells < 0");
+    return CS_OK;
+}
+
+// Inverse of the symmetric positive definite 5x5 matrix A by Cholesky.
+bool spd_inverse5(const double *A, double *inv)
+{
+    double Lc[25] = {0};
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = A[5 * i + j];
+            for (int k = 0; k < j; ++k) s -= Lc[5 * i + k] * Lc[5 * j + k];
+            if (i == j) {
+                if (!(s > 0)) return false;
+                Lc[5 * i + i] = std::sqrt(s);
+            } else {
+                Lc[5 * i + j] = s / Lc[5 * j + j];
+            }
+        }
+    for (int col = 0; col < 5; ++col) {
+        double e[5] = {0, 0, 0, 0, 0}, z[5], x[5];
+        e[col] = 1.0;
+        for (int i = 0; i < 5; ++i) {
+            double s = e[i];
+            for (int k = 0; k < i; ++k) s -= Lc[5 * i + k] * z[k];
+            z[i] = s / Lc[5 * i + i];
+        }
+        for (int i = 4; i >= 0; --i) {
+            double s = z[i];
+            for (int k = i + 1; k < 5; ++k) s -= Lc[5 * k + i] * x[k];
+            x[i] = s / Lc[5 * i + i];
+        }
+        for (int i = 0; i < 5; ++i) inv[5 * i + col] = x[i];
+    }
+    return true;
+}
+
+void fill_geom(Geom &g, int N, double L, double lambda)
+{
+    g.N = N;
+    g.h = N / 2;
+    g.M = N * N * N;
+    g.L = L;
+    g.dv = 2.0 * L / N;
+    g.dz = M_PI / L;
+    g.lambda = lambda;
+    g.off[0] = 0;
+    for (int m3 = 0; m3 < N; ++m3) g.off[m3 + 1] = g.off[m3] + (kmax_of(m3, g.h, N) - kmin_of(m3, g.h) + 1);
+    for (int m3 = N + 1; m3 <= kMaxN; ++m3) g.off[m3] = g.off[N];
+    g.TS = g.off[N];
+    g.TSp = (g.TS + 3) & ~3;
+}
+
+size_t spectral_bytes(const Handle &hd, int ncells)
+{
+    return (size_t)ngroups_of(ncells) * hd.g.M * kGroup * 2 * elem_bytes(hd.precision);
+}
+
+// Carve the workspace: F, Qh, X, Y (spectral), Qt, f1 (state), scal.
+size_t workspace_bytes(const Handle &hd, int ncells, size_t *offs)
+{
+    const size_t sb = align_up(spectral_bytes(hd, ncells), 256);
+    const size_t st = align_up((size_t)ncells * hd.g.M * sizeof(double), 256);
+    const size_t sc = align_up(sizeof(double) * (8 + (size_t)ncells + 8), 256);
+    size_t o = 0;
+    for (int i = 0; i < 4; ++i) {
+        if (offs) offs[i] = o;
+        o += sb;
+    }
+    for (int i = 4; i < 6; ++i) {
+        if (offs) offs[i] = o;
+        o += st;
+    }
+    if (offs) offs[6] = o;
+    o += sc;
+    return o;
+}
+
+int ensure_workspace(Handle &hd, int ncells)
+{
+    if (ncells <= hd.ws_cells) return CS_OK;
+    size_t offs[7];
+    const size_t bytes = workspace_bytes(hd, ncells, offs);
+    if (hd.ws) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_error(e, "synchronise before growing the workspace");
+        cudaFree(hd.ws);
+        hd.ws = nullptr;
+        hd.ws_cells = 0;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(CS_ENOMEM, "cudaMalloc of the workspace failed (" + std::to_string(bytes) + " bytes)");
+    }
+    char *b = (char *)p;
+    hd.ws = p;
+    hd.ws_bytes = bytes;
+    hd.ws_cells = ncells;
+    hd.F = b + offs[0];
+    hd.Qh = b + offs[1];
+    hd.X = b + offs[2];
+    hd.Y = b + offs[3];
+    hd.Qt = (double *)(b + offs[4]);
+    hd.f1 = (double *)(b + offs[5]);
+    hd.scal = (double *)(b + offs[6]);
+    return CS_OK;
+}
+
+int collide_into(Handle &hd, const double *f, int ncells, double eps, double *Qt, cudaStream_t s)
+{
+    int rc = launch_forward(hd, f, ncells, s);
+    if (rc) return rc;
+    rc = launch_convolve(hd, ncells, s);
+    if (rc) return rc;
+    return launch_inverse(hd, ncells, eps, Qt, s);
+}
+
+// one Heun step of df/dt = P Qt(f) / eps, in place
+int heun_collision(Handle &hd, double *f, int ncells, double dt, double eps, cudaStream_t s)
+{
+    int rc = collide_into(hd, f, ncells, eps, hd.Qt, s);
+    if (rc) return rc;
+    rc = launch_conserve(hd, hd.Qt, ncells, 1, 1.0, f, 0.0, nullptr, dt, hd.f1, nullptr, s);
+    if (rc) return rc;
+    rc = collide_into(hd, hd.f1, ncells, eps, hd.Qt, s);
+    if (rc) return rc;
+    return launch_conserve(hd, hd.Qt, ncells, 1, 0.5, f, 0.5, hd.f1, 0.5 * dt, f, nullptr, s);
+}
+
+int heun_transport(Handle &hd, double *f, int ncells, const cs_domain &dom, double dt, cudaStream_t s)
+{
+    int rc = launch_transport_stage(hd, f, ncells, dom, 1.0, f, 0.0, nullptr, dt, hd.f1, s);
+    if (rc) return rc;
+    return launch_transport_stage(hd, hd.f1, ncells, dom, 0.5, f, 0.5, hd.f1, 0.5 * dt, f, s);
+}
+
+int check_domain(const Handle &hd, const cs_domain *dom, int ncells)
+{
+    if (dom == nullptr) return set_error(CS_EINVAL, "domain is NULL");
+    if (ncells < 2) return set_error(CS_EINVAL, "transport needs ncells >= 2");
+    if (!(dom->wall_T > 0) || !is_finite(dom->wall_T)) return set_error(CS_EINVAL, "wall_T must be finite and > 0");
+    for (int i = 0; i < 3; ++i)
+        if (!is_finite(dom->wall_V[i])) return set_error(CS_EINVAL, "wall_V must be finite");
+    int rc = check_device_ptr(dom->dx, "domain.dx");
+    if (rc) return rc;
+    (void)hd;
+    return check_device_ptr(dom->f_far, "domain.f_far");
+}
+
+}  // namespace
+
+int set_error(int code, const std::string &msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_error(cudaError_t e, const char *what)
+{
+    return set_error(CS_ECUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+}  // namespace cs
+
+using namespace cs;
+
+extern "C" {
+
+int cs_version(void) { return 100; }
+
+const char *cs_last_error(void) { return g_last_error.c_str(); }
+
+int cs_weights_bytes(int N, int precision, size_t *bytes)
+{
+    if (N < 4 || N > kMaxN || (N & 1)) return set_error(CS_EINVAL, "N must be even, 4 <= N <= 32");
+    if (precision != CS_FP64 && precision != CS_FP32) return set_error(CS_EINVAL, "precision must be CS_FP64 or CS_FP32");
+    if (!bytes) return set_error(CS_EINVAL, "bytes is NULL");
+    Geom g{};
+    fill_geom(g, N, 1.0, 0.0);
+    const long long tiles = count_tiles(N, nullptr);
+    *bytes = (size_t)tiles * g.TSp * elem_bytes(precision) + sizeof(int) * (N * N + 1) +
+             (size_t)N * N * (sizeof(double2) + sizeof(float2));
+    return CS_OK;
+}
+
+int cs_weights_build(int N, double L, double lambda, int precision, cudaStream_t stream, cs_handle_t *out)
+{
+    if (N < 4 || N > kMaxN || (N & 1)) return set_error(CS_EINVAL, "N must be even, 4 <= N <= 32");
+    if (!(L > 0) || !is_finite(L)) return set_error(CS_EINVAL, "L must be finite and > 0");
+    if (!(lambda >= 0.0 && lambda <= 1.0)) return set_error(CS_EINVAL, "lambda must lie in [0, 1]");
+    if (precision != CS_FP64 && precision != CS_FP32) return set_error(CS_EINVAL, "precision must be CS_FP64 or CS_FP32");
+    if (!out) return set_error(CS_EINVAL, "out is NULL");
+    cs_handle_s *hs = new (std::nothrow) cs_handle_s();
+    if (!hs) return set_error(CS_ENOMEM, "host allocation of the handle failed");
+    Handle &hd = hs->h;
+    cudaGetDevice(&hd.device);
+    hd.precision = precision;
+    fill_geom(hd.g, N, L, lambda);
+    // twiddles exp(-i 2 pi ((k-h)(j-h) mod N) / N)
+    std::vector<double2> t64(N * N);
+    std::vector<float2> t32(N * N);
+    for (int k = 0; k < N; ++k)
+        for (int j = 0; j < N; ++j) {
+            long r = (long)(k - N / 2) * (long)(j - N / 2) % N;
+            if (r < 0) r += N;
+            const double ang = 2.0 * M_PI * (double)r / (double)N;
+            t64[k * N + j] = make_double2(std::cos(ang), -std::sin(ang));
+            t32[k * N + j] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+        }
+    // (C C^T)^{-1}
+    {
+        double A[25] = {0};
+        const double w = hd.g.dv * hd.g.dv * hd.g.dv;
+        for (int j = 0; j < hd.g.M; ++j) {
+            const double v1 = hd.g.dv * (j / (N * N) - N / 2);
+            const double v2 = hd.g.dv * ((j / N) % N - N / 2);
+            const double v3 = hd.g.dv * (j % N - N / 2);
+            const double r[5] = {w, w * v1, w * v2, w * v3, w * (v1 * v1 + v2 * v2 + v3 * v3)};
+            for (int a = 0; a < 5; ++a)
+                for (int b = 0; b < 5; ++b) A[5 * a + b] += r[a] * r[b];
+        }
+        if (!spd_inverse5(A, hd.cct_inv)) {
+            delete hs;
+            return set_error(CS_EINVAL, "C C^T is not positive definite");
+        }
+    }
+    cudaError_t e = cudaMalloc(&hd.tw64, sizeof(double2) * N * N);
+    if (e == cudaSuccess) e = cudaMalloc(&hd.tw32, sizeof(float2) * N * N);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cs_handle_destroy(hs);
+        return set_error(CS_ENOMEM, "cudaMalloc of the twiddle tables failed");
+    }
+    e = cudaMemcpyAsync(hd.tw64, t64.data(), sizeof(double2) * N * N, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hd.tw32, t32.data(), sizeof(float2) * N * N, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) {
+        const int rc = cuda_error(e, "copy of the twiddle tables");
+        cs_handle_destroy(hs);
+        return rc;
+    }
+    int rc = build_weights(hd, stream);
+    if (rc == CS_OK) {
+        // host vectors above must outlive the async copies
+        e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) rc = cuda_error(e, "weight build");
+    }
+    if (rc != CS_OK) {
+        const std::string msg = g_last_error;
+        cudaStreamSynchronize(stream);
+        cs_handle_destroy(hs);
+        return set_error(rc, msg);
+    }
+    *out = hs;
+    return CS_OK;
+}
+
+int cs_handle_destroy(cs_handle_t h)
+{
+    if (!h) return CS_OK;
+    Handle &hd = h->h;
+    cudaFree(hd.ghat);
+    cudaFree(hd.pencil_tile0);
+    cudaFree(hd.tw64);
+    cudaFree(hd.tw32);
+    cudaFree(hd.ws);
+    delete h;
+    return CS_OK;
+}
+
+int cs_handle_info(cs_handle_t h, int *N, double *L, double *lambda, int *precision, size_t *weight_bytes)
+{
+    if (int rc = check_handle(h)) return rc;
+    const Handle &hd = h->h;
+    if (N) *N = hd.g.N;
+    if (L) *L = hd.g.L;
+    if (lambda) *lambda = hd.g.lambda;
+    if (precision) *precision = hd.precision;
+    if (weight_bytes) *weight_bytes = hd.ghat_bytes;
+    return CS_OK;
+}
+
+int cs_reserve(cs_handle_t h, int ncells)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (int rc = check_cells(ncells)) return rc;
+    return ensure_workspace(h->h, ncells);
+}
+
+int cs_weights_sample(cs_handle_t h, const int *km, int n, double *out)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (n < 0 || (n > 0 && (!km || !out))) return set_error(CS_EINVAL, "bad sample arrays");
+    const int N = h->h.g.N;
+    for (int i = 0; i < 6 * n; ++i)
+        if (km[i] < 0 || km[i] >= N) return set_error(CS_EINVAL, "sample index out of range");
+    if (n == 0) return CS_OK;
+    return sample_weights(h->h, km, n, out);
+}
+
+int cs_transform(cs_handle_t h, const double *f, int ncells, double *fhat, cudaStream_t s)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (int rc = check_cells(ncells)) return rc;
+    if (ncells == 0) return CS_OK;
+    if (int rc = check_device_ptr(f, "f")) return rc;
+    if (int rc = check_device_ptr(fhat, "fhat")) return rc;
+    Handle &hd = h->h;
+    if (int rc = ensure_workspace(hd, ncells)) return rc;
+    if (int rc = launch_forward(hd, f, ncells, s)) return rc;
+    return launch_spectral_to_natural(hd, hd.F, ncells, fhat, s);
+}
+
+int cs_convolve(cs_handle_t h, const double *fhat, int ncells, double *qhat, cudaStream_t s)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (int rc = check_cells(ncells)) return rc;
+    if (ncells == 0) return CS_OK;
+    if (int rc = check_device_ptr(fhat, "fhat")) return rc;
+    if (int rc = check_device_ptr(qhat, "qhat")) return rc;
+    Handle &hd = h->h;
+    if (int rc = ensure_workspace(hd, ncells)) return rc;
+    if (int rc = launch_natural_to_spectral(hd, fhat, ncells, hd.F, s)) return rc;
+    if (int rc = launch_convolve(hd, ncells, s)) return rc;
+    return launch_spectral_to_natural(hd, hd.Qh, ncells, qhat, s);
+}
+
+int cs_inverse(cs_handle_t h, const double *qhat, int ncells, double eps, double *Q, cudaStream_t s)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (int rc = check_cells(ncells)) return rc;
+    if (!(eps > 0) || !is_finite(eps)) return set_error(CS_EINVAL, "eps must be finite and > 0");
+    if (ncells == 0) return CS_OK;
+    if (int rc = check_device_ptr(qhat, "qhat")) return rc;
+    if (int rc = check_device_ptr(Q, "Q")) return rc;
+    Handle &hd = h->h;
+    if (int rc = ensure_workspace(hd, ncells)) return rc;
+    if (int rc = launch_natural_to_spectral(hd, qhat, ncells, hd.Qh, s)) return rc;
+    return launch_inverse(hd, ncells, eps, Q, s);
+}
+
+int cs_collide(cs_handle_t h, const double *f, int ncells, double eps, double *Q, int conserve, cudaStream_t s)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (int rc = check_cells(ncells)) return rc;
+    if (!(eps > 0) || !is_finite(eps)) return set_error(CS_EINVAL, "eps must be finite and > 0");
+    if (ncells == 0) return CS_OK;
+    if (int rc = check_device_ptr(f, "f")) return rc;
+    if (int rc = check_device_ptr(Q, "Q")) return rc;
+    Handle &hd = h->h;
+    const size_t bytes = (size_t)ncells * hd.g.M * sizeof(double);
+    if ((const char *)f < (const char *)Q + bytes && (const char *)Q < (const char *)f + bytes)
+        return set_error(CS_EINVAL, "f and Q overlap");
+    if (int rc = ensure_workspace(hd, ncells)) return rc;
+    if (int rc = collide_into(hd, f, ncells, eps, Q, s)) return rc;
+    if (conserve) return launch_conserve(hd, Q, ncells, 1, 0.0, nullptr, 0.0, nullptr, 1.0, Q, nullptr, s);
+    return CS_OK;
+}
+
+int cs_conserve(cs_handle_t h, double *Q, int ncells, double *moments, cudaStream_t s)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (int rc = check_cells(ncells)) return rc;
+    if (ncells == 0) return CS_OK;
+    if (int rc = check_device_ptr(Q, "Q")) return rc;
+    if (int rc = check_device_ptr(moments, "moments", true)) return rc;
+    return launch_conserve(h->h, Q, ncells, 1, 0.0, nullptr, 0.0, nullptr, 1.0, Q, moments, s);
+}
+
+int cs_moments(cs_handle_t h, const double *f, int ncells, double *out, cudaStream_t s)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (int rc = check_cells(ncells)) return rc;
+    if (ncells == 0) return CS_OK;
+    if (int rc = check_device_ptr(f, "f")) return rc;
+    if (int rc = check_device_ptr(out, "out")) return rc;
+    return launch_moments(h->h, f, ncells, out, s);
+}
+
+int cs_relax(cs_handle_t h, double *f, int ncells, double dt, double eps, int nsteps, cudaStream_t s)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (int rc = check_cells(ncells)) return rc;
+    if (!is_finite(dt)) return set_error(CS_EINVAL, "dt must be finite");
+    if (!(eps > 0) || !is_finite(eps)) return set_error(CS_EINVAL, "eps must be finite and > 0");
+    if (nsteps < 0) return set_error(CS_EINVAL, "nsteps < 0");
+    if (ncells == 0 || nsteps == 0) return CS_OK;
+    if (int rc = check_device_ptr(f, "f")) return rc;
+    Handle &hd = h->h;
+    if (int rc = ensure_workspace(hd, ncells)) return rc;
+    for (int i = 0; i < nsteps; ++i)
+        if (int rc = heun_collision(hd, f, ncells, dt, eps, s)) return rc;
+    return CS_OK;
+}
+
+int cs_transport(cs_handle_t h, double *f, int ncells, const cs_domain *dom, double dt, cudaStream_t s)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (int rc = check_cells(ncells)) return rc;
+    if (!is_finite(dt)) return set_error(CS_EINVAL, "dt must be finite");
+    Handle &hd = h->h;
+    if (int rc = check_domain(hd, dom, ncells)) return rc;
+    if (int rc = check_device_ptr(f, "f")) return rc;
+    if (int rc = ensure_workspace(hd, ncells)) return rc;
+    return heun_transport(hd, f, ncells, *dom, dt, s);
+}
+
+int cs_step(cs_handle_t h, double *f, int ncells, const cs_domain *dom, double dt, double eps, int nsteps,
+            cudaStream_t s)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (int rc = check_cells(ncells)) return rc;
+    if (!is_finite(dt)) return set_error(CS_EINVAL, "dt must be finite");
+    if (!(eps > 0) || !is_finite(eps)) return set_error(CS_EINVAL, "eps must be finite and > 0");
+    if (nsteps < 0) return set_error(CS_EINVAL, "nsteps < 0");
+    Handle &hd = h->h;
+    if (int rc = check_domain(hd, dom, ncells)) return rc;
+    if (int rc = check_device_ptr(f, "f")) return rc;
+    if (int rc = ensure_workspace(hd, ncells)) return rc;
+    for (int i = 0; i < nsteps; ++i) {
+        if (int rc = heun_transport(hd, f, ncells, *dom, 0.5 * dt, s)) return rc;
+        if (int rc = heun_collision(hd, f, ncells, dt, eps, s)) return rc;
+        if (int rc = heun_transport(hd, f, ncells, *dom, 0.5 * dt, s)) return rc;
+    }
+    return CS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,317 @@
+// K0: the convolution weights Ghat(xi, zeta) of Sec. 2.2 (eq. GHat_calc),
+// isotropic b = 1/(4 pi), beta = 1, radial integral cut at r0 = L:
+//   Ghat = sqrt(2/pi) int_0^{r0} r^{lambda+2} [sinc(r a) sinc(r b) - sinc(r c)] dr,
+//   a = |zeta|/2, b = |xi - zeta/2|, c = |xi|.
+// For lambda = 0, 1 the closed forms of Sec. 2.2 are used with
+// p = a - b, q = a + b (so that sinc(ar) sinc(br) = [cos(pr) - cos(qr)] / (2ab r^2));
+// other lambda use composite Gauss-Legendre on the radial integral.
+//
+// Table layout.  Output zeta_k is split into pencils (k1, k2) along k3.  For
+// pencil (k1, k2) with K = k + N/2 the valid xi_m satisfy, per axis,
+// m_i in [max(0, K_i - N + 1), min(N - 1, K_i)] (Sec. 3.2: terms whose
+// zeta_k - xi_m leaves the grid are dropped), and the partner index is
+// s = K - m.  The pair (m, s) and (s, m) multiply the same fhat product, so
+// the table keeps one "tile" per (m1, m2) in the lower half
+//   2 m1 < K1,  or  2 m1 = K1 and 2 m2 <= K2,
+// holding for every valid (m3, k3) the weight Ghat(m, k) + Ghat(K - m, k);
+// the centre tile (m1, m2) = (s1, s2) keeps the plain weight Ghat(m, k).
+// Inside a tile the pairs are ordered by m3, then k3 in
+// [max(0, m3 - N/2), min(N - 1, m3 + N/2 - 1)]; a tile holds 3N^2/4 pairs,
+// padded to a multiple of 4.  Tiles of one pencil are consecutive, pencils in
+// (k1, k2) order.
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "cs_internal.cuh"
+
+namespace cs {
+
+namespace {
+
+constexpr int kQuadNodes = 24;
+
+struct QuadRule {
+    double x[kQuadNodes];
+    double w[kQuadNodes];
+};
+
+// Gauss-Legendre rule on [-1, 1] (Newton iteration on P_n from its recurrence).
+QuadRule make_rule()
+{
+    QuadRule r{};
+    const int n = kQuadNodes;
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        double pn = 0, pm = 0;
+        for (int it = 0; it < 100; ++it) {
+            pn = 1.0;
+            pm = 0.0;
+            for (int j = 1; j <= n; ++j) {
+                const double t = pm;
+                pm = pn;
+                pn = ((2 * j - 1) * z * pm - (j - 1) * t) / j;
+            }
+            const double d = n * (z * pn - pm) / (z * z - 1.0);
+            const double dz = pn / d;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        pn = 1.0;
+        pm = 0.0;
+        for (int j = 1; j <= n; ++j) {
+            const double t = pm;
+            pm = pn;
+            pn = ((2 * j - 1) * z * pm - (j - 1) * t) / j;
+        }
+        const double d = n * (z * pn - pm) / (z * z - 1.0);
+        r.x[i] = z;
+        r.w[i] = 2.0 / ((1.0 - z * z) * d * d);
+    }
+    return r;
+}
+
+__device__ double series_cos_moment(double x, double r0, double lam)
+{
+    // int_0^r0 r^lam cos(x r) dr = r0^{lam+1} sum_n (-1)^n y^{2n} / ((2n)! (2n + lam + 1))
+    const double y2 = (x * r0) * (x * r0);
+    double term = 1.0, sum = 0.0;
+    for (int n = 0; n < 40; ++n) {
+        const double t = term / (2.0 * n + lam + 1.0);
+        sum += t;
+        if (fabs(t) < 1e-18 * fabs(sum) && n > 2) break;
+        term *= -y2 / ((2.0 * n + 1.0) * (2.0 * n + 2.0));
+    }
+    return pow(r0, lam + 1.0) * sum;
+}
+
+__device__ double series_sinc_moment(double x, double r0, double lam)
+{
+    // int_0^r0 r^{lam+2} sinc(x r) dr = r0^{lam+3} sum_n (-1)^n y^{2n} / ((2n+1)! (2n + lam + 3))
+    const double y2 = (x * r0) * (x * r0);
+    double term = 1.0, sum = 0.0;
+    for (int n = 0; n < 40; ++n) {
+        const double t = term / (2.0 * n + lam + 3.0);
+        sum += t;
+        if (fabs(t) < 1e-18 * fabs(sum) && n > 2) break;
+        term *= -y2 / ((2.0 * n + 2.0) * (2.0 * n + 3.0));
+    }
+    return pow(r0, lam + 3.0) * sum;
+}
+
+// Phi(x) = int_0^r0 r^lam cos(x r) dr, lam in {0, 1}
+__device__ double cos_moment(double x, double r0, int lam)
+{
+    const double y = x * r0;
+    if (fabs(y) < 0.5) return series_cos_moment(x, r0, lam);
+    double s, c;
+    sincos(y, &s, &c);
+    if (lam == 0) return s / x;
+    return (y * s + c - 1.0) / (x * x);
+}
+
+// Psi(x) = int_0^r0 r^{lam+2} sinc(x r) dr, lam in {0, 1}
+__device__ double sinc_moment(double x, double r0, int lam)
+{
+    const double y = x * r0;
+    if (fabs(y) < 1.0) return series_sinc_moment(x, r0, lam);
+    double s, c;
+    sincos(y, &s, &c);
+    if (lam == 0) return (s - y * c) / (x * x * x);
+    return ((2.0 - y * y) * c + 2.0 * y * s - 2.0) / (x * x * x * x);
+}
+
+__device__ double dsinc(double x)
+{
+    if (fabs(x) < 1e-4) return 1.0 - x * x * (1.0 / 6.0) + x * x * x * x * (1.0 / 120.0);
+    return sin(x) / x;
+}
+
+// radial integral of the bracket by composite Gauss-Legendre, first panel
+// graded geometrically toward r = 0 for r^{lambda+2}
+__device__ double radial_bracket_quad(double a, double b, double c, double r0, double lam,
+                                      const QuadRule &q)
+{
+    const int np = (int)ceil((a + b + c) * r0 / 3.0) + 2;
+    const double hw = r0 / np;
+    double total = 0.0;
+    for (int p = 0; p < np; ++p) {
+        const int nsub = (p == 0) ? 12 : 1;
+        for (int sidx = 0; sidx < nsub; ++sidx) {
+            double lo, hi;
+            if (p == 0) {
+                hi = hw * exp2(-(double)(nsub - 1 - sidx));
+                lo = (sidx == 0) ? 0.0 : hw * exp2(-(double)(nsub - sidx));
+            } else {
+                lo = p * hw;
+                hi = (p + 1) * hw;
+            }
+            const double mid = 0.5 * (lo + hi), half = 0.5 * (hi - lo);
+            for (int i = 0; i < kQuadNodes; ++i) {
+                const double r = mid + half * q.x[i];
+                total += half * q.w[i] * pow(r, lam + 2.0) * (dsinc(a * r) * dsinc(b * r) - dsinc(c * r));
+            }
+        }
+    }
+    return total;
+}
+
+// Ghat for centred integer indices kp = k - N/2 (zeta), mp = m - N/2 (xi).
+__device__ double ghat_centered(const Geom &g, const QuadRule &q, int kp1, int kp2, int kp3,
+                                int mp1, int mp2, int mp3)
+{
+    const long kk = (long)kp1 * kp1 + (long)kp2 * kp2 + (long)kp3 * kp3;
+    if (kk == 0) return 0.0;  // G(u, 0) = 0
+    const long mm = (long)mp1 * mp1 + (long)mp2 * mp2 + (long)mp3 * mp3;
+    const long d1 = 2 * mp1 - kp1, d2 = 2 * mp2 - kp2, d3 = 2 * mp3 - kp3;
+    const long bb = d1 * d1 + d2 * d2 + d3 * d3;
+    const long mk = (long)mp1 * kp1 + (long)mp2 * kp2 + (long)mp3 * kp3;
+    const double dz = g.dz, r0 = g.L;
+    const double a = 0.5 * dz * sqrt((double)kk);
+    const double b = 0.5 * dz * sqrt((double)bb);
+    const double c = dz * sqrt((double)mm);
+    const double pref = 0.79788456080286535588;  // sqrt(2 / pi) = 4 pi / (2 pi)^{3/2}
+    const double lam = g.lambda;
+    if (lam == 0.0 || lam == 1.0) {
+        const int il = (int)lam;
+        double t1;
+        if (bb == 0) {
+            t1 = sinc_moment(a, r0, il);
+        } else {
+            // p = a - b = (a^2 - b^2)/(a + b), a^2 - b^2 = dz^2 (m'.k' - |m'|^2) exactly
+            const double qv = a + b;
+            const double pv = dz * dz * (double)(mk - mm) / qv;
+            t1 = (cos_moment(pv, r0, il) - cos_moment(qv, r0, il)) / (2.0 * a * b);
+        }
+        const double t2 = (mm == 0) ? sinc_moment(0.0, r0, il) : sinc_moment(c, r0, il);
+        return pref * (t1 - t2);
+    }
+    return pref * radial_bracket_quad(a, b, c, r0, lam, q);
+}
+
+template <typename T>
+__global__ void build_table_kernel(Geom g, QuadRule q, const int *__restrict__ tile0, long long total,
+                                   T *__restrict__ out)
+{
+    const long long tile = blockIdx.x;
+    if (tile >= total) return;
+    const int N = g.N, h = g.h;
+    // pencil of this tile: largest P with tile0[P] <= tile
+    int lo = 0, hi = N * N - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tile0[mid] <= tile) lo = mid; else hi = mid - 1;
+    }
+    const int P = lo;
+    const int k1 = P / N, k2 = P % N;
+    const int K1 = k1 + h, K2 = k2 + h;
+    const int lo1 = max(0, K1 - N + 1), hi1 = min(N - 1, K1);
+    const int lo2 = max(0, K2 - N + 1), hi2 = min(N - 1, K2);
+    const int v1 = hi1 - lo1 + 1, v2 = hi2 - lo2 + 1;
+    const long long t = tile - tile0[P];
+    const int nfull = (v1 / 2) * v2;
+    int m1, m2;
+    if (t < nfull) {
+        m1 = lo1 + (int)(t / v2);
+        m2 = lo2 + (int)(t % v2);
+    } else {
+        m1 = K1 / 2;
+        m2 = lo2 + (int)(t - nfull);
+    }
+    const bool centre = (2 * m1 == K1) && (2 * m2 == K2);
+    const int s1 = K1 - m1, s2 = K2 - m2;
+    T *dst = out + tile * g.TSp;
+    for (int p = threadIdx.x; p < g.TSp; p += blockDim.x) {
+        if (p >= g.TS) {
+            dst[p] = T(0);
+            continue;
+        }
+        int m3 = 0;
+        while (m3 + 1 < N && g.off[m3 + 1] <= p) ++m3;
+        const int k3 = kmin_of(m3, h) + (p - g.off[m3]);
+        const int K3 = k3 + h, s3 = K3 - m3;
+        double w = ghat_centered(g, q, k1 - h, k2 - h, k3 - h, m1 - h, m2 - h, m3 - h);
+        if (!centre) w += ghat_centered(g, q, k1 - h, k2 - h, k3 - h, s1 - h, s2 - h, s3 - h);
+        dst[p] = (T)w;
+    }
+}
+
+__global__ void sample_kernel(Geom g, QuadRule q, const int *__restrict__ km, int n, double *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int *e = km + 6 * i;
+    const int h = g.h;
+    out[i] = ghat_centered(g, q, e[0] - h, e[1] - h, e[2] - h, e[3] - h, e[4] - h, e[5] - h);
+}
+
+}  // namespace
+
+long long count_tiles(int N, int *pencil_tile0)
+{
+    const int h = N / 2;
+    long long total = 0;
+    for (int k1 = 0; k1 < N; ++k1)
+        for (int k2 = 0; k2 < N; ++k2) {
+            const int K1 = k1 + h, K2 = k2 + h;
+            const int v1 = (K1 < N - 1 ? K1 : N - 1) - (K1 - N + 1 > 0 ? K1 - N + 1 : 0) + 1;
+            const int v2 = (K2 < N - 1 ? K2 : N - 1) - (K2 - N + 1 > 0 ? K2 - N + 1 : 0) + 1;
+            if (pencil_tile0) pencil_tile0[k1 * N + k2] = (int)total;
+            total += (long long)(v1 * v2 + 1) / 2;
+        }
+    if (pencil_tile0) pencil_tile0[N * N] = (int)total;
+    return total;
+}
+
+int build_weights(Handle &hd, cudaStream_t s)
+{
+    const Geom &g = hd.g;
+    std::vector<int> tile0(g.N * g.N + 1);
+    hd.total_tiles = count_tiles(g.N, tile0.data());
+    cudaError_t e = cudaMalloc(&hd.pencil_tile0, sizeof(int) * tile0.size());
+    if (e != cudaSuccess) return set_error(CS_ENOMEM, "cudaMalloc of the pencil index failed");
+    e = cudaMemcpyAsync(hd.pencil_tile0, tile0.data(), sizeof(int) * tile0.size(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_error(e, "copy of the pencil index");
+    hd.ghat_bytes = (size_t)hd.total_tiles * g.TSp * elem_bytes(hd.precision);
+    e = cudaMalloc(&hd.ghat, hd.ghat_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(CS_ENOMEM, "cudaMalloc of the weight table failed (" +
+                                        std::to_string(hd.ghat_bytes) + " bytes)");
+    }
+    const QuadRule q = make_rule();
+    if (hd.precision == CS_FP32)
+        build_table_kernel<float><<<(unsigned)hd.total_tiles, 128, 0, s>>>(g, q, hd.pencil_tile0, hd.total_tiles,
+                                                                            (float *)hd.ghat);
+    else
+        build_table_kernel<double><<<(unsigned)hd.total_tiles, 128, 0, s>>>(g, q, hd.pencil_tile0, hd.total_tiles,
+                                                                             (double *)hd.ghat);
+    CS_CHECK_LAUNCH("weight table build");
+    return CS_OK;
+}
+
+int sample_weights(Handle &hd, const int *km_host, int n, double *out_host)
+{
+    int *dkm = nullptr;
+    double *dout = nullptr;
+    cudaError_t e = cudaMalloc(&dkm, sizeof(int) * 6 * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&dout, sizeof(double) * (size_t)n);
+    if (e != cudaSuccess) {
+        cudaFree(dkm);
+        return set_error(CS_ENOMEM, "cudaMalloc in cs_weights_sample failed");
+    }
+    e = cudaMemcpy(dkm, km_host, sizeof(int) * 6 * (size_t)n, cudaMemcpyHostToDevice);
+    int rc = CS_OK;
+    if (e == cudaSuccess) {
+        const QuadRule q = make_rule();
+        sample_kernel<<<(n + 127) / 128, 128>>>(hd.g, q, dkm, n, dout);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpy(out_host, dout, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost);
+    }
+    if (e != cudaSuccess) rc = cuda_error(e, "cs_weights_sample");
+    cudaFree(dkm);
+    cudaFree(dout);
+    return rc;
+}
+
+}  // namespace cs

@@ -1,0 +1,66 @@
+"""The C-ABI library builds, loads and exports every entry point include/cs.h declares.
+
+No call here launches GPU work: only host-side queries and argument checks
+that fail before anything is enqueued.
+"""
+import ctypes
+import pathlib
+import re
+
+import pytest
+
+ROOT = pathlib.Path(__file__).resolve().parents[1]
+
+
+@pytest.fixture(scope="module")
+def libcs():
+    from paper_1301_4195_gb300 import build
+    build.build()
+    import torch  # noqa: F401  (brings the CUDA runtime into the process)
+    from paper_1301_4195_gb300 import api
+    return api
+
+
+def declared_symbols():
+    text = (ROOT / "include" / "cs.h").read_text()
+    return sorted(set(re.findall(r"^\s*(?:int|const char \*)\s*(cs_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ("cs_weights_build", "cs_collide", "cs_conserve", "cs_step", "cs_moments",
+                     "cs_weights_bytes", "cs_handle_destroy", "cs_relax", "cs_transport"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libcs):
+    lib = ctypes.CDLL(str(libcs.library_path()))
+    missing = [n for n in declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_only_queries(libcs):
+    assert libcs.cs_version() >= 100
+    b16 = libcs.cs_weights_bytes(16, libcs.CS_FP32)
+    b32 = libcs.cs_weights_bytes(32, libcs.CS_FP32)
+    # symmetrised half of the 27 N^6 / 64 valid pairs, 4 bytes each, plus small tables
+    assert 0.49 * 27 * 16 ** 6 / 64 * 4 < b16 < 0.53 * 27 * 16 ** 6 / 64 * 4 + 1e5
+    assert b32 > 60 * b16
+    assert libcs.cs_weights_bytes(16, libcs.CS_FP64) > 1.9 * b16
+
+
+@pytest.mark.parametrize("N,L,lam,prec", [(5, 6.0, 1.0, 0), (34, 6.0, 1.0, 0), (2, 6.0, 1.0, 0),
+                                          (8, -1.0, 1.0, 0), (8, 6.0, 1.5, 0), (8, 6.0, -0.1, 0),
+                                          (8, 6.0, 1.0, 7), (8, float("nan"), 1.0, 0)])
+def test_weights_build_rejects_bad_arguments(libcs, N, L, lam, prec):
+    with pytest.raises(libcs.CSError) as e:
+        libcs.cs_weights_build(N, L, lam, prec, stream=0)
+    assert e.value.code == libcs.CS_EINVAL
+    assert libcs.lib().cs_last_error().decode()
+
+
+def test_null_handle_is_rejected(libcs):
+    lib = libcs.lib()
+    assert lib.cs_collide(None, None, 1, 1.0, None, 1, None) == libcs.CS_EINVAL
+    assert lib.cs_handle_destroy(None) == libcs.CS_OK
+    assert lib.cs_weights_bytes(16, 0, None) == libcs.CS_EINVAL
