@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Throughput of the conservative spectral collision step on GB300.
+
+One bench "step" is one Strang-split time step of the 1-D wall boundary-layer
+problem (transport dt/2, Heun collision dt = two evaluations of the collision
+operator with the conservation projection, transport dt/2): every step of the
+hot path.  The metric is nominal pair-updates per second,
+    (collision evaluations) x (cells) x N^6 / time,
+the count the paper's N^6 cost model uses.
+
+Default workload (N=1): N = 16, L = 6, lambda = 1, 128 cells of width
+min(dx0 1.05^j, 0.5), dx0 = 1/8, wall at T_w = 1.5 against a unit Maxwellian
+gas, dt = 0.01; transforms and convolution in float, weights, projection,
+transport and state in double.  Secondary objects in the same line: the same
+step in double precision ("fp64") and the N = 32, 256-cell workload ("n32").
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs its own replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Q(f) pair-updates/s FP32+FP64-cons vs FP64 at N=16/32, err; serve p50/p99"
+UNIT = "pair-updates/s"
+L_BOX = 6.0
+LAM = 1.0
+DT = 0.01
+WALL_T = 1.5
+WORKLOADS = {
+    "wall16": dict(N=16, ncells=128),
+    "wall32": dict(N=32, ncells=256),
+}
+MAX_SM_MHZ = 2070.0
+SMS = 152
+FP32_LANES = 128
+
+
+def describe(wl: str) -> str:
+    p = WORKLOADS[wl]
+    return (f"1-D wall boundary layer, N={p['N']}, L=6, lambda=1, {p['ncells']} cells "
+            f"(dx_j=min(0.125*1.05^j,0.5)), T_w=1.5 vs unit Maxwellian, dt=0.01, one Strang step "
+            f"(2 collision evaluations + 4 transport stages)")
+
+
+def tiles_total(N: int) -> int:
+    h = N // 2
+    tot = 0
+    for k1 in range(N):
+        for k2 in range(N):
+            v1 = min(k1 + h, N - 1) - max(0, k1 + h - N + 1) + 1
+            v2 = min(k2 + h, N - 1) - max(0, k2 + h - N + 1) + 1
+            tot += (v1 * v2 + 1) // 2
+    return tot
+
+
+def unique_pairs_per_cell(N: int) -> int:
+    """Pairs the symmetrised half-tile convolution visits per cell per evaluation."""
+    return tiles_total(N) * (3 * N * N // 4)
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names[1:], parts[5:9]):
+                if val.lower() in ("active", "0x1") or val == "1":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- our arm
+def make_state(api, inputs, torch, N, ncells, device):
+    dx = inputs.wall_grid(ncells)
+    f0 = inputs.wall_initial(N, L_BOX, ncells)
+    far = inputs.maxwellian(N, L_BOX, 1.0, (0.0, 0.0, 0.0), 1.0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+    return f0, t(f0), t(dx), t(far)
+
+
+def time_steps(torch, h, fd, dxd, fard, K, W, flush, profile=False):
+    """W untimed warm-up steps, then K steps each timed with CUDA events on the
+    current stream, the L2 flushed before each; returns the summed device ms."""
+    from paper_1301_4195_gb300 import api
+    for _ in range(W):
+        h.step(fd, dxd, fard, WALL_T, (0.0, 0.0, 0.0), DT, nsteps=1)
+    torch.cuda.synchronize()
+    if profile:
+        api.cs_profile(h.ptr, True)
+        api.cs_profile_read(h.ptr, reset=True)
+    evs = []
+    for _ in range(K):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        h.step(fd, dxd, fard, WALL_T, (0.0, 0.0, 0.0), DT, nsteps=1)
+        b.record()
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    total = sum(a.elapsed_time(b) for a, b in evs)
+    prof = None
+    if profile:
+        prof = api.cs_profile_read(h.ptr, reset=True)
+        api.cs_profile(h.ptr, False)
+    return total, prof
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1301_4195_gb300 import api, build, inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.gpus > 1 and world != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} needs torchrun with {args.gpus} ranks (WORLD_SIZE={world})")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=device)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    build.build()
+
+    wl = WORKLOADS[args.workload]
+    N, ncells = wl["N"], (args.cells or wl["ncells"])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)  # > L2 (129 MB)
+
+    h32 = api.Handle(N, L_BOX, LAM, "fp32")
+    h32.reserve(ncells)
+    f0, fd, dxd, fard = make_state(api, inputs, torch, N, ncells, device)
+
+    # warm-up + timed region (barrier and synchronize on both sides, max over ranks)
+    for _ in range(args.warmup):
+        h32.step(fd, dxd, fard, WALL_T, (0.0, 0.0, 0.0), DT, nsteps=1)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    total_ms, prof = time_steps(torch, h32, fd, dxd, fard, args.steps, 0, flush, profile=True)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+        t = torch.tensor([total_ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    # the profiled run above carries event pairs; time once more without them
+    plain_ms, _ = time_steps(torch, h32, fd, dxd, fard, args.steps, 0, flush, profile=False)
+    if world > 1:
+        t = torch.tensor([plain_ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        plain_ms = float(t.item())
+    ms_step = plain_ms / args.steps
+    evals_per_step = 2
+    pairs_step = evals_per_step * ncells * N ** 6
+    value = world * pairs_step / (ms_step * 1e-3)
+
+    # roofline of the dominant kernel (the convolution), timed live above
+    conv_ms, conv_n = prof["convolve"]
+    conv_avg = conv_ms / max(conv_n, 1)
+    flops_launch = 10.0 * unique_pairs_per_cell(N) * ncells
+    peak_tflops = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    achieved = flops_launch / (conv_avg * 1e-3) / 1e12
+    step_stage_ms = {k: v[0] / args.steps for k, v in prof.items()}
+
+    # e2e: host state in pinned memory, copied in and out around the public call every step
+    fh = torch.from_numpy(f0.copy()).pin_memory()
+    fdev = torch.empty_like(fd)
+    for _ in range(2):
+        fdev.copy_(fh, non_blocking=True)
+        h32.step(fdev, dxd, fard, WALL_T, (0.0, 0.0, 0.0), DT, nsteps=1)
+        fh.copy_(fdev, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fdev.copy_(fh, non_blocking=True)
+        h32.step(fdev, dxd, fard, WALL_T, (0.0, 0.0, 0.0), DT, nsteps=1)
+        fh.copy_(fdev, non_blocking=True)
+        b.record()
+        b.synchronize()
+        e2e_ms += a.elapsed_time(b)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    state_bytes = ncells * N ** 3 * 8
+    e2e = {"value": world * pairs_step * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes}
+
+    # the same step in double precision (the plain FP64 GPU form)
+    h64 = api.Handle(N, L_BOX, LAM, "fp64")
+    h64.reserve(ncells)
+    _, fd64, _, _ = make_state(api, inputs, torch, N, ncells, device)
+    k64 = max(2, min(args.steps, 5))
+    ms64, _ = time_steps(torch, h64, fd64, dxd, fard, k64, 1, flush)
+    fp64 = {"value": pairs_step / (ms64 / k64 * 1e-3), "ms_per_step": ms64 / k64}
+
+    # the N = 32, 256-cell workload (secondary)
+    n32 = None
+    if args.workload == "wall16" and not args.skip_n32:
+        N2, nc2 = WORKLOADS["wall32"]["N"], WORKLOADS["wall32"]["ncells"]
+        hb = api.Handle(N2, L_BOX, LAM, "fp32")
+        hb.reserve(nc2)
+        _, fb, dxb, farb = make_state(api, inputs, torch, N2, nc2, device)
+        kb = max(2, min(args.steps, 4))
+        msb, profb = time_steps(torch, hb, fb, dxb, farb, kb, 1, flush, profile=True)
+        cms, cn = profb["convolve"]
+        cavg = cms / max(cn, 1)
+        fl2 = 10.0 * unique_pairs_per_cell(N2) * nc2
+        n32 = {"workload": describe("wall32"), "value": 2 * nc2 * N2 ** 6 / (msb / kb * 1e-3),
+               "ms_per_step": msb / kb, "conv_ms": cavg,
+               "roofline": {"bound": "alu", "achieved": fl2 / (cavg * 1e-3) / 1e12, "peak": peak_tflops,
+                            "unit": "TFLOP/s", "frac": fl2 / (cavg * 1e-3) / 1e12 / peak_tflops,
+                            "traffic": None}}
+        hb.close()
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": describe(args.workload), "N": N, "cells_per_gpu": ncells, "L": L_BOX,
+                   "lambda": LAM, "dt": DT, "precision": "f32 transforms+convolution, f64 weights/projection/"
+                   "transport/state", "l2": "256 MiB buffer written before every timed step",
+                   "parallelism": f"replicas x{world} (cells are independent)"},
+        "clocks": clk,
+        "e2e": e2e,
+        "gpu_launches": 24 * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": None,
+                     "kernel": "conv (step a2)", "avg_launch_ms": conv_avg,
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                     "flops_per_launch": flops_launch},
+        "stage_ms_per_step": step_stage_ms,
+        "fp64": fp64,
+        "speedup_vs_fp64": fp64["ms_per_step"] / ms_step,
+    }
+    if n32:
+        out["n32"] = n32
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"], out["error_vs_oracle"] = cpu_baseline(args, api, inputs, torch, device, h32, h64)
+    h32.close()
+    h64.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(args, api, inputs, torch, device, h32, h64):
+    """The oracle, as it stands, on this host's cores: one collision evaluation
+    (transform, convolution, inverse, projection) of a sample of the workload's
+    cells; also the GPU results' error against it on that sample."""
+    import oracle
+    oracle.build()
+    wl = WORKLOADS[args.workload]
+    N = wl["N"]
+    nsample = 16
+    # sample cells: the wall state after a few steps has non-trivial collisions
+    f0 = inputs.random_mixture_cells(N, L_BOX, nsample, first_id=5000)
+    cores = os.cpu_count() or 1
+    reps, t_total = 0, 0.0
+    ref = None
+    while t_total < 10.0 and reps < 200:
+        t0 = time.perf_counter()
+        ref = oracle.collide(f0, N, L_BOX, LAM, nthreads=cores)
+        t_total += time.perf_counter() - t0
+        reps += 1
+    cpu = {"value": reps * nsample * N ** 6 / t_total, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{reps} x one collision evaluation of {nsample} random-mixture cells at N={N} "
+                     f"(L=6, lambda=1), OpenMP over zeta outputs"}
+    err = {}
+    fd = torch.from_numpy(f0).to(device)
+    for name, h in (("fp32", h32), ("fp64", h64)):
+        q = h.collide(fd).cpu().numpy()
+        err[name] = float(np.abs(q - ref).max() / np.abs(ref).max())
+    return cpu, err
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(args):
+    """The CPU oracle as the reference arm: each step is one Strang step of a
+    bounded sample (16 of the workload's cells) on this host's cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_1301_4195_gb300 import inputs
+    oracle.build()
+    wl = WORKLOADS[args.workload]
+    N, ncells = wl["N"], 16
+    dx = inputs.wall_grid(wl["ncells"])[:ncells]
+    f = inputs.wall_initial(N, L_BOX, ncells)
+    far = inputs.maxwellian(N, L_BOX, 1.0, (0, 0, 0), 1.0)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        f = oracle.strang_step(f, N, L_BOX, LAM, dx, WALL_T, (0, 0, 0), far, DT, nthreads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = oracle.strang_step(f, N, L_BOX, LAM, dx, WALL_T, (0, 0, 0), far, DT, nthreads=cores)
+    el = time.perf_counter() - t0
+    value = args.steps * 2 * ncells * N ** 6 / el
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": describe(args.workload), "N": N, "cells_per_step_sample": ncells,
+                      "note": "reference = the FP64 CPU oracle (the paper has no code)"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"Strang steps of {ncells} of the {wl['ncells']} cells"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="wall16")
+    ap.add_argument("--cells", type=int, default=0, help="override the workload's cell count (profiling runs)")
+    ap.add_argument("--skip-n32", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

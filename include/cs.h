@@ -179,6 +179,28 @@ int cs_transport(cs_handle_t h, double *f, int ncells, const cs_domain *dom, dou
 int cs_step(cs_handle_t h, double *f, int ncells, const cs_domain *dom, double dt, double eps,
             int nsteps, cudaStream_t stream);
 
+/* Per-stage timing.  While enabled on a handle, each stage that handle
+ * launches is bracketed by two CUDA events recorded on the stream it is
+ * launched on; cs_profile_read synchronises on those events and returns the
+ * summed device time and the number of bracketed launches per stage.
+ * Stage ids (index into the arrays): */
+#define CS_K_FORWARD 0   /* step a1: the three transform passes */
+#define CS_K_CONVOLVE 1  /* step a2: the convolution kernel */
+#define CS_K_INVERSE 2   /* step a3: the three inverse passes */
+#define CS_K_CONSERVE 3  /* step a4 (+ the Runge-Kutta combination) */
+#define CS_K_TRANSPORT 4 /* one transport stage (wall flux + update) */
+#define CS_K_COUNT 5
+
+/* Enable (1) or disable (0) stage timing on h.  Do not enable it while a
+ * stream that h launches on is being captured into a CUDA graph.
+ * Errors: CS_EINVAL. */
+int cs_profile(cs_handle_t h, int enable);
+
+/* total_ms, launches (host, out) [CS_K_COUNT] each (either may be NULL);
+ * reset != 0 clears the records.  Blocks until the recorded events complete.
+ * Errors: CS_EINVAL, CS_ECUDA. */
+int cs_profile_read(cs_handle_t h, double *total_ms, long long *launches, int reset);
+
 #ifdef __cplusplus
 }
 #endif

@@ -63,7 +63,11 @@ _SIGS = {
     "cs_relax": (_i, [_vp, _vp, _i, _d, _d, _i, _vp]),
     "cs_transport": (_i, [_vp, _vp, _i, ctypes.POINTER(Domain), _d, _vp]),
     "cs_step": (_i, [_vp, _vp, _i, ctypes.POINTER(Domain), _d, _d, _i, _vp]),
+    "cs_profile": (_i, [_vp, _i]),
+    "cs_profile_read": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong), _i]),
 }
+
+STAGES = ("forward", "convolve", "inverse", "conserve", "transport")
 
 
 def library_path() -> pathlib.Path:
@@ -193,6 +197,18 @@ def cs_transport(h, f, ncells, dom: Domain, dt, stream=None):
 
 def cs_step(h, f, ncells, dom: Domain, dt, eps, nsteps, stream=None):
     _check(lib().cs_step(h, _dptr(f, "f"), ncells, ctypes.byref(dom), dt, eps, nsteps, _stream(stream)))
+
+
+def cs_profile(h, enable: bool):
+    _check(lib().cs_profile(h, int(bool(enable))))
+
+
+def cs_profile_read(h, reset: bool = True) -> dict:
+    """{stage: (total_ms, launches)} of the stages bracketed since the last reset."""
+    ms = (_d * len(STAGES))()
+    n = (ctypes.c_longlong * len(STAGES))()
+    _check(lib().cs_profile_read(h, ms, n, int(bool(reset))))
+    return {k: (ms[i], n[i]) for i, k in enumerate(STAGES)}
 
 
 # ------------------------------------------------------------------ convenience object

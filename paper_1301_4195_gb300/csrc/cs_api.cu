@@ -160,13 +160,45 @@ int ensure_workspace(Handle &hd, int ncells)
     return CS_OK;
 }
 
+int timed_forward(Handle &hd, const double *f, int ncells, cudaStream_t s)
+{
+    StageTimer t(hd, CS_K_FORWARD, s);
+    return launch_forward(hd, f, ncells, s);
+}
+
+int timed_convolve(Handle &hd, int ncells, cudaStream_t s)
+{
+    StageTimer t(hd, CS_K_CONVOLVE, s);
+    return launch_convolve(hd, ncells, s);
+}
+
+int timed_inverse(Handle &hd, int ncells, double eps, double *Qt, cudaStream_t s)
+{
+    StageTimer t(hd, CS_K_INVERSE, s);
+    return launch_inverse(hd, ncells, eps, Qt, s);
+}
+
+int timed_conserve(Handle &hd, const double *Qt, int ncells, int project, double a, const double *x, double b,
+                   const double *y, double c, double *out, double *moments, cudaStream_t s)
+{
+    StageTimer t(hd, CS_K_CONSERVE, s);
+    return launch_conserve(hd, Qt, ncells, project, a, x, b, y, c, out, moments, s);
+}
+
+int timed_transport(Handle &hd, const double *fin, int ncells, const cs_domain &dom, double a, const double *x,
+                    double b, const double *y, double c, double *out, cudaStream_t s)
+{
+    StageTimer t(hd, CS_K_TRANSPORT, s);
+    return launch_transport_stage(hd, fin, ncells, dom, a, x, b, y, c, out, s);
+}
+
 int collide_into(Handle &hd, const double *f, int ncells, double eps, double *Qt, cudaStream_t s)
 {
-    int rc = launch_forward(hd, f, ncells, s);
+    int rc = timed_forward(hd, f, ncells, s);
     if (rc) return rc;
-    rc = launch_convolve(hd, ncells, s);
+    rc = timed_convolve(hd, ncells, s);
     if (rc) return rc;
-    return launch_inverse(hd, ncells, eps, Qt, s);
+    return timed_inverse(hd, ncells, eps, Qt, s);
 }
 
 // one Heun step of df/dt = P Qt(f) / eps, in place
@@ -174,18 +206,18 @@ int heun_collision(Handle &hd, double *f, int ncells, double dt, double eps, cud
 {
     int rc = collide_into(hd, f, ncells, eps, hd.Qt, s);
     if (rc) return rc;
-    rc = launch_conserve(hd, hd.Qt, ncells, 1, 1.0, f, 0.0, nullptr, dt, hd.f1, nullptr, s);
+    rc = timed_conserve(hd, hd.Qt, ncells, 1, 1.0, f, 0.0, nullptr, dt, hd.f1, nullptr, s);
     if (rc) return rc;
     rc = collide_into(hd, hd.f1, ncells, eps, hd.Qt, s);
     if (rc) return rc;
-    return launch_conserve(hd, hd.Qt, ncells, 1, 0.5, f, 0.5, hd.f1, 0.5 * dt, f, nullptr, s);
+    return timed_conserve(hd, hd.Qt, ncells, 1, 0.5, f, 0.5, hd.f1, 0.5 * dt, f, nullptr, s);
 }
 
 int heun_transport(Handle &hd, double *f, int ncells, const cs_domain &dom, double dt, cudaStream_t s)
 {
-    int rc = launch_transport_stage(hd, f, ncells, dom, 1.0, f, 0.0, nullptr, dt, hd.f1, s);
+    int rc = timed_transport(hd, f, ncells, dom, 1.0, f, 0.0, nullptr, dt, hd.f1, s);
     if (rc) return rc;
-    return launch_transport_stage(hd, hd.f1, ncells, dom, 0.5, f, 0.5, hd.f1, 0.5 * dt, f, s);
+    return timed_transport(hd, hd.f1, ncells, dom, 0.5, f, 0.5, hd.f1, 0.5 * dt, f, s);
 }
 
 int check_domain(const Handle &hd, const cs_domain *dom, int ncells)
@@ -202,6 +234,35 @@ int check_domain(const Handle &hd, const cs_domain *dom, int ncells)
 }
 
 }  // namespace
+
+StageTimer::StageTimer(Handle &hd, int k, cudaStream_t s) : hd_(&hd), s_(s), k_(k)
+{
+    if (!hd.prof) return;
+    cudaEvent_t a;
+    if (!hd.pool.empty()) {
+        a = hd.pool.back();
+        hd.pool.pop_back();
+    } else if (cudaEventCreate(&a) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    if (!hd.pool.empty()) {
+        b_ = hd.pool.back();
+        hd.pool.pop_back();
+    } else if (cudaEventCreate(&b_) != cudaSuccess) {
+        cudaGetLastError();
+        hd.pool.push_back(a);
+        b_ = nullptr;
+        return;
+    }
+    cudaEventRecord(a, s);
+    hd.recs.push_back({a, b_, k});
+}
+
+StageTimer::~StageTimer()
+{
+    if (b_) cudaEventRecord(b_, s_);
+}
 
 int set_error(int code, const std::string &msg)
 {
@@ -308,10 +369,50 @@ int cs_weights_build(int N, double L, double lambda, int precision, cudaStream_t
     return CS_OK;
 }
 
+int cs_profile(cs_handle_t h, int enable)
+{
+    if (int rc = check_handle(h)) return rc;
+    h->h.prof = enable != 0;
+    return CS_OK;
+}
+
+int cs_profile_read(cs_handle_t h, double *total_ms, long long *launches, int reset)
+{
+    if (int rc = check_handle(h)) return rc;
+    Handle &hd = h->h;
+    double ms[CS_K_COUNT] = {0};
+    long long n[CS_K_COUNT] = {0};
+    for (const auto &r : hd.recs) {
+        cudaError_t e = cudaEventSynchronize(r.b);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+        if (e != cudaSuccess) return cuda_error(e, "cs_profile_read");
+        ms[r.k] += t;
+        n[r.k] += 1;
+    }
+    if (total_ms)
+        for (int i = 0; i < CS_K_COUNT; ++i) total_ms[i] = ms[i];
+    if (launches)
+        for (int i = 0; i < CS_K_COUNT; ++i) launches[i] = n[i];
+    if (reset) {
+        for (const auto &r : hd.recs) {
+            hd.pool.push_back(r.a);
+            hd.pool.push_back(r.b);
+        }
+        hd.recs.clear();
+    }
+    return CS_OK;
+}
+
 int cs_handle_destroy(cs_handle_t h)
 {
     if (!h) return CS_OK;
     Handle &hd = h->h;
+    for (const auto &r : hd.recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : hd.pool) cudaEventDestroy(e);
     cudaFree(hd.ghat);
     cudaFree(hd.pencil_tile0);
     cudaFree(hd.tw64);
@@ -360,7 +461,7 @@ int cs_transform(cs_handle_t h, const double *f, int ncells, double *fhat, cudaS
     if (int rc = check_device_ptr(fhat, "fhat")) return rc;
     Handle &hd = h->h;
     if (int rc = ensure_workspace(hd, ncells)) return rc;
-    if (int rc = launch_forward(hd, f, ncells, s)) return rc;
+    if (int rc = timed_forward(hd, f, ncells, s)) return rc;
     return launch_spectral_to_natural(hd, hd.F, ncells, fhat, s);
 }
 
@@ -374,7 +475,7 @@ int cs_convolve(cs_handle_t h, const double *fhat, int ncells, double *qhat, cud
     Handle &hd = h->h;
     if (int rc = ensure_workspace(hd, ncells)) return rc;
     if (int rc = launch_natural_to_spectral(hd, fhat, ncells, hd.F, s)) return rc;
-    if (int rc = launch_convolve(hd, ncells, s)) return rc;
+    if (int rc = timed_convolve(hd, ncells, s)) return rc;
     return launch_spectral_to_natural(hd, hd.Qh, ncells, qhat, s);
 }
 
@@ -389,7 +490,7 @@ int cs_inverse(cs_handle_t h, const double *qhat, int ncells, double eps, double
     Handle &hd = h->h;
     if (int rc = ensure_workspace(hd, ncells)) return rc;
     if (int rc = launch_natural_to_spectral(hd, qhat, ncells, hd.Qh, s)) return rc;
-    return launch_inverse(hd, ncells, eps, Q, s);
+    return timed_inverse(hd, ncells, eps, Q, s);
 }
 
 int cs_collide(cs_handle_t h, const double *f, int ncells, double eps, double *Q, int conserve, cudaStream_t s)
@@ -406,7 +507,7 @@ int cs_collide(cs_handle_t h, const double *f, int ncells, double eps, double *Q
         return set_error(CS_EINVAL, "f and Q overlap");
     if (int rc = ensure_workspace(hd, ncells)) return rc;
     if (int rc = collide_into(hd, f, ncells, eps, Q, s)) return rc;
-    if (conserve) return launch_conserve(hd, Q, ncells, 1, 0.0, nullptr, 0.0, nullptr, 1.0, Q, nullptr, s);
+    if (conserve) return timed_conserve(hd, Q, ncells, 1, 0.0, nullptr, 0.0, nullptr, 1.0, Q, nullptr, s);
     return CS_OK;
 }
 
@@ -417,7 +518,7 @@ int cs_conserve(cs_handle_t h, double *Q, int ncells, double *moments, cudaStrea
     if (ncells == 0) return CS_OK;
     if (int rc = check_device_ptr(Q, "Q")) return rc;
     if (int rc = check_device_ptr(moments, "moments", true)) return rc;
-    return launch_conserve(h->h, Q, ncells, 1, 0.0, nullptr, 0.0, nullptr, 1.0, Q, moments, s);
+    return timed_conserve(h->h, Q, ncells, 1, 0.0, nullptr, 0.0, nullptr, 1.0, Q, moments, s);
 }
 
 int cs_moments(cs_handle_t h, const double *f, int ncells, double *out, cudaStream_t s)

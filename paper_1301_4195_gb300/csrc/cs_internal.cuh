@@ -14,6 +14,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "../../include/cs.h"
 
@@ -60,6 +61,27 @@ struct Handle {
     // pieces of the workspace (set by layout_workspace)
     void *F = nullptr, *Qh = nullptr, *X = nullptr, *Y = nullptr;
     double *Qt = nullptr, *f1 = nullptr, *r1 = nullptr, *scal = nullptr;
+    // stage timing (cs_profile)
+    bool prof = false;
+    struct Rec {
+        cudaEvent_t a, b;
+        int k;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+};
+
+// Brackets one stage with events when profiling is on (cs_api.cu).
+class StageTimer {
+public:
+    StageTimer(Handle &hd, int k, cudaStream_t s);
+    ~StageTimer();
+
+private:
+    Handle *hd_;
+    cudaStream_t s_;
+    int k_;
+    cudaEvent_t b_ = nullptr;
 };
 
 // ---- errors (cs_api.cu)
