@@ -179,6 +179,32 @@ int cs_transport(cs_handle_t h, double *f, int ncells, const cs_domain *dom, dou
 int cs_step(cs_handle_t h, double *f, int ncells, const cs_domain *dom, double dt, double eps,
             int nsteps, cudaStream_t stream);
 
+/* cs_collide without any device allocation.  The paper has no counterpart:
+ * this exists for callers that cannot call cudaMalloc -- code running inside
+ * another runtime's host callback or plugin that owns every allocation, a
+ * real-time loop that must not block on the allocator, a process whose
+ * device memory is budgeted up front.  cs_collide may grow the handle's
+ * workspace with cudaMalloc; this call keeps its intermediate arrays in one
+ * 64 MiB array compiled into the library instead, and calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *   Arguments, layouts and results are those of cs_collide (same kernels).
+ *   Size limit: the three spectral intermediates must fit in 64 MiB, i.e.
+ *   at most 64 cells at N = 32 in CS_FP32, 32 cells at N = 32 in CS_FP64,
+ *   672 cells at N = 16 in CS_FP32; larger ncells returns CS_EINVAL and a
+ *   message with the limit for the handle's N and precision.
+ *   Every GPU that loads the library holds the 64 MiB array until the
+ *   process exits.  All calls on a device share it and it keeps the last
+ *   call's contents (each call writes every element it later reads, so
+ *   nothing needs clearing); calls whose GPU work overlaps in time -- on two
+ *   streams, or from two host threads without ordering -- race on it and
+ *   return wrong results.  Order them on one stream or with events.
+ *   The first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress, with that device current); make that first call
+ *   before capturing the stream into a CUDA graph.
+ * Errors: CS_EINVAL, CS_ENOTSUP, CS_ECUDA. */
+int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, double eps, double *Q, int conserve,
+                       cudaStream_t stream);
+
 /* Per-stage timing.  While enabled on a handle, each stage that handle
  * launches is bracketed by two CUDA events recorded on the stream it is
  * launched on; cs_profile_read synchronises on those events and returns the

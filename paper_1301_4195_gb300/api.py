@@ -211,6 +211,16 @@ def cs_profile_read(h, reset: bool = True) -> dict:
     return {k: (ms[i], n[i]) for i, k in enumerate(STAGES)}
 
 
+def cs_collide_noalloc(h, f, ncells, eps, Q, conserve=1, stream=None):
+    """cs_collide for callers that must not allocate device memory: the
+    intermediates live in a fixed 64 MiB array inside the library (see cs.h
+    for the cell limits and the rule that overlapping calls race)."""
+    fn = lib().cs_collide_noalloc
+    fn.restype = _i
+    fn.argtypes = [_vp, _vp, _i, _d, _vp, _i, _vp]
+    _check(fn(h, _dptr(f, "f"), ncells, eps, _dptr(Q, "Q"), int(conserve), _stream(stream)))
+
+
 # ------------------------------------------------------------------ convenience object
 class Handle:
     """Owns one cs_handle_t (weights for one (N, L, lambda, precision))."""

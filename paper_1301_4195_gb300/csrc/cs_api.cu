@@ -11,10 +11,6 @@
 
 #include "cs_internal.cuh"
 
-struct cs_handle_s {
-    cs::Handle h;
-};
-
 namespace cs {
 
 namespace {

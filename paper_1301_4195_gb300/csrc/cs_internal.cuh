@@ -125,3 +125,8 @@ int launch_transport_stage(const Handle &hd, const double *fin, int ncells, cons
                            double *out, cudaStream_t s);
 
 }  // namespace cs
+
+// The opaque handle of the C ABI.
+struct cs_handle_s {
+    cs::Handle h;
+};
