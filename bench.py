@@ -251,12 +251,14 @@ def run_ours(args):
            "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes}
 
     # the same step in double precision (the plain FP64 GPU form)
-    h64 = api.Handle(N, L_BOX, LAM, "fp64")
-    h64.reserve(ncells)
-    _, fd64, _, _ = make_state(api, inputs, torch, N, ncells, device)
-    k64 = max(2, min(args.steps, 5))
-    ms64, _ = time_steps(torch, h64, fd64, dxd, fard, k64, 1, flush)
-    fp64 = {"value": pairs_step / (ms64 / k64 * 1e-3), "ms_per_step": ms64 / k64}
+    h64, fp64 = None, None
+    if not args.skip_fp64:
+        h64 = api.Handle(N, L_BOX, LAM, "fp64")
+        h64.reserve(ncells)
+        _, fd64, _, _ = make_state(api, inputs, torch, N, ncells, device)
+        k64 = max(2, min(args.steps, 5))
+        ms64, _ = time_steps(torch, h64, fd64, dxd, fard, k64, 1, flush)
+        fp64 = {"value": pairs_step / (ms64 / k64 * 1e-3), "ms_per_step": ms64 / k64}
 
     # the N = 32, 256-cell workload (secondary)
     n32 = None
@@ -295,14 +297,15 @@ def run_ours(args):
                      "flops_per_launch": flops_launch},
         "stage_ms_per_step": step_stage_ms,
         "fp64": fp64,
-        "speedup_vs_fp64": fp64["ms_per_step"] / ms_step,
+        "speedup_vs_fp64": fp64["ms_per_step"] / ms_step if fp64 else None,
     }
     if n32:
         out["n32"] = n32
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"], out["error_vs_oracle"] = cpu_baseline(args, api, inputs, torch, device, h32, h64)
     h32.close()
-    h64.close()
+    if h64:
+        h64.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -334,6 +337,8 @@ def cpu_baseline(args, api, inputs, torch, device, h32, h64):
     err = {}
     fd = torch.from_numpy(f0).to(device)
     for name, h in (("fp32", h32), ("fp64", h64)):
+        if h is None:
+            continue
         q = h.collide(fd).cpu().numpy()
         err[name] = float(np.abs(q - ref).max() / np.abs(ref).max())
     return cpu, err
@@ -384,6 +389,7 @@ def main():
     ap.add_argument("--cells", type=int, default=0, help="override the workload's cell count (profiling runs)")
     ap.add_argument("--skip-n32", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true", help="omit the double-precision comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -70,6 +70,13 @@ const char *cs_last_error(void);
  *   bytes (host, out).  Errors: CS_EINVAL. */
 int cs_weights_bytes(int N, int precision, size_t *bytes);
 
+/* Order of the (m3, k3) pairs inside one weight tile for grid size N and a
+ * precision (host only, no GPU work): map[p] = m3 * 256 + k3 for entry p, or
+ * -1 for padding; *entries = the tile stride.  Pass map = NULL to query the
+ * size.  Every valid pair (Sec. 3.2: k3 - m3 + N/2 in [0, N-1]) appears once.
+ * Errors: CS_EINVAL (bad N or precision, or cap < stride with map != NULL). */
+int cs_tile_layout(int N, int precision, int *map, int cap, int *entries);
+
 /* Build the convolution weights of Sec. 2.2 (eq. GHat_calc; closed forms for
  * lambda = 0 and 1, radial Gauss-Legendre quadrature otherwise), in double on
  * the device (kept in float for CS_FP32), together with the constants of the
@@ -96,6 +103,12 @@ int cs_handle_info(cs_handle_t h, int *N, double *L, double *lambda, int *precis
  * it is already large enough).  Synchronises the device when it reallocates.
  * Errors: CS_EINVAL, CS_ENOMEM. */
 int cs_reserve(cs_handle_t h, int ncells);
+
+/* Device-side status of h: synchronises the device, then returns CS_ETIMEOUT
+ * if a bounded wait inside one of h's kernels expired since the last call
+ * (the results of that call are invalid; no kernel traps or hangs instead),
+ * else CS_OK, and clears the status.  Errors: CS_EINVAL, CS_ECUDA. */
+int cs_status(cs_handle_t h);
 
 /* Ghat(xi_m, zeta_k) (unsymmetrised, Sec. 2.2) evaluated on the device by the
  * same function that fills the table, for n index pairs.

@@ -63,6 +63,8 @@ _SIGS = {
     "cs_relax": (_i, [_vp, _vp, _i, _d, _d, _i, _vp]),
     "cs_transport": (_i, [_vp, _vp, _i, ctypes.POINTER(Domain), _d, _vp]),
     "cs_step": (_i, [_vp, _vp, _i, ctypes.POINTER(Domain), _d, _d, _i, _vp]),
+    "cs_tile_layout": (_i, [_i, _i, ctypes.POINTER(_i), _i, ctypes.POINTER(_i)]),
+    "cs_status": (_i, [_vp]),
     "cs_profile": (_i, [_vp, _i]),
     "cs_profile_read": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong), _i]),
 }
@@ -127,6 +129,19 @@ def cs_weights_bytes(N: int, precision: int) -> int:
     out = ctypes.c_size_t()
     _check(lib().cs_weights_bytes(N, precision, ctypes.byref(out)))
     return out.value
+
+
+def cs_tile_layout(N: int, precision: int) -> list:
+    n = _i()
+    _check(lib().cs_tile_layout(N, precision, None, 0, ctypes.byref(n)))
+    arr = (_i * n.value)()
+    _check(lib().cs_tile_layout(N, precision, arr, n.value, ctypes.byref(n)))
+    return list(arr)
+
+
+def cs_status(h: int):
+    """Raise CSError(CS_ETIMEOUT) if a bounded device wait expired (synchronises)."""
+    _check(lib().cs_status(h))
 
 
 def cs_weights_build(N: int, L: float, lam: float, precision: int = CS_FP64, stream=None) -> int:

@@ -53,6 +53,17 @@ __device__ void block_sum5(double v[5], double *sh /* [5][kThreads/32] */)
     __syncthreads();
 }
 
+// v_k = dv (k - N/2) and its square, per axis, in shared memory: the double
+// work per point is then 7 operations for the moments and 9 for the update
+__device__ __forceinline__ void fill_axis(const Geom &g, double *va, double *v2a)
+{
+    for (int i = threadIdx.x; i < g.N; i += blockDim.x) {
+        const double v = g.dv * (i - g.h);
+        va[i] = v;
+        v2a[i] = v * v;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) conserve_kernel(Geom g, Proj pj, const double *Qt, int project,
                                                             double a, const double *x, double b,
                                                             const double *y, double c, double *out,
@@ -60,40 +71,50 @@ __global__ void __launch_bounds__(kThreads) conserve_kernel(Geom g, Proj pj, con
 {
     __shared__ double sh[5 * 32];
     __shared__ double ycoef[5];
+    __shared__ double va[kMaxN], v2a[kMaxN];
+    fill_axis(g, va, v2a);
+    __syncthreads();
+    const int N = g.N, NN = g.N * g.N;
     const int cell = blockIdx.x;
     const size_t base = (size_t)cell * g.M;
+    const double w = g.dv * g.dv * g.dv;
     double mom[5] = {0, 0, 0, 0, 0};
     if (project || moments) {
         for (int j = threadIdx.x; j < g.M; j += blockDim.x) {
-            double r[5];
-            c_row(g, j, r);
+            const int i1 = j / NN, i2 = (j / N) % N, i3 = j % N;
             const double q = Qt[base + j];
-#pragma unroll
-            for (int i = 0; i < 5; ++i) mom[i] += r[i] * q;
+            mom[0] += q;
+            mom[1] = fma(va[i1], q, mom[1]);
+            mom[2] = fma(va[i2], q, mom[2]);
+            mom[3] = fma(va[i3], q, mom[3]);
+            mom[4] = fma(v2a[i1] + v2a[i2] + v2a[i3], q, mom[4]);
         }
         block_sum5(mom, sh);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) mom[i] *= w;
     }
     if (threadIdx.x == 0) {
         for (int i = 0; i < 5; ++i) {
             double s = 0;
             if (project)
                 for (int k = 0; k < 5; ++k) s += pj.ainv[5 * i + k] * mom[k];
-            ycoef[i] = s;
+            ycoef[i] = w * s;  // C^T y = w (1, v1, v2, v3, |v|^2) . y
             if (moments) moments[5 * (size_t)cell + i] = mom[i];
         }
     }
     __syncthreads();
-    double yc[5];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) yc[i] = ycoef[i];
+    const double y0 = ycoef[0], y1 = ycoef[1], y2 = ycoef[2], y3 = ycoef[3], y4 = ycoef[4];
     for (int j = threadIdx.x; j < g.M; j += blockDim.x) {
-        double r[5];
-        c_row(g, j, r);
+        const int i1 = j / NN, i2 = (j / N) % N, i3 = j % N;
         double q = Qt[base + j];
-        if (project) q -= r[0] * yc[0] + r[1] * yc[1] + r[2] * yc[2] + r[3] * yc[3] + r[4] * yc[4];
+        if (project) {
+            const double corr = fma(y4, v2a[i1] + v2a[i2] + v2a[i3],
+                                    fma(y3, va[i3], fma(y2, va[i2], fma(y1, va[i1], y0))));
+            q -= corr;
+        }
         double o = c * q;
-        if (x) o += a * x[base + j];
-        if (y) o += b * y[base + j];
+        if (x) o = fma(a, x[base + j], o);
+        if (y) o = fma(b, y[base + j], o);
         out[base + j] = o;
     }
 }

@@ -83,7 +83,9 @@ bool spd_inverse5(const double *A, double *inv)
     return true;
 }
 
-void fill_geom(Geom &g, int N, double L, double lambda)
+}  // namespace
+
+void fill_geom(Geom &g, int N, double L, double lambda, int precision)
 {
     g.N = N;
     g.h = N / 2;
@@ -92,12 +94,53 @@ void fill_geom(Geom &g, int N, double L, double lambda)
     g.dv = 2.0 * L / N;
     g.dz = M_PI / L;
     g.lambda = lambda;
+    // ROWS layout: rows of a tile (one per m3) padded to a multiple of 4 entries
     g.off[0] = 0;
-    for (int m3 = 0; m3 < N; ++m3) g.off[m3 + 1] = g.off[m3] + (kmax_of(m3, g.h, N) - kmin_of(m3, g.h) + 1);
+    g.TS = 0;
+    for (int m3 = 0; m3 < N; ++m3) {
+        const int w = kmax_of(m3, g.h, N) - kmin_of(m3, g.h) + 1;
+        g.TS += w;
+        g.off[m3 + 1] = g.off[m3] + ((w + 3) & ~3);
+    }
     for (int m3 = N + 1; m3 <= kMaxN; ++m3) g.off[m3] = g.off[N];
-    g.TS = g.off[N];
-    g.TSp = (g.TS + 3) & ~3;
+    g.K = precision == CS_FP32 ? strip_width(N) : 0;
+    if (g.K) {
+        g.layout = LAYOUT_STRIP;
+        g.TSp = strip_stride(N, g.K);
+    } else {
+        g.layout = LAYOUT_ROWS;
+        g.TSp = g.off[N];
+    }
 }
+
+void tile_entry_map(const Geom &g, std::vector<int> &map)
+{
+    const int N = g.N, H = g.h, K = g.K;
+    map.assign(g.TSp, -1);
+    auto put = [&](int p, int m3, int k3) { map[p] = (m3 << 8) | k3; };
+    if (g.layout == LAYOUT_ROWS) {
+        for (int m3 = 0; m3 < N; ++m3)
+            for (int k3 = kmin_of(m3, H); k3 <= kmax_of(m3, H, N); ++k3) put(g.off[m3] + k3 - kmin_of(m3, H), m3, k3);
+        return;
+    }
+    for (int w = 0; w < N / K; ++w) {
+        const int k0 = w * K, base = strip_seg_off(N, K, w), lu = strip_lu(N, K, w);
+        if (strip_is_a(N, K, w)) {
+            for (int r = 0; r < lu; ++r)
+                for (int j = 0; j < K; ++j) put(base + r * K + j, r, k0 + j);
+            for (int t = 1; t < K; ++t)
+                for (int j = t; j < K; ++j) put(base + lu * K + strip_tri_a_off(K, t) + (j - t), k0 + H + t, k0 + j);
+        } else {
+            for (int t = 0; t < K - 1; ++t)
+                for (int j = 0; j <= t; ++j) put(base + strip_tri_b_off(t) + j, k0 - H + 1 + t, k0 + j);
+            const int ub = base + strip_round4(strip_tri(K));
+            for (int r = 0; r < lu; ++r)
+                for (int j = 0; j < K; ++j) put(ub + r * K + j, k0 + K - H + r, k0 + j);
+        }
+    }
+}
+
+namespace {
 
 size_t spectral_bytes(const Handle &hd, int ncells)
 {
@@ -109,7 +152,7 @@ size_t workspace_bytes(const Handle &hd, int ncells, size_t *offs)
 {
     const size_t sb = align_up(spectral_bytes(hd, ncells), 256);
     const size_t st = align_up((size_t)ncells * hd.g.M * sizeof(double), 256);
-    const size_t sc = align_up(sizeof(double) * (8 + (size_t)ncells + 8), 256);
+    const size_t sc = align_up(sizeof(double) * (transport_table_doubles(hd.g.N, ncells) + 8), 256);
     size_t o = 0;
     for (int i = 0; i < 4; ++i) {
         if (offs) offs[i] = o;
@@ -287,10 +330,25 @@ int cs_weights_bytes(int N, int precision, size_t *bytes)
     if (precision != CS_FP64 && precision != CS_FP32) return set_error(CS_EINVAL, "precision must be CS_FP64 or CS_FP32");
     if (!bytes) return set_error(CS_EINVAL, "bytes is NULL");
     Geom g{};
-    fill_geom(g, N, 1.0, 0.0);
+    fill_geom(g, N, 1.0, 0.0, precision);
     const long long tiles = count_tiles(N, nullptr);
     *bytes = (size_t)tiles * g.TSp * elem_bytes(precision) + sizeof(int) * (N * N + 1) +
              (size_t)N * N * (sizeof(double2) + sizeof(float2));
+    return CS_OK;
+}
+
+int cs_tile_layout(int N, int precision, int *map, int cap, int *entries)
+{
+    if (N < 4 || N > kMaxN || (N & 1)) return set_error(CS_EINVAL, "N must be even, 4 <= N <= 32");
+    if (precision != CS_FP64 && precision != CS_FP32) return set_error(CS_EINVAL, "precision must be CS_FP64 or CS_FP32");
+    Geom g{};
+    fill_geom(g, N, 1.0, 0.0, precision);
+    if (entries) *entries = g.TSp;
+    if (!map) return CS_OK;
+    if (cap < g.TSp) return set_error(CS_EINVAL, "map capacity below the tile stride");
+    std::vector<int> m;
+    tile_entry_map(g, m);
+    for (int i = 0; i < g.TSp; ++i) map[i] = m[i];
     return CS_OK;
 }
 
@@ -306,7 +364,7 @@ int cs_weights_build(int N, double L, double lambda, int precision, cudaStream_t
     Handle &hd = hs->h;
     cudaGetDevice(&hd.device);
     hd.precision = precision;
-    fill_geom(hd.g, N, L, lambda);
+    fill_geom(hd.g, N, L, lambda, precision);
     // twiddles exp(-i 2 pi ((k-h)(j-h) mod N) / N)
     std::vector<double2> t64(N * N);
     std::vector<float2> t32(N * N);
@@ -337,6 +395,8 @@ int cs_weights_build(int N, double L, double lambda, int precision, cudaStream_t
     }
     cudaError_t e = cudaMalloc(&hd.tw64, sizeof(double2) * N * N);
     if (e == cudaSuccess) e = cudaMalloc(&hd.tw32, sizeof(float2) * N * N);
+    if (e == cudaSuccess) e = cudaMalloc(&hd.err, 256);
+    if (e == cudaSuccess) e = cudaMemsetAsync(hd.err, 0, 256, stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         cs_handle_destroy(hs);
@@ -362,6 +422,20 @@ int cs_weights_build(int N, double L, double lambda, int precision, cudaStream_t
         return set_error(rc, msg);
     }
     *out = hs;
+    return CS_OK;
+}
+
+int cs_status(cs_handle_t h)
+{
+    if (int rc = check_handle(h)) return rc;
+    Handle &hd = h->h;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_error(e, "cs_status: synchronise");
+    int word = 0;
+    e = cudaMemcpy(&word, hd.err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(hd.err, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_error(e, "cs_status: read");
+    if (word) return set_error(CS_ETIMEOUT, "a bounded wait inside a kernel expired; its results are invalid");
     return CS_OK;
 }
 
@@ -411,6 +485,8 @@ int cs_handle_destroy(cs_handle_t h)
     for (auto e : hd.pool) cudaEventDestroy(e);
     cudaFree(hd.ghat);
     cudaFree(hd.pencil_tile0);
+    cudaFree(hd.pencil_order);
+    cudaFree(hd.err);
     cudaFree(hd.tw64);
     cudaFree(hd.tw32);
     cudaFree(hd.ws);
@@ -552,6 +628,7 @@ int cs_transport(cs_handle_t h, double *f, int ncells, const cs_domain *dom, dou
     if (int rc = check_domain(hd, dom, ncells)) return rc;
     if (int rc = check_device_ptr(f, "f")) return rc;
     if (int rc = ensure_workspace(hd, ncells)) return rc;
+    if (int rc = launch_transport_prep(hd, ncells, *dom, s)) return rc;
     return heun_transport(hd, f, ncells, *dom, dt, s);
 }
 
@@ -567,6 +644,8 @@ int cs_step(cs_handle_t h, double *f, int ncells, const cs_domain *dom, double d
     if (int rc = check_domain(hd, dom, ncells)) return rc;
     if (int rc = check_device_ptr(f, "f")) return rc;
     if (int rc = ensure_workspace(hd, ncells)) return rc;
+    if (nsteps > 0)
+        if (int rc = launch_transport_prep(hd, ncells, *dom, s)) return rc;
     for (int i = 0; i < nsteps; ++i) {
         if (int rc = heun_transport(hd, f, ncells, *dom, 0.5 * dt, s)) return rc;
         if (int rc = heun_collision(hd, f, ncells, dt, eps, s)) return rc;

@@ -28,17 +28,64 @@ template <> struct C2<double> { using type = double2; };
 template <> struct C2<float> { using type = float2; };
 template <typename T> using c2_t = typename C2<T>::type;
 
+// Order of the (m3, k3) pairs inside one weight tile.
+//   ROWS:  rows m3 = 0..N-1, each row the valid k3 ascending, padded to a
+//          multiple of 4 entries (generic and pencil kernels).
+//   STRIP: for the strip kernel (float, N in {8, 16, 24, 32}): the k3 range is
+//          cut into strips of K outputs; each strip's pairs are stored together
+//          (see strip_* below).
+enum Layout { LAYOUT_ROWS = 0, LAYOUT_STRIP = 1 };
+
 // Geometry of one handle, passed to kernels by value.
 struct Geom {
     int N, h, M;          // h = N/2, M = N^3
-    int TS, TSp;          // valid (m3,k3) pairs per tile = 3N^2/4; padded to a multiple of 4
+    int TS, TSp;          // valid (m3,k3) pairs per tile = 3N^2/4; tile stride of the layout
+    int layout, K;        // tile layout and, for LAYOUT_STRIP, the strip width
     double L, dv, dz;     // half-width, velocity and Fourier spacings
     double lambda;
-    int off[kMaxN + 1];   // off[m3]: first pair of row m3 inside a tile (rows ordered by m3)
+    int off[kMaxN + 1];   // ROWS layout: off[m3] = first entry of row m3 inside a tile
 };
 
 __host__ __device__ inline int kmin_of(int m3, int h) { return m3 - h > 0 ? m3 - h : 0; }
 __host__ __device__ inline int kmax_of(int m3, int h, int N) { return m3 + h - 1 < N - 1 ? m3 + h - 1 : N - 1; }
+
+// ---- STRIP layout.  Strip w covers k3 in [k0, k0 + K), k0 = w K, K | N/2,
+// K % 4 == 0.  With H = N/2 a strip is of one of two kinds:
+//   A (k0 < H):  "uniform" rows m3 = 0 .. k0 + H (all K outputs valid, K entries
+//                each), then a triangle t = 1 .. K-1: m3 = k0 + H + t with
+//                outputs j = t .. K-1 (K - t entries each);
+//   B (k0 >= H): triangle t = 0 .. K-2: m3 = k0 - H + 1 + t with outputs
+//                j = 0 .. t, padded to a multiple of 4 entries, then uniform
+//                rows m3 = k0 + K - H .. N - 1.
+// Strips are stored one after another, each padded to a multiple of 4.
+__host__ __device__ constexpr int strip_round4(int x) { return (x + 3) & ~3; }
+__host__ __device__ constexpr bool strip_is_a(int N, int K, int w) { return w * K < N / 2; }
+__host__ __device__ constexpr int strip_lu(int N, int K, int w)
+{
+    return strip_is_a(N, K, w) ? w * K + N / 2 + 1 : N + N / 2 - w * K - K;
+}
+__host__ __device__ constexpr int strip_tri(int K) { return K * (K - 1) / 2; }
+__host__ __device__ constexpr int strip_seg_size(int N, int K, int w) { return strip_lu(N, K, w) * K + strip_round4(strip_tri(K)); }
+__host__ __device__ constexpr int strip_seg_off(int N, int K, int w)
+{
+    int o = 0;
+    for (int i = 0; i < w; ++i) o += strip_seg_size(N, K, i);
+    return o;
+}
+__host__ __device__ constexpr int strip_stride(int N, int K) { return strip_seg_off(N, K, N / K); }
+__host__ __device__ constexpr int strip_tri_a_off(int K, int t)  // kind A, rows t = 1 .. K-1
+{
+    int o = 0;
+    for (int i = 1; i < t; ++i) o += K - i;
+    return o;
+}
+__host__ __device__ constexpr int strip_tri_b_off(int t) { return t * (t + 1) / 2; }  // kind B, rows t = 0 .. K-2
+
+// strip width used for (N, float); 0 = the strip kernel does not serve N
+__host__ __device__ constexpr int strip_width(int N)
+{
+    return N == 8 ? 4 : N == 16 ? 8 : N == 24 ? 12 : N == 32 ? 8 : 0;
+}
 
 struct Handle {
     int device = 0;
@@ -49,6 +96,9 @@ struct Handle {
     size_t ghat_bytes = 0;
     long long total_tiles = 0;
     int *pencil_tile0 = nullptr;  // device int[N*N + 1]: first tile of each pencil
+    int *pencil_order = nullptr;  // device int[N*N]: pencils by decreasing tile count
+    std::vector<int> order_host;
+    int *err = nullptr;           // device word: bit 0 set when a bounded device wait expired
     // transforms: twiddles exp(-i 2 pi ((k-h)(j-h) mod N) / N), [k][j]
     double2 *tw64 = nullptr;
     float2 *tw32 = nullptr;
@@ -96,6 +146,11 @@ int cuda_error(cudaError_t e, const char *what);
 inline size_t elem_bytes(int precision) { return precision == CS_FP32 ? 4 : 8; }
 inline int ngroups_of(int ncells) { return (ncells + kGroup - 1) / kGroup; }
 
+// ---- cs_api.cu
+void fill_geom(Geom &g, int N, double L, double lambda, int precision);
+// entry map of one tile: map[p] = (m3 << 8) | k3, or -1 for padding; size g.TSp
+void tile_entry_map(const Geom &g, std::vector<int> &map);
+
 // ---- weights.cu
 long long count_tiles(int N, int *pencil_tile0_host /* may be null, size N*N+1 */);
 int build_weights(Handle &hd, cudaStream_t s);
@@ -107,8 +162,9 @@ int launch_inverse(const Handle &hd, int ncells, double scale_eps, double *Qt, c
 int launch_spectral_to_natural(const Handle &hd, const void *src, int ncells, double *dst, cudaStream_t s);
 int launch_natural_to_spectral(const Handle &hd, const double *src, int ncells, void *dst, cudaStream_t s);
 
-// ---- convolve.cu
+// ---- convolve.cu, conv_strip.cu
 int launch_convolve(const Handle &hd, int ncells, cudaStream_t s);  // hd.F -> hd.Qh
+int launch_strip(const Handle &hd, int ncells, cudaStream_t s);     // float, LAYOUT_STRIP
 
 // ---- conserve.cu
 // out = a*x + b*y + c*(P Qt)   (P = projection if project, else identity), per cell
@@ -119,6 +175,10 @@ int launch_conserve(const Handle &hd, const double *Qt, int ncells, int project,
 int launch_moments(const Handle &hd, const double *f, int ncells, double *out, cudaStream_t s);
 
 // ---- transport.cu
+// doubles of workspace the transport tables need; tables are filled by
+// launch_transport_prep once per call (geometry, wall Maxwellian flux)
+size_t transport_table_doubles(int N, int ncells);
+int launch_transport_prep(const Handle &hd, int ncells, const cs_domain &dom, cudaStream_t s);
 // out = a*x + b*y + c*rhs(fin)   with rhs the finite-volume transport operator
 int launch_transport_stage(const Handle &hd, const double *fin, int ncells, const cs_domain &dom,
                            double a, const double *x, double b, const double *y, double c,

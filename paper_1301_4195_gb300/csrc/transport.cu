@@ -9,160 +9,221 @@
 // its ghost); the far end has two ghost cells equal to f_far for v1 < 0 and
 // to the last cell for v1 >= 0.
 //
-// Per Heun stage: wall_kernel (one block) computes the cell centres and
-// sigma_w of the stage input; stage_kernel (one thread per cell and velocity)
-// evaluates the two face fluxes of its cell and writes a x + b y + c rhs.
+// Double precision is slow on this part (1/64 of float), so the kernels keep
+// the double work per point small:
+//   prep_kernel   once per call: cell geometry (inverse distances, no
+//                 division later), v1 per velocity, v1 M_w(v) per velocity and
+//                 its discrete flux D = sum_{v1>0} v1 M_w dv^3;
+//   sigma_kernel  per Heun stage: sigma_w = (outgoing flux of cell 0) / D;
+//   face_kernel   per stage: every face flux once (one slope each);
+//   update_kernel per stage: out = a x + b y + c (F_{j-1/2} - F_{j+1/2}) / dx_j.
 #include "cs_internal.cuh"
 
 namespace cs {
 
 namespace {
 
-constexpr int kWallThreads = 1024;
+constexpr int kSigmaThreads = 512;
+
+// Layout of the transport tables in the workspace `scal` (doubles):
+//   [0] sigma_w   [1] D
+//   inv_fwd[j] = 1 / (x_{j+1} - x_j),      j = 0 .. nc   (ghost centres past the end)
+//   inv_ctr[j] = 1 / (x_{j+1} - x_{j-1}),  j = 1 .. nc
+//   inv_dx[j]  = 1 / dx_j,                 j = 0 .. nc - 1
+//   xs[j]      = cell centre,               j = 0 .. nc + 1
+//   v1[k]      = dv (k - N/2),              k = 0 .. N - 1
+//   mw[v]      = v1 M_w(v) for v1 > 0, else 0,  v = 0 .. N^3 - 1
+// and the face fluxes F[c][v], c = 0 .. nc, after them.
+struct Tab {
+    double *scal, *inv_fwd, *inv_ctr, *inv_dx, *xs, *v1, *mw, *face;
+};
+
+__host__ __device__ inline Tab tab_of(double *scal, int nc, int N)
+{
+    Tab t;
+    t.scal = scal;
+    t.inv_fwd = scal + 8;
+    t.inv_ctr = t.inv_fwd + (nc + 2);
+    t.inv_dx = t.inv_ctr + (nc + 2);
+    t.xs = t.inv_dx + (nc + 2);
+    t.v1 = t.xs + (nc + 2);
+    t.mw = t.v1 + ((N + 7) & ~7);
+    t.face = t.mw + (size_t)N * N * N;
+    return t;
+}
 
 struct Wall {
     double T, V1, V2, V3;
 };
 
-__device__ __forceinline__ void vel(const Geom &g, int j, double &v1, double &v2, double &v3)
+__global__ void __launch_bounds__(1024) prep_kernel(Geom g, Wall w, int nc, const double *__restrict__ dx,
+                                                    double *__restrict__ scal)
 {
-    const int N = g.N, h = g.h;
-    v1 = g.dv * (j / (N * N) - h);
-    v2 = g.dv * ((j / N) % N - h);
-    v3 = g.dv * (j % N - h);
-}
-
-__device__ __forceinline__ double wall_maxwellian(const Wall &w, double v1, double v2, double v3)
-{
-    const double e = (v1 - w.V1) * (v1 - w.V1) + (v2 - w.V2) * (v2 - w.V2) + (v3 - w.V3) * (v3 - w.V3);
-    return pow(2.0 * M_PI * w.T, -1.5) * exp(-e / (2.0 * w.T));
-}
-
-// scal[0] = sigma_w; scal[8 + j] = x_j for j = 0..nc-1 (cell centres)
-__global__ void __launch_bounds__(kWallThreads) wall_kernel(Geom g, Wall w, const double *__restrict__ f, int nc,
-                                                            const double *__restrict__ dx, double *__restrict__ scal)
-{
-    __shared__ double sh[2 * 32];
-    double *xc = scal + 8;
+    __shared__ double sh[32];
+    const Tab t = tab_of(scal, nc, g.N);
     if (threadIdx.x == 0) {
         double edge = 0.0;
         for (int j = 0; j < nc; ++j) {
-            xc[j] = edge + 0.5 * dx[j];
+            t.xs[j] = edge + 0.5 * dx[j];
             edge += dx[j];
         }
+        t.xs[nc] = t.xs[nc - 1] + dx[nc - 1];
+        t.xs[nc + 1] = t.xs[nc] + dx[nc - 1];
     }
-    const double w3 = g.dv * g.dv * g.dv;
-    const double x0 = 0.5 * dx[0], x1 = dx[0] + 0.5 * dx[1];
-    double out = 0.0, mw = 0.0;
-    for (int j = threadIdx.x; j < g.M; j += blockDim.x) {
-        double v1, v2, v3;
-        vel(g, j, v1, v2, v3);
-        if (v1 < 0) {
-            const double f0 = f[j], f1 = f[(size_t)g.M + j];
-            const double s0 = (f1 - f0) / (x1 - x0);
-            out += -v1 * (f0 - 0.5 * dx[0] * s0) * w3;
-        } else if (v1 > 0) {
-            mw += v1 * wall_maxwellian(w, v1, v2, v3) * w3;
+    if (threadIdx.x < g.N) t.v1[threadIdx.x] = g.dv * ((int)threadIdx.x - g.h);
+    __syncthreads();
+    for (int j = threadIdx.x; j <= nc; j += blockDim.x) {
+        t.inv_fwd[j] = 1.0 / (t.xs[j + 1] - t.xs[j]);
+        if (j >= 1) t.inv_ctr[j] = 1.0 / (t.xs[j + 1] - t.xs[j - 1]);
+        if (j < nc) t.inv_dx[j] = 1.0 / dx[j];
+    }
+    const int N = g.N;
+    const double norm = pow(2.0 * M_PI * w.T, -1.5), w3 = g.dv * g.dv * g.dv;
+    double D = 0.0;
+    for (int v = threadIdx.x; v < g.M; v += blockDim.x) {
+        const double v1 = g.dv * (v / (N * N) - g.h);
+        const double v2 = g.dv * ((v / N) % N - g.h);
+        const double v3 = g.dv * (v % N - g.h);
+        double m = 0.0;
+        if (v1 > 0) {
+            const double e = (v1 - w.V1) * (v1 - w.V1) + (v2 - w.V2) * (v2 - w.V2) + (v3 - w.V3) * (v3 - w.V3);
+            m = v1 * norm * exp(-e / (2.0 * w.T));
+            D += m * w3;
         }
+        t.mw[v] = m;
     }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        out += __shfl_xor_sync(0xffffffffu, out, o);
-        mw += __shfl_xor_sync(0xffffffffu, mw, o);
-    }
-    if (lane == 0) {
-        sh[wid] = out;
-        sh[32 + wid] = mw;
-    }
+    for (int o = 16; o > 0; o >>= 1) D += __shfl_xor_sync(0xffffffffu, D, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = D;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double so = 0, sm = 0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-            so += sh[k];
-            sm += sh[32 + k];
-        }
-        scal[0] = so / sm;
+        double s = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k];
+        t.scal[1] = s;
     }
 }
 
+// sigma_w of the stage input: outgoing flux of the reconstructed wall-face values
+__global__ void __launch_bounds__(kSigmaThreads) sigma_kernel(Geom g, const double *__restrict__ f, int nc,
+                                                              const double *__restrict__ dx, double *__restrict__ scal)
+{
+    __shared__ double sh[32];
+    const Tab t = tab_of(scal, nc, g.N);
+    const int NN = g.N * g.N;
+    const int half = g.h * NN;  // velocities with v1 < 0 come first (index k1 < N/2)
+    const double i01 = t.inv_fwd[0], hx = 0.5 * dx[0];
+    double out = 0.0;
+    for (int v = threadIdx.x; v < half; v += blockDim.x) {
+        const double f0 = f[v], f1 = f[(size_t)g.M + v];
+        out -= t.v1[v / NN] * (f0 - hx * ((f1 - f0) * i01));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) out += __shfl_xor_sync(0xffffffffu, out, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = out;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k];
+        t.scal[0] = s * (g.dv * g.dv * g.dv) / t.scal[1];
+    }
+}
+
+// 3-argument minmod on the bit patterns: 0 unless all three share a sign,
+// else the argument of least magnitude (exact; no double compares)
 __device__ __forceinline__ double minmod3(double a, double b, double c)
 {
-    if (a > 0 && b > 0 && c > 0) return fmin(a, fmin(b, c));
-    if (a < 0 && b < 0 && c < 0) return fmax(a, fmax(b, c));
-    return 0.0;
+    const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b), ic = __double_as_longlong(c);
+    if (((ia ^ ib) | (ia ^ ic)) < 0) return 0.0;
+    const unsigned long long mask = 0x7fffffffffffffffull;
+    unsigned long long m = (unsigned long long)ia & mask;
+    const unsigned long long mb = (unsigned long long)ib & mask, mc = (unsigned long long)ic & mask;
+    m = mb < m ? mb : m;
+    m = mc < m ? mc : m;
+    return __longlong_as_double((long long)(m | ((unsigned long long)ia & ~mask)));
 }
 
-struct Column {
-    const double *f, *ffar, *dx, *xc;
-    int nc, M, v;
-    double v1;
-    __device__ double val(int j) const
-    {
-        if (j < nc) return f[(size_t)j * M + v];
-        return v1 < 0 ? ffar[v] : f[(size_t)(nc - 1) * M + v];
-    }
-    __device__ double pos(int j) const
-    {
-        if (j < nc) return xc[j];
-        return xc[nc - 1] + (j - nc + 1) * dx[nc - 1];
-    }
-    __device__ double slope(int j) const
-    {
-        if (j == 0) return (val(1) - val(0)) / (pos(1) - pos(0));
-        const double fm = val(j - 1), f0 = val(j), fp = val(j + 1);
-        const double xm = pos(j - 1), x0 = pos(j), xp = pos(j + 1);
-        return minmod3((fp - f0) / (xp - x0), (f0 - fm) / (x0 - xm), (fp - fm) / (xp - xm));
-    }
-    __device__ double width(int j) const { return j < nc ? dx[j] : dx[nc - 1]; }
-};
-
-__global__ void stage_kernel(Geom g, Wall w, const double *__restrict__ fin, int nc, const double *__restrict__ dx,
-                             const double *__restrict__ ffar, const double *__restrict__ scal, double a,
-                             const double *x, double b, const double *y, double c, double *out)
+// flux through face c (between cells c-1 and c), c = 0 .. nc, one thread per (face, v)
+__global__ void face_kernel(Geom g, const double *__restrict__ fin, int nc, const double *__restrict__ dx,
+                            const double *__restrict__ ffar, double *__restrict__ scal)
 {
+    const Tab t = tab_of(scal, nc, g.N);
+    const int M = g.M, NN = g.N * g.N;
+    const int c = blockIdx.y;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < M; v += gridDim.x * blockDim.x) {
+        const double v1 = t.v1[v / NN];
+        const double ghost = v1 < 0 ? ffar[v] : fin[(size_t)(nc - 1) * M + v];
+        auto val = [&](int j) { return j < nc ? fin[(size_t)j * M + v] : ghost; };
+        double F;
+        if (c == 0) {
+            if (v1 > 0) {
+                F = t.scal[0] * t.mw[v];
+            } else {
+                const double f0 = val(0), f1 = val(1);
+                F = v1 * (f0 - 0.5 * dx[0] * ((f1 - f0) * t.inv_fwd[0]));
+            }
+        } else {
+            // upwind cell u: c-1 for v1 >= 0, c for v1 < 0 (u = nc is a ghost, slope 0)
+            const bool right = v1 >= 0;
+            const int u = right ? c - 1 : c;
+            const double fu = val(u);
+            double s = 0.0;
+            if (u < nc) {
+                const double fp = val(u + 1);
+                if (u == 0) {
+                    s = (fp - fu) * t.inv_fwd[0];
+                } else {
+                    const double fm = val(u - 1);
+                    s = minmod3((fp - fu) * t.inv_fwd[u], (fu - fm) * t.inv_fwd[u - 1], (fp - fm) * t.inv_ctr[u]);
+                }
+            }
+            const double half = 0.5 * (u < nc ? dx[u] : dx[nc - 1]);
+            F = v1 * (right ? fma(half, s, fu) : fma(-half, s, fu));
+        }
+        t.face[(size_t)c * M + v] = F;
+    }
+}
+
+__global__ void update_kernel(Geom g, int nc, const double *__restrict__ scal, double a, const double *x, double b,
+                              const double *y, double c, double *out)
+{
+    const Tab t = tab_of(const_cast<double *>(scal), nc, g.N);
     const size_t n = (size_t)nc * g.M;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const int cell = (int)(i / g.M), v = (int)(i % g.M);
-        double v1, v2, v3;
-        vel(g, v, v1, v2, v3);
-        Column col{fin, ffar, dx, scal + 8, nc, g.M, v, v1};
-        // face cell - 1/2
-        double Fl;
-        if (cell == 0) {
-            if (v1 > 0)
-                Fl = v1 * scal[0] * wall_maxwellian(w, v1, v2, v3);
-            else
-                Fl = v1 * (col.val(0) - 0.5 * dx[0] * col.slope(0));
-        } else if (v1 >= 0) {
-            Fl = v1 * (col.val(cell - 1) + 0.5 * col.width(cell - 1) * col.slope(cell - 1));
-        } else {
-            Fl = v1 * (col.val(cell) - 0.5 * col.width(cell) * col.slope(cell));
-        }
-        // face cell + 1/2
-        double Fr;
-        if (v1 >= 0)
-            Fr = v1 * (col.val(cell) + 0.5 * col.width(cell) * col.slope(cell));
-        else
-            Fr = v1 * (col.val(cell + 1) - 0.5 * col.width(cell + 1) * col.slope(cell + 1));
-        const double rhs = -(Fr - Fl) / dx[cell];
+        const int cell = (int)(i / g.M);
+        const double rhs = (t.face[i] - t.face[i + g.M]) * t.inv_dx[cell];
         double o = c * rhs;
-        if (x) o += a * x[i];
-        if (y) o += b * y[i];
+        if (x) o = fma(a, x[i], o);
+        if (y) o = fma(b, y[i], o);
         out[i] = o;
     }
 }
 
 }  // namespace
 
+size_t transport_table_doubles(int N, int ncells)
+{
+    return 8 + 4 * ((size_t)ncells + 2) + ((N + 7) & ~7) + (size_t)N * N * N * (ncells + 2);
+}
+
+int launch_transport_prep(const Handle &hd, int ncells, const cs_domain &dom, cudaStream_t s)
+{
+    const Wall w{dom.wall_T, dom.wall_V[0], dom.wall_V[1], dom.wall_V[2]};
+    prep_kernel<<<1, 1024, 0, s>>>(hd.g, w, ncells, dom.dx, hd.scal);
+    CS_CHECK_LAUNCH("transport tables");
+    return CS_OK;
+}
+
 int launch_transport_stage(const Handle &hd, const double *fin, int ncells, const cs_domain &dom, double a,
                            const double *x, double b, const double *y, double c, double *out, cudaStream_t s)
 {
-    const Wall w{dom.wall_T, dom.wall_V[0], dom.wall_V[1], dom.wall_V[2]};
-    wall_kernel<<<1, kWallThreads, 0, s>>>(hd.g, w, fin, ncells, dom.dx, hd.scal);
-    const size_t n = (size_t)ncells * hd.g.M;
-    const unsigned blocks = (unsigned)((n + 255) / 256 < 65535 ? (n + 255) / 256 : 65535);
-    stage_kernel<<<blocks, 256, 0, s>>>(hd.g, w, fin, ncells, dom.dx, dom.f_far, hd.scal, a, x, b, y, c, out);
+    const int M = hd.g.M;
+    sigma_kernel<<<1, kSigmaThreads, 0, s>>>(hd.g, fin, ncells, dom.dx, hd.scal);
+    const int tpb = 256;
+    dim3 fgrid((unsigned)((M + tpb - 1) / tpb), (unsigned)(ncells + 1));
+    face_kernel<<<fgrid, tpb, 0, s>>>(hd.g, fin, ncells, dom.dx, dom.f_far, hd.scal);
+    const size_t n = (size_t)ncells * M;
+    const unsigned blocks = (unsigned)((n + tpb - 1) / tpb < 65535 ? (n + tpb - 1) / tpb : 65535);
+    update_kernel<<<blocks, tpb, 0, s>>>(hd.g, ncells, hd.scal, a, x, b, y, c, out);
     CS_CHECK_LAUNCH("transport stage");
     return CS_OK;
 }

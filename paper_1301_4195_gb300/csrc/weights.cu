@@ -16,9 +16,11 @@
 // holding for every valid (m3, k3) the weight Ghat(m, k) + Ghat(K - m, k);
 // the centre tile (m1, m2) = (s1, s2) keeps the plain weight Ghat(m, k).
 // Inside a tile the pairs are ordered by m3, then k3 in
-// [max(0, m3 - N/2), min(N - 1, m3 + N/2 - 1)]; a tile holds 3N^2/4 pairs,
-// padded to a multiple of 4.  Tiles of one pencil are consecutive, pencils in
-// (k1, k2) order.
+// [max(0, m3 - N/2), min(N - 1, m3 + N/2 - 1)]; a tile holds 3N^2/4 pairs and
+// each row (one m3) is padded with zeros to a multiple of 4 entries so rows
+// start on 16-byte boundaries.  Tiles of one pencil are consecutive, pencils
+// in (k1, k2) order.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -191,7 +193,7 @@ __device__ double ghat_centered(const Geom &g, const QuadRule &q, int kp1, int k
 
 template <typename T>
 __global__ void build_table_kernel(Geom g, QuadRule q, const int *__restrict__ tile0, long long total,
-                                   T *__restrict__ out)
+                                   const int *__restrict__ emap, T *__restrict__ out)
 {
     const long long tile = blockIdx.x;
     if (tile >= total) return;
@@ -222,14 +224,13 @@ __global__ void build_table_kernel(Geom g, QuadRule q, const int *__restrict__ t
     const int s1 = K1 - m1, s2 = K2 - m2;
     T *dst = out + tile * g.TSp;
     for (int p = threadIdx.x; p < g.TSp; p += blockDim.x) {
-        if (p >= g.TS) {
+        const int e = emap[p];
+        if (e < 0) {  // padding
             dst[p] = T(0);
             continue;
         }
-        int m3 = 0;
-        while (m3 + 1 < N && g.off[m3 + 1] <= p) ++m3;
-        const int k3 = kmin_of(m3, h) + (p - g.off[m3]);
-        const int K3 = k3 + h, s3 = K3 - m3;
+        const int m3 = e >> 8, k3 = e & 255;
+        const int s3 = k3 + h - m3;
         double w = ghat_centered(g, q, k1 - h, k2 - h, k3 - h, m1 - h, m2 - h, m3 - h);
         if (!centre) w += ghat_centered(g, q, k1 - h, k2 - h, k3 - h, s1 - h, s2 - h, s3 - h);
         dst[p] = (T)w;
@@ -268,9 +269,25 @@ int build_weights(Handle &hd, cudaStream_t s)
     const Geom &g = hd.g;
     std::vector<int> tile0(g.N * g.N + 1);
     hd.total_tiles = count_tiles(g.N, tile0.data());
+    // heaviest pencils first, so the longest work items start earliest
+    hd.order_host.resize(g.N * g.N);
+    for (int i = 0; i < g.N * g.N; ++i) hd.order_host[i] = i;
+    std::stable_sort(hd.order_host.begin(), hd.order_host.end(), [&](int x, int y) {
+        return tile0[x + 1] - tile0[x] > tile0[y + 1] - tile0[y];
+    });
     cudaError_t e = cudaMalloc(&hd.pencil_tile0, sizeof(int) * tile0.size());
-    if (e != cudaSuccess) return set_error(CS_ENOMEM, "cudaMalloc of the pencil index failed");
+    if (e == cudaSuccess) e = cudaMalloc(&hd.pencil_order, sizeof(int) * hd.order_host.size());
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(CS_ENOMEM, "cudaMalloc of the pencil index failed");
+    }
     e = cudaMemcpyAsync(hd.pencil_tile0, tile0.data(), sizeof(int) * tile0.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hd.pencil_order, hd.order_host.data(), sizeof(int) * hd.order_host.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_error(e, "copy of the pencil index");
+    // the host copies above are read asynchronously: keep tile0 alive until the stream passes
+    e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_error(e, "copy of the pencil index");
     hd.ghat_bytes = (size_t)hd.total_tiles * g.TSp * elem_bytes(hd.precision);
     e = cudaMalloc(&hd.ghat, hd.ghat_bytes);
@@ -279,14 +296,30 @@ int build_weights(Handle &hd, cudaStream_t s)
         return set_error(CS_ENOMEM, "cudaMalloc of the weight table failed (" +
                                         std::to_string(hd.ghat_bytes) + " bytes)");
     }
+    std::vector<int> emap;
+    tile_entry_map(g, emap);
+    int *demap = nullptr;
+    e = cudaMalloc(&demap, sizeof(int) * emap.size());
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(CS_ENOMEM, "cudaMalloc of the tile entry map failed");
+    }
+    e = cudaMemcpyAsync(demap, emap.data(), sizeof(int) * emap.size(), cudaMemcpyHostToDevice, s);
     const QuadRule q = make_rule();
-    if (hd.precision == CS_FP32)
-        build_table_kernel<float><<<(unsigned)hd.total_tiles, 128, 0, s>>>(g, q, hd.pencil_tile0, hd.total_tiles,
-                                                                            (float *)hd.ghat);
-    else
-        build_table_kernel<double><<<(unsigned)hd.total_tiles, 128, 0, s>>>(g, q, hd.pencil_tile0, hd.total_tiles,
-                                                                             (double *)hd.ghat);
-    CS_CHECK_LAUNCH("weight table build");
+    if (e == cudaSuccess) {
+        if (hd.precision == CS_FP32)
+            build_table_kernel<float><<<(unsigned)hd.total_tiles, 128, 0, s>>>(g, q, hd.pencil_tile0,
+                                                                                hd.total_tiles, demap, (float *)hd.ghat);
+        else
+            build_table_kernel<double><<<(unsigned)hd.total_tiles, 128, 0, s>>>(g, q, hd.pencil_tile0,
+                                                                                 hd.total_tiles, demap, (double *)hd.ghat);
+        e = cudaGetLastError();
+    }
+    // the map (and the host vector behind the async copy) must outlive the kernel
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaFree(demap);
+    if (e != cudaSuccess) return cuda_error(e, "weight table build");
+    if (e2 != cudaSuccess) return cuda_error(e2, "weight table build");
     return CS_OK;
 }
 

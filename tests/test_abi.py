@@ -43,8 +43,10 @@ def test_host_only_queries(libcs):
     assert libcs.cs_version() >= 100
     b16 = libcs.cs_weights_bytes(16, libcs.CS_FP32)
     b32 = libcs.cs_weights_bytes(32, libcs.CS_FP32)
-    # symmetrised half of the 27 N^6 / 64 valid pairs, 4 bytes each, plus small tables
-    assert 0.49 * 27 * 16 ** 6 / 64 * 4 < b16 < 0.53 * 27 * 16 ** 6 / 64 * 4 + 1e5
+    # symmetrised half of the 27 N^6 / 64 valid pairs, 4 bytes each, rows padded to
+    # multiples of 4 entries (+13% at N = 16, +6% at N = 32), plus small tables
+    assert 0.49 * 27 * 16 ** 6 / 64 * 4 < b16 < 0.58 * 27 * 16 ** 6 / 64 * 4 + 1e5
+    assert 0.49 * 27 * 32 ** 6 / 64 * 4 < b32 < 0.55 * 27 * 32 ** 6 / 64 * 4 + 1e5
     assert b32 > 60 * b16
     assert libcs.cs_weights_bytes(16, libcs.CS_FP64) > 1.9 * b16
 
@@ -64,3 +66,16 @@ def test_null_handle_is_rejected(libcs):
     assert lib.cs_collide(None, None, 1, 1.0, None, 1, None) == libcs.CS_EINVAL
     assert lib.cs_handle_destroy(None) == libcs.CS_OK
     assert lib.cs_weights_bytes(16, 0, None) == libcs.CS_EINVAL
+
+
+@pytest.mark.parametrize("N", list(range(4, 33, 2)))
+@pytest.mark.parametrize("prec", [0, 1])
+def test_tile_layout_covers_every_valid_pair_once(libcs, N, prec):
+    """Sec. 3.2: the pairs (m3, k3) with k3 - m3 + N/2 in [0, N-1]; every one of them
+    must sit at exactly one entry of a tile, the rest being padding."""
+    m = libcs.cs_tile_layout(N, prec)
+    assert len(m) % 4 == 0
+    got = sorted(e for e in m if e >= 0)
+    want = sorted(m3 * 256 + k3 for m3 in range(N) for k3 in range(N) if 0 <= k3 - m3 + N // 2 <= N - 1)
+    assert got == want
+    assert len(want) == 3 * N * N // 4
