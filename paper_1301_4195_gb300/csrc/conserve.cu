@@ -64,47 +64,69 @@ __device__ __forceinline__ void fill_axis(const Geom &g, double *va, double *v2a
     }
 }
 
-__global__ void __launch_bounds__(kThreads) conserve_kernel(Geom g, Proj pj, const double *Qt, int project,
-                                                            double a, const double *x, double b,
-                                                            const double *y, double c, double *out,
-                                                            double *moments)
+// Double precision runs at 1/64 of float here, so a cell is spread over
+// `parts` blocks: moments_part_kernel writes one partial 5-vector per block,
+// apply_kernel sums a cell's partials in a fixed order (deterministic),
+// forms y = (C C^T)^{-1} C Qt and writes out = a x + b y + c (Qt - C^T y).
+__global__ void __launch_bounds__(kThreads) moments_part_kernel(Geom g, const double *__restrict__ Qt, int parts,
+                                                                double *__restrict__ partial)
 {
     __shared__ double sh[5 * 32];
-    __shared__ double ycoef[5];
     __shared__ double va[kMaxN], v2a[kMaxN];
     fill_axis(g, va, v2a);
     __syncthreads();
     const int N = g.N, NN = g.N * g.N;
-    const int cell = blockIdx.x;
+    const int cell = blockIdx.x / parts, part = blockIdx.x % parts;
+    const int chunk = (g.M + parts - 1) / parts;
+    const int j0 = part * chunk, j1 = min(g.M, j0 + chunk);
     const size_t base = (size_t)cell * g.M;
-    const double w = g.dv * g.dv * g.dv;
     double mom[5] = {0, 0, 0, 0, 0};
-    if (project || moments) {
-        for (int j = threadIdx.x; j < g.M; j += blockDim.x) {
-            const int i1 = j / NN, i2 = (j / N) % N, i3 = j % N;
-            const double q = Qt[base + j];
-            mom[0] += q;
-            mom[1] = fma(va[i1], q, mom[1]);
-            mom[2] = fma(va[i2], q, mom[2]);
-            mom[3] = fma(va[i3], q, mom[3]);
-            mom[4] = fma(v2a[i1] + v2a[i2] + v2a[i3], q, mom[4]);
-        }
-        block_sum5(mom, sh);
-#pragma unroll
-        for (int i = 0; i < 5; ++i) mom[i] *= w;
+    for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+        const int i1 = j / NN, i2 = (j / N) % N, i3 = j % N;
+        const double q = Qt[base + j];
+        mom[0] += q;
+        mom[1] = fma(va[i1], q, mom[1]);
+        mom[2] = fma(va[i2], q, mom[2]);
+        mom[3] = fma(va[i3], q, mom[3]);
+        mom[4] = fma(v2a[i1] + v2a[i2] + v2a[i3], q, mom[4]);
     }
+    block_sum5(mom, sh);
+    if (threadIdx.x < 5) partial[(size_t)blockIdx.x * 5 + threadIdx.x] = mom[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kThreads) apply_kernel(Geom g, Proj pj, const double *Qt, int project, int parts,
+                                                         const double *__restrict__ partial, double a,
+                                                         const double *x, double b, const double *y, double c,
+                                                         double *out, double *moments)
+{
+    __shared__ double va[kMaxN], v2a[kMaxN];
+    __shared__ double ycoef[5];
+    fill_axis(g, va, v2a);
+    const int N = g.N, NN = g.N * g.N;
+    const int cell = blockIdx.x / parts, part = blockIdx.x % parts;
+    const double w = g.dv * g.dv * g.dv;
     if (threadIdx.x == 0) {
+        double mom[5] = {0, 0, 0, 0, 0};
+        if (project || moments)
+            for (int q = 0; q < parts; ++q)
+                for (int i = 0; i < 5; ++i) mom[i] += partial[((size_t)cell * parts + q) * 5 + i];
+        for (int i = 0; i < 5; ++i) {
+            mom[i] *= w;
+            if (moments && part == 0) moments[5 * (size_t)cell + i] = mom[i];
+        }
         for (int i = 0; i < 5; ++i) {
             double s = 0;
             if (project)
                 for (int k = 0; k < 5; ++k) s += pj.ainv[5 * i + k] * mom[k];
             ycoef[i] = w * s;  // C^T y = w (1, v1, v2, v3, |v|^2) . y
-            if (moments) moments[5 * (size_t)cell + i] = mom[i];
         }
     }
     __syncthreads();
     const double y0 = ycoef[0], y1 = ycoef[1], y2 = ycoef[2], y3 = ycoef[3], y4 = ycoef[4];
-    for (int j = threadIdx.x; j < g.M; j += blockDim.x) {
+    const int chunk = (g.M + parts - 1) / parts;
+    const int j0 = part * chunk, j1 = min(g.M, j0 + chunk);
+    const size_t base = (size_t)cell * g.M;
+    for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
         const int i1 = j / NN, i2 = (j / N) % N, i3 = j % N;
         double q = Qt[base + j];
         if (project) {
@@ -140,12 +162,17 @@ __global__ void __launch_bounds__(kThreads) moments_kernel(Geom g, const double 
 
 }  // namespace
 
+int conserve_parts(int M) { return M >= 32768 ? 8 : M >= 4096 ? 4 : 1; }
+
 int launch_conserve(const Handle &hd, const double *Qt, int ncells, int project, double a, const double *x,
                     double b, const double *y, double c, double *out, double *moments, cudaStream_t s)
 {
     Proj pj;
     for (int i = 0; i < 25; ++i) pj.ainv[i] = hd.cct_inv[i];
-    conserve_kernel<<<ncells, kThreads, 0, s>>>(hd.g, pj, Qt, project, a, x, b, y, c, out, moments);
+    const int parts = conserve_parts(hd.g.M);
+    const unsigned blocks = (unsigned)(ncells * parts);
+    if (project || moments) moments_part_kernel<<<blocks, kThreads, 0, s>>>(hd.g, Qt, parts, hd.part5);
+    apply_kernel<<<blocks, kThreads, 0, s>>>(hd.g, pj, Qt, project, parts, hd.part5, a, x, b, y, c, out, moments);
     CS_CHECK_LAUNCH("conservation projection");
     return CS_OK;
 }

@@ -203,35 +203,41 @@ __device__ __forceinline__ void strip_b(const float2 *arow, const float2 *brow, 
     uniform_run<K, U, R>(arow, brow, g + strip_round4(strip_tri(K)), k0 + K - H, N - K, lu, lane, acc);
 }
 
-template <int N, int K, int U, int NST>
+// GPC cell groups per CTA share each stage's weight tile (each group has its
+// own two rows); warp = (group g_local, strip w)
+template <int N, int K, int U, int NST, int GPC>
 struct StripCfg {
     static constexpr int W = N / K;
+    static constexpr int WARPS = W * GPC;
     static constexpr int M = N * N * N;
     static constexpr int TSV = strip_stride(N, K);
     static constexpr uint32_t ROWB = N * kGroup * sizeof(float2);
     static constexpr uint32_t GB = TSV * sizeof(float);
-    static constexpr uint32_t STAGE = (2 * ROWB + GB + 127) / 128 * 128;
+    static constexpr uint32_t STAGE = (2 * GPC * ROWB + GB + 127) / 128 * 128;
     static constexpr size_t SMEM = (size_t)NST * STAGE + 2 * NST * sizeof(uint64_t) + 16;
 };
 
-template <int N, int K, int U, int NST>
-__global__ void __launch_bounds__(32 * (N / K)) conv_strip_kernel(const float *__restrict__ ghat,
-                                                                  const int *__restrict__ tile0,
-                                                                  const int *__restrict__ order, int ngroups,
-                                                                  const float2 *__restrict__ F,
-                                                                  float2 *__restrict__ Qh, float omega, int *err)
+template <int N, int K, int U, int NST, int GPC>
+__global__ void __launch_bounds__(32 * (N / K) * GPC) conv_strip_kernel(const float *__restrict__ ghat,
+                                                                        const int *__restrict__ tile0,
+                                                                        const int *__restrict__ order, int nblocks,
+                                                                        const float2 *__restrict__ F,
+                                                                        float2 *__restrict__ Qh, float omega,
+                                                                        int *err)
 {
-    using C = StripCfg<N, K, U, NST>;
+    using C = StripCfg<N, K, U, NST, GPC>;
     constexpr int H = N / 2;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + NST * C::STAGE);
     uint64_t *empty = full + NST;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + NST);
 
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp_id = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gl = warp_id / C::W, warp = warp_id % C::W;  // group within the CTA, strip
     const int item = blockIdx.x;
-    const int pencil = order[item / ngroups];
-    const int grp = item % ngroups;
+    const int pencil = order[item / nblocks];
+    const int gblk = item % nblocks;
+    const int grp = gblk * GPC + gl;
     const int k1 = pencil / N, k2 = pencil % N;
     const int K1 = k1 + H, K2 = k2 + H;
     const int lo1 = max(0, K1 - N + 1), hi1 = min(N - 1, K1);
@@ -239,13 +245,13 @@ __global__ void __launch_bounds__(32 * (N / K)) conv_strip_kernel(const float *_
     const int v2 = hi2 - lo2 + 1;
     const int nfull = ((hi1 - lo1 + 1) / 2) * v2;
     const int T = tile0[pencil + 1] - tile0[pencil];
-    const float2 *Fg = F + (size_t)grp * C::M * kGroup;
+    const float2 *Fb0 = F + (size_t)gblk * GPC * C::M * kGroup;  // first group of this CTA
     const float *Gp = ghat + (size_t)tile0[pencil] * C::TSV;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NST; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], C::W);
+            mbar_init(&empty[s], C::WARPS);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -267,10 +273,15 @@ __global__ void __launch_bounds__(32 * (N / K)) conv_strip_kernel(const float *_
         int m1, m2;
         rows_of(t, m1, m2);
         unsigned char *st = smem + s * C::STAGE;
-        mbar_arrive_expect_tx(&full[s], 2 * C::ROWB + C::GB);
-        bulk_copy(st, Fg + (size_t)(m1 * N + m2) * N * kGroup, C::ROWB, &full[s]);
-        bulk_copy(st + C::ROWB, Fg + (size_t)((K1 - m1) * N + (K2 - m2)) * N * kGroup, C::ROWB, &full[s]);
-        bulk_copy(st + 2 * C::ROWB, Gp + (size_t)t * C::TSV, C::GB, &full[s]);
+        mbar_arrive_expect_tx(&full[s], 2 * GPC * C::ROWB + C::GB);
+#pragma unroll
+        for (int q = 0; q < GPC; ++q) {
+            const float2 *Fq = Fb0 + (size_t)q * C::M * kGroup;
+            bulk_copy(st + q * C::ROWB, Fq + (size_t)(m1 * N + m2) * N * kGroup, C::ROWB, &full[s]);
+            bulk_copy(st + (GPC + q) * C::ROWB, Fq + (size_t)((K1 - m1) * N + (K2 - m2)) * N * kGroup, C::ROWB,
+                      &full[s]);
+        }
+        bulk_copy(st + 2 * GPC * C::ROWB, Gp + (size_t)t * C::TSV, C::GB, &full[s]);
     };
 
     int issued = 0;
@@ -309,9 +320,9 @@ __global__ void __launch_bounds__(32 * (N / K)) conv_strip_kernel(const float *_
             cur_m1 = m1;
         }
         const unsigned char *st = smem + s * C::STAGE;
-        const float2 *arow = reinterpret_cast<const float2 *>(st);
-        const float2 *brow = reinterpret_cast<const float2 *>(st + C::ROWB);
-        const float *gt = reinterpret_cast<const float *>(st + 2 * C::ROWB) + seg;
+        const float2 *arow = reinterpret_cast<const float2 *>(st + gl * C::ROWB);
+        const float2 *brow = reinterpret_cast<const float2 *>(st + (GPC + gl) * C::ROWB);
+        const float *gt = reinterpret_cast<const float *>(st + 2 * GPC * C::ROWB) + seg;
         if (kind_a)
             strip_a<N, K, U>(arow, brow, gt, k0, lane, acc);
         else
@@ -348,24 +359,32 @@ __global__ void __launch_bounds__(32 * (N / K)) conv_strip_kernel(const float *_
     }
 }
 
-template <int N, int K, int U, int NST>
+template <int N, int K, int U, int NST, int GPC>
 int launch_cfg(const Handle &hd, int ncells, cudaStream_t s)
 {
-    using C = StripCfg<N, K, U, NST>;
+    using C = StripCfg<N, K, U, NST, GPC>;
     static_assert(K % 4 == 0 && (N / 2) % K == 0, "strip width must divide N/2 and be a multiple of 4");
     static_assert(C::STAGE % 16 == 0 && C::ROWB % 16 == 0 && C::GB % 16 == 0, "bulk copies need 16-byte units");
-    auto kern = conv_strip_kernel<N, K, U, NST>;
+    auto kern = conv_strip_kernel<N, K, U, NST, GPC>;
     if (C::SMEM > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         if (e != cudaSuccess) return cuda_error(e, "strip kernel shared-memory attribute");
     }
     const int ng = ngroups_of(ncells);
-    const unsigned blocks = (unsigned)(N * N * ng);
+    const int nblocks = ng / GPC;  // callers pick GPC dividing ng
+    const unsigned blocks = (unsigned)(N * N * nblocks);
     const float omega = (float)(hd.g.dz * hd.g.dz * hd.g.dz);
-    kern<<<blocks, 32 * C::W, C::SMEM, s>>>((const float *)hd.ghat, hd.pencil_tile0, hd.pencil_order, ng,
-                                            (const float2 *)hd.F, (float2 *)hd.Qh, omega, hd.err);
+    kern<<<blocks, 32 * C::WARPS, C::SMEM, s>>>((const float *)hd.ghat, hd.pencil_tile0, hd.pencil_order, nblocks,
+                                                (const float2 *)hd.F, (float2 *)hd.Qh, omega, hd.err);
     CS_CHECK_LAUNCH("convolution (strip kernel)");
     return CS_OK;
+}
+
+template <int N, int K, int U, int NST1, int NST2>
+int launch_n(const Handle &hd, int ncells, cudaStream_t s)
+{
+    if (ngroups_of(ncells) % 2 == 0) return launch_cfg<N, K, U, NST2, 2>(hd, ncells, s);
+    return launch_cfg<N, K, U, NST1, 1>(hd, ncells, s);
 }
 
 }  // namespace
@@ -373,10 +392,10 @@ int launch_cfg(const Handle &hd, int ncells, cudaStream_t s)
 int launch_strip(const Handle &hd, int ncells, cudaStream_t s)
 {
     switch (hd.g.N) {
-    case 8: return launch_cfg<8, 4, 4, 4>(hd, ncells, s);
-    case 16: return launch_cfg<16, 8, 8, 4>(hd, ncells, s);
-    case 24: return launch_cfg<24, 12, 4, 3>(hd, ncells, s);
-    case 32: return launch_cfg<32, 8, 8, 3>(hd, ncells, s);
+    case 8: return launch_n<8, 4, 4, 4, 4>(hd, ncells, s);
+    case 16: return launch_n<16, 8, 8, 4, 3>(hd, ncells, s);
+    case 24: return launch_n<24, 12, 4, 3, 2>(hd, ncells, s);
+    case 32: return launch_n<32, 8, 8, 3, 3>(hd, ncells, s);
     default: return set_error(CS_ENOTSUP, "strip kernel: unsupported N");
     }
 }

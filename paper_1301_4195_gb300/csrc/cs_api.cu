@@ -147,12 +147,14 @@ size_t spectral_bytes(const Handle &hd, int ncells)
     return (size_t)ngroups_of(ncells) * hd.g.M * kGroup * 2 * elem_bytes(hd.precision);
 }
 
-// Carve the workspace: F, Qh, X, Y (spectral), Qt, f1 (state), scal.
+// Carve the workspace: F, Qh, X, Y (spectral), Qt, f1 (state), scal
+// (transport tables), part5 (projection partials).
 size_t workspace_bytes(const Handle &hd, int ncells, size_t *offs)
 {
     const size_t sb = align_up(spectral_bytes(hd, ncells), 256);
     const size_t st = align_up((size_t)ncells * hd.g.M * sizeof(double), 256);
     const size_t sc = align_up(sizeof(double) * (transport_table_doubles(hd.g.N, ncells) + 8), 256);
+    const size_t sp = align_up(sizeof(double) * 5 * (size_t)ncells * conserve_parts(hd.g.M), 256);
     size_t o = 0;
     for (int i = 0; i < 4; ++i) {
         if (offs) offs[i] = o;
@@ -164,13 +166,22 @@ size_t workspace_bytes(const Handle &hd, int ncells, size_t *offs)
     }
     if (offs) offs[6] = o;
     o += sc;
+    if (offs) offs[7] = o;
+    o += sp;
     return o;
+}
+
+void drop_graphs(Handle &hd)
+{
+    for (auto &g : hd.graphs) cudaGraphExecDestroy(g.exec);
+    hd.graphs.clear();
 }
 
 int ensure_workspace(Handle &hd, int ncells)
 {
     if (ncells <= hd.ws_cells) return CS_OK;
-    size_t offs[7];
+    drop_graphs(hd);  // captured steps point into the old workspace
+    size_t offs[8];
     const size_t bytes = workspace_bytes(hd, ncells, offs);
     if (hd.ws) {
         cudaError_t e = cudaDeviceSynchronize();
@@ -196,6 +207,7 @@ int ensure_workspace(Handle &hd, int ncells)
     hd.Qt = (double *)(b + offs[4]);
     hd.f1 = (double *)(b + offs[5]);
     hd.scal = (double *)(b + offs[6]);
+    hd.part5 = (double *)(b + offs[7]);
     return CS_OK;
 }
 
@@ -257,6 +269,58 @@ int heun_transport(Handle &hd, double *f, int ncells, const cs_domain &dom, doub
     int rc = timed_transport(hd, f, ncells, dom, 1.0, f, 0.0, nullptr, dt, hd.f1, s);
     if (rc) return rc;
     return timed_transport(hd, hd.f1, ncells, dom, 0.5, f, 0.5, hd.f1, 0.5 * dt, f, s);
+}
+
+// Run `body` (which enqueues one step on the stream it is given) nsteps times
+// on stream s.  Without profiling, the step is captured once into a CUDA graph
+// on the handle's private stream, cached under `key` (every pointer and scalar
+// the captured kernels read), and replayed; capture problems fall back to
+// launching the kernels directly.
+template <typename Body>
+int run_steps(Handle &hd, Handle::GraphEntry key, int nsteps, cudaStream_t s, Body body)
+{
+    if (nsteps <= 0) return CS_OK;
+    if (hd.prof || !hd.use_graphs) {
+        for (int i = 0; i < nsteps; ++i)
+            if (int rc = body(s)) return rc;
+        return CS_OK;
+    }
+    cudaGraphExec_t exec = nullptr;
+    for (auto &g : hd.graphs)
+        if (g.kind == key.kind && g.f == key.f && g.dx == key.dx && g.ffar == key.ffar && g.ncells == key.ncells &&
+            g.wall_T == key.wall_T && g.wall_V[0] == key.wall_V[0] && g.wall_V[1] == key.wall_V[1] &&
+            g.wall_V[2] == key.wall_V[2] && g.dt == key.dt && g.eps == key.eps)
+            exec = g.exec;
+    if (!exec) {
+        if (!hd.cap_stream && cudaStreamCreateWithFlags(&hd.cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            hd.use_graphs = false;
+            return run_steps(hd, key, nsteps, s, body);
+        }
+        cudaGraph_t graph = nullptr;
+        bool ok = cudaStreamBeginCapture(hd.cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        const int rc = ok ? body(hd.cap_stream) : CS_OK;
+        if (ok) ok = cudaStreamEndCapture(hd.cap_stream, &graph) == cudaSuccess && rc == CS_OK;
+        if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+        if (graph) cudaGraphDestroy(graph);
+        if (!ok) {
+            cudaGetLastError();
+            if (rc != CS_OK) return rc;
+            hd.use_graphs = false;  // this build or device cannot capture: launch directly from now on
+            return run_steps(hd, key, nsteps, s, body);
+        }
+        if (hd.graphs.size() >= 16) {
+            cudaGraphExecDestroy(hd.graphs.front().exec);
+            hd.graphs.erase(hd.graphs.begin());
+        }
+        key.exec = exec;
+        hd.graphs.push_back(key);
+    }
+    for (int i = 0; i < nsteps; ++i) {
+        cudaError_t e = cudaGraphLaunch(exec, s);
+        if (e != cudaSuccess) return cuda_error(e, "replay of a captured step");
+    }
+    return CS_OK;
 }
 
 int check_domain(const Handle &hd, const cs_domain *dom, int ncells)
@@ -483,6 +547,8 @@ int cs_handle_destroy(cs_handle_t h)
         cudaEventDestroy(r.b);
     }
     for (auto e : hd.pool) cudaEventDestroy(e);
+    drop_graphs(hd);
+    if (hd.cap_stream) cudaStreamDestroy(hd.cap_stream);
     cudaFree(hd.ghat);
     cudaFree(hd.pencil_tile0);
     cudaFree(hd.pencil_order);
@@ -614,9 +680,8 @@ int cs_relax(cs_handle_t h, double *f, int ncells, double dt, double eps, int ns
     if (int rc = check_device_ptr(f, "f")) return rc;
     Handle &hd = h->h;
     if (int rc = ensure_workspace(hd, ncells)) return rc;
-    for (int i = 0; i < nsteps; ++i)
-        if (int rc = heun_collision(hd, f, ncells, dt, eps, s)) return rc;
-    return CS_OK;
+    Handle::GraphEntry key{2, f, nullptr, nullptr, ncells, 0.0, {0.0, 0.0, 0.0}, dt, eps, nullptr};
+    return run_steps(hd, key, nsteps, s, [&](cudaStream_t st) { return heun_collision(hd, f, ncells, dt, eps, st); });
 }
 
 int cs_transport(cs_handle_t h, double *f, int ncells, const cs_domain *dom, double dt, cudaStream_t s)
@@ -644,14 +709,15 @@ int cs_step(cs_handle_t h, double *f, int ncells, const cs_domain *dom, double d
     if (int rc = check_domain(hd, dom, ncells)) return rc;
     if (int rc = check_device_ptr(f, "f")) return rc;
     if (int rc = ensure_workspace(hd, ncells)) return rc;
-    if (nsteps > 0)
-        if (int rc = launch_transport_prep(hd, ncells, *dom, s)) return rc;
-    for (int i = 0; i < nsteps; ++i) {
-        if (int rc = heun_transport(hd, f, ncells, *dom, 0.5 * dt, s)) return rc;
-        if (int rc = heun_collision(hd, f, ncells, dt, eps, s)) return rc;
-        if (int rc = heun_transport(hd, f, ncells, *dom, 0.5 * dt, s)) return rc;
-    }
-    return CS_OK;
+    const cs_domain d = *dom;
+    Handle::GraphEntry key{1, f, d.dx, d.f_far, ncells, d.wall_T, {d.wall_V[0], d.wall_V[1], d.wall_V[2]},
+                           dt, eps, nullptr};
+    return run_steps(hd, key, nsteps, s, [&](cudaStream_t st) {
+        if (int rc = launch_transport_prep(hd, ncells, d, st)) return rc;
+        if (int rc = heun_transport(hd, f, ncells, d, 0.5 * dt, st)) return rc;
+        if (int rc = heun_collision(hd, f, ncells, dt, eps, st)) return rc;
+        return heun_transport(hd, f, ncells, d, 0.5 * dt, st);
+    });
 }
 
 }  // extern "C"

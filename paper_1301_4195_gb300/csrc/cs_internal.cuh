@@ -111,6 +111,18 @@ struct Handle {
     // pieces of the workspace (set by layout_workspace)
     void *F = nullptr, *Qh = nullptr, *X = nullptr, *Y = nullptr;
     double *Qt = nullptr, *f1 = nullptr, *r1 = nullptr, *scal = nullptr;
+    double *part5 = nullptr;  // per-block partial moments of the projection
+    // replayable steps (cs_step, cs_relax): one captured step per argument set
+    struct GraphEntry {
+        int kind;  // 1 = Strang step, 2 = homogeneous Heun step
+        const void *f, *dx, *ffar;
+        int ncells;
+        double wall_T, wall_V[3], dt, eps;
+        cudaGraphExec_t exec;
+    };
+    std::vector<GraphEntry> graphs;
+    cudaStream_t cap_stream = nullptr;
+    bool use_graphs = true;
     // stage timing (cs_profile)
     bool prof = false;
     struct Rec {
@@ -173,6 +185,7 @@ int launch_conserve(const Handle &hd, const double *Qt, int ncells, int project,
                     const double *x, double b, const double *y, double c, double *out,
                     double *moments, cudaStream_t s);
 int launch_moments(const Handle &hd, const double *f, int ncells, double *out, cudaStream_t s);
+int conserve_parts(int M);  // blocks per cell of the projection
 
 // ---- transport.cu
 // doubles of workspace the transport tables need; tables are filled by

@@ -102,10 +102,12 @@ extern "C" int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, do
     if ((const char *)f < (const char *)Q + state && (const char *)Q < (const char *)f + state)
         return set_error(CS_EINVAL, "f and Q overlap");
     // three spectral buffers: forward X, Y -> F; convolution F -> Qh (reusing X's
-    // space); inverse Qh -> X', Y' (reusing Y's and F's space)
-    const size_t need = 3 * buffer_bytes(hd, ncells);
+    // space); inverse Qh -> X', Y' (reusing Y's and F's space); then the
+    // per-block partial moments of the projection
+    const size_t part_bytes = (sizeof(double) * 5 * (size_t)ncells * conserve_parts(hd.g.M) + 255) / 256 * 256;
+    const size_t need = 3 * buffer_bytes(hd, ncells) + part_bytes;
     if (need > kScratchBytes) {
-        const size_t per_group = 3 * buffer_bytes(hd, 1);
+        const size_t per_group = 3 * buffer_bytes(hd, 1) + 5 * sizeof(double) * kGroup * conserve_parts(hd.g.M);
         return set_error(CS_EINVAL, "cs_collide_noalloc: " + std::to_string(ncells) + " cells need " +
                                         std::to_string(need) + " bytes of scratch; the fixed array holds " +
                                         std::to_string(kScratchBytes) + " (at most " +
@@ -130,9 +132,10 @@ extern "C" int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, do
     inv.Qh = A;
     inv.X = B;
     inv.Y = C;
+    inv.part5 = (double *)(C + buffer_bytes(hd, ncells));
     if (int rc = launch_forward(fwd, f, ncells, stream)) return rc;
     if (int rc = launch_convolve(fwd, ncells, stream)) return rc;
     if (int rc = launch_inverse(inv, ncells, eps, Q, stream)) return rc;
-    if (conserve) return launch_conserve(hd, Q, ncells, 1, 0.0, nullptr, 0.0, nullptr, 1.0, Q, nullptr, stream);
+    if (conserve) return launch_conserve(inv, Q, ncells, 1, 0.0, nullptr, 0.0, nullptr, 1.0, Q, nullptr, stream);
     return CS_OK;
 }

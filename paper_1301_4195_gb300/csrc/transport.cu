@@ -11,9 +11,10 @@
 //
 // Double precision is slow on this part (1/64 of float), so the kernels keep
 // the double work per point small:
-//   prep_kernel   once per call: cell geometry (inverse distances, no
-//                 division later), v1 per velocity, v1 M_w(v) per velocity and
-//                 its discrete flux D = sum_{v1>0} v1 M_w dv^3;
+//   prep_mw_kernel, prep_geo_kernel   once per call: v1 M_w(v) per velocity
+//                 and its discrete flux D = sum_{v1>0} v1 M_w dv^3 (partials
+//                 summed in a fixed order), cell geometry (inverse distances,
+//                 so no division later), v1 per velocity index;
 //   sigma_kernel  per Heun stage: sigma_w = (outgoing flux of cell 0) / D;
 //   face_kernel   per stage: every face flux once (one slope each);
 //   update_kernel per stage: out = a x + b y + c (F_{j-1/2} - F_{j+1/2}) / dx_j.
@@ -33,9 +34,13 @@ constexpr int kSigmaThreads = 512;
 //   xs[j]      = cell centre,               j = 0 .. nc + 1
 //   v1[k]      = dv (k - N/2),              k = 0 .. N - 1
 //   mw[v]      = v1 M_w(v) for v1 > 0, else 0,  v = 0 .. N^3 - 1
+//   part[b]    = partial sums of D, one per block of prep_mw_kernel
 // and the face fluxes F[c][v], c = 0 .. nc, after them.
+constexpr int kPrepThreads = 256;
+constexpr int kMaxPrepBlocks = (kMaxN * kMaxN * kMaxN + kPrepThreads - 1) / kPrepThreads;
+
 struct Tab {
-    double *scal, *inv_fwd, *inv_ctr, *inv_dx, *xs, *v1, *mw, *face;
+    double *scal, *inv_fwd, *inv_ctr, *inv_dx, *xs, *v1, *mw, *part, *face;
 };
 
 __host__ __device__ inline Tab tab_of(double *scal, int nc, int N)
@@ -48,7 +53,8 @@ __host__ __device__ inline Tab tab_of(double *scal, int nc, int N)
     t.xs = t.inv_dx + (nc + 2);
     t.v1 = t.xs + (nc + 2);
     t.mw = t.v1 + ((N + 7) & ~7);
-    t.face = t.mw + (size_t)N * N * N;
+    t.part = t.mw + (size_t)N * N * N;
+    t.face = t.part + kMaxPrepBlocks;
     return t;
 }
 
@@ -56,31 +62,16 @@ struct Wall {
     double T, V1, V2, V3;
 };
 
-__global__ void __launch_bounds__(1024) prep_kernel(Geom g, Wall w, int nc, const double *__restrict__ dx,
-                                                    double *__restrict__ scal)
+// v1 M_w(v) for every velocity and one partial sum of D per block
+__global__ void __launch_bounds__(kPrepThreads) prep_mw_kernel(Geom g, Wall w, int nc, double *__restrict__ scal)
 {
-    __shared__ double sh[32];
+    __shared__ double sh[kPrepThreads / 32];
     const Tab t = tab_of(scal, nc, g.N);
-    if (threadIdx.x == 0) {
-        double edge = 0.0;
-        for (int j = 0; j < nc; ++j) {
-            t.xs[j] = edge + 0.5 * dx[j];
-            edge += dx[j];
-        }
-        t.xs[nc] = t.xs[nc - 1] + dx[nc - 1];
-        t.xs[nc + 1] = t.xs[nc] + dx[nc - 1];
-    }
-    if (threadIdx.x < g.N) t.v1[threadIdx.x] = g.dv * ((int)threadIdx.x - g.h);
-    __syncthreads();
-    for (int j = threadIdx.x; j <= nc; j += blockDim.x) {
-        t.inv_fwd[j] = 1.0 / (t.xs[j + 1] - t.xs[j]);
-        if (j >= 1) t.inv_ctr[j] = 1.0 / (t.xs[j + 1] - t.xs[j - 1]);
-        if (j < nc) t.inv_dx[j] = 1.0 / dx[j];
-    }
     const int N = g.N;
     const double norm = pow(2.0 * M_PI * w.T, -1.5), w3 = g.dv * g.dv * g.dv;
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
     double D = 0.0;
-    for (int v = threadIdx.x; v < g.M; v += blockDim.x) {
+    if (v < g.M) {
         const double v1 = g.dv * (v / (N * N) - g.h);
         const double v2 = g.dv * ((v / N) % N - g.h);
         const double v3 = g.dv * (v % N - g.h);
@@ -88,7 +79,7 @@ __global__ void __launch_bounds__(1024) prep_kernel(Geom g, Wall w, int nc, cons
         if (v1 > 0) {
             const double e = (v1 - w.V1) * (v1 - w.V1) + (v2 - w.V2) * (v2 - w.V2) + (v3 - w.V3) * (v3 - w.V3);
             m = v1 * norm * exp(-e / (2.0 * w.T));
-            D += m * w3;
+            D = m * w3;
         }
         t.mw[v] = m;
     }
@@ -98,8 +89,34 @@ __global__ void __launch_bounds__(1024) prep_kernel(Geom g, Wall w, int nc, cons
     __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k];
-        t.scal[1] = s;
+        for (int k = 0; k < kPrepThreads / 32; ++k) s += sh[k];
+        t.part[blockIdx.x] = s;
+    }
+}
+
+// cell geometry, v1 table and D (partials summed in a fixed order)
+__global__ void __launch_bounds__(256) prep_geo_kernel(Geom g, int nc, int nparts, const double *__restrict__ dx,
+                                                       double *__restrict__ scal)
+{
+    const Tab t = tab_of(scal, nc, g.N);
+    if (threadIdx.x == 0) {
+        double edge = 0.0;
+        for (int j = 0; j < nc; ++j) {
+            t.xs[j] = edge + 0.5 * dx[j];
+            edge += dx[j];
+        }
+        t.xs[nc] = t.xs[nc - 1] + dx[nc - 1];
+        t.xs[nc + 1] = t.xs[nc] + dx[nc - 1];
+        double D = 0.0;
+        for (int b = 0; b < nparts; ++b) D += t.part[b];
+        t.scal[1] = D;
+    }
+    if (threadIdx.x < g.N) t.v1[threadIdx.x] = g.dv * ((int)threadIdx.x - g.h);
+    __syncthreads();
+    for (int j = threadIdx.x; j <= nc; j += blockDim.x) {
+        t.inv_fwd[j] = 1.0 / (t.xs[j + 1] - t.xs[j]);
+        if (j >= 1) t.inv_ctr[j] = 1.0 / (t.xs[j + 1] - t.xs[j - 1]);
+        if (j < nc) t.inv_dx[j] = 1.0 / dx[j];
     }
 }
 
@@ -202,13 +219,15 @@ __global__ void update_kernel(Geom g, int nc, const double *__restrict__ scal, d
 
 size_t transport_table_doubles(int N, int ncells)
 {
-    return 8 + 4 * ((size_t)ncells + 2) + ((N + 7) & ~7) + (size_t)N * N * N * (ncells + 2);
+    return 8 + 4 * ((size_t)ncells + 2) + ((N + 7) & ~7) + kMaxPrepBlocks + (size_t)N * N * N * (ncells + 2);
 }
 
 int launch_transport_prep(const Handle &hd, int ncells, const cs_domain &dom, cudaStream_t s)
 {
     const Wall w{dom.wall_T, dom.wall_V[0], dom.wall_V[1], dom.wall_V[2]};
-    prep_kernel<<<1, 1024, 0, s>>>(hd.g, w, ncells, dom.dx, hd.scal);
+    const int nparts = (hd.g.M + kPrepThreads - 1) / kPrepThreads;
+    prep_mw_kernel<<<nparts, kPrepThreads, 0, s>>>(hd.g, w, ncells, hd.scal);
+    prep_geo_kernel<<<1, 256, 0, s>>>(hd.g, ncells, nparts, dom.dx, hd.scal);
     CS_CHECK_LAUNCH("transport tables");
     return CS_OK;
 }

@@ -259,3 +259,28 @@ def test_n32_256_cells_sampled(cs, orc, prec, tol):
     for i, c in enumerate(idx):
         assert rel(got[c], ref[i]) < tol, c
     assert drift(orc, got, N) < 1e-12
+
+
+# ------------------------------------------------------------------ replay and status
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_graph_replay_matches_direct_launches(cs, prec):
+    """cs_step replays a captured CUDA graph; with stage timing on it launches the
+    kernels directly.  Both must give bit-identical states (same kernels, same order)."""
+    N, nc = 16, 40
+    dx, f, far = _wall(N, nc)
+    h = handle(cs, N, 1.0, prec)
+    fa, fb = dev(f), dev(f)
+    h.step(fa, dev(dx), dev(far), 1.5, (0, 0, 0), 0.01, nsteps=3)
+    cs.cs_profile(h.ptr, True)
+    h.step(fb, dev(dx), dev(far), 1.5, (0, 0, 0), 0.01, nsteps=3)
+    cs.cs_profile(h.ptr, False)
+    cs.cs_profile_read(h.ptr, reset=True)
+    assert np.array_equal(host(fa), host(fb))
+    ga, gb = dev(f), dev(f)
+    h.relax(ga, 0.01, 4)
+    cs.cs_profile(h.ptr, True)
+    h.relax(gb, 0.01, 4)
+    cs.cs_profile(h.ptr, False)
+    cs.cs_profile_read(h.ptr, reset=True)
+    assert np.array_equal(host(ga), host(gb))
+    cs.cs_status(h.ptr)  # no bounded device wait expired
