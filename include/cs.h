@@ -218,6 +218,22 @@ int cs_step(cs_handle_t h, double *f, int ncells, const cs_domain *dom, double d
 int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, double eps, double *Q, int conserve,
                        cudaStream_t stream);
 
+/* Launch choices of the convolution (autotuner parameters).
+ *   CS_TUNE_GROUPS_PER_CTA  1 or 2 groups of 32 cells share each weight tile
+ *                           in shared memory (2 needs an even group count)
+ *   CS_TUNE_CTAS_PER_SM     resident CTAs per SM of the persistent kernel
+ *                           (capped by what fits)
+ * value 0 restores the automatic choice.  Errors: CS_EINVAL. */
+#define CS_TUNE_GROUPS_PER_CTA 1
+#define CS_TUNE_CTAS_PER_SM 2
+int cs_tune(cs_handle_t h, int param, int value);
+
+/* Time the convolution's launch choices on ncells synthetic cells on
+ * `stream` (synchronising), keep the fastest in the handle and return its
+ * time per launch in *ms (may be NULL).  Uses the workspace (cs_reserve).
+ * Errors: CS_EINVAL, CS_ENOMEM, CS_ECUDA. */
+int cs_autotune(cs_handle_t h, int ncells, cudaStream_t stream, double *ms);
+
 /* Per-stage timing.  While enabled on a handle, each stage that handle
  * launches is bracketed by two CUDA events recorded on the stream it is
  * launched on; cs_profile_read synchronises on those events and returns the

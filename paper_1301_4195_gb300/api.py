@@ -65,6 +65,8 @@ _SIGS = {
     "cs_step": (_i, [_vp, _vp, _i, ctypes.POINTER(Domain), _d, _d, _i, _vp]),
     "cs_tile_layout": (_i, [_i, _i, ctypes.POINTER(_i), _i, ctypes.POINTER(_i)]),
     "cs_status": (_i, [_vp]),
+    "cs_tune": (_i, [_vp, _i, _i]),
+    "cs_autotune": (_i, [_vp, _i, _vp, ctypes.POINTER(_d)]),
     "cs_profile": (_i, [_vp, _i]),
     "cs_profile_read": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong), _i]),
 }
@@ -212,6 +214,21 @@ def cs_transport(h, f, ncells, dom: Domain, dt, stream=None):
 
 def cs_step(h, f, ncells, dom: Domain, dt, eps, nsteps, stream=None):
     _check(lib().cs_step(h, _dptr(f, "f"), ncells, ctypes.byref(dom), dt, eps, nsteps, _stream(stream)))
+
+
+CS_TUNE_GROUPS_PER_CTA = 1
+CS_TUNE_CTAS_PER_SM = 2
+
+
+def cs_tune(h, param: int, value: int):
+    _check(lib().cs_tune(h, param, value))
+
+
+def cs_autotune(h, ncells: int, stream=None) -> float:
+    """Time the convolution launch choices on ncells cells, keep the fastest; returns ms."""
+    ms = _d()
+    _check(lib().cs_autotune(h, ncells, _stream(stream), ctypes.byref(ms)))
+    return ms.value
 
 
 def cs_profile(h, enable: bool):

@@ -3,10 +3,11 @@
 //   Qhat(zeta_k) = dzeta^3 sum_m Ghat(xi_m, zeta_k) fhat(xi_m) fhat(zeta_k - xi_m),
 // over the symmetrised half-tiles of the weight table (weights.cu).
 //
-// Work decomposition.  One CTA owns one output pencil (k1, k2, all k3) of one
-// group of 32 cells (one cell per lane).  The pencil's k3 range is cut into
-// N/K strips of K outputs; warp w owns strip w and keeps only its K complex
-// accumulators (plus a compensation pair) in registers.
+// Work decomposition.  A work item is one output pencil (k1, k2, all k3) of
+// GPC groups of 32 cells (one cell per lane).  The pencil's k3 range is cut
+// into N/K strips of K outputs; warp (group g, strip w) keeps only its K
+// complex accumulators (plus a compensation pair) in registers.  CTAs are
+// persistent and take items from an atomic counter, heaviest pencils first.
 //
 // Data movement.  Per (m1, m2) tile the CTA needs the partner rows
 // fhat(m1, m2, :) and fhat(s1, s2, :) of its 32 cells and the tile's weights.
@@ -32,6 +33,7 @@
 // Waits.  Every mbarrier wait is bounded by %globaltimer (2 s); on expiry the
 // kernel sets bit 0 of *err, tells the other warps through shared memory,
 // waits (bounded) for the copies it issued, and returns; cs_status() reports it.
+#include <algorithm>
 #include <cstdint>
 
 #include "cs_internal.cuh"
@@ -160,51 +162,86 @@ __device__ __forceinline__ void uniform_run(const float2 *arow, const float2 *br
     if constexpr (R > 0) uniform_block<K, R>(arow, brow, g + r * K, m3s + r, C - r - (R - 1), lane, acc);
 }
 
-// strip of kind A: uniform rows m3 = 0 .. k0+H, then triangle rows m3 = k0+H+t,
-// t = 1..K-1, outputs j = t..K-1, partner s3 = j - t
+// Strip of kind A: uniform rows m3 = 0 .. k0+H (partner s3 = k0+H-m3+j),
+// then the triangle m3 = k0+H+t, t = 1..K-1, outputs j = t..K-1 (s3 = j-t).
+// The last R = (H+1) mod U uniform rows join the triangle in a compile-time
+// tail (partners s3 = 0 .. R+K-2, weights read as float4: R*K + pad(K(K-1)/2)).
 template <int N, int K, int U>
 __device__ __forceinline__ void strip_a(const float2 *arow, const float2 *brow, const float *g, int k0, int lane,
                                         float2 (&acc)[K])
 {
     constexpr int H = N / 2;
     constexpr int R = (H + 1) % U;
+    constexpr int TAILG = R * K + strip_round4(strip_tri(K));
     const int lu = k0 + H + 1;
-    uniform_run<K, U, R>(arow, brow, g, 0, k0 + H, lu, lane, acc);
-    const float *gt = g + lu * K;
-    float2 b[K - 1];
+    uniform_run<K, U, 0>(arow, brow, g, 0, k0 + H, lu - R, lane, acc);
+    const float *gt = g + (lu - R) * K;
+    float gv[TAILG];
 #pragma unroll
-    for (int i = 0; i < K - 1; ++i) b[i] = brow[i * kGroup + lane];
+    for (int q = 0; q < TAILG / 4; ++q) {
+        const float4 v = reinterpret_cast<const float4 *>(gt)[q];
+        gv[4 * q] = v.x;
+        gv[4 * q + 1] = v.y;
+        gv[4 * q + 2] = v.z;
+        gv[4 * q + 3] = v.w;
+    }
+    float2 b[R + K - 1];
 #pragma unroll
-    for (int t = 1; t < K; ++t) {
+    for (int i = 0; i < R + K - 1; ++i) b[i] = brow[i * kGroup + lane];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {  // full rows m3 = lu - R + i, s3 = R - 1 - i + j
+        const float2 a = arow[(lu - R + i) * kGroup + lane];
+#pragma unroll
+        for (int j = 0; j < K; ++j) cmad(acc[j], gv[i * K + j], a, b[R - 1 - i + j]);
+    }
+#pragma unroll
+    for (int t = 1; t < K; ++t) {  // triangle
         const float2 a = arow[(k0 + H + t) * kGroup + lane];
 #pragma unroll
-        for (int j = t; j < K; ++j) cmad(acc[j], gt[strip_tri_a_off(K, t) + j - t], a, b[j - t]);
+        for (int j = t; j < K; ++j) cmad(acc[j], gv[R * K + strip_tri_a_off(K, t) + j - t], a, b[j - t]);
     }
 }
 
-// strip of kind B: triangle rows m3 = k0-H+1+t, t = 0..K-2, outputs j = 0..t,
-// partner s3 = N-1+j-t; then uniform rows m3 = k0+K-H .. N-1 (s3 = N-K-r+j)
+// Strip of kind B: triangle m3 = k0-H+1+t, t = 0..K-2, outputs j = 0..t
+// (s3 = N-1+j-t), then uniform rows m3 = k0+K-H+r (s3 = N-K-r+j).  The first
+// R = (N+H-K) mod U uniform rows join the triangle in a compile-time head.
 template <int N, int K, int U>
 __device__ __forceinline__ void strip_b(const float2 *arow, const float2 *brow, const float *g, int k0, int lane,
                                         float2 (&acc)[K])
 {
     constexpr int H = N / 2;
     constexpr int R = (N + H - K) % U;
-    float2 b[K - 1];
+    constexpr int TRI4 = strip_round4(strip_tri(K));
+    constexpr int HEADG = TRI4 + R * K;
+    float gv[HEADG];
 #pragma unroll
-    for (int i = 0; i < K - 1; ++i) b[i] = brow[(N - K + 1 + i) * kGroup + lane];
+    for (int q = 0; q < HEADG / 4; ++q) {
+        const float4 v = reinterpret_cast<const float4 *>(g)[q];
+        gv[4 * q] = v.x;
+        gv[4 * q + 1] = v.y;
+        gv[4 * q + 2] = v.z;
+        gv[4 * q + 3] = v.w;
+    }
+    constexpr int B0 = N - K - R + 1;  // lowest partner index of the head
+    float2 b[K + R - 1];
 #pragma unroll
-    for (int t = 0; t < K - 1; ++t) {
+    for (int i = 0; i < K + R - 1; ++i) b[i] = brow[(B0 + i) * kGroup + lane];
+#pragma unroll
+    for (int t = 0; t < K - 1; ++t) {  // triangle
         const float2 a = arow[(k0 - H + 1 + t) * kGroup + lane];
 #pragma unroll
-        for (int j = 0; j <= t; ++j) cmad(acc[j], g[strip_tri_b_off(t) + j], a, b[K - 2 + j - t]);
+        for (int j = 0; j <= t; ++j) cmad(acc[j], gv[strip_tri_b_off(t) + j], a, b[N - 1 + j - t - B0]);
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i) {  // first R uniform rows
+        const float2 a = arow[(k0 + K - H + i) * kGroup + lane];
+#pragma unroll
+        for (int j = 0; j < K; ++j) cmad(acc[j], gv[TRI4 + i * K + j], a, b[N - K - i + j - B0]);
     }
     const int lu = N + H - k0 - K;
-    uniform_run<K, U, R>(arow, brow, g + strip_round4(strip_tri(K)), k0 + K - H, N - K, lu, lane, acc);
+    uniform_run<K, U, 0>(arow, brow, g + HEADG, k0 + K - H + R, N - K - R, lu - R, lane, acc);
 }
 
-// GPC cell groups per CTA share each stage's weight tile (each group has its
-// own two rows); warp = (group g_local, strip w)
 template <int N, int K, int U, int NST, int GPC>
 struct StripCfg {
     static constexpr int W = N / K;
@@ -217,13 +254,41 @@ struct StripCfg {
     static constexpr size_t SMEM = (size_t)NST * STAGE + 2 * NST * sizeof(uint64_t) + 16;
 };
 
+// Tile coordinates of one pencil, advanced in the order of the weight table:
+// m1 = lo1 .. K1/2; m2 = lo2 .. hi2, except m2 = lo2 .. K2/2 when 2 m1 = K1.
+struct TileWalk {
+    int m1, m2, m2end, lo2, hi2, K1, K2;
+    __device__ void start(int lo1, int lo2_, int hi2_, int K1_, int K2_)
+    {
+        lo2 = lo2_;
+        hi2 = hi2_;
+        K1 = K1_;
+        K2 = K2_;
+        m1 = lo1;
+        m2 = lo2;
+        m2end = (2 * m1 < K1) ? hi2 : K2 / 2;
+    }
+    __device__ void next()
+    {
+        if (++m2 > m2end) {
+            ++m1;
+            m2 = lo2;
+            m2end = (2 * m1 < K1) ? hi2 : K2 / 2;
+        }
+    }
+};
+
+// Persistent kernel: CTAs take (pencil, group block) items from an atomic
+// counter, heaviest pencils first, so the tail of the launch holds only the
+// smallest items.  The stage ring runs across items: ring use u sits in
+// slot u % NST, phase u / NST.
 template <int N, int K, int U, int NST, int GPC>
 __global__ void __launch_bounds__(32 * (N / K) * GPC) conv_strip_kernel(const float *__restrict__ ghat,
                                                                         const int *__restrict__ tile0,
                                                                         const int *__restrict__ order, int nblocks,
                                                                         const float2 *__restrict__ F,
                                                                         float2 *__restrict__ Qh, float omega,
-                                                                        int *err)
+                                                                        int *err, int *counter)
 {
     using C = StripCfg<N, K, U, NST, GPC>;
     constexpr int H = N / 2;
@@ -231,22 +296,14 @@ __global__ void __launch_bounds__(32 * (N / K) * GPC) conv_strip_kernel(const fl
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + NST * C::STAGE);
     uint64_t *empty = full + NST;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + NST);
+    __shared__ int s_item;
 
     const int warp_id = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gl = warp_id / C::W, warp = warp_id % C::W;  // group within the CTA, strip
-    const int item = blockIdx.x;
-    const int pencil = order[item / nblocks];
-    const int gblk = item % nblocks;
-    const int grp = gblk * GPC + gl;
-    const int k1 = pencil / N, k2 = pencil % N;
-    const int K1 = k1 + H, K2 = k2 + H;
-    const int lo1 = max(0, K1 - N + 1), hi1 = min(N - 1, K1);
-    const int lo2 = max(0, K2 - N + 1), hi2 = min(N - 1, K2);
-    const int v2 = hi2 - lo2 + 1;
-    const int nfull = ((hi1 - lo1 + 1) / 2) * v2;
-    const int T = tile0[pencil + 1] - tile0[pencil];
-    const float2 *Fb0 = F + (size_t)gblk * GPC * C::M * kGroup;  // first group of this CTA
-    const float *Gp = ghat + (size_t)tile0[pencil] * C::TSV;
+    const int k0 = warp * K;
+    const bool kind_a = k0 < H;
+    const int seg = strip_seg_off(N, K, warp);
+    const int nitems = N * N * nblocks;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NST; ++s) {
@@ -259,89 +316,102 @@ __global__ void __launch_bounds__(32 * (N / K) * GPC) conv_strip_kernel(const fl
     }
     __syncthreads();
 
-    auto rows_of = [&](int t, int &m1, int &m2) {
-        if (t < nfull) {
-            m1 = lo1 + t / v2;
-            m2 = lo2 + t % v2;
-        } else {
-            m1 = K1 / 2;
-            m2 = lo2 + (t - nfull);
-        }
-    };
-    auto issue = [&](int t) {
-        const int s = t % NST;
-        int m1, m2;
-        rows_of(t, m1, m2);
-        unsigned char *st = smem + s * C::STAGE;
-        mbar_arrive_expect_tx(&full[s], 2 * GPC * C::ROWB + C::GB);
-#pragma unroll
-        for (int q = 0; q < GPC; ++q) {
-            const float2 *Fq = Fb0 + (size_t)q * C::M * kGroup;
-            bulk_copy(st + q * C::ROWB, Fq + (size_t)(m1 * N + m2) * N * kGroup, C::ROWB, &full[s]);
-            bulk_copy(st + (GPC + q) * C::ROWB, Fq + (size_t)((K1 - m1) * N + (K2 - m2)) * N * kGroup, C::ROWB,
-                      &full[s]);
-        }
-        bulk_copy(st + 2 * GPC * C::ROWB, Gp + (size_t)t * C::TSV, C::GB, &full[s]);
-    };
-
-    int issued = 0;
-    if (threadIdx.x == 0)
-        for (; issued < NST && issued < T; ++issued) issue(issued);
-
-    const int k0 = warp * K;
-    const bool kind_a = k0 < H;
-    const int seg = strip_seg_off(N, K, warp);
-    float2 acc[K], hi[K], lo[K];
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-        acc[j] = make_float2(0.f, 0.f);
-        hi[j] = make_float2(0.f, 0.f);
-        lo[j] = make_float2(0.f, 0.f);
-    }
-    int cur_m1 = lo1;
+    uint32_t tt = 0;  // ring uses consumed by this CTA before the current item
+    uint32_t issued = 0;
     bool ok = true;
-    int t = 0;
-    for (; t < T; ++t) {
-        const int s = t % NST;
-        const uint32_t par = (uint32_t)(t / NST) & 1u;
-        if (!wait_phase(&full[s], par, abort_flag, err, kWaitNs)) {
+    for (;;) {
+        // thread 0 decides for the whole CTA, so every thread leaves the loop together
+        if (threadIdx.x == 0) s_item = *abort_flag ? nitems : atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= nitems) break;
+        const int pencil = order[item / nblocks];
+        const int gblk = item % nblocks;
+        const int grp = gblk * GPC + gl;
+        const int k1 = pencil / N, k2 = pencil % N;
+        const int K1 = k1 + H, K2 = k2 + H;
+        const int lo1 = max(0, K1 - N + 1);
+        const int lo2 = max(0, K2 - N + 1), hi2 = min(N - 1, K2);
+        const int T = tile0[pencil + 1] - tile0[pencil];
+        const float2 *Fb0 = F + (size_t)gblk * GPC * C::M * kGroup;
+        const float *Gp = ghat + (size_t)tile0[pencil] * C::TSV;
+
+        TileWalk pw;  // producer's walk (thread 0), NST tiles ahead of the consumers
+        int pt = 0;
+        auto issue_next = [&]() -> bool {
+            const uint32_t u = tt + pt;
+            const int s = u % NST;
+            if (u >= NST && !wait_phase(&empty[s], ((u / NST) + 1) & 1u, abort_flag, err, kWaitNs)) return false;
+            unsigned char *st = smem + s * C::STAGE;
+            mbar_arrive_expect_tx(&full[s], 2 * GPC * C::ROWB + C::GB);
+#pragma unroll
+            for (int q = 0; q < GPC; ++q) {
+                const float2 *Fq = Fb0 + (size_t)q * C::M * kGroup;
+                bulk_copy(st + q * C::ROWB, Fq + (size_t)(pw.m1 * N + pw.m2) * N * kGroup, C::ROWB, &full[s]);
+                bulk_copy(st + (GPC + q) * C::ROWB, Fq + (size_t)((K1 - pw.m1) * N + (K2 - pw.m2)) * N * kGroup,
+                          C::ROWB, &full[s]);
+            }
+            bulk_copy(st + 2 * GPC * C::ROWB, Gp + (size_t)pt * C::TSV, C::GB, &full[s]);
+            ++pt;
+            ++issued;
+            pw.next();
+            return true;
+        };
+        if (threadIdx.x == 0) {
+            pw.start(lo1, lo2, hi2, K1, K2);
+            while (pt < NST && pt < T)
+                if (!issue_next()) {
+                    ok = false;
+                    break;
+                }
+        }
+
+        float2 acc[K], hi[K], lo[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            acc[j] = make_float2(0.f, 0.f);
+            hi[j] = make_float2(0.f, 0.f);
+            lo[j] = make_float2(0.f, 0.f);
+        }
+        TileWalk cw;
+        cw.start(lo1, lo2, hi2, K1, K2);
+        int cur_m1 = lo1;
+        for (int t = 0; t < T && ok; ++t) {
+            const uint32_t u = tt + t;
+            const int s = u % NST;
+            if (!wait_phase(&full[s], (u / NST) & 1u, abort_flag, err, kWaitNs)) {
+                ok = false;
+                break;
+            }
+            if (cw.m1 != cur_m1) {  // new m1 slab: fold the finished one
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    two_sum(hi[j].x, lo[j].x, acc[j].x);
+                    two_sum(hi[j].y, lo[j].y, acc[j].y);
+                    acc[j] = make_float2(0.f, 0.f);
+                }
+                cur_m1 = cw.m1;
+            }
+            const unsigned char *st = smem + s * C::STAGE;
+            const float2 *arow = reinterpret_cast<const float2 *>(st + gl * C::ROWB);
+            const float2 *brow = reinterpret_cast<const float2 *>(st + (GPC + gl) * C::ROWB);
+            const float *gt = reinterpret_cast<const float *>(st + 2 * GPC * C::ROWB) + seg;
+            if (kind_a)
+                strip_a<N, K, U>(arow, brow, gt, k0, lane, acc);
+            else
+                strip_b<N, K, U>(arow, brow, gt, k0, lane, acc);
+            cw.next();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+            if (threadIdx.x == 0 && pt < T)
+                if (!issue_next()) ok = false;
+            __syncwarp();
+        }
+        if (__syncthreads_or(!ok || *abort_flag)) {  // CTA-uniform
             ok = false;
             break;
         }
-        int m1, m2;
-        rows_of(t, m1, m2);
-        if (m1 != cur_m1) {  // new slab: fold the finished one
-#pragma unroll
-            for (int j = 0; j < K; ++j) {
-                two_sum(hi[j].x, lo[j].x, acc[j].x);
-                two_sum(hi[j].y, lo[j].y, acc[j].y);
-                acc[j] = make_float2(0.f, 0.f);
-            }
-            cur_m1 = m1;
-        }
-        const unsigned char *st = smem + s * C::STAGE;
-        const float2 *arow = reinterpret_cast<const float2 *>(st + gl * C::ROWB);
-        const float2 *brow = reinterpret_cast<const float2 *>(st + (GPC + gl) * C::ROWB);
-        const float *gt = reinterpret_cast<const float *>(st + 2 * GPC * C::ROWB) + seg;
-        if (kind_a)
-            strip_a<N, K, U>(arow, brow, gt, k0, lane, acc);
-        else
-            strip_b<N, K, U>(arow, brow, gt, k0, lane, acc);
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);
-        if (threadIdx.x == 0 && issued < T) {
-            // stage s is refilled with tile t + NST once every warp released tile t
-            if (!wait_phase(&empty[s], par, abort_flag, err, kWaitNs)) {
-                ok = false;
-            } else {
-                issue(issued);
-                ++issued;
-            }
-        }
-        __syncwarp();
-        if (!ok) break;
-    }
-    if (ok && !*abort_flag) {
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             two_sum(hi[j].x, lo[j].x, acc[j].x);
@@ -349,12 +419,13 @@ __global__ void __launch_bounds__(32 * (N / K) * GPC) conv_strip_kernel(const fl
             Qh[((size_t)grp * C::M + (size_t)pencil * N + k0 + j) * kGroup + lane] =
                 make_float2(omega * (hi[j].x + lo[j].x), omega * (hi[j].y + lo[j].y));
         }
+        tt += T;
     }
-    if (threadIdx.x == 0 && !ok) {
+    if (threadIdx.x == 0 && (!ok || *abort_flag)) {
         // give the copies this thread issued a bounded time to land before the CTA exits
-        for (int u = t; u < issued; ++u) {
+        for (uint32_t u = tt; u < issued; ++u) {
             volatile int dummy = 0;
-            wait_phase(&full[u % NST], (uint32_t)(u / NST) & 1u, &dummy, err, kWaitNs / 20);
+            wait_phase(&full[u % NST], (u / NST) & 1u, &dummy, err, kWaitNs / 20);
         }
     }
 }
@@ -372,10 +443,29 @@ int launch_cfg(const Handle &hd, int ncells, cudaStream_t s)
     }
     const int ng = ngroups_of(ncells);
     const int nblocks = ng / GPC;  // callers pick GPC dividing ng
-    const unsigned blocks = (unsigned)(N * N * nblocks);
+    const int nitems = N * N * nblocks;
+    static int per_sm[2] = {0, 0};  // resident CTAs per SM, per GPC variant
+    int &occ = per_sm[GPC - 1];
+    if (occ == 0) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, 32 * C::WARPS, C::SMEM) != cudaSuccess || v < 1) {
+            cudaGetLastError();
+            v = 1;
+        }
+        occ = v;
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, hd.device);
+    // automatic: about two items per resident CTA, so the queue can balance
+    // pencils of unequal size (measured best at N = 16, 128 cells)
+    const int autoper = std::max(1, std::min(occ, (int)((nitems + 2 * sms - 1) / (2 * std::max(1, sms)))));
+    const int per = hd.tune_ctas > 0 ? std::min(hd.tune_ctas, occ) : autoper;
+    const int grid = std::min(nitems, std::max(1, sms) * per);
     const float omega = (float)(hd.g.dz * hd.g.dz * hd.g.dz);
-    kern<<<blocks, 32 * C::WARPS, C::SMEM, s>>>((const float *)hd.ghat, hd.pencil_tile0, hd.pencil_order, nblocks,
-                                                (const float2 *)hd.F, (float2 *)hd.Qh, omega, hd.err);
+    cudaError_t e = cudaMemsetAsync(hd.counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return cuda_error(e, "strip kernel work counter");
+    kern<<<grid, 32 * C::WARPS, C::SMEM, s>>>((const float *)hd.ghat, hd.pencil_tile0, hd.pencil_order, nblocks,
+                                              (const float2 *)hd.F, (float2 *)hd.Qh, omega, hd.err, hd.counter);
     CS_CHECK_LAUNCH("convolution (strip kernel)");
     return CS_OK;
 }
@@ -383,7 +473,9 @@ int launch_cfg(const Handle &hd, int ncells, cudaStream_t s)
 template <int N, int K, int U, int NST1, int NST2>
 int launch_n(const Handle &hd, int ncells, cudaStream_t s)
 {
-    if (ngroups_of(ncells) % 2 == 0) return launch_cfg<N, K, U, NST2, 2>(hd, ncells, s);
+    const bool even = ngroups_of(ncells) % 2 == 0;
+    const bool two = hd.tune_gpc == 2 || (hd.tune_gpc == 0 && N <= 16);  // measured: 1 group per CTA wins at N = 32
+    if (even && two) return launch_cfg<N, K, U, NST2, 2>(hd, ncells, s);
     return launch_cfg<N, K, U, NST1, 1>(hd, ncells, s);
 }
 

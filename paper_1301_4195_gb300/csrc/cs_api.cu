@@ -243,25 +243,35 @@ int timed_transport(Handle &hd, const double *fin, int ncells, const cs_domain &
     return launch_transport_stage(hd, fin, ncells, dom, a, x, b, y, c, out, s);
 }
 
-int collide_into(Handle &hd, const double *f, int ncells, double eps, double *Qt, cudaStream_t s)
+// One collision evaluation written as out = a x + b y + c P(Qt(f)/eps)
+// (P = projection if project): forward transform, convolution, inverse
+// transform, projection and combination.  With whole-cell kernels (float,
+// N <= 16) the last three steps are one launch, timed as the inverse stage.
+int collide_combine(Handle &hd, const double *f, int ncells, double eps, int project, double a, const double *x,
+                    double b, const double *y, double c, double *out, cudaStream_t s)
 {
     int rc = timed_forward(hd, f, ncells, s);
     if (rc) return rc;
     rc = timed_convolve(hd, ncells, s);
     if (rc) return rc;
-    return timed_inverse(hd, ncells, eps, Qt, s);
+    if (fused_available(hd)) {
+        StageTimer t(hd, CS_K_INVERSE, s);
+        return launch_inverse_project(hd, ncells, eps, project, a, x, b, y, c, out, nullptr, s);
+    }
+    const bool direct = (x == nullptr && y == nullptr && c == 1.0);
+    double *qt = direct ? out : hd.Qt;
+    rc = timed_inverse(hd, ncells, eps, qt, s);
+    if (rc) return rc;
+    if (!project && direct) return CS_OK;
+    return timed_conserve(hd, qt, ncells, project, a, x, b, y, c, out, nullptr, s);
 }
 
 // one Heun step of df/dt = P Qt(f) / eps, in place
 int heun_collision(Handle &hd, double *f, int ncells, double dt, double eps, cudaStream_t s)
 {
-    int rc = collide_into(hd, f, ncells, eps, hd.Qt, s);
+    int rc = collide_combine(hd, f, ncells, eps, 1, 1.0, f, 0.0, nullptr, dt, hd.f1, s);
     if (rc) return rc;
-    rc = timed_conserve(hd, hd.Qt, ncells, 1, 1.0, f, 0.0, nullptr, dt, hd.f1, nullptr, s);
-    if (rc) return rc;
-    rc = collide_into(hd, hd.f1, ncells, eps, hd.Qt, s);
-    if (rc) return rc;
-    return timed_conserve(hd, hd.Qt, ncells, 1, 0.5, f, 0.5, hd.f1, 0.5 * dt, f, nullptr, s);
+    return collide_combine(hd, hd.f1, ncells, eps, 1, 0.5, f, 0.5, hd.f1, 0.5 * dt, f, s);
 }
 
 int heun_transport(Handle &hd, double *f, int ncells, const cs_domain &dom, double dt, cudaStream_t s)
@@ -461,6 +471,7 @@ int cs_weights_build(int N, double L, double lambda, int precision, cudaStream_t
     if (e == cudaSuccess) e = cudaMalloc(&hd.tw32, sizeof(float2) * N * N);
     if (e == cudaSuccess) e = cudaMalloc(&hd.err, 256);
     if (e == cudaSuccess) e = cudaMemsetAsync(hd.err, 0, 256, stream);
+    hd.counter = hd.err ? hd.err + 32 : nullptr;
     if (e != cudaSuccess) {
         cudaGetLastError();
         cs_handle_destroy(hs);
@@ -486,6 +497,80 @@ int cs_weights_build(int N, double L, double lambda, int precision, cudaStream_t
         return set_error(rc, msg);
     }
     *out = hs;
+    return CS_OK;
+}
+
+int cs_tune(cs_handle_t h, int param, int value)
+{
+    if (int rc = check_handle(h)) return rc;
+    Handle &hd = h->h;
+    switch (param) {
+    case CS_TUNE_GROUPS_PER_CTA:
+        if (value < 0 || value > 2) return set_error(CS_EINVAL, "groups per CTA must be 0, 1 or 2");
+        hd.tune_gpc = value;
+        break;
+    case CS_TUNE_CTAS_PER_SM:
+        if (value < 0 || value > 64) return set_error(CS_EINVAL, "CTAs per SM must be in 0..64");
+        hd.tune_ctas = value;
+        break;
+    default: return set_error(CS_EINVAL, "unknown tuning parameter");
+    }
+    drop_graphs(hd);  // captured steps hold the old launch configuration
+    return CS_OK;
+}
+
+int cs_autotune(cs_handle_t h, int ncells, cudaStream_t s, double *ms)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (ncells < 1) return set_error(CS_EINVAL, "ncells must be >= 1");
+    Handle &hd = h->h;
+    if (int rc = ensure_workspace(hd, ncells)) return rc;
+    // spectral input: any finite values exercise the same work
+    cudaError_t e = cudaMemsetAsync(hd.F, 0, (size_t)ngroups_of(ncells) * hd.g.M * kGroup * 2 * elem_bytes(hd.precision), s);
+    if (e != cudaSuccess) return cuda_error(e, "cs_autotune: input");
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+        return set_error(CS_ECUDA, "cs_autotune: events");
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, hd.device);
+    const int cand[][2] = {{0, 0}, {1, 0}, {2, 1}, {2, 2}, {2, 3}, {1, 2}, {1, 3}, {1, 4}, {1, 6}};
+    double best = 1e300;
+    int bg = 0, bc = 0;
+    const int keep_g = hd.tune_gpc, keep_c = hd.tune_ctas;
+    int rc = CS_OK;
+    for (const auto &c : cand) {
+        hd.tune_gpc = c[0];
+        hd.tune_ctas = c[1];
+        if ((rc = launch_convolve(hd, ncells, s)) != CS_OK) break;  // warm-up
+        cudaEventRecord(a, s);
+        for (int r = 0; r < 3 && rc == CS_OK; ++r) rc = launch_convolve(hd, ncells, s);
+        cudaEventRecord(b, s);
+        if (rc != CS_OK) break;
+        e = cudaEventSynchronize(b);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+        if (e != cudaSuccess) {
+            rc = cuda_error(e, "cs_autotune: timing");
+            break;
+        }
+        if (t / 3.0 < best) {
+            best = t / 3.0;
+            bg = c[0];
+            bc = c[1];
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc != CS_OK) {
+        hd.tune_gpc = keep_g;
+        hd.tune_ctas = keep_c;
+        return rc;
+    }
+    hd.tune_gpc = bg;
+    hd.tune_ctas = bc;
+    drop_graphs(hd);
+    if (ms) *ms = best;
+    (void)sms;
     return CS_OK;
 }
 
@@ -644,9 +729,7 @@ int cs_collide(cs_handle_t h, const double *f, int ncells, double eps, double *Q
     if ((const char *)f < (const char *)Q + bytes && (const char *)Q < (const char *)f + bytes)
         return set_error(CS_EINVAL, "f and Q overlap");
     if (int rc = ensure_workspace(hd, ncells)) return rc;
-    if (int rc = collide_into(hd, f, ncells, eps, Q, s)) return rc;
-    if (conserve) return timed_conserve(hd, Q, ncells, 1, 0.0, nullptr, 0.0, nullptr, 1.0, Q, nullptr, s);
-    return CS_OK;
+    return collide_combine(hd, f, ncells, eps, conserve ? 1 : 0, 0.0, nullptr, 0.0, nullptr, 1.0, Q, s);
 }
 
 int cs_conserve(cs_handle_t h, double *Q, int ncells, double *moments, cudaStream_t s)

@@ -99,6 +99,7 @@ struct Handle {
     int *pencil_order = nullptr;  // device int[N*N]: pencils by decreasing tile count
     std::vector<int> order_host;
     int *err = nullptr;           // device word: bit 0 set when a bounded device wait expired
+    int *counter = nullptr;       // device word: work counter of the persistent convolution (err + 32)
     // transforms: twiddles exp(-i 2 pi ((k-h)(j-h) mod N) / N), [k][j]
     double2 *tw64 = nullptr;
     float2 *tw32 = nullptr;
@@ -123,6 +124,9 @@ struct Handle {
     std::vector<GraphEntry> graphs;
     cudaStream_t cap_stream = nullptr;
     bool use_graphs = true;
+    // convolution launch choices (0 = automatic), set by cs_tune / cs_autotune
+    int tune_gpc = 0;     // cell groups per CTA of the strip kernel (1 or 2)
+    int tune_ctas = 0;    // resident CTAs per SM of the persistent strip kernel
     // stage timing (cs_profile)
     bool prof = false;
     struct Rec {
@@ -173,6 +177,13 @@ int launch_forward(const Handle &hd, const double *f, int ncells, cudaStream_t s
 int launch_inverse(const Handle &hd, int ncells, double scale_eps, double *Qt, cudaStream_t s);  // hd.Qh -> Qt
 int launch_spectral_to_natural(const Handle &hd, const void *src, int ncells, double *dst, cudaStream_t s);
 int launch_natural_to_spectral(const Handle &hd, const double *src, int ncells, void *dst, cudaStream_t s);
+
+// ---- fused.cu (float, N <= 16: whole-cell transforms in shared memory)
+bool fused_available(const Handle &hd);
+int launch_forward_fused(const Handle &hd, const double *f, int ncells, cudaStream_t s);
+// out = a x + b y + c P(Qt), Qt the inverse transform of hd.Qh (P = projection if project)
+int launch_inverse_project(const Handle &hd, int ncells, double eps, int project, double a, const double *x,
+                           double b, const double *y, double c, double *out, double *moments, cudaStream_t s);
 
 // ---- convolve.cu, conv_strip.cu
 int launch_convolve(const Handle &hd, int ncells, cudaStream_t s);  // hd.F -> hd.Qh

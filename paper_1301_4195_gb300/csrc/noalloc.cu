@@ -70,6 +70,7 @@ Handle view_of(const Handle &hd)
     v.pencil_tile0 = hd.pencil_tile0;
     v.pencil_order = hd.pencil_order;
     v.err = hd.err;
+    v.counter = hd.counter;
     v.tw64 = hd.tw64;
     v.tw32 = hd.tw32;
     for (int i = 0; i < 25; ++i) v.cct_inv[i] = hd.cct_inv[i];

@@ -196,11 +196,14 @@ int inverse_impl(const Handle &hd, int ncells, double eps, double *Qt, cudaStrea
 
 int launch_forward(const Handle &hd, const double *f, int ncells, cudaStream_t s)
 {
+    if (fused_available(hd)) return launch_forward_fused(hd, f, ncells, s);
     return hd.precision == CS_FP32 ? forward_impl<float>(hd, f, ncells, s) : forward_impl<double>(hd, f, ncells, s);
 }
 
 int launch_inverse(const Handle &hd, int ncells, double eps, double *Qt, cudaStream_t s)
 {
+    if (fused_available(hd))
+        return launch_inverse_project(hd, ncells, eps, 0, 0.0, nullptr, 0.0, nullptr, 1.0, Qt, nullptr, s);
     return hd.precision == CS_FP32 ? inverse_impl<float>(hd, ncells, eps, Qt, s)
                                    : inverse_impl<double>(hd, ncells, eps, Qt, s);
 }
