@@ -47,7 +47,7 @@ WORKLOADS = {
 MAX_SM_MHZ = 2070.0
 # DRAM bytes (read + write) per convolution launch from ncu captures of the
 # current kernel (profiles/), keyed by (N, cells); None where not captured
-TRAFFIC = {}
+TRAFFIC = {(16, 128): 18414592, (32, 256): 3027302912 + 64243712}
 SMS = 152
 FP32_LANES = 128
 
@@ -317,6 +317,13 @@ def run_ours(args):
     }
     if n32:
         out["n32"] = n32
+    if not args.skip_serve and world == 1:
+        from paper_1301_4195_gb300 import serve
+        torch.cuda.synchronize()
+        out["serve"] = serve.serve_bench(48, args.serve_rate, horizon=(0.1, 0.5))
+        out["serve"]["load"] = (f"48 Poisson requests at {args.serve_rate}/s, N in {{12,16,24,32}}, "
+                                f"lambda in {{0,1}}, 2-4 Maxwellian mixtures, horizon U[0.1,0.5] at dt=0.01, "
+                                f"weight tables resident")
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"], out["error_vs_oracle"] = cpu_baseline(args, api, inputs, torch, device, h32, h64)
     h32.close()
@@ -406,6 +413,8 @@ def main():
     ap.add_argument("--skip-n32", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true", help="omit the double-precision comparison")
+    ap.add_argument("--skip-serve", action="store_true", help="omit the serving run")
+    ap.add_argument("--serve-rate", type=float, default=100.0, help="Poisson arrival rate of the serving run (1/s)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
