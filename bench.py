@@ -317,6 +317,8 @@ def run_ours(args):
     }
     if n32:
         out["n32"] = n32
+    if not args.skip_batched and world == 1:
+        out["batched"] = batched_run(api, inputs, torch, device, args)
     if not args.skip_serve and world == 1:
         from paper_1301_4195_gb300 import serve
         torch.cuda.synchronize()
@@ -333,6 +335,42 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def batched_run(api, inputs, torch, device, args):
+    """Uneven cells in one replayed graph: 4096 cells at N = 16 and 1024 at
+    N = 24, half lambda = 0 and half lambda = 1, random 2-3 Maxwellian
+    mixtures; one cs_collide_batched call = one collision evaluation of all."""
+    specs = [(16, 0.0, 2048), (16, 1.0, 2048), (24, 0.0, 512), (24, 1.0, 512)]
+    hs, fs, qs, first = [], [], [], 20000
+    for N, lam, n in specs:
+        h = api.Handle(N, L_BOX, lam, "fp32")
+        h.reserve(n)
+        api.cs_autotune(h.ptr, n)
+        hs.append(h)
+        fs.append(torch.from_numpy(inputs.random_mixture_cells(N, L_BOX, n, first_id=first)).to(device))
+        qs.append(torch.empty_like(fs[-1]))
+        first += n
+    entries = [(h.ptr, f, q, n) for h, f, q, (_, _, n) in zip(hs, fs, qs, specs)]
+    for _ in range(2):
+        api.cs_collide_batched(entries)
+    torch.cuda.synchronize()
+    reps, total = 3, 0.0
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        api.cs_collide_batched(entries)
+        b.record()
+        b.synchronize()
+        total += a.elapsed_time(b)
+    ms = total / reps
+    pairs = sum(n * N ** 6 for N, _, n in specs)
+    for h in hs:
+        h.close()
+    return {"workload": "4096 cells N=16 + 1024 cells N=24, lambda 0/1 half each, random mixtures, "
+                        "one graph replay per collision evaluation (cs_collide_batched), autotuned",
+            "ms_per_call": ms, "value": pairs / (ms * 1e-3), "unit": UNIT}
 
 
 def cpu_baseline(args, api, inputs, torch, device, h32, h64):
@@ -414,6 +452,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true", help="omit the double-precision comparison")
     ap.add_argument("--skip-serve", action="store_true", help="omit the serving run")
+    ap.add_argument("--skip-batched", action="store_true", help="omit the uneven-N batched run")
     ap.add_argument("--serve-rate", type=float, default=100.0, help="Poisson arrival rate of the serving run (1/s)")
     args = ap.parse_args()
     if args.warmup < 3:

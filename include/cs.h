@@ -147,6 +147,26 @@ int cs_inverse(cs_handle_t h, const double *qhat, int ncells, double eps, double
 int cs_collide(cs_handle_t h, const double *f, int ncells, double eps, double *Q, int conserve,
                cudaStream_t stream);
 
+/* One entry of a batched collision evaluation. */
+typedef struct {
+    cs_handle_t handle; /* weights and workspace of this entry (N, L, lambda, precision) */
+    const double *f;    /* device, [ncells][N^3] */
+    double *Q;          /* device, [ncells][N^3], must not overlap f */
+    int ncells;
+} cs_batch_entry;
+
+/* The collision operator for n entries of possibly different N and lambda,
+ * as one replayable unit: the first call with a given list of entries
+ * captures every entry's kernels into one CUDA graph with one parallel
+ * branch per entry (so entries overlap on the device), later calls with the
+ * same entries, eps and conserve replay it with a single graph launch on
+ * `stream`.  Each entry's result equals cs_collide on that entry.  Every
+ * entry needs its own handle; handles must not be used elsewhere while the
+ * call runs.  Cached graphs are dropped when one of their handles is
+ * destroyed or its workspace grows.
+ * Errors: CS_EINVAL (NULL, duplicate handle, bad sizes), CS_ENOMEM, CS_ECUDA. */
+int cs_collide_batched(const cs_batch_entry *entries, int n, double eps, int conserve, cudaStream_t stream);
+
 /* Step a4, the conservation projection of Sec. 3.3, in place, in double:
  *   Q <- Q - C^T (C C^T)^{-1} C Q,  C = dv^3 (1, v1, v2, v3, |v|^2) (5 x N^3).
  *   Q        (device, in/out) [ncells][N^3]

@@ -44,6 +44,11 @@ class Domain(ctypes.Structure):
     _fields_ = [("dx", _vp), ("f_far", _vp), ("wall_T", _d), ("wall_V", _d * 3)]
 
 
+class BatchEntry(ctypes.Structure):
+    """cs_batch_entry: handle, f (device), Q (device), ncells."""
+    _fields_ = [("handle", _vp), ("f", _vp), ("Q", _vp), ("ncells", _i)]
+
+
 _SIGS = {
     "cs_version": (_i, []),
     "cs_last_error": (ctypes.c_char_p, []),
@@ -65,6 +70,7 @@ _SIGS = {
     "cs_step": (_i, [_vp, _vp, _i, ctypes.POINTER(Domain), _d, _d, _i, _vp]),
     "cs_tile_layout": (_i, [_i, _i, ctypes.POINTER(_i), _i, ctypes.POINTER(_i)]),
     "cs_status": (_i, [_vp]),
+    "cs_collide_batched": (_i, [ctypes.POINTER(BatchEntry), _i, _d, _i, _vp]),
     "cs_tune": (_i, [_vp, _i, _i]),
     "cs_autotune": (_i, [_vp, _i, _vp, ctypes.POINTER(_d)]),
     "cs_profile": (_i, [_vp, _i]),
@@ -190,6 +196,14 @@ def cs_inverse(h, qhat, ncells, eps, Q, stream=None):
 
 def cs_collide(h, f, ncells, eps, Q, conserve=1, stream=None):
     _check(lib().cs_collide(h, _dptr(f, "f"), ncells, eps, _dptr(Q, "Q"), int(conserve), _stream(stream)))
+
+
+def cs_collide_batched(entries, eps=1.0, conserve=1, stream=None):
+    """entries: list of (handle_ptr, f, Q, ncells) with device tensors f, Q."""
+    arr = (BatchEntry * max(1, len(entries)))()
+    for i, (h, f, Q, n) in enumerate(entries):
+        arr[i] = BatchEntry(h, _dptr(f, "f"), _dptr(Q, "Q"), int(n))
+    _check(lib().cs_collide_batched(arr, len(entries), eps, int(conserve), _stream(stream)))
 
 
 def cs_conserve(h, Q, ncells, moments=None, stream=None):

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -200,6 +201,7 @@ int ensure_workspace(Handle &hd, int ncells)
     hd.ws = p;
     hd.ws_bytes = bytes;
     hd.ws_cells = ncells;
+    ++hd.ws_generation;
     hd.F = b + offs[0];
     hd.Qh = b + offs[1];
     hd.X = b + offs[2];
@@ -388,11 +390,135 @@ int cuda_error(cudaError_t e, const char *what)
     return set_error(CS_ECUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
 }
 
+// ---- batched collision graphs (library-wide cache)
+namespace {
+
+struct BatchGraph {
+    std::vector<cs_handle_t> handles;
+    std::vector<unsigned> generations;
+    std::vector<const void *> f, q;
+    std::vector<int> ncells;
+    double eps;
+    int conserve;
+    cudaGraphExec_t exec;
+};
+
+std::mutex g_batch_mutex;
+std::vector<BatchGraph> g_batch_graphs;
+cudaStream_t g_batch_streams[17] = {};  // [0] capture root, [1..] branches
+
+void drop_batch_graphs_of(cs_handle_t h)
+{
+    std::lock_guard<std::mutex> lock(g_batch_mutex);
+    for (size_t i = 0; i < g_batch_graphs.size();) {
+        bool uses = false;
+        for (auto x : g_batch_graphs[i].handles) uses |= (x == h);
+        if (uses) {
+            cudaGraphExecDestroy(g_batch_graphs[i].exec);
+            g_batch_graphs.erase(g_batch_graphs.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+}
+
+}  // namespace
+
 }  // namespace cs
 
 using namespace cs;
 
 extern "C" {
+
+int cs_collide_batched(const cs_batch_entry *entries, int n, double eps, int conserve, cudaStream_t stream)
+{
+    if (n < 0 || (n > 0 && !entries)) return set_error(CS_EINVAL, "bad entry list");
+    if (n > 16) return set_error(CS_EINVAL, "at most 16 entries per batched call");
+    if (!(eps > 0) || !is_finite(eps)) return set_error(CS_EINVAL, "eps must be finite and > 0");
+    for (int i = 0; i < n; ++i) {
+        const cs_batch_entry &e = entries[i];
+        if (int rc = check_handle(e.handle)) return rc;
+        if (int rc = check_cells(e.ncells)) return rc;
+        for (int j = 0; j < i; ++j)
+            if (entries[j].handle == e.handle) return set_error(CS_EINVAL, "each batch entry needs its own handle");
+        if (e.ncells == 0) continue;
+        if (int rc = check_device_ptr(e.f, "entry f")) return rc;
+        if (int rc = check_device_ptr(e.Q, "entry Q")) return rc;
+        const size_t bytes = (size_t)e.ncells * e.handle->h.g.M * sizeof(double);
+        if ((const char *)e.f < (const char *)e.Q + bytes && (const char *)e.Q < (const char *)e.f + bytes)
+            return set_error(CS_EINVAL, "entry f and Q overlap");
+        if (e.handle->h.prof) return set_error(CS_EINVAL, "stage timing must be off for batched calls");
+        if (int rc = ensure_workspace(e.handle->h, e.ncells)) return rc;
+    }
+    std::lock_guard<std::mutex> lock(g_batch_mutex);
+    cudaGraphExec_t exec = nullptr;
+    for (auto &g : g_batch_graphs) {
+        if ((int)g.handles.size() != n || g.eps != eps || g.conserve != conserve) continue;
+        bool same = true;
+        for (int i = 0; i < n && same; ++i)
+            same = g.handles[i] == entries[i].handle && g.generations[i] == entries[i].handle->h.ws_generation &&
+                   g.f[i] == entries[i].f && g.q[i] == entries[i].Q && g.ncells[i] == entries[i].ncells;
+        if (same) exec = g.exec;
+    }
+    if (!exec) {
+        for (int i = 0; i <= n; ++i)
+            if (!g_batch_streams[i] &&
+                cudaStreamCreateWithFlags(&g_batch_streams[i], cudaStreamNonBlocking) != cudaSuccess) {
+                cudaGetLastError();
+                return set_error(CS_ECUDA, "cs_collide_batched: stream creation failed");
+            }
+        cudaStream_t root = g_batch_streams[0];
+        std::vector<cudaEvent_t> ev(n + 1, nullptr);
+        for (auto &e : ev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                for (auto x : ev)
+                    if (x) cudaEventDestroy(x);
+                return set_error(CS_ECUDA, "cs_collide_batched: event creation failed");
+            }
+        cudaGraph_t graph = nullptr;
+        int rc = CS_OK;
+        cudaError_t e = cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaEventRecord(ev[0], root);
+            for (int i = 0; i < n && rc == CS_OK; ++i) {
+                cudaStream_t br = g_batch_streams[i + 1];
+                cudaStreamWaitEvent(br, ev[0], 0);
+                if (entries[i].ncells > 0)
+                    rc = collide_combine(entries[i].handle->h, entries[i].f, entries[i].ncells, eps, conserve ? 1 : 0,
+                                         0.0, nullptr, 0.0, nullptr, 1.0, entries[i].Q, br);
+                cudaEventRecord(ev[i + 1], br);
+                cudaStreamWaitEvent(root, ev[i + 1], 0);
+            }
+            e = cudaStreamEndCapture(root, &graph);
+        }
+        if (e == cudaSuccess && rc == CS_OK) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        for (auto x : ev) cudaEventDestroy(x);
+        if (rc != CS_OK) return rc;
+        if (e != cudaSuccess) return cuda_error(e, "cs_collide_batched: graph capture");
+        if (g_batch_graphs.size() >= 16) {
+            cudaGraphExecDestroy(g_batch_graphs.front().exec);
+            g_batch_graphs.erase(g_batch_graphs.begin());
+        }
+        BatchGraph bg;
+        for (int i = 0; i < n; ++i) {
+            bg.handles.push_back(entries[i].handle);
+            bg.generations.push_back(entries[i].handle->h.ws_generation);
+            bg.f.push_back(entries[i].f);
+            bg.q.push_back(entries[i].Q);
+            bg.ncells.push_back(entries[i].ncells);
+        }
+        bg.eps = eps;
+        bg.conserve = conserve;
+        bg.exec = exec;
+        g_batch_graphs.push_back(bg);
+    }
+    cudaError_t e = cudaGraphLaunch(exec, stream);
+    if (e != cudaSuccess) return cuda_error(e, "cs_collide_batched: replay");
+    return CS_OK;
+}
+
 
 int cs_version(void) { return 100; }
 
@@ -626,6 +752,7 @@ int cs_profile_read(cs_handle_t h, double *total_ms, long long *launches, int re
 int cs_handle_destroy(cs_handle_t h)
 {
     if (!h) return CS_OK;
+    drop_batch_graphs_of(h);
     Handle &hd = h->h;
     for (const auto &r : hd.recs) {
         cudaEventDestroy(r.a);

@@ -109,6 +109,7 @@ struct Handle {
     int ws_cells = 0;
     void *ws = nullptr;
     size_t ws_bytes = 0;
+    unsigned ws_generation = 0;  // bumped whenever the workspace moves
     // pieces of the workspace (set by layout_workspace)
     void *F = nullptr, *Qh = nullptr, *X = nullptr, *Y = nullptr;
     double *Qt = nullptr, *f1 = nullptr, *r1 = nullptr, *scal = nullptr;

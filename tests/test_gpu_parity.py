@@ -284,3 +284,27 @@ def test_graph_replay_matches_direct_launches(cs, prec):
     cs.cs_profile_read(h.ptr, reset=True)
     assert np.array_equal(host(ga), host(gb))
     cs.cs_status(h.ptr)  # no bounded device wait expired
+
+
+def test_collide_batched_matches_individual_calls(cs):
+    """Uneven N and lambda in one replayed graph: every entry equals cs_collide."""
+    specs = [(16, 0.0, 40), (16, 1.0, 24), (24, 0.0, 8), (24, 1.0, 33), (8, 1.0, 1)]
+    hs = [cs.Handle(N, L, lam, "fp32") for N, lam, _ in specs]
+    fs = [dev(I.random_mixture_cells(N, L, n, first_id=600 + 50 * i)) for i, (N, _, n) in enumerate(specs)]
+    qs = [torch.empty_like(f) for f in fs]
+    refs = []
+    for h, f, (N, lam, n) in zip(hs, fs, specs):
+        q = torch.empty_like(f)
+        cs.cs_collide(h.ptr, f, n, 1.0, q, 1)
+        refs.append(host(q))
+    entries = [(h.ptr, f, q, n) for h, f, q, (_, _, n) in zip(hs, fs, qs, specs)]
+    for _ in range(2):  # capture, then replay
+        for q in qs:
+            q.fill_(float("nan"))
+        cs.cs_collide_batched(entries)
+        for q, r in zip(qs, refs):
+            assert np.array_equal(host(q), r)
+    with pytest.raises(cs.CSError):
+        cs.cs_collide_batched([(hs[0].ptr, fs[0], qs[0], 40), (hs[0].ptr, fs[0], qs[1], 24)])  # same handle twice
+    for h in hs:
+        h.close()
