@@ -124,6 +124,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest of every rank's x (the job's time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ----------------------------------------------------------------- our arm
 def make_state(api, inputs, torch, N, ncells, device):
     dx = inputs.wall_grid(ncells)
@@ -193,26 +204,28 @@ def run_ours(args):
     # warm-up + timed region (barrier and synchronize on both sides, max over ranks)
     for _ in range(args.warmup):
         h32.step(fd, dxd, fard, WALL_T, (0.0, 0.0, 0.0), DT, nsteps=1)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # timed region: K steps (CUDA graph replays), barrier + synchronize on both
+    # sides, max over ranks; clocks sampled throughout
     clocks = ClockSampler(local)
     clocks.start()
-    total_ms, prof = time_steps(torch, h32, fd, dxd, fard, args.steps, 0, flush, profile=True)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    if world > 1:
-        dist.barrier()
-        t = torch.tensor([total_ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    # the profiled run above carries event pairs; time once more without them
+    barrier()
+    api.cs_launch_count(reset=True)
     plain_ms, _ = time_steps(torch, h32, fd, dxd, fard, args.steps, 0, flush, profile=False)
-    if world > 1:
-        t = torch.tensor([plain_ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        plain_ms = float(t.item())
+    launches = api.cs_launch_count(reset=True)  # kernels of ours in the timed steps (graph nodes x replays)
+    barrier()
+    plain_ms = max_over_ranks(plain_ms, device)
+    # the same K steps again with per-stage events (direct launches) for the
+    # stage times and the convolution's average launch duration
+    _, prof = time_steps(torch, h32, fd, dxd, fard, args.steps, 0, flush, profile=True)
+    barrier()
+    clk = clocks.stop()
     ms_step = plain_ms / args.steps
     evals_per_step = 2
     pairs_step = evals_per_step * ncells * N ** 6
@@ -251,10 +264,7 @@ def run_ours(args):
         b.record()
         b.synchronize()
         e2e_ms += a.elapsed_time(b)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, device)
     state_bytes = ncells * N ** 3 * 8
     e2e = {"value": world * pairs_step * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
            "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes}
@@ -303,7 +313,8 @@ def run_ours(args):
                    "parallelism": f"replicas x{world} (cells are independent)"},
         "clocks": clk,
         "e2e": e2e,
-        "gpu_launches": 24 * args.steps,
+        "gpu_launches": launches,
+        "gpu_launches_per_step": launches / args.steps,
         "roofline": {"bound": "alu", "achieved": achieved_ops, "peak": peak_tops,
                      "unit": "T FP32-FMA-pipe instructions/s", "frac": achieved_ops / peak_tops,
                      "traffic": TRAFFIC.get((N, ncells)),

@@ -206,6 +206,43 @@ typedef struct {
 int cs_transport(cs_handle_t h, double *f, int ncells, const cs_domain *dom, double dt,
                  cudaStream_t stream);
 
+/* Sharded transport (Sec. 4.2, distributed memory): the x-grid of
+ * total_cells cells is split into contiguous shards, one per process (or
+ * several per process); the collision step is local to each cell, and the
+ * transport of a shard needs two ghost cells per side, filled by the caller
+ * from the neighbouring shards before every stage.  A shard's state lives in
+ * a window of ncells + 4 cells: window cell i is grid cell first_cell - 2 + i
+ * (cells 0, 1 and ncells+2, ncells+3 are the ghosts).  Ghosts that fall
+ * outside the grid are never read: the wall and far-end boundaries of
+ * cs_transport apply there.  A stage computes every face exactly as the
+ * unsharded grid does, so shards reproduce cs_transport bit for bit.
+ *
+ * cs_transport_shard_prepare computes the handle's transport tables (cell
+ * geometry of the whole grid, wall Maxwellian) and makes room for a shard of
+ * ncells cells; it must precede the stages, and again after any
+ * cs_transport / cs_step call on the same handle (which overwrite the
+ * tables).  dom->dx has total_cells entries.  ncells >= 2,
+ * 0 <= first_cell <= total_cells - ncells.
+ * Errors: CS_EINVAL, CS_ENOMEM, CS_ECUDA. */
+int cs_transport_shard_prepare(cs_handle_t h, int ncells, int first_cell, int total_cells,
+                               const cs_domain *dom, cudaStream_t stream);
+
+/* One Runge-Kutta stage of the transport on a shard:
+ *   out = a x + b y + c R(f),  R_j = -(F_{j+1/2} - F_{j-1/2}) / dx_j,
+ * for the shard's cells, F the fluxes of cs_transport (Sec. 3.4).
+ *   f_win (device) [ncells + 4][N^3] the window, ghosts filled.
+ *   x, y  (device, may be NULL: term dropped) [ncells][N^3].
+ *   out   (device) [ncells][N^3]; may alias x, y or the window's own cells
+ *         (the fluxes are complete before any cell is written).
+ * A Heun step of length dt is two stages: f1 = f + dt R(f), then, after the
+ * ghosts of f1 are exchanged, f = f/2 + f1/2 + (dt/2) R(f1).
+ * Errors: CS_EINVAL (also when the tables were not prepared for this
+ * total_cells, dx and wall), CS_ECUDA. */
+int cs_transport_shard_stage(cs_handle_t h, const double *f_win, int ncells, int first_cell,
+                             int total_cells, const cs_domain *dom, double a, const double *x,
+                             double b, const double *y, double c, double *out,
+                             cudaStream_t stream);
+
 /* nsteps Strang-split steps (Sec. 3.1): transport dt/2, collision dt (Heun on
  * P_N Qt / eps), transport dt/2, in place.  f (device, in/out) [ncells][N^3].
  * Errors: CS_EINVAL, CS_ENOMEM, CS_ECUDA. */
@@ -275,6 +312,16 @@ int cs_profile(cs_handle_t h, int enable);
  * reset != 0 clears the records.  Blocks until the recorded events complete.
  * Errors: CS_EINVAL, CS_ECUDA. */
 int cs_profile_read(cs_handle_t h, double *total_ms, long long *launches, int reset);
+
+/* Kernels this library has put on streams since it was loaded (or since the
+ * last reset), over all handles and threads: direct launches count when they
+ * are enqueued, a replayed CUDA graph counts its kernel nodes at each replay
+ * (launches made while a stream is being captured count only through the
+ * replays).  Memset and copy operations are not counted.  The paper has no
+ * counterpart; this is measurement plumbing.
+ *   kernels (host, out); reset != 0 zeroes the count after reading it.
+ * Errors: CS_EINVAL (kernels NULL). */
+int cs_launch_count(long long *kernels, int reset);
 
 #ifdef __cplusplus
 }

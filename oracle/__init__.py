@@ -78,6 +78,9 @@ def _load():
                                                       ctypes.c_double, ctypes.c_int, ctypes.c_int]),
                 "or_transport_rk2": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp,
                                                     ctypes.c_double, _dp, _dp, ctypes.c_double]),
+                "or_transport_rhs_window": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                                           ctypes.c_int, ctypes.c_int, _dp, _dp,
+                                                           ctypes.c_double, _dp, _dp, _dp]),
                 "or_wall_flux": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp,
                                                 ctypes.c_double, _dp, _dp]),
                 "or_strang_step": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -244,6 +247,25 @@ def transport_rk2(f: np.ndarray, N: int, L: float, dx: np.ndarray, Tw: float, Vw
     assert fc.shape[0] == dxa.shape[0] >= 2
     _load().or_transport_rk2(N, L, fc.shape[0], _d(fc), _d(dxa), Tw, _d(vw), _d(ff), dt)
     return fc.reshape(-1, N, N, N)
+
+
+def transport_rhs_window(fw: np.ndarray, N: int, L: float, nc: int, first: int, dx: np.ndarray, Tw: float,
+                         Vw, ffar: np.ndarray) -> np.ndarray:
+    """Transport right-hand side -(F_{j+1/2} - F_{j-1/2}) / dx_j (Sec. 3.4) of the
+    cells first .. first+ncl-1 of an nc-cell grid, from the window fw of
+    ncl + 4 cells (grid cells first-2 .. first+ncl+1; those outside the grid
+    are not read).  dx holds all nc widths."""
+    fwc = _cells(fw, N)
+    ncl = fwc.shape[0] - 4
+    dxa = np.ascontiguousarray(dx, dtype=np.float64)
+    vw = np.ascontiguousarray(Vw, dtype=np.float64)
+    ff = np.ascontiguousarray(ffar, dtype=np.float64).reshape(-1)
+    assert dxa.shape[0] == nc and ncl >= 1
+    rhs = np.empty((ncl, N ** 3))
+    rc = _load().or_transport_rhs_window(N, L, nc, first, ncl, _d(fwc), _d(dxa), Tw, _d(vw), _d(ff), _d(rhs))
+    if rc != 0:
+        raise ValueError("bad shard bounds")
+    return rhs.reshape(-1, N, N, N)
 
 
 def wall_flux(f: np.ndarray, N: int, L: float, dx: np.ndarray, Tw: float, Vw):

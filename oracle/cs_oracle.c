@@ -557,9 +557,16 @@ static double minmod3(double a, double b, double c)
     return 0.0;
 }
 
-/* rhs = -(F_{j+1/2} - F_{j-1/2}) / dx_j for all cells */
-static void transport_rhs(int N, double L, int nc, const double *f, const double *dx,
-                          double Tw, const double *Vw, const double *ffar, double *rhs)
+/* rhs = -(F_{j+1/2} - F_{j-1/2}) / dx_j for the cells first .. first+ncl-1
+ * of a grid of nc cells (widths dx[0..nc-1]), read from a window fw that
+ * holds the cells first-2 .. first+ncl+1 (window cell i = grid cell
+ * first - 2 + i).  Window cells outside 0..nc-1 are never read: the column
+ * below starts out NaN everywhere and only the window is copied into it, so
+ * a read of anything else would show up as NaN in rhs.  The whole grid is
+ * the case first = 0, ncl = nc.                                             */
+static void transport_rhs_window(int N, double L, int nc, int first, int ncl, const double *fw,
+                                 const double *dx, double Tw, const double *Vw, const double *ffar,
+                                 double *rhs)
 {
     int M = N * N * N;
     double dv = or_dv(N, L);
@@ -577,51 +584,65 @@ static void transport_rhs(int N, double L, int nc, const double *f, const double
     double *fx = (double *)malloc(sizeof(double) * (nc + 3));
     double *slope = (double *)malloc(sizeof(double) * (nc + 2)); /* slope[j+1], j=-1..nc */
     double *face = (double *)malloc(sizeof(double) * (nc + 1));  /* F_{j-1/2}, j=0..nc */
+    int lo = first - 2 < 0 ? 0 : first - 2;                      /* grid cells in the window */
+    int hi = first + ncl + 1 > nc - 1 ? nc - 1 : first + ncl + 1;
+#define FW(c, j) fw[(size_t)M * ((c) - first + 2) + (j)]
 
     /* wall: outgoing flux of the reconstructed face values, and the
-     * discrete flux of M_w over v1 > 0                                        */
-    double out_flux = 0.0, mw_flux = 0.0;
-    for (int j = 0; j < M; ++j) {
-        double v1 = dv * (j / (N * N) - N / 2);
-        double v2 = dv * ((j / N) % N - N / 2);
-        double v3 = dv * (j % N - N / 2);
-        if (v1 < 0) {
-            double f0 = f[j], f1 = f[(size_t)M + j];
-            double s0 = (f1 - f0) / (x[2] - x[1]);
-            out_flux += -v1 * (f0 - 0.5 * dx[0] * s0) * w3;
-        } else if (v1 > 0) {
-            double e = (v1 - Vw[0]) * (v1 - Vw[0]) + (v2 - Vw[1]) * (v2 - Vw[1]) +
-                       (v3 - Vw[2]) * (v3 - Vw[2]);
-            double mw = pow(2.0 * OR_PI * Tw, -1.5) * exp(-e / (2.0 * Tw));
-            mw_flux += v1 * mw * w3;
+     * discrete flux of M_w over v1 > 0 (needed only where the wall face
+     * F_{-1/2} is one of this window's faces)                                 */
+    double sigma_w = 0.0;
+    if (first == 0) {
+        double out_flux = 0.0, mw_flux = 0.0;
+        for (int j = 0; j < M; ++j) {
+            double v1 = dv * (j / (N * N) - N / 2);
+            double v2 = dv * ((j / N) % N - N / 2);
+            double v3 = dv * (j % N - N / 2);
+            if (v1 < 0) {
+                double f0 = FW(0, j), f1 = FW(1, j);
+                double s0 = (f1 - f0) / (x[2] - x[1]);
+                out_flux += -v1 * (f0 - 0.5 * dx[0] * s0) * w3;
+            } else if (v1 > 0) {
+                double e = (v1 - Vw[0]) * (v1 - Vw[0]) + (v2 - Vw[1]) * (v2 - Vw[1]) +
+                           (v3 - Vw[2]) * (v3 - Vw[2]);
+                double mw = pow(2.0 * OR_PI * Tw, -1.5) * exp(-e / (2.0 * Tw));
+                mw_flux += v1 * mw * w3;
+            }
         }
+        sigma_w = out_flux / mw_flux;
     }
-    double sigma_w = out_flux / mw_flux;
 
     for (int j = 0; j < M; ++j) {
         double v1 = dv * (j / (N * N) - N / 2);
         double v2 = dv * ((j / N) % N - N / 2);
         double v3 = dv * (j % N - N / 2);
-        /* gather the column f_j(v), with ghosts */
-        for (int c = 0; c < nc; ++c) fx[c + 1] = f[(size_t)M * c + j];
+        /* gather the column f_c(v) of the window's cells, with ghosts */
+        for (int c = -1; c <= nc + 1; ++c) fx[c + 1] = NAN;
+        for (int c = lo; c <= hi; ++c) fx[c + 1] = FW(c, j);
         fx[0] = 0.0; /* the left ghost only enters through s_0 below */
-        double gr = (v1 < 0) ? ffar[j] : fx[nc];
-        fx[nc + 1] = gr;
-        fx[nc + 2] = gr;
-        /* slopes for cells -1 .. nc (index j+1); cell -1 is never used.
-         * With f_{-1} the linear extrapolation of f_0, f_1 all three minmod
-         * arguments of cell 0 equal the one-sided slope, taken directly.     */
-        slope[0] = 0.0;
-        slope[1] = (fx[2] - fx[1]) / (x[2] - x[1]);
-        for (int c = 1; c <= nc; ++c) {
-            int i = c + 1;
-            double a = (fx[i + 1] - fx[i]) / (x[i + 1] - x[i]);
-            double b = (fx[i] - fx[i - 1]) / (x[i] - x[i - 1]);
-            double cc = (fx[i + 1] - fx[i - 1]) / (x[i + 1] - x[i - 1]);
-            slope[i] = minmod3(a, b, cc);
+        if (first + ncl + 1 >= nc) { /* the far end is in the window */
+            double gr = (v1 < 0) ? ffar[j] : fx[nc];
+            fx[nc + 1] = gr;
+            fx[nc + 2] = gr;
         }
-        /* faces j - 1/2 for j = 0 .. nc */
-        for (int c = 0; c <= nc; ++c) {
+        /* slopes for cells first-1 .. first+ncl (index c+1); cell -1 is never
+         * used.  With f_{-1} the linear extrapolation of f_0, f_1 all three
+         * minmod arguments of cell 0 equal the one-sided slope, taken directly. */
+        for (int c = first - 1; c <= first + ncl; ++c) {
+            int i = c + 1;
+            if (c < 0) {
+                slope[i] = 0.0;
+            } else if (c == 0) {
+                slope[i] = (fx[2] - fx[1]) / (x[2] - x[1]);
+            } else {
+                double a = (fx[i + 1] - fx[i]) / (x[i + 1] - x[i]);
+                double b = (fx[i] - fx[i - 1]) / (x[i] - x[i - 1]);
+                double cc = (fx[i + 1] - fx[i - 1]) / (x[i + 1] - x[i - 1]);
+                slope[i] = minmod3(a, b, cc);
+            }
+        }
+        /* faces c - 1/2 for c = first .. first+ncl */
+        for (int c = first; c <= first + ncl; ++c) {
             double F;
             if (c == 0) {
                 if (v1 > 0) {
@@ -643,13 +664,38 @@ static void transport_rhs(int N, double L, int nc, const double *f, const double
             }
             face[c] = F;
         }
-        for (int c = 0; c < nc; ++c)
-            rhs[(size_t)M * c + j] = -(face[c + 1] - face[c]) / dx[c];
+        for (int c = first; c < first + ncl; ++c)
+            rhs[(size_t)M * (c - first) + j] = -(face[c + 1] - face[c]) / dx[c];
     }
+#undef FW
     free(x);
     free(fx);
     free(slope);
     free(face);
+}
+
+/* the whole grid: f [nc][M] placed in a window with two empty cells per side */
+static void transport_rhs(int N, double L, int nc, const double *f, const double *dx,
+                          double Tw, const double *Vw, const double *ffar, double *rhs)
+{
+    size_t M = (size_t)N * N * N;
+    double *fw = (double *)malloc(sizeof(double) * M * (nc + 4));
+    for (size_t i = 0; i < M * 2; ++i) fw[i] = NAN;
+    memcpy(fw + 2 * M, f, sizeof(double) * M * nc);
+    for (size_t i = 0; i < M * 2; ++i) fw[M * (nc + 2) + i] = NAN;
+    transport_rhs_window(N, L, nc, 0, nc, fw, dx, Tw, Vw, ffar, rhs);
+    free(fw);
+}
+
+/* The right-hand side of one shard, exposed for the sharded-transport tests:
+ * rhs [ncl][M] for cells first .. first+ncl-1 from the window fw [ncl+4][M]. */
+int or_transport_rhs_window(int N, double L, int nc, int first, int ncl, const double *fw,
+                            const double *dx, double Tw, const double *Vw, const double *ffar,
+                            double *rhs)
+{
+    if (first < 0 || ncl < 1 || first + ncl > nc || nc < 2) return -1;
+    transport_rhs_window(N, L, nc, first, ncl, fw, dx, Tw, Vw, ffar, rhs);
+    return 0;
 }
 
 int or_transport_rk2(int N, double L, int nc, double *f, const double *dx, double Tw,

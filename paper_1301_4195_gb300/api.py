@@ -75,6 +75,10 @@ _SIGS = {
     "cs_autotune": (_i, [_vp, _i, _vp, ctypes.POINTER(_d)]),
     "cs_profile": (_i, [_vp, _i]),
     "cs_profile_read": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong), _i]),
+    "cs_launch_count": (_i, [ctypes.POINTER(ctypes.c_longlong), _i]),
+    "cs_transport_shard_prepare": (_i, [_vp, _i, _i, _i, ctypes.POINTER(Domain), _vp]),
+    "cs_transport_shard_stage": (_i, [_vp, _vp, _i, _i, _i, ctypes.POINTER(Domain), _d, _vp, _d, _vp, _d, _vp,
+                                      _vp]),
 }
 
 STAGES = ("forward", "convolve", "inverse", "conserve", "transport")
@@ -230,6 +234,18 @@ def cs_step(h, f, ncells, dom: Domain, dt, eps, nsteps, stream=None):
     _check(lib().cs_step(h, _dptr(f, "f"), ncells, ctypes.byref(dom), dt, eps, nsteps, _stream(stream)))
 
 
+def cs_transport_shard_prepare(h, ncells, first_cell, total_cells, dom: Domain, stream=None):
+    _check(lib().cs_transport_shard_prepare(h, ncells, first_cell, total_cells, ctypes.byref(dom), _stream(stream)))
+
+
+def cs_transport_shard_stage(h, f_win, ncells, first_cell, total_cells, dom: Domain, a, x, b, y, c, out,
+                             stream=None):
+    """out = a x + b y + c R(f) on a shard; f_win holds ncells + 4 cells (two ghosts per side)."""
+    _check(lib().cs_transport_shard_stage(h, _dptr(f_win, "f_win"), ncells, first_cell, total_cells,
+                                          ctypes.byref(dom), float(a), _dptr(x, "x"), float(b), _dptr(y, "y"),
+                                          float(c), _dptr(out, "out"), _stream(stream)))
+
+
 CS_TUNE_GROUPS_PER_CTA = 1
 CS_TUNE_CTAS_PER_SM = 2
 
@@ -255,6 +271,13 @@ def cs_profile_read(h, reset: bool = True) -> dict:
     n = (ctypes.c_longlong * len(STAGES))()
     _check(lib().cs_profile_read(h, ms, n, int(bool(reset))))
     return {k: (ms[i], n[i]) for i, k in enumerate(STAGES)}
+
+
+def cs_launch_count(reset: bool = False) -> int:
+    """Kernels the library has enqueued (graph replays count their kernel nodes)."""
+    n = ctypes.c_longlong()
+    _check(lib().cs_launch_count(ctypes.byref(n), int(bool(reset))))
+    return n.value
 
 
 def cs_collide_noalloc(h, f, ncells, eps, Q, conserve=1, stream=None):

@@ -173,14 +173,14 @@ int launch_conserve(const Handle &hd, const double *Qt, int ncells, int project,
     const unsigned blocks = (unsigned)(ncells * parts);
     if (project || moments) moments_part_kernel<<<blocks, kThreads, 0, s>>>(hd.g, Qt, parts, hd.part5);
     apply_kernel<<<blocks, kThreads, 0, s>>>(hd.g, pj, Qt, project, parts, hd.part5, a, x, b, y, c, out, moments);
-    CS_CHECK_LAUNCH("conservation projection");
+    CS_LAUNCHED((project || moments) ? 2 : 1, s, "conservation projection");
     return CS_OK;
 }
 
 int launch_moments(const Handle &hd, const double *f, int ncells, double *out, cudaStream_t s)
 {
     moments_kernel<<<ncells, kThreads, 0, s>>>(hd.g, f, out);
-    CS_CHECK_LAUNCH("moments");
+    CS_LAUNCHED(1, s, "moments");
     return CS_OK;
 }
 

@@ -466,7 +466,7 @@ int launch_cfg(const Handle &hd, int ncells, cudaStream_t s)
     if (e != cudaSuccess) return cuda_error(e, "strip kernel work counter");
     kern<<<grid, 32 * C::WARPS, C::SMEM, s>>>((const float *)hd.ghat, hd.pencil_tile0, hd.pencil_order, nblocks,
                                               (const float2 *)hd.F, (float2 *)hd.Qh, omega, hd.err, hd.counter);
-    CS_CHECK_LAUNCH("convolution (strip kernel)");
+    CS_LAUNCHED(1, s, "convolution (strip kernel)");
     return CS_OK;
 }
 

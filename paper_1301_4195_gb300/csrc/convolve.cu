@@ -239,7 +239,7 @@ int launch_pencil(const Handle &hd, int ncells, cudaStream_t s)
     const float omega = (float)(hd.g.dz * hd.g.dz * hd.g.dz);
     conv_pencil_kernel<N><<<blocks, 128, 0, s>>>((const float *)hd.ghat, hd.pencil_tile0, hd.pencil_order, ng,
                                                  (const float2 *)hd.F, (float2 *)hd.Qh, (float2 *)hd.Y, omega);
-    CS_CHECK_LAUNCH("convolution (pencil kernel)");
+    CS_LAUNCHED(1, s, "convolution (pencil kernel)");
     return CS_OK;
 }
 
@@ -260,7 +260,7 @@ int convolve_impl(const Handle &hd, int ncells, cudaStream_t s)
     dim3 grid((unsigned)((g.M + 3) / 4), (unsigned)ngroups_of(ncells));
     conv_generic_kernel<T><<<grid, 128, 0, s>>>(g, (const T *)hd.ghat, hd.pencil_tile0, (const c2_t<T> *)hd.F,
                                                 (c2_t<T> *)hd.Qh, omega);
-    CS_CHECK_LAUNCH("convolution");
+    CS_LAUNCHED(1, s, "convolution");
     return CS_OK;
 }
 

@@ -2,6 +2,7 @@
 // handle (weights, constants, workspace) and the order of kernel launches for
 // each entry point.  No exception crosses the ABI; every failure returns a
 // CS_E* code and leaves a message for cs_last_error().
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -16,6 +17,7 @@ namespace cs {
 
 namespace {
 thread_local std::string g_last_error;
+std::atomic<long long> g_kernels{0};
 
 bool is_finite(double x) { return std::isfinite(x); }
 
@@ -150,11 +152,11 @@ size_t spectral_bytes(const Handle &hd, int ncells)
 
 // Carve the workspace: F, Qh, X, Y (spectral), Qt, f1 (state), scal
 // (transport tables), part5 (projection partials).
-size_t workspace_bytes(const Handle &hd, int ncells, size_t *offs)
+size_t workspace_bytes(const Handle &hd, int ncells, int geo_cells, size_t *offs)
 {
     const size_t sb = align_up(spectral_bytes(hd, ncells), 256);
     const size_t st = align_up((size_t)ncells * hd.g.M * sizeof(double), 256);
-    const size_t sc = align_up(sizeof(double) * (transport_table_doubles(hd.g.N, ncells) + 8), 256);
+    const size_t sc = align_up(sizeof(double) * (transport_table_doubles(hd.g.N, ncells, geo_cells) + 8), 256);
     const size_t sp = align_up(sizeof(double) * 5 * (size_t)ncells * conserve_parts(hd.g.M), 256);
     size_t o = 0;
     for (int i = 0; i < 4; ++i) {
@@ -178,12 +180,17 @@ void drop_graphs(Handle &hd)
     hd.graphs.clear();
 }
 
-int ensure_workspace(Handle &hd, int ncells)
+// Workspace for ncells cells whose transport tables cover a grid of
+// geo_cells cells (a shard of a larger grid; at least ncells).  Grows only.
+int ensure_workspace(Handle &hd, int ncells, int geo_cells = 0)
 {
-    if (ncells <= hd.ws_cells) return CS_OK;
+    if (geo_cells < ncells) geo_cells = ncells;
+    if (ncells <= hd.ws_cells && geo_cells <= hd.ws_geo_cells) return CS_OK;
+    if (ncells < hd.ws_cells) ncells = hd.ws_cells;
+    if (geo_cells < hd.ws_geo_cells) geo_cells = hd.ws_geo_cells;
     drop_graphs(hd);  // captured steps point into the old workspace
     size_t offs[8];
-    const size_t bytes = workspace_bytes(hd, ncells, offs);
+    const size_t bytes = workspace_bytes(hd, ncells, geo_cells, offs);
     if (hd.ws) {
         cudaError_t e = cudaDeviceSynchronize();
         if (e != cudaSuccess) return cuda_error(e, "synchronise before growing the workspace");
@@ -201,6 +208,8 @@ int ensure_workspace(Handle &hd, int ncells)
     hd.ws = p;
     hd.ws_bytes = bytes;
     hd.ws_cells = ncells;
+    hd.ws_geo_cells = geo_cells;
+    hd.shard_tables.total_cells = -1;
     ++hd.ws_generation;
     hd.F = b + offs[0];
     hd.Qh = b + offs[1];
@@ -242,7 +251,7 @@ int timed_transport(Handle &hd, const double *fin, int ncells, const cs_domain &
                     double b, const double *y, double c, double *out, cudaStream_t s)
 {
     StageTimer t(hd, CS_K_TRANSPORT, s);
-    return launch_transport_stage(hd, fin, ncells, dom, a, x, b, y, c, out, s);
+    return launch_transport_stage(hd, fin, 0, 0, ncells, ncells, dom, a, x, b, y, c, out, s);
 }
 
 // One collision evaluation written as out = a x + b y + c P(Qt(f)/eps)
@@ -301,8 +310,10 @@ int run_steps(Handle &hd, Handle::GraphEntry key, int nsteps, cudaStream_t s, Bo
     for (auto &g : hd.graphs)
         if (g.kind == key.kind && g.f == key.f && g.dx == key.dx && g.ffar == key.ffar && g.ncells == key.ncells &&
             g.wall_T == key.wall_T && g.wall_V[0] == key.wall_V[0] && g.wall_V[1] == key.wall_V[1] &&
-            g.wall_V[2] == key.wall_V[2] && g.dt == key.dt && g.eps == key.eps)
+            g.wall_V[2] == key.wall_V[2] && g.dt == key.dt && g.eps == key.eps) {
             exec = g.exec;
+            key.kernels = g.kernels;
+        }
     if (!exec) {
         if (!hd.cap_stream && cudaStreamCreateWithFlags(&hd.cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
             cudaGetLastError();
@@ -314,6 +325,7 @@ int run_steps(Handle &hd, Handle::GraphEntry key, int nsteps, cudaStream_t s, Bo
         const int rc = ok ? body(hd.cap_stream) : CS_OK;
         if (ok) ok = cudaStreamEndCapture(hd.cap_stream, &graph) == cudaSuccess && rc == CS_OK;
         if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+        if (ok) key.kernels = graph_kernel_nodes(graph);
         if (graph) cudaGraphDestroy(graph);
         if (!ok) {
             cudaGetLastError();
@@ -331,6 +343,7 @@ int run_steps(Handle &hd, Handle::GraphEntry key, int nsteps, cudaStream_t s, Bo
     for (int i = 0; i < nsteps; ++i) {
         cudaError_t e = cudaGraphLaunch(exec, s);
         if (e != cudaSuccess) return cuda_error(e, "replay of a captured step");
+        note_replay(key.kernels);
     }
     return CS_OK;
 }
@@ -390,6 +403,38 @@ int cuda_error(cudaError_t e, const char *what)
     return set_error(CS_ECUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
 }
 
+void note_kernels(cudaStream_t s, int n)
+{
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+        cudaGetLastError();
+        st = cudaStreamCaptureStatusNone;
+    }
+    if (st == cudaStreamCaptureStatusNone) g_kernels += n;
+}
+
+void note_replay(int kernels) { g_kernels += kernels; }
+
+int graph_kernel_nodes(cudaGraph_t g)
+{
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n && cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int k = 0;
+    for (size_t i = 0; i < n; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
+}
+
 // ---- batched collision graphs (library-wide cache)
 namespace {
 
@@ -401,6 +446,7 @@ struct BatchGraph {
     double eps;
     int conserve;
     cudaGraphExec_t exec;
+    int kernels = 0;  // kernel nodes of the graph
 };
 
 std::mutex g_batch_mutex;
@@ -452,13 +498,17 @@ int cs_collide_batched(const cs_batch_entry *entries, int n, double eps, int con
     }
     std::lock_guard<std::mutex> lock(g_batch_mutex);
     cudaGraphExec_t exec = nullptr;
+    int kernels_of_exec = 0;
     for (auto &g : g_batch_graphs) {
         if ((int)g.handles.size() != n || g.eps != eps || g.conserve != conserve) continue;
         bool same = true;
         for (int i = 0; i < n && same; ++i)
             same = g.handles[i] == entries[i].handle && g.generations[i] == entries[i].handle->h.ws_generation &&
                    g.f[i] == entries[i].f && g.q[i] == entries[i].Q && g.ncells[i] == entries[i].ncells;
-        if (same) exec = g.exec;
+        if (same) {
+            exec = g.exec;
+            kernels_of_exec = g.kernels;
+        }
     }
     if (!exec) {
         for (int i = 0; i <= n; ++i)
@@ -493,6 +543,8 @@ int cs_collide_batched(const cs_batch_entry *entries, int n, double eps, int con
             e = cudaStreamEndCapture(root, &graph);
         }
         if (e == cudaSuccess && rc == CS_OK) e = cudaGraphInstantiate(&exec, graph, 0);
+        int kernels = 0;
+        if (e == cudaSuccess && rc == CS_OK) kernels = graph_kernel_nodes(graph);
         if (graph) cudaGraphDestroy(graph);
         for (auto x : ev) cudaEventDestroy(x);
         if (rc != CS_OK) return rc;
@@ -512,10 +564,20 @@ int cs_collide_batched(const cs_batch_entry *entries, int n, double eps, int con
         bg.eps = eps;
         bg.conserve = conserve;
         bg.exec = exec;
+        bg.kernels = kernels;
+        kernels_of_exec = kernels;
         g_batch_graphs.push_back(bg);
     }
     cudaError_t e = cudaGraphLaunch(exec, stream);
     if (e != cudaSuccess) return cuda_error(e, "cs_collide_batched: replay");
+    note_replay(kernels_of_exec);
+    return CS_OK;
+}
+
+int cs_launch_count(long long *kernels, int reset)
+{
+    if (!kernels) return set_error(CS_EINVAL, "kernels is NULL");
+    *kernels = reset ? g_kernels.exchange(0) : g_kernels.load();
     return CS_OK;
 }
 
@@ -903,6 +965,7 @@ int cs_transport(cs_handle_t h, double *f, int ncells, const cs_domain *dom, dou
     if (int rc = check_domain(hd, dom, ncells)) return rc;
     if (int rc = check_device_ptr(f, "f")) return rc;
     if (int rc = ensure_workspace(hd, ncells)) return rc;
+    hd.shard_tables.total_cells = -1;
     if (int rc = launch_transport_prep(hd, ncells, *dom, s)) return rc;
     return heun_transport(hd, f, ncells, *dom, dt, s);
 }
@@ -920,6 +983,7 @@ int cs_step(cs_handle_t h, double *f, int ncells, const cs_domain *dom, double d
     if (int rc = check_device_ptr(f, "f")) return rc;
     if (int rc = ensure_workspace(hd, ncells)) return rc;
     const cs_domain d = *dom;
+    hd.shard_tables.total_cells = -1;
     Handle::GraphEntry key{1, f, d.dx, d.f_far, ncells, d.wall_T, {d.wall_V[0], d.wall_V[1], d.wall_V[2]},
                            dt, eps, nullptr};
     return run_steps(hd, key, nsteps, s, [&](cudaStream_t st) {
@@ -928,6 +992,51 @@ int cs_step(cs_handle_t h, double *f, int ncells, const cs_domain *dom, double d
         if (int rc = heun_collision(hd, f, ncells, dt, eps, st)) return rc;
         return heun_transport(hd, f, ncells, d, 0.5 * dt, st);
     });
+}
+
+
+int cs_transport_shard_prepare(cs_handle_t h, int ncells, int first_cell, int total_cells, const cs_domain *dom,
+                               cudaStream_t s)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (int rc = check_cells(ncells)) return rc;
+    if (int rc = check_cells(total_cells)) return rc;
+    if (ncells < 2 || first_cell < 0 || first_cell > total_cells - ncells)
+        return set_error(CS_EINVAL, "shard must hold >= 2 cells inside 0 .. total_cells-1");
+    Handle &hd = h->h;
+    if (int rc = check_domain(hd, dom, total_cells)) return rc;
+    if (int rc = ensure_workspace(hd, ncells, total_cells)) return rc;
+    if (int rc = launch_transport_prep(hd, total_cells, *dom, s)) return rc;
+    hd.shard_tables.total_cells = total_cells;
+    hd.shard_tables.dx = dom->dx;
+    hd.shard_tables.wall_T = dom->wall_T;
+    for (int i = 0; i < 3; ++i) hd.shard_tables.wall_V[i] = dom->wall_V[i];
+    return CS_OK;
+}
+
+int cs_transport_shard_stage(cs_handle_t h, const double *f_win, int ncells, int first_cell, int total_cells,
+                             const cs_domain *dom, double a, const double *x, double b, const double *y, double c,
+                             double *out, cudaStream_t s)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (int rc = check_cells(ncells)) return rc;
+    Handle &hd = h->h;
+    if (dom == nullptr) return set_error(CS_EINVAL, "domain is NULL");
+    const auto &t = hd.shard_tables;
+    if (t.total_cells != total_cells || t.dx != dom->dx || t.wall_T != dom->wall_T || t.wall_V[0] != dom->wall_V[0] ||
+        t.wall_V[1] != dom->wall_V[1] || t.wall_V[2] != dom->wall_V[2])
+        return set_error(CS_EINVAL, "transport tables not prepared for this grid and wall "
+                                    "(call cs_transport_shard_prepare first)");
+    if (ncells < 2 || first_cell < 0 || first_cell > total_cells - ncells || ncells > hd.ws_cells)
+        return set_error(CS_EINVAL, "shard must hold 2 .. reserved cells inside 0 .. total_cells-1");
+    if (!is_finite(a) || !is_finite(b) || !is_finite(c)) return set_error(CS_EINVAL, "a, b, c must be finite");
+    if (int rc = check_device_ptr(f_win, "f_win")) return rc;
+    if (int rc = check_device_ptr(dom->f_far, "domain.f_far")) return rc;
+    if (int rc = check_device_ptr(out, "out")) return rc;
+    if (int rc = check_device_ptr(x, "x", true)) return rc;
+    if (int rc = check_device_ptr(y, "y", true)) return rc;
+    StageTimer tm(hd, CS_K_TRANSPORT, s);
+    return launch_transport_stage(hd, f_win, 2, first_cell, ncells, total_cells, *dom, a, x, b, y, c, out, s);
 }
 
 }  // extern "C"

@@ -107,6 +107,15 @@ struct Handle {
     double cct_inv[25] = {};
     // workspace
     int ws_cells = 0;
+    int ws_geo_cells = 0;         // grid size the transport tables have room for
+    // what the transport tables in `scal` were last prepared for by
+    // cs_transport_shard_prepare (total_cells < 0: not prepared, or
+    // overwritten since by cs_transport / cs_step or a workspace move)
+    struct {
+        int total_cells = -1;
+        const double *dx = nullptr;
+        double wall_T = 0, wall_V[3] = {0, 0, 0};
+    } shard_tables;
     void *ws = nullptr;
     size_t ws_bytes = 0;
     unsigned ws_generation = 0;  // bumped whenever the workspace moves
@@ -121,6 +130,7 @@ struct Handle {
         int ncells;
         double wall_T, wall_V[3], dt, eps;
         cudaGraphExec_t exec;
+        int kernels;  // kernel nodes of the captured step
     };
     std::vector<GraphEntry> graphs;
     cudaStream_t cap_stream = nullptr;
@@ -158,6 +168,17 @@ int cuda_error(cudaError_t e, const char *what);
     do {                                                         \
         cudaError_t _e = cudaGetLastError();                     \
         if (_e != cudaSuccess) return ::cs::cuda_error(_e, what); \
+    } while (0)
+// Library-wide count of kernels put on streams (cs_launch_count): n launches
+// just enqueued on s count now unless s is being captured, in which case the
+// graph's kernel nodes count at each replay instead.
+void note_kernels(cudaStream_t s, int n);
+int graph_kernel_nodes(cudaGraph_t g);
+void note_replay(int kernels);
+#define CS_LAUNCHED(n, s, what)        \
+    do {                               \
+        CS_CHECK_LAUNCH(what);         \
+        ::cs::note_kernels((s), (n));  \
     } while (0)
 
 inline size_t elem_bytes(int precision) { return precision == CS_FP32 ? 4 : 8; }
@@ -202,11 +223,15 @@ int conserve_parts(int M);  // blocks per cell of the projection
 // ---- transport.cu
 // doubles of workspace the transport tables need; tables are filled by
 // launch_transport_prep once per call (geometry, wall Maxwellian flux)
-size_t transport_table_doubles(int N, int ncells);
-int launch_transport_prep(const Handle &hd, int ncells, const cs_domain &dom, cudaStream_t s);
-// out = a*x + b*y + c*rhs(fin)   with rhs the finite-volume transport operator
-int launch_transport_stage(const Handle &hd, const double *fin, int ncells, const cs_domain &dom,
-                           double a, const double *x, double b, const double *y, double c,
+// transport tables for a grid of total_cells cells and the face fluxes of a
+// shard of ncells of them (the whole grid: ncells = total_cells)
+size_t transport_table_doubles(int N, int ncells, int total_cells);
+int launch_transport_prep(const Handle &hd, int total_cells, const cs_domain &dom, cudaStream_t s);
+// one transport stage, out = a x + b y + c rhs(fin), rhs the finite-volume
+// operator, for cells first .. first+ncells-1, read from fin with `ghost`
+// leading ghost cells (0: fin holds exactly the cells; 2: a window)
+int launch_transport_stage(const Handle &hd, const double *fin, int ghost, int first, int ncells, int total_cells,
+                           const cs_domain &dom, double a, const double *x, double b, const double *y, double c,
                            double *out, cudaStream_t s);
 
 }  // namespace cs

@@ -198,7 +198,7 @@ int forward_n(const Handle &hd, const double *f, int ncells, cudaStream_t s)
     const float cf = (float)(pow(2.0 * M_PI, -1.5) * hd.g.dv * hd.g.dv * hd.g.dv);
     const unsigned blocks = (unsigned)(ngroups_of(ncells) * kGroup);
     forward_fused_kernel<N><<<blocks, kFusedThreads, fused_smem<N>(), s>>>(f, ncells, hd.tw32, cf, (float2 *)hd.F);
-    CS_CHECK_LAUNCH("forward transform (fused)");
+    CS_LAUNCHED(1, s, "forward transform (fused)");
     return CS_OK;
 }
 
@@ -211,7 +211,7 @@ int inverse_n(const Handle &hd, int ncells, double eps, int project, double a, c
     const float ci = (float)(pow(2.0 * M_PI, -1.5) * hd.g.dz * hd.g.dz * hd.g.dz / eps);
     inverse_project_kernel<N><<<ncells, kFusedThreads, fused_smem<N>(), s>>>(
         (const float2 *)hd.Qh, hd.tw32, ci, hd.g.dv, project, pj, a, x, b, y, c, out, moments);
-    CS_CHECK_LAUNCH("inverse transform and projection (fused)");
+    CS_LAUNCHED(1, s, "inverse transform and projection (fused)");
     return CS_OK;
 }
 

@@ -169,7 +169,7 @@ int forward_impl(const Handle &hd, const double *f, int ncells, cudaStream_t s)
                                                                           (c2_t<T> *)hd.Y);
     line_kernel<T><<<blocks, threads, sizeof(c2_t<T>) * N * kGroup, s>>>(N, 1, 0, (T)cf, tw, (const c2_t<T> *)hd.Y,
                                                                           (c2_t<T> *)hd.F);
-    CS_CHECK_LAUNCH("forward transform");
+    CS_LAUNCHED(3, s, "forward transform");
     return CS_OK;
 }
 
@@ -188,7 +188,7 @@ int inverse_impl(const Handle &hd, int ncells, double eps, double *Qt, cudaStrea
                                                                           (c2_t<T> *)hd.Y);
     const size_t sm = sizeof(c2_t<T>) * N * kGroup + sizeof(double) * N * kGroup;
     inverse_rows_kernel<T><<<blocks, threads, sm, s>>>(N, ci, tw, (const c2_t<T> *)hd.Y, ncells, Qt);
-    CS_CHECK_LAUNCH("inverse transform");
+    CS_LAUNCHED(3, s, "inverse transform");
     return CS_OK;
 }
 
@@ -215,7 +215,7 @@ int launch_spectral_to_natural(const Handle &hd, const void *src, int ncells, do
         to_natural_kernel<float><<<1024, 256, 0, s>>>(N, (const float2 *)src, ncells, dst);
     else
         to_natural_kernel<double><<<1024, 256, 0, s>>>(N, (const double2 *)src, ncells, dst);
-    CS_CHECK_LAUNCH("spectral layout conversion");
+    CS_LAUNCHED(1, s, "spectral layout conversion");
     return CS_OK;
 }
 
@@ -226,7 +226,7 @@ int launch_natural_to_spectral(const Handle &hd, const double *src, int ncells, 
         from_natural_kernel<float><<<1024, 256, 0, s>>>(N, src, ncells, (float2 *)dst);
     else
         from_natural_kernel<double><<<1024, 256, 0, s>>>(N, src, ncells, (double2 *)dst);
-    CS_CHECK_LAUNCH("spectral layout conversion");
+    CS_LAUNCHED(1, s, "spectral layout conversion");
     return CS_OK;
 }
 

@@ -18,6 +18,14 @@
 //   sigma_kernel  per Heun stage: sigma_w = (outgoing flux of cell 0) / D;
 //   face_kernel   per stage: every face flux once (one slope each);
 //   update_kernel per stage: out = a x + b y + c (F_{j-1/2} - F_{j+1/2}) / dx_j.
+//
+// The stage kernels work on a shard: cells first .. first+ncl-1 of a grid of
+// nct cells (the whole grid is first = 0, ncl = nct).  Cell j of the grid is
+// read at fin + (j - first + G) M, G = 0 for the caller's plain array and 2
+// for a window with two ghost cells per side (grid cells first-2 ..
+// first+ncl+1), which is all a shard's faces read: the flux through face c
+// needs cells c-2 .. c+1.  The geometry tables always cover the whole grid,
+// so a shard computes every face exactly as the unsharded grid does.
 #include "cs_internal.cuh"
 
 namespace cs {
@@ -35,7 +43,8 @@ constexpr int kSigmaThreads = 512;
 //   v1[k]      = dv (k - N/2),              k = 0 .. N - 1
 //   mw[v]      = v1 M_w(v) for v1 > 0, else 0,  v = 0 .. N^3 - 1
 //   part[b]    = partial sums of D, one per block of prep_mw_kernel
-// and the face fluxes F[c][v], c = 0 .. nc, after them.
+// and the face fluxes F[c][v] of the shard's faces, c = 0 .. ncl, after them
+// (nc above is the whole grid's cell count).
 constexpr int kPrepThreads = 256;
 constexpr int kMaxPrepBlocks = (kMaxN * kMaxN * kMaxN + kPrepThreads - 1) / kPrepThreads;
 
@@ -159,17 +168,24 @@ __device__ __forceinline__ double minmod3(double a, double b, double c)
     return __longlong_as_double((long long)(m | ((unsigned long long)ia & ~mask)));
 }
 
-// flux through face c (between cells c-1 and c), c = 0 .. nc, one thread per (face, v)
-__global__ void face_kernel(Geom g, const double *__restrict__ fin, int nc, const double *__restrict__ dx,
-                            const double *__restrict__ ffar, double *__restrict__ scal)
+// flux through face c (between cells c-1 and c), c = first .. first+ncl, one
+// thread per (face, v); face c is stored at c - first
+__global__ void face_kernel(Geom g, const double *__restrict__ fin, int first, int ncl, int nc, int G,
+                            const double *__restrict__ dx, const double *__restrict__ ffar, double *__restrict__ scal)
 {
     const Tab t = tab_of(scal, nc, g.N);
     const int M = g.M, NN = g.N * g.N;
-    const int c = blockIdx.y;
+    const int c = first + blockIdx.y;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < M; v += gridDim.x * blockDim.x) {
         const double v1 = t.v1[v / NN];
-        const double ghost = v1 < 0 ? ffar[v] : fin[(size_t)(nc - 1) * M + v];
-        auto val = [&](int j) { return j < nc ? fin[(size_t)j * M + v] : ghost; };
+        // grid cell j (j = nc, nc + 1: far-end ghosts) as stored in fin
+        auto val = [&](int j) {
+            if (j >= nc) {
+                if (v1 < 0) return ffar[v];
+                j = nc - 1;
+            }
+            return fin[(ptrdiff_t)(j - first + G) * M + v];
+        };
         double F;
         if (c == 0) {
             if (v1 > 0) {
@@ -196,17 +212,17 @@ __global__ void face_kernel(Geom g, const double *__restrict__ fin, int nc, cons
             const double half = 0.5 * (u < nc ? dx[u] : dx[nc - 1]);
             F = v1 * (right ? fma(half, s, fu) : fma(-half, s, fu));
         }
-        t.face[(size_t)c * M + v] = F;
+        t.face[(size_t)blockIdx.y * M + v] = F;
     }
 }
 
-__global__ void update_kernel(Geom g, int nc, const double *__restrict__ scal, double a, const double *x, double b,
-                              const double *y, double c, double *out)
+__global__ void update_kernel(Geom g, int first, int ncl, int nc, const double *__restrict__ scal, double a,
+                              const double *x, double b, const double *y, double c, double *out)
 {
     const Tab t = tab_of(const_cast<double *>(scal), nc, g.N);
-    const size_t n = (size_t)nc * g.M;
+    const size_t n = (size_t)ncl * g.M;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const int cell = (int)(i / g.M);
+        const int cell = first + (int)(i / g.M);
         const double rhs = (t.face[i] - t.face[i + g.M]) * t.inv_dx[cell];
         double o = c * rhs;
         if (x) o = fma(a, x[i], o);
@@ -217,33 +233,38 @@ __global__ void update_kernel(Geom g, int nc, const double *__restrict__ scal, d
 
 }  // namespace
 
-size_t transport_table_doubles(int N, int ncells)
+size_t transport_table_doubles(int N, int ncells, int total_cells)
 {
-    return 8 + 4 * ((size_t)ncells + 2) + ((N + 7) & ~7) + kMaxPrepBlocks + (size_t)N * N * N * (ncells + 2);
+    return 8 + 4 * ((size_t)total_cells + 2) + ((N + 7) & ~7) + kMaxPrepBlocks + (size_t)N * N * N * (ncells + 2);
 }
 
-int launch_transport_prep(const Handle &hd, int ncells, const cs_domain &dom, cudaStream_t s)
+int launch_transport_prep(const Handle &hd, int total_cells, const cs_domain &dom, cudaStream_t s)
 {
     const Wall w{dom.wall_T, dom.wall_V[0], dom.wall_V[1], dom.wall_V[2]};
     const int nparts = (hd.g.M + kPrepThreads - 1) / kPrepThreads;
-    prep_mw_kernel<<<nparts, kPrepThreads, 0, s>>>(hd.g, w, ncells, hd.scal);
-    prep_geo_kernel<<<1, 256, 0, s>>>(hd.g, ncells, nparts, dom.dx, hd.scal);
-    CS_CHECK_LAUNCH("transport tables");
+    prep_mw_kernel<<<nparts, kPrepThreads, 0, s>>>(hd.g, w, total_cells, hd.scal);
+    prep_geo_kernel<<<1, 256, 0, s>>>(hd.g, total_cells, nparts, dom.dx, hd.scal);
+    CS_LAUNCHED(2, s, "transport tables");
     return CS_OK;
 }
 
-int launch_transport_stage(const Handle &hd, const double *fin, int ncells, const cs_domain &dom, double a,
-                           const double *x, double b, const double *y, double c, double *out, cudaStream_t s)
+int launch_transport_stage(const Handle &hd, const double *fin, int ghost, int first, int ncells, int total_cells,
+                           const cs_domain &dom, double a, const double *x, double b, const double *y, double c,
+                           double *out, cudaStream_t s)
 {
     const int M = hd.g.M;
-    sigma_kernel<<<1, kSigmaThreads, 0, s>>>(hd.g, fin, ncells, dom.dx, hd.scal);
+    int launched = 2;
+    if (first == 0) {  // the wall face belongs to this shard: sigma_w from grid cells 0 and 1
+        sigma_kernel<<<1, kSigmaThreads, 0, s>>>(hd.g, fin + (size_t)ghost * M, total_cells, dom.dx, hd.scal);
+        ++launched;
+    }
     const int tpb = 256;
     dim3 fgrid((unsigned)((M + tpb - 1) / tpb), (unsigned)(ncells + 1));
-    face_kernel<<<fgrid, tpb, 0, s>>>(hd.g, fin, ncells, dom.dx, dom.f_far, hd.scal);
+    face_kernel<<<fgrid, tpb, 0, s>>>(hd.g, fin, first, ncells, total_cells, ghost, dom.dx, dom.f_far, hd.scal);
     const size_t n = (size_t)ncells * M;
     const unsigned blocks = (unsigned)((n + tpb - 1) / tpb < 65535 ? (n + tpb - 1) / tpb : 65535);
-    update_kernel<<<blocks, tpb, 0, s>>>(hd.g, ncells, hd.scal, a, x, b, y, c, out);
-    CS_CHECK_LAUNCH("transport stage");
+    update_kernel<<<blocks, tpb, 0, s>>>(hd.g, first, ncells, total_cells, hd.scal, a, x, b, y, c, out);
+    CS_LAUNCHED(launched, s, "transport stage");
     return CS_OK;
 }
 

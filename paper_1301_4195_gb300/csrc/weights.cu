@@ -314,6 +314,7 @@ int build_weights(Handle &hd, cudaStream_t s)
             build_table_kernel<double><<<(unsigned)hd.total_tiles, 128, 0, s>>>(g, q, hd.pencil_tile0,
                                                                                  hd.total_tiles, demap, (double *)hd.ghat);
         e = cudaGetLastError();
+        if (e == cudaSuccess) note_kernels(s, 1);
     }
     // the map (and the host vector behind the async copy) must outlive the kernel
     const cudaError_t e2 = cudaStreamSynchronize(s);
@@ -339,6 +340,7 @@ int sample_weights(Handle &hd, const int *km_host, int n, double *out_host)
         const QuadRule q = make_rule();
         sample_kernel<<<(n + 127) / 128, 128>>>(hd.g, q, dkm, n, dout);
         e = cudaGetLastError();
+        if (e == cudaSuccess) note_kernels(nullptr, 1);
         if (e == cudaSuccess) e = cudaMemcpy(out_host, dout, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost);
     }
     if (e != cudaSuccess) rc = cuda_error(e, "cs_weights_sample");

@@ -99,3 +99,14 @@ def wall_initial(N: int, L: float, ncells: int) -> np.ndarray:
     """Unit Maxwellian (rho = 1, V = 0, T = 1) in every cell, [ncells, N, N, N]."""
     m = maxwellian(N, L, 1.0, (0.0, 0.0, 0.0), 1.0)
     return np.broadcast_to(m, (ncells, N, N, N)).copy()
+
+
+def wall_profile(N: int, L: float, ncells: int) -> np.ndarray:
+    """A wall-problem state with structure in x, [ncells, N, N, N]: Maxwellians
+    whose density, drift and temperature vary smoothly with the cell index,
+    so every face of the grid carries a non-trivial flux and slope."""
+    out = np.empty((ncells, N, N, N))
+    for j in range(ncells):
+        s = j / max(ncells - 1, 1)
+        out[j] = maxwellian(N, L, 1.0 + 0.3 * np.sin(3.0 * s), (0.4 * np.cos(5.0 * s), 0.1, 0.0), 1.0 + 0.2 * s)
+    return out

@@ -51,6 +51,12 @@ def test_host_only_queries(libcs):
     assert libcs.cs_weights_bytes(16, libcs.CS_FP64) > 1.9 * b16
 
 
+def test_launch_count_is_host_side(libcs):
+    libcs.cs_launch_count(reset=True)
+    assert libcs.cs_launch_count() == 0
+    assert libcs.lib().cs_launch_count(None, 0) == libcs.CS_EINVAL
+
+
 @pytest.mark.parametrize("N,L,lam,prec", [(5, 6.0, 1.0, 0), (34, 6.0, 1.0, 0), (2, 6.0, 1.0, 0),
                                           (8, -1.0, 1.0, 0), (8, 6.0, 1.5, 0), (8, 6.0, -0.1, 0),
                                           (8, 6.0, 1.0, 7), (8, float("nan"), 1.0, 0)])

@@ -270,12 +270,22 @@ def test_graph_replay_matches_direct_launches(cs, prec):
     dx, f, far = _wall(N, nc)
     h = handle(cs, N, 1.0, prec)
     fa, fb = dev(f), dev(f)
-    h.step(fa, dev(dx), dev(far), 1.5, (0, 0, 0), 0.01, nsteps=3)
+    dxd, fard = dev(dx), dev(far)
+    cs.cs_launch_count(reset=True)
+    h.step(fa, dxd, fard, 1.5, (0, 0, 0), 0.01, nsteps=3)
+    replayed = cs.cs_launch_count(reset=True)
     cs.cs_profile(h.ptr, True)
-    h.step(fb, dev(dx), dev(far), 1.5, (0, 0, 0), 0.01, nsteps=3)
+    h.step(fb, dxd, fard, 1.5, (0, 0, 0), 0.01, nsteps=3)
+    direct = cs.cs_launch_count(reset=True)
     cs.cs_profile(h.ptr, False)
     cs.cs_profile_read(h.ptr, reset=True)
     assert np.array_equal(host(fa), host(fb))
+    # a replay counts the graph's kernel nodes: the same kernels as the direct launches
+    assert replayed == direct and direct % 3 == 0
+    if prec == "fp32":
+        # per step: transport tables 2, four transport stages x 3, two collision
+        # evaluations x (forward, convolution, inverse + projection)
+        assert direct == 3 * 20
     ga, gb = dev(f), dev(f)
     h.relax(ga, 0.01, 4)
     cs.cs_profile(h.ptr, True)
