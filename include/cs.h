@@ -232,8 +232,7 @@ int cs_transport_shard_prepare(cs_handle_t h, int ncells, int first_cell, int to
  * for the shard's cells, F the fluxes of cs_transport (Sec. 3.4).
  *   f_win (device) [ncells + 4][N^3] the window, ghosts filled.
  *   x, y  (device, may be NULL: term dropped) [ncells][N^3].
- *   out   (device) [ncells][N^3]; may alias x, y or the window's own cells
- *         (the fluxes are complete before any cell is written).
+ *   out   (device) [ncells][N^3]; may alias x or y, must not overlap f_win.
  * A Heun step of length dt is two stages: f1 = f + dt R(f), then, after the
  * ghosts of f1 are exchanged, f = f/2 + f1/2 + (dt/2) R(f1).
  * Errors: CS_EINVAL (also when the tables were not prepared for this

@@ -4,7 +4,12 @@
 // over the symmetrised half-tiles of the weight table (weights.cu).
 //
 // Work decomposition.  A work item is one output pencil (k1, k2, all k3) of
-// GPC groups of 32 cells (one cell per lane).  The pencil's k3 range is cut
+// GPC groups of 32 cells (one cell per lane), or, with S = 2 parts, one half
+// of that pencil's tiles: part 0 sums the first ceil(T/2) tiles into Qh,
+// part 1 the rest into Qh2, and the consumer adds the two partial sums in
+// that fixed order.  Halving the items lets more, smaller CTAs share an SM
+// without a long tail; the split depends only on N and the precision, so a
+// cell's result never depends on how many cells share the launch.  The pencil's k3 range is cut
 // into N/K strips of K outputs; warp (group g, strip w) keeps only its K
 // complex accumulators (plus a compensation pair) in registers.  CTAs are
 // persistent and take items from an atomic counter, heaviest pencils first.
@@ -282,12 +287,13 @@ struct TileWalk {
 // counter, heaviest pencils first, so the tail of the launch holds only the
 // smallest items.  The stage ring runs across items: ring use u sits in
 // slot u % NST, phase u / NST.
-template <int N, int K, int U, int NST, int GPC>
+template <int N, int K, int U, int NST, int GPC, int S>
 __global__ void __launch_bounds__(32 * (N / K) * GPC) conv_strip_kernel(const float *__restrict__ ghat,
                                                                         const int *__restrict__ tile0,
                                                                         const int *__restrict__ order, int nblocks,
                                                                         const float2 *__restrict__ F,
-                                                                        float2 *__restrict__ Qh, float omega,
+                                                                        float2 *__restrict__ Qh,
+                                                                        float2 *__restrict__ Qh2, float omega,
                                                                         int *err, int *counter)
 {
     using C = StripCfg<N, K, U, NST, GPC>;
@@ -303,7 +309,7 @@ __global__ void __launch_bounds__(32 * (N / K) * GPC) conv_strip_kernel(const fl
     const int k0 = warp * K;
     const bool kind_a = k0 < H;
     const int seg = strip_seg_off(N, K, warp);
-    const int nitems = N * N * nblocks;
+    const int nitems = N * N * nblocks * S;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NST; ++s) {
@@ -326,16 +332,21 @@ __global__ void __launch_bounds__(32 * (N / K) * GPC) conv_strip_kernel(const fl
         const int item = s_item;
         __syncthreads();
         if (item >= nitems) break;
-        const int pencil = order[item / nblocks];
-        const int gblk = item % nblocks;
+        const int part = item % S, rest = item / S;
+        const int pencil = order[rest / nblocks];
+        const int gblk = rest % nblocks;
         const int grp = gblk * GPC + gl;
         const int k1 = pencil / N, k2 = pencil % N;
         const int K1 = k1 + H, K2 = k2 + H;
         const int lo1 = max(0, K1 - N + 1);
         const int lo2 = max(0, K2 - N + 1), hi2 = min(N - 1, K2);
-        const int T = tile0[pencil + 1] - tile0[pencil];
+        const int Tall = tile0[pencil + 1] - tile0[pencil];
+        const int tb = part == 0 ? 0 : (Tall + 1) / 2;  // this part's tiles: tb .. te-1
+        const int te = (S == 1 || part == 1) ? Tall : (Tall + 1) / 2;
+        const int T = te - tb;
         const float2 *Fb0 = F + (size_t)gblk * GPC * C::M * kGroup;
-        const float *Gp = ghat + (size_t)tile0[pencil] * C::TSV;
+        const float *Gp = ghat + (size_t)(tile0[pencil] + tb) * C::TSV;
+        float2 *Qout = part == 0 ? Qh : Qh2;
 
         TileWalk pw;  // producer's walk (thread 0), NST tiles ahead of the consumers
         int pt = 0;
@@ -360,6 +371,7 @@ __global__ void __launch_bounds__(32 * (N / K) * GPC) conv_strip_kernel(const fl
         };
         if (threadIdx.x == 0) {
             pw.start(lo1, lo2, hi2, K1, K2);
+            for (int i = 0; i < tb; ++i) pw.next();
             while (pt < NST && pt < T)
                 if (!issue_next()) {
                     ok = false;
@@ -376,7 +388,8 @@ __global__ void __launch_bounds__(32 * (N / K) * GPC) conv_strip_kernel(const fl
         }
         TileWalk cw;
         cw.start(lo1, lo2, hi2, K1, K2);
-        int cur_m1 = lo1;
+        for (int i = 0; i < tb; ++i) cw.next();
+        int cur_m1 = cw.m1;
         for (int t = 0; t < T && ok; ++t) {
             const uint32_t u = tt + t;
             const int s = u % NST;
@@ -416,7 +429,7 @@ __global__ void __launch_bounds__(32 * (N / K) * GPC) conv_strip_kernel(const fl
         for (int j = 0; j < K; ++j) {
             two_sum(hi[j].x, lo[j].x, acc[j].x);
             two_sum(hi[j].y, lo[j].y, acc[j].y);
-            Qh[((size_t)grp * C::M + (size_t)pencil * N + k0 + j) * kGroup + lane] =
+            Qout[((size_t)grp * C::M + (size_t)pencil * N + k0 + j) * kGroup + lane] =
                 make_float2(omega * (hi[j].x + lo[j].x), omega * (hi[j].y + lo[j].y));
         }
         tt += T;
@@ -430,20 +443,20 @@ __global__ void __launch_bounds__(32 * (N / K) * GPC) conv_strip_kernel(const fl
     }
 }
 
-template <int N, int K, int U, int NST, int GPC>
+template <int N, int K, int U, int NST, int GPC, int S>
 int launch_cfg(const Handle &hd, int ncells, cudaStream_t s)
 {
     using C = StripCfg<N, K, U, NST, GPC>;
     static_assert(K % 4 == 0 && (N / 2) % K == 0, "strip width must divide N/2 and be a multiple of 4");
     static_assert(C::STAGE % 16 == 0 && C::ROWB % 16 == 0 && C::GB % 16 == 0, "bulk copies need 16-byte units");
-    auto kern = conv_strip_kernel<N, K, U, NST, GPC>;
+    auto kern = conv_strip_kernel<N, K, U, NST, GPC, S>;
     if (C::SMEM > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         if (e != cudaSuccess) return cuda_error(e, "strip kernel shared-memory attribute");
     }
     const int ng = ngroups_of(ncells);
     const int nblocks = ng / GPC;  // callers pick GPC dividing ng
-    const int nitems = N * N * nblocks;
+    const int nitems = N * N * nblocks * S;
     static int per_sm[2] = {0, 0};  // resident CTAs per SM, per GPC variant
     int &occ = per_sm[GPC - 1];
     if (occ == 0) {
@@ -465,29 +478,35 @@ int launch_cfg(const Handle &hd, int ncells, cudaStream_t s)
     cudaError_t e = cudaMemsetAsync(hd.counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return cuda_error(e, "strip kernel work counter");
     kern<<<grid, 32 * C::WARPS, C::SMEM, s>>>((const float *)hd.ghat, hd.pencil_tile0, hd.pencil_order, nblocks,
-                                              (const float2 *)hd.F, (float2 *)hd.Qh, omega, hd.err, hd.counter);
+                                              (const float2 *)hd.F, (float2 *)hd.Qh, (float2 *)hd.Qh2, omega,
+                                              hd.err, hd.counter);
     CS_LAUNCHED(1, s, "convolution (strip kernel)");
     return CS_OK;
 }
 
-template <int N, int K, int U, int NST1, int NST2>
+template <int N, int K, int U, int NST1, int NST2, int S>
 int launch_n(const Handle &hd, int ncells, cudaStream_t s)
 {
     const bool even = ngroups_of(ncells) % 2 == 0;
     const bool two = hd.tune_gpc == 2 || (hd.tune_gpc == 0 && N <= 16);  // measured: 1 group per CTA wins at N = 32
-    if (even && two) return launch_cfg<N, K, U, NST2, 2>(hd, ncells, s);
-    return launch_cfg<N, K, U, NST1, 1>(hd, ncells, s);
+    if (even && two) return launch_cfg<N, K, U, NST2, 2, S>(hd, ncells, s);
+    return launch_cfg<N, K, U, NST1, 1, S>(hd, ncells, s);
 }
 
 }  // namespace
 
+int conv_parts(const Handle &hd)
+{
+    return (hd.precision == CS_FP32 && hd.g.layout == LAYOUT_STRIP && hd.g.N == 16) ? 2 : 1;
+}
+
 int launch_strip(const Handle &hd, int ncells, cudaStream_t s)
 {
     switch (hd.g.N) {
-    case 8: return launch_n<8, 4, 4, 4, 4>(hd, ncells, s);
-    case 16: return launch_n<16, 8, 8, 4, 3>(hd, ncells, s);
-    case 24: return launch_n<24, 12, 4, 3, 2>(hd, ncells, s);
-    case 32: return launch_n<32, 8, 8, 3, 3>(hd, ncells, s);
+    case 8: return launch_n<8, 4, 4, 4, 4, 1>(hd, ncells, s);
+    case 16: return launch_n<16, 8, 8, 3, 3, 2>(hd, ncells, s);
+    case 24: return launch_n<24, 12, 4, 3, 2, 1>(hd, ncells, s);
+    case 32: return launch_n<32, 8, 8, 3, 3, 1>(hd, ncells, s);
     default: return set_error(CS_ENOTSUP, "strip kernel: unsupported N");
     }
 }

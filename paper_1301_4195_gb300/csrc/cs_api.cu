@@ -156,7 +156,7 @@ size_t workspace_bytes(const Handle &hd, int ncells, int geo_cells, size_t *offs
 {
     const size_t sb = align_up(spectral_bytes(hd, ncells), 256);
     const size_t st = align_up((size_t)ncells * hd.g.M * sizeof(double), 256);
-    const size_t sc = align_up(sizeof(double) * (transport_table_doubles(hd.g.N, ncells, geo_cells) + 8), 256);
+    const size_t sc = align_up(sizeof(double) * (transport_table_doubles(hd.g.N, geo_cells) + 8), 256);
     const size_t sp = align_up(sizeof(double) * 5 * (size_t)ncells * conserve_parts(hd.g.M), 256);
     size_t o = 0;
     for (int i = 0; i < 4; ++i) {
@@ -213,6 +213,7 @@ int ensure_workspace(Handle &hd, int ncells, int geo_cells = 0)
     ++hd.ws_generation;
     hd.F = b + offs[0];
     hd.Qh = b + offs[1];
+    hd.Qh2 = b + offs[2];  // X: unused by the whole-cell transforms, the only consumers of a split
     hd.X = b + offs[2];
     hd.Y = b + offs[3];
     hd.Qt = (double *)(b + offs[4]);
@@ -237,7 +238,7 @@ int timed_convolve(Handle &hd, int ncells, cudaStream_t s)
 int timed_inverse(Handle &hd, int ncells, double eps, double *Qt, cudaStream_t s)
 {
     StageTimer t(hd, CS_K_INVERSE, s);
-    return launch_inverse(hd, ncells, eps, Qt, s);
+    return launch_inverse(hd, ncells, eps, Qt, s, conv_second(hd));
 }
 
 int timed_conserve(Handle &hd, const double *Qt, int ncells, int project, double a, const double *x, double b,
@@ -267,7 +268,7 @@ int collide_combine(Handle &hd, const double *f, int ncells, double eps, int pro
     if (rc) return rc;
     if (fused_available(hd)) {
         StageTimer t(hd, CS_K_INVERSE, s);
-        return launch_inverse_project(hd, ncells, eps, project, a, x, b, y, c, out, nullptr, s);
+        return launch_inverse_project(hd, ncells, eps, project, a, x, b, y, c, out, conv_second(hd), s);
     }
     const bool direct = (x == nullptr && y == nullptr && c == 1.0);
     double *qt = direct ? out : hd.Qt;
@@ -721,7 +722,7 @@ int cs_autotune(cs_handle_t h, int ncells, cudaStream_t s, double *ms)
         return set_error(CS_ECUDA, "cs_autotune: events");
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, hd.device);
-    const int cand[][2] = {{0, 0}, {1, 0}, {2, 1}, {2, 2}, {2, 3}, {1, 2}, {1, 3}, {1, 4}, {1, 6}};
+    const int cand[][2] = {{0, 0}, {1, 0}, {2, 1}, {2, 2}, {2, 3}, {2, 4}, {1, 2}, {1, 3}, {1, 4}, {1, 6}, {1, 8}};
     double best = 1e300;
     int bg = 0, bc = 0;
     const int keep_g = hd.tune_gpc, keep_c = hd.tune_ctas;
@@ -888,7 +889,7 @@ int cs_convolve(cs_handle_t h, const double *fhat, int ncells, double *qhat, cud
     if (int rc = ensure_workspace(hd, ncells)) return rc;
     if (int rc = launch_natural_to_spectral(hd, fhat, ncells, hd.F, s)) return rc;
     if (int rc = timed_convolve(hd, ncells, s)) return rc;
-    return launch_spectral_to_natural(hd, hd.Qh, ncells, qhat, s);
+    return launch_spectral_to_natural(hd, hd.Qh, ncells, qhat, s, conv_second(hd));
 }
 
 int cs_inverse(cs_handle_t h, const double *qhat, int ncells, double eps, double *Q, cudaStream_t s)
@@ -902,7 +903,8 @@ int cs_inverse(cs_handle_t h, const double *qhat, int ncells, double eps, double
     Handle &hd = h->h;
     if (int rc = ensure_workspace(hd, ncells)) return rc;
     if (int rc = launch_natural_to_spectral(hd, qhat, ncells, hd.Qh, s)) return rc;
-    return timed_inverse(hd, ncells, eps, Q, s);
+    StageTimer t(hd, CS_K_INVERSE, s);
+    return launch_inverse(hd, ncells, eps, Q, s);  // one given sum, no second part
 }
 
 int cs_collide(cs_handle_t h, const double *f, int ncells, double eps, double *Q, int conserve, cudaStream_t s)
@@ -1035,6 +1037,9 @@ int cs_transport_shard_stage(cs_handle_t h, const double *f_win, int ncells, int
     if (int rc = check_device_ptr(out, "out")) return rc;
     if (int rc = check_device_ptr(x, "x", true)) return rc;
     if (int rc = check_device_ptr(y, "y", true)) return rc;
+    const size_t M = hd.g.M;
+    const double *o0 = out, *o1 = out + (size_t)ncells * M, *w0 = f_win, *w1 = f_win + (size_t)(ncells + 4) * M;
+    if (o0 < w1 && w0 < o1) return set_error(CS_EINVAL, "out overlaps f_win");
     StageTimer tm(hd, CS_K_TRANSPORT, s);
     return launch_transport_stage(hd, f_win, 2, first_cell, ncells, total_cells, *dom, a, x, b, y, c, out, s);
 }

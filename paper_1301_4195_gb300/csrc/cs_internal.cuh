@@ -121,6 +121,7 @@ struct Handle {
     unsigned ws_generation = 0;  // bumped whenever the workspace moves
     // pieces of the workspace (set by layout_workspace)
     void *F = nullptr, *Qh = nullptr, *X = nullptr, *Y = nullptr;
+    void *Qh2 = nullptr;  // second partial sum of a split convolution (conv_parts == 2); aliases X
     double *Qt = nullptr, *f1 = nullptr, *r1 = nullptr, *scal = nullptr;
     double *part5 = nullptr;  // per-block partial moments of the projection
     // replayable steps (cs_step, cs_relax): one captured step per argument set
@@ -196,19 +197,28 @@ int sample_weights(Handle &hd, const int *km_host, int n, double *out_host);
 
 // ---- transform.cu
 int launch_forward(const Handle &hd, const double *f, int ncells, cudaStream_t s);   // f -> hd.F
-int launch_inverse(const Handle &hd, int ncells, double scale_eps, double *Qt, cudaStream_t s);  // hd.Qh -> Qt
-int launch_spectral_to_natural(const Handle &hd, const void *src, int ncells, double *dst, cudaStream_t s);
+// hd.Qh (+ qh2, the second partial sum of a split convolution, if not NULL) -> Qt
+int launch_inverse(const Handle &hd, int ncells, double scale_eps, double *Qt, cudaStream_t s,
+                   const void *qh2 = nullptr);
+// grouped spectral src (+ src2 if not NULL) -> [ncells][N^3][2] doubles
+int launch_spectral_to_natural(const Handle &hd, const void *src, int ncells, double *dst, cudaStream_t s,
+                               const void *src2 = nullptr);
 int launch_natural_to_spectral(const Handle &hd, const double *src, int ncells, void *dst, cudaStream_t s);
 
 // ---- fused.cu (float, N <= 16: whole-cell transforms in shared memory)
 bool fused_available(const Handle &hd);
 int launch_forward_fused(const Handle &hd, const double *f, int ncells, cudaStream_t s);
-// out = a x + b y + c P(Qt), Qt the inverse transform of hd.Qh (P = projection if project)
+// out = a x + b y + P(c Qt), Qt the inverse transform of hd.Qh (+ qh2 if not
+// NULL), P the projection if project (else the identity)
 int launch_inverse_project(const Handle &hd, int ncells, double eps, int project, double a, const double *x,
-                           double b, const double *y, double c, double *out, double *moments, cudaStream_t s);
+                           double b, const double *y, double c, double *out, const void *qh2, cudaStream_t s);
 
 // ---- convolve.cu, conv_strip.cu
-int launch_convolve(const Handle &hd, int ncells, cudaStream_t s);  // hd.F -> hd.Qh
+int launch_convolve(const Handle &hd, int ncells, cudaStream_t s);  // hd.F -> hd.Qh (and hd.Qh2)
+// 2 when the convolution of this handle leaves two partial sums (hd.Qh and
+// hd.Qh2, to be added in that order), else 1; fixed per N and precision
+int conv_parts(const Handle &hd);
+inline const void *conv_second(const Handle &hd) { return conv_parts(hd) == 2 ? hd.Qh2 : nullptr; }
 int launch_strip(const Handle &hd, int ncells, cudaStream_t s);     // float, LAYOUT_STRIP
 
 // ---- conserve.cu
@@ -223,13 +233,13 @@ int conserve_parts(int M);  // blocks per cell of the projection
 // ---- transport.cu
 // doubles of workspace the transport tables need; tables are filled by
 // launch_transport_prep once per call (geometry, wall Maxwellian flux)
-// transport tables for a grid of total_cells cells and the face fluxes of a
-// shard of ncells of them (the whole grid: ncells = total_cells)
-size_t transport_table_doubles(int N, int ncells, int total_cells);
+// transport tables (geometry, wall Maxwellian) for a grid of total_cells cells
+size_t transport_table_doubles(int N, int total_cells);
 int launch_transport_prep(const Handle &hd, int total_cells, const cs_domain &dom, cudaStream_t s);
 // one transport stage, out = a x + b y + c rhs(fin), rhs the finite-volume
 // operator, for cells first .. first+ncells-1, read from fin with `ghost`
-// leading ghost cells (0: fin holds exactly the cells; 2: a window)
+// leading ghost cells (0: fin holds exactly the cells; 2: a window); out must
+// not overlap fin (it may alias x or y)
 int launch_transport_stage(const Handle &hd, const double *fin, int ghost, int first, int ncells, int total_cells,
                            const cs_domain &dom, double a, const double *x, double b, const double *y, double c,
                            double *out, cudaStream_t s);

@@ -129,14 +129,16 @@ extern "C" int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, do
     fwd.Y = B;
     fwd.F = C;
     fwd.Qh = A;
+    fwd.Qh2 = B;  // a split convolution's second partial sum (Y is free again after the forward passes)
     Handle inv = view_of(hd);
     inv.Qh = A;
+    inv.Qh2 = B;  // read before the inverse writes anything (whole-cell kernel, the only split consumer)
     inv.X = B;
     inv.Y = C;
     inv.part5 = (double *)(C + buffer_bytes(hd, ncells));
     if (int rc = launch_forward(fwd, f, ncells, stream)) return rc;
     if (int rc = launch_convolve(fwd, ncells, stream)) return rc;
-    if (int rc = launch_inverse(inv, ncells, eps, Q, stream)) return rc;
+    if (int rc = launch_inverse(inv, ncells, eps, Q, stream, conv_second(inv))) return rc;
     if (conserve) return launch_conserve(inv, Q, ncells, 1, 0.0, nullptr, 0.0, nullptr, 1.0, Q, nullptr, stream);
     return CS_OK;
 }

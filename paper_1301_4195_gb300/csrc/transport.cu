@@ -11,13 +11,15 @@
 //
 // Double precision is slow on this part (1/64 of float), so the kernels keep
 // the double work per point small:
-//   prep_mw_kernel, prep_geo_kernel   once per call: v1 M_w(v) per velocity
-//                 and its discrete flux D = sum_{v1>0} v1 M_w dv^3 (partials
-//                 summed in a fixed order), cell geometry (inverse distances,
-//                 so no division later), v1 per velocity index;
-//   sigma_kernel  per Heun stage: sigma_w = (outgoing flux of cell 0) / D;
-//   face_kernel   per stage: every face flux once (one slope each);
-//   update_kernel per stage: out = a x + b y + c (F_{j-1/2} - F_{j+1/2}) / dx_j.
+//   prep_kernel   once per call, one entry per thread: v1 M_w(v) per
+//                 velocity (factors, normalisation and its discrete flux
+//                 D = sum_{v1>0} v1 M_w dv^3 from the host), cell geometry
+//                 (inverse distances, so no division later), v1 per index;
+//   stage_kernel  per Runge-Kutta stage: a block takes 4 cells x 128
+//                 velocities, computes their 5 faces (one slope each, from 8
+//                 loaded cells) and out = a x + b y + c (F_{j-1/2} - F_{j+1/2}) / dx_j;
+//                 the block at the wall first sums sigma_w = (outgoing flux of
+//                 cell 0) / D itself, so no kernel boundary separates the two.
 //
 // The stage kernels work on a shard: cells first .. first+ncl-1 of a grid of
 // nct cells (the whole grid is first = 0, ncl = nct).  Cell j of the grid is
@@ -26,30 +28,31 @@
 // first+ncl+1), which is all a shard's faces read: the flux through face c
 // needs cells c-2 .. c+1.  The geometry tables always cover the whole grid,
 // so a shard computes every face exactly as the unsharded grid does.
+#include <algorithm>
+#include <cmath>
+
 #include "cs_internal.cuh"
 
 namespace cs {
 
 namespace {
 
-constexpr int kSigmaThreads = 512;
-
 // Layout of the transport tables in the workspace `scal` (doubles):
-//   [0] sigma_w   [1] D
+//   [0] unused   [1] D
 //   inv_fwd[j] = 1 / (x_{j+1} - x_j),      j = 0 .. nc   (ghost centres past the end)
 //   inv_ctr[j] = 1 / (x_{j+1} - x_{j-1}),  j = 1 .. nc
 //   inv_dx[j]  = 1 / dx_j,                 j = 0 .. nc - 1
-//   xs[j]      = cell centre,               j = 0 .. nc + 1
+//   hdx[j]     = dx_j / 2,                 j = 0 .. nc - 1
 //   v1[k]      = dv (k - N/2),              k = 0 .. N - 1
 //   mw[v]      = v1 M_w(v) for v1 > 0, else 0,  v = 0 .. N^3 - 1
-//   part[b]    = partial sums of D, one per block of prep_mw_kernel
-// and the face fluxes F[c][v] of the shard's faces, c = 0 .. ncl, after them
-// (nc above is the whole grid's cell count).
-constexpr int kPrepThreads = 256;
-constexpr int kMaxPrepBlocks = (kMaxN * kMaxN * kMaxN + kPrepThreads - 1) / kPrepThreads;
+// (nc above is the whole grid's cell count).  The centre distances come from
+// the widths, x_{j+1} - x_j = (dx_j + dx_{j+1}) / 2 and x_{j+1} - x_{j-1} =
+// dx_{j-1}/2 + dx_j + dx_{j+1}/2, with the ghosts past the end as wide as the
+// last cell: every entry is local, so no running sum over the grid is needed.
+constexpr int kPrepThreads = 64;
 
 struct Tab {
-    double *scal, *inv_fwd, *inv_ctr, *inv_dx, *xs, *v1, *mw, *part, *face;
+    double *scal, *inv_fwd, *inv_ctr, *inv_dx, *hdx, *v1, *mw;
 };
 
 __host__ __device__ inline Tab tab_of(double *scal, int nc, int N)
@@ -59,99 +62,48 @@ __host__ __device__ inline Tab tab_of(double *scal, int nc, int N)
     t.inv_fwd = scal + 8;
     t.inv_ctr = t.inv_fwd + (nc + 2);
     t.inv_dx = t.inv_ctr + (nc + 2);
-    t.xs = t.inv_dx + (nc + 2);
-    t.v1 = t.xs + (nc + 2);
+    t.hdx = t.inv_dx + (nc + 2);
+    t.v1 = t.hdx + (nc + 2);
     t.mw = t.v1 + ((N + 7) & ~7);
-    t.part = t.mw + (size_t)N * N * N;
-    t.face = t.part + kMaxPrepBlocks;
     return t;
 }
 
-struct Wall {
-    double T, V1, V2, V3;
+// The wall Maxwellian factorised per axis,
+//   M_w = (2 pi T_w)^{-3/2} e_1(v1) e_2(v2) e_3(v3),  e_a(v) = exp(-(v - V_a)^2 / (2 T_w)),
+// with the 3N factors, the normalisation and D = sum_{v1>0} v1 M_w dv^3
+// (factorised the same way) evaluated on the host: the device then needs no
+// double-precision transcendental at all (each costs ~100 slow double ops).
+struct WallTab {
+    double e[3][kMaxN];
+    double norm, D;
 };
 
-// v1 M_w(v) for every velocity and one partial sum of D per block
-__global__ void __launch_bounds__(kPrepThreads) prep_mw_kernel(Geom g, Wall w, int nc, double *__restrict__ scal)
+// The transport tables in one launch, one entry per thread: v1 M_w(v) for
+// every velocity, the geometry of every face from the widths, v1, D.
+__global__ void __launch_bounds__(kPrepThreads) prep_kernel(Geom g, WallTab w, int nc, const double *__restrict__ dx,
+                                                            double *__restrict__ scal)
 {
-    __shared__ double sh[kPrepThreads / 32];
     const Tab t = tab_of(scal, nc, g.N);
     const int N = g.N;
-    const double norm = pow(2.0 * M_PI * w.T, -1.5), w3 = g.dv * g.dv * g.dv;
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    double D = 0.0;
-    if (v < g.M) {
-        const double v1 = g.dv * (v / (N * N) - g.h);
-        const double v2 = g.dv * ((v / N) % N - g.h);
-        const double v3 = g.dv * (v % N - g.h);
-        double m = 0.0;
-        if (v1 > 0) {
-            const double e = (v1 - w.V1) * (v1 - w.V1) + (v2 - w.V2) * (v2 - w.V2) + (v3 - w.V3) * (v3 - w.V3);
-            m = v1 * norm * exp(-e / (2.0 * w.T));
-            D = m * w3;
+    const int i = blockIdx.x * kPrepThreads + threadIdx.x;
+    if (i < g.M) {
+        const int k1 = i / (N * N), k2 = (i / N) % N, k3 = i % N;
+        const double v1 = g.dv * (k1 - g.h);
+        t.mw[i] = v1 > 0 ? v1 * w.norm * (w.e[0][k1] * w.e[1][k2] * w.e[2][k3]) : 0.0;
+    }
+    if (i <= nc) {
+        const double dl = i >= 1 ? dx[i - 1] : 0.0;          // dx_{j-1}
+        const double dj = i < nc ? dx[i] : dx[nc - 1];        // dx_j (ghost: the last width)
+        const double dr = i + 1 < nc ? dx[i + 1] : dx[nc - 1];  // dx_{j+1}
+        t.inv_fwd[i] = 2.0 / (dj + dr);
+        if (i >= 1) t.inv_ctr[i] = 2.0 / (dl + 2.0 * dj + dr);
+        if (i < nc) {
+            t.inv_dx[i] = 1.0 / dj;
+            t.hdx[i] = 0.5 * dj;
         }
-        t.mw[v] = m;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) D += __shfl_xor_sync(0xffffffffu, D, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = D;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int k = 0; k < kPrepThreads / 32; ++k) s += sh[k];
-        t.part[blockIdx.x] = s;
-    }
-}
-
-// cell geometry, v1 table and D (partials summed in a fixed order)
-__global__ void __launch_bounds__(256) prep_geo_kernel(Geom g, int nc, int nparts, const double *__restrict__ dx,
-                                                       double *__restrict__ scal)
-{
-    const Tab t = tab_of(scal, nc, g.N);
-    if (threadIdx.x == 0) {
-        double edge = 0.0;
-        for (int j = 0; j < nc; ++j) {
-            t.xs[j] = edge + 0.5 * dx[j];
-            edge += dx[j];
-        }
-        t.xs[nc] = t.xs[nc - 1] + dx[nc - 1];
-        t.xs[nc + 1] = t.xs[nc] + dx[nc - 1];
-        double D = 0.0;
-        for (int b = 0; b < nparts; ++b) D += t.part[b];
-        t.scal[1] = D;
-    }
-    if (threadIdx.x < g.N) t.v1[threadIdx.x] = g.dv * ((int)threadIdx.x - g.h);
-    __syncthreads();
-    for (int j = threadIdx.x; j <= nc; j += blockDim.x) {
-        t.inv_fwd[j] = 1.0 / (t.xs[j + 1] - t.xs[j]);
-        if (j >= 1) t.inv_ctr[j] = 1.0 / (t.xs[j + 1] - t.xs[j - 1]);
-        if (j < nc) t.inv_dx[j] = 1.0 / dx[j];
-    }
-}
-
-// sigma_w of the stage input: outgoing flux of the reconstructed wall-face values
-__global__ void __launch_bounds__(kSigmaThreads) sigma_kernel(Geom g, const double *__restrict__ f, int nc,
-                                                              const double *__restrict__ dx, double *__restrict__ scal)
-{
-    __shared__ double sh[32];
-    const Tab t = tab_of(scal, nc, g.N);
-    const int NN = g.N * g.N;
-    const int half = g.h * NN;  // velocities with v1 < 0 come first (index k1 < N/2)
-    const double i01 = t.inv_fwd[0], hx = 0.5 * dx[0];
-    double out = 0.0;
-    for (int v = threadIdx.x; v < half; v += blockDim.x) {
-        const double f0 = f[v], f1 = f[(size_t)g.M + v];
-        out -= t.v1[v / NN] * (f0 - hx * ((f1 - f0) * i01));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) out += __shfl_xor_sync(0xffffffffu, out, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = out;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k];
-        t.scal[0] = s * (g.dv * g.dv * g.dv) / t.scal[1];
-    }
+    if (i < N) t.v1[i] = g.dv * (i - g.h);
+    if (i == 0) t.scal[1] = w.D;
 }
 
 // 3-argument minmod on the bit patterns: 0 unless all three share a sign,
@@ -168,83 +120,138 @@ __device__ __forceinline__ double minmod3(double a, double b, double c)
     return __longlong_as_double((long long)(m | ((unsigned long long)ia & ~mask)));
 }
 
-// flux through face c (between cells c-1 and c), c = first .. first+ncl, one
-// thread per (face, v); face c is stored at c - first
-__global__ void face_kernel(Geom g, const double *__restrict__ fin, int first, int ncl, int nc, int G,
-                            const double *__restrict__ dx, const double *__restrict__ ffar, double *__restrict__ scal)
-{
-    const Tab t = tab_of(scal, nc, g.N);
-    const int M = g.M, NN = g.N * g.N;
-    const int c = first + blockIdx.y;
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < M; v += gridDim.x * blockDim.x) {
-        const double v1 = t.v1[v / NN];
-        // grid cell j (j = nc, nc + 1: far-end ghosts) as stored in fin
-        auto val = [&](int j) {
-            if (j >= nc) {
-                if (v1 < 0) return ffar[v];
-                j = nc - 1;
-            }
-            return fin[(ptrdiff_t)(j - first + G) * M + v];
-        };
-        double F;
-        if (c == 0) {
-            if (v1 > 0) {
-                F = t.scal[0] * t.mw[v];
-            } else {
-                const double f0 = val(0), f1 = val(1);
-                F = v1 * (f0 - 0.5 * dx[0] * ((f1 - f0) * t.inv_fwd[0]));
-            }
-        } else {
-            // upwind cell u: c-1 for v1 >= 0, c for v1 < 0 (u = nc is a ghost, slope 0)
-            const bool right = v1 >= 0;
-            const int u = right ? c - 1 : c;
-            const double fu = val(u);
-            double s = 0.0;
-            if (u < nc) {
-                const double fp = val(u + 1);
-                if (u == 0) {
-                    s = (fp - fu) * t.inv_fwd[0];
-                } else {
-                    const double fm = val(u - 1);
-                    s = minmod3((fp - fu) * t.inv_fwd[u], (fu - fm) * t.inv_fwd[u - 1], (fp - fm) * t.inv_ctr[u]);
-                }
-            }
-            const double half = 0.5 * (u < nc ? dx[u] : dx[nc - 1]);
-            F = v1 * (right ? fma(half, s, fu) : fma(-half, s, fu));
-        }
-        t.face[(size_t)blockIdx.y * M + v] = F;
-    }
-}
+constexpr int kStageThreads = 128;  // velocities per block
+constexpr int kStageCells = 4;      // cells per block: their 5 faces from 8 loaded cells per velocity
 
-__global__ void update_kernel(Geom g, int first, int ncl, int nc, const double *__restrict__ scal, double a,
-                              const double *x, double b, const double *y, double c, double *out)
+// One transport stage for the velocities of block x and the shard cells
+// cl0 .. cl1-1 (cl0 = 4 blockIdx.y): the faces first+cl0 .. first+cl1 once
+// each, then out = a x + b y + c (F_{j-1/2} - F_{j+1/2}) / dx_j.  A block
+// whose first face is the wall also computes sigma_w from grid cells 0 and 1
+// of the stage input; every such block sums in the same order, so all of them
+// hold the same value.  Reads fin only, writes out only: out must not overlap
+// fin (it may alias x or y, read and written by the same thread).
+__global__ void __launch_bounds__(kStageThreads) stage_kernel(Geom g, const double *__restrict__ fin, int first,
+                                                              int ncl, int nc, int G, const double *__restrict__ dx,
+                                                              const double *__restrict__ ffar,
+                                                              const double *__restrict__ scal, double a, const double *x,
+                                                              double b, const double *y, double c, double *out)
 {
+    __shared__ double sh[kStageThreads / 32];
+    __shared__ double s_coef[kStageCells];  // c / dx_j of the block's cells
     const Tab t = tab_of(const_cast<double *>(scal), nc, g.N);
-    const size_t n = (size_t)ncl * g.M;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const int cell = first + (int)(i / g.M);
-        const double rhs = (t.face[i] - t.face[i + g.M]) * t.inv_dx[cell];
-        double o = c * rhs;
-        if (x) o = fma(a, x[i], o);
-        if (y) o = fma(b, y[i], o);
-        out[i] = o;
+    const int M = g.M, NN = g.N * g.N;
+    const int cl0 = blockIdx.y * kStageCells;
+    const int ncb = min(kStageCells, ncl - cl0);  // cells of this block
+    const int v = blockIdx.x * kStageThreads + threadIdx.x;
+    const int c0 = first + cl0;                   // grid index of the block's first cell and face
+
+    double sigma = 0.0;
+    if (c0 == 0) {  // block-uniform
+        const int half = g.h * NN;  // velocities with v1 < 0 come first
+        const double i01 = t.inv_fwd[0], hx = 0.5 * dx[0];
+        const double *f0p = fin + (size_t)G * M;
+        double o = 0.0;
+        for (int u = threadIdx.x; u < half; u += kStageThreads) {
+            const double f0 = f0p[u], f1 = f0p[(size_t)M + u];
+            o -= t.v1[u / NN] * (f0 - hx * ((f1 - f0) * i01));
+        }
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) o += __shfl_xor_sync(0xffffffffu, o, s);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = o;
+        __syncthreads();
+        double tot = 0.0;
+#pragma unroll
+        for (int k = 0; k < kStageThreads / 32; ++k) tot += sh[k];
+        sigma = tot * (g.dv * g.dv * g.dv) / t.scal[1];
+    }
+    if (threadIdx.x < ncb) s_coef[threadIdx.x] = c * t.inv_dx[c0 + threadIdx.x];
+    __syncthreads();
+    if (v >= M) return;
+    const double v1 = t.v1[v / NN];
+    // grid cells c0-2 .. c0+ncb+1 at this velocity; j >= nc are the far-end
+    // ghosts (f_far for v1 < 0, else the last cell); j < 0 is never read
+    double fv[kStageCells + 4];
+#pragma unroll
+    for (int i = 0; i < kStageCells + 4; ++i) {
+        const int j = c0 - 2 + i;
+        fv[i] = 0.0;
+        if (i <= ncb + 3 && j >= 0) {
+            if (j < nc)
+                fv[i] = fin[(ptrdiff_t)(j - first + G) * M + v];
+            else  // j >= nc only where the block reaches the grid's last cell
+                fv[i] = v1 < 0 ? ffar[v] : fin[(ptrdiff_t)(nc - 1 - first + G) * M + v];
+        }
+    }
+    // forward difference quotients of the loaded cells, d[i] = (f_{j+1} - f_j)
+    // / (x_{j+1} - x_j) for j = c0-2+i: each is the forward quotient of one
+    // face's upwind cell and the backward quotient of the next face's
+    double d[kStageCells + 3];
+#pragma unroll
+    for (int i = 0; i < kStageCells + 3; ++i) {
+        const int j = c0 - 2 + i;
+        d[i] = (i <= ncb + 2 && j >= 0) ? (fv[i + 1] - fv[i]) * t.inv_fwd[j] : 0.0;
+    }
+    double Fprev = 0.0;
+#pragma unroll
+    for (int i = 0; i <= kStageCells; ++i) {
+        if (i > ncb) break;
+        const int cf = c0 + i;  // face between grid cells cf-1 and cf
+        double F;
+        if (cf == 0) {
+            F = v1 > 0 ? sigma * t.mw[v] : v1 * (fv[i + 2] - t.hdx[0] * d[i + 2]);
+        } else {
+            // upwind cell u: cf-1 for v1 >= 0, cf for v1 < 0 (u = nc is a ghost, slope 0);
+            // register slots are fixed: i is a compile-time index
+            const bool right = v1 >= 0;
+            const int u = right ? cf - 1 : cf;
+            const double fm = right ? fv[i] : fv[i + 1];      // cell u-1
+            const double fu = right ? fv[i + 1] : fv[i + 2];  // cell u
+            const double fp = right ? fv[i + 2] : fv[i + 3];  // cell u+1
+            const double dF = right ? d[i + 1] : d[i + 2];     // (f_{u+1} - f_u) / (x_{u+1} - x_u)
+            const double dB = right ? d[i] : d[i + 1];         // (f_u - f_{u-1}) / (x_u - x_{u-1})
+            double sl = 0.0;
+            if (u < nc) sl = u == 0 ? dF : minmod3(dF, dB, (fp - fm) * t.inv_ctr[u]);
+            const double hw = u < nc ? t.hdx[u] : t.hdx[nc - 1];
+            F = v1 * (right ? fma(hw, sl, fu) : fma(-hw, sl, fu));
+        }
+        if (i > 0) {  // cell cf-1 = local cl0 + i - 1
+            const size_t idx = (size_t)(cl0 + i - 1) * M + v;
+            double o = (Fprev - F) * s_coef[i - 1];
+            if (x) o = fma(a, x[idx], o);
+            if (y) o = fma(b, y[idx], o);
+            out[idx] = o;
+        }
+        Fprev = F;
     }
 }
 
 }  // namespace
 
-size_t transport_table_doubles(int N, int ncells, int total_cells)
+size_t transport_table_doubles(int N, int total_cells)
 {
-    return 8 + 4 * ((size_t)total_cells + 2) + ((N + 7) & ~7) + kMaxPrepBlocks + (size_t)N * N * N * (ncells + 2);
+    return 8 + 4 * ((size_t)total_cells + 2) + ((N + 7) & ~7) + (size_t)N * N * N;
 }
 
 int launch_transport_prep(const Handle &hd, int total_cells, const cs_domain &dom, cudaStream_t s)
 {
-    const Wall w{dom.wall_T, dom.wall_V[0], dom.wall_V[1], dom.wall_V[2]};
-    const int nparts = (hd.g.M + kPrepThreads - 1) / kPrepThreads;
-    prep_mw_kernel<<<nparts, kPrepThreads, 0, s>>>(hd.g, w, total_cells, hd.scal);
-    prep_geo_kernel<<<1, 256, 0, s>>>(hd.g, total_cells, nparts, dom.dx, hd.scal);
-    CS_LAUNCHED(2, s, "transport tables");
+    const Geom &g = hd.g;
+    WallTab w{};
+    const double V[3] = {dom.wall_V[0], dom.wall_V[1], dom.wall_V[2]};
+    double S[3] = {0.0, 0.0, 0.0};  // S_1 = sum_{v1>0} v1 e_1, S_2 = sum e_2, S_3 = sum e_3
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < g.N; ++k) {
+            const double v = g.dv * (k - g.h), d = v - V[a];
+            w.e[a][k] = std::exp(-(d * d) / (2.0 * dom.wall_T));
+            if (a > 0)
+                S[a] += w.e[a][k];
+            else if (v > 0)
+                S[0] += v * w.e[0][k];
+        }
+    w.norm = std::pow(2.0 * M_PI * dom.wall_T, -1.5);
+    w.D = w.norm * S[0] * S[1] * S[2] * (g.dv * g.dv * g.dv);
+    const int n = std::max(g.M, total_cells + 1);
+    prep_kernel<<<(n + kPrepThreads - 1) / kPrepThreads, kPrepThreads, 0, s>>>(g, w, total_cells, dom.dx, hd.scal);
+    CS_LAUNCHED(1, s, "transport tables");
     return CS_OK;
 }
 
@@ -252,19 +259,11 @@ int launch_transport_stage(const Handle &hd, const double *fin, int ghost, int f
                            const cs_domain &dom, double a, const double *x, double b, const double *y, double c,
                            double *out, cudaStream_t s)
 {
-    const int M = hd.g.M;
-    int launched = 2;
-    if (first == 0) {  // the wall face belongs to this shard: sigma_w from grid cells 0 and 1
-        sigma_kernel<<<1, kSigmaThreads, 0, s>>>(hd.g, fin + (size_t)ghost * M, total_cells, dom.dx, hd.scal);
-        ++launched;
-    }
-    const int tpb = 256;
-    dim3 fgrid((unsigned)((M + tpb - 1) / tpb), (unsigned)(ncells + 1));
-    face_kernel<<<fgrid, tpb, 0, s>>>(hd.g, fin, first, ncells, total_cells, ghost, dom.dx, dom.f_far, hd.scal);
-    const size_t n = (size_t)ncells * M;
-    const unsigned blocks = (unsigned)((n + tpb - 1) / tpb < 65535 ? (n + tpb - 1) / tpb : 65535);
-    update_kernel<<<blocks, tpb, 0, s>>>(hd.g, first, ncells, total_cells, hd.scal, a, x, b, y, c, out);
-    CS_LAUNCHED(launched, s, "transport stage");
+    const dim3 grid((unsigned)((hd.g.M + kStageThreads - 1) / kStageThreads),
+                    (unsigned)((ncells + kStageCells - 1) / kStageCells));
+    stage_kernel<<<grid, kStageThreads, 0, s>>>(hd.g, fin, first, ncells, total_cells, ghost, dom.dx, dom.f_far,
+                                                hd.scal, a, x, b, y, c, out);
+    CS_LAUNCHED(1, s, "transport stage");
     return CS_OK;
 }
 

@@ -283,9 +283,9 @@ def test_graph_replay_matches_direct_launches(cs, prec):
     # a replay counts the graph's kernel nodes: the same kernels as the direct launches
     assert replayed == direct and direct % 3 == 0
     if prec == "fp32":
-        # per step: transport tables 2, four transport stages x 3, two collision
+        # per step: transport tables 1, four transport stages x 1, two collision
         # evaluations x (forward, convolution, inverse + projection)
-        assert direct == 3 * 20
+        assert direct == 3 * 11
     ga, gb = dev(f), dev(f)
     h.relax(ga, 0.01, 4)
     cs.cs_profile(h.ptr, True)

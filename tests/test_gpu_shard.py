@@ -112,8 +112,11 @@ def test_stage_needs_prepared_tables(cs):
     h.transport(fa, dxd, fard, 1.5, (0.0, 0.0, 0.0), 0.01)
     with pytest.raises(cs.CSError):
         cs.cs_transport_shard_stage(h.ptr, w, n, 0, total, dom, 0.0, None, 0.0, None, 1.0, out)
-    # shards outside the grid
+    # out inside the window it reads
     cs.cs_transport_shard_prepare(h.ptr, n, 0, total, dom)
+    with pytest.raises(cs.CSError):
+        cs.cs_transport_shard_stage(h.ptr, w, n, 0, total, dom, 0.0, None, 0.0, None, 1.0, w[2:2 + n])
+    # shards outside the grid
     for first, nn in ((-1, 5), (6, 5), (0, 1)):
         with pytest.raises(cs.CSError):
             cs.cs_transport_shard_stage(h.ptr, w, nn, first, total, dom, 0.0, None, 0.0, None, 1.0, out)
