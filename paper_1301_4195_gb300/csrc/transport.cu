@@ -3,6 +3,12 @@
 //   F_{j+1/2} = v1 (f_j + dx_j/2 s_j)            (v1 >= 0)
 //             = v1 (f_{j+1} - dx_{j+1}/2 s_{j+1}) (v1 <  0),
 //   s_j = minmod of the forward, backward and central difference quotients.
+// On any grid the central quotient is a convex combination of the other two,
+// (f_{j+1} - f_{j-1}) / (x_{j+1} - x_{j-1}) = (a (x_{j+1} - x_j) + b (x_j - x_{j-1})) / (x_{j+1} - x_{j-1}),
+// so it lies between them and the three-argument minmod equals the
+// two-argument one of the forward and backward quotients a, b; the kernels
+// take the latter (two double operations less per face; in floating point
+// the two can differ only where a and b agree to rounding).
 // Boundaries: the wall face at x = 0 carries v1 sigma_w M_w(v) for v1 > 0
 // (diffuse reflection, Sec. 2.1 eq. BC) with sigma_w making the discrete net
 // mass flux zero; cell 0 takes the one-sided slope (linear extrapolation into
@@ -40,7 +46,6 @@ namespace {
 // Layout of the transport tables in the workspace `scal` (doubles):
 //   [0] unused   [1] D
 //   inv_fwd[j] = 1 / (x_{j+1} - x_j),      j = 0 .. nc   (ghost centres past the end)
-//   inv_ctr[j] = 1 / (x_{j+1} - x_{j-1}),  j = 1 .. nc
 //   inv_dx[j]  = 1 / dx_j,                 j = 0 .. nc - 1
 //   hdx[j]     = dx_j / 2,                 j = 0 .. nc - 1
 //   v1[k]      = dv (k - N/2),              k = 0 .. N - 1
@@ -52,7 +57,7 @@ namespace {
 constexpr int kPrepThreads = 64;
 
 struct Tab {
-    double *scal, *inv_fwd, *inv_ctr, *inv_dx, *hdx, *v1, *mw;
+    double *scal, *inv_fwd, *inv_dx, *hdx, *v1, *mw;
 };
 
 __host__ __device__ inline Tab tab_of(double *scal, int nc, int N)
@@ -60,8 +65,7 @@ __host__ __device__ inline Tab tab_of(double *scal, int nc, int N)
     Tab t;
     t.scal = scal;
     t.inv_fwd = scal + 8;
-    t.inv_ctr = t.inv_fwd + (nc + 2);
-    t.inv_dx = t.inv_ctr + (nc + 2);
+    t.inv_dx = t.inv_fwd + (nc + 2);
     t.hdx = t.inv_dx + (nc + 2);
     t.v1 = t.hdx + (nc + 2);
     t.mw = t.v1 + ((N + 7) & ~7);
@@ -92,11 +96,9 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(Geom g, WallTab w, i
         t.mw[i] = v1 > 0 ? v1 * w.norm * (w.e[0][k1] * w.e[1][k2] * w.e[2][k3]) : 0.0;
     }
     if (i <= nc) {
-        const double dl = i >= 1 ? dx[i - 1] : 0.0;          // dx_{j-1}
         const double dj = i < nc ? dx[i] : dx[nc - 1];        // dx_j (ghost: the last width)
         const double dr = i + 1 < nc ? dx[i + 1] : dx[nc - 1];  // dx_{j+1}
         t.inv_fwd[i] = 2.0 / (dj + dr);
-        if (i >= 1) t.inv_ctr[i] = 2.0 / (dl + 2.0 * dj + dr);
         if (i < nc) {
             t.inv_dx[i] = 1.0 / dj;
             t.hdx[i] = 0.5 * dj;
@@ -106,18 +108,15 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(Geom g, WallTab w, i
     if (i == 0) t.scal[1] = w.D;
 }
 
-// 3-argument minmod on the bit patterns: 0 unless all three share a sign,
-// else the argument of least magnitude (exact; no double compares)
-__device__ __forceinline__ double minmod3(double a, double b, double c)
+// minmod(a, b) on the bit patterns: 0 unless a and b share a sign, else the
+// argument of least magnitude (exact; no double compares)
+__device__ __forceinline__ double minmod2(double a, double b)
 {
-    const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b), ic = __double_as_longlong(c);
-    if (((ia ^ ib) | (ia ^ ic)) < 0) return 0.0;
+    const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+    if ((ia ^ ib) < 0) return 0.0;
     const unsigned long long mask = 0x7fffffffffffffffull;
-    unsigned long long m = (unsigned long long)ia & mask;
-    const unsigned long long mb = (unsigned long long)ib & mask, mc = (unsigned long long)ic & mask;
-    m = mb < m ? mb : m;
-    m = mc < m ? mc : m;
-    return __longlong_as_double((long long)(m | ((unsigned long long)ia & ~mask)));
+    const unsigned long long ma = (unsigned long long)ia & mask, mb = (unsigned long long)ib & mask;
+    return ma < mb ? a : b;
 }
 
 constexpr int kStageThreads = 128;  // velocities per block
@@ -204,13 +203,11 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(Geom g, const doub
             // register slots are fixed: i is a compile-time index
             const bool right = v1 >= 0;
             const int u = right ? cf - 1 : cf;
-            const double fm = right ? fv[i] : fv[i + 1];      // cell u-1
             const double fu = right ? fv[i + 1] : fv[i + 2];  // cell u
-            const double fp = right ? fv[i + 2] : fv[i + 3];  // cell u+1
             const double dF = right ? d[i + 1] : d[i + 2];     // (f_{u+1} - f_u) / (x_{u+1} - x_u)
             const double dB = right ? d[i] : d[i + 1];         // (f_u - f_{u-1}) / (x_u - x_{u-1})
             double sl = 0.0;
-            if (u < nc) sl = u == 0 ? dF : minmod3(dF, dB, (fp - fm) * t.inv_ctr[u]);
+            if (u < nc) sl = u == 0 ? dF : minmod2(dF, dB);
             const double hw = u < nc ? t.hdx[u] : t.hdx[nc - 1];
             F = v1 * (right ? fma(hw, sl, fu) : fma(-hw, sl, fu));
         }
@@ -229,7 +226,7 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(Geom g, const doub
 
 size_t transport_table_doubles(int N, int total_cells)
 {
-    return 8 + 4 * ((size_t)total_cells + 2) + ((N + 7) & ~7) + (size_t)N * N * N;
+    return 8 + 3 * ((size_t)total_cells + 2) + ((N + 7) & ~7) + (size_t)N * N * N;
 }
 
 int launch_transport_prep(const Handle &hd, int total_cells, const cs_domain &dom, cudaStream_t s)
