@@ -232,7 +232,7 @@ def run_ours(args):
     value = world * pairs_step / (ms_step * 1e-3)
 
     # roofline of the dominant kernel (the convolution), timed live above:
-    # FP32 FMA-pipe instructions, 6 per (pair, cell) (4 FFMA + 2 FMUL), against
+    # FP32 FMA-pipe lane operations, 6 per (pair, cell) (one FMUL2 + two FFMA2), against
     # 152 SMs x 128 lanes x 2070 MHz; flops (10 per pair) reported beside it
     conv_ms, conv_n = prof["convolve"]
     conv_avg = conv_ms / max(conv_n, 1)
@@ -296,7 +296,7 @@ def run_ours(args):
         n32 = {"workload": describe("wall32"), "value": 2 * nc2 * N2 ** 6 / (msb / kb * 1e-3),
                "ms_per_step": msb / kb, "conv_ms": cavg,
                "roofline": {"bound": "alu", "achieved": 6.0 * pc2 / (cavg * 1e-3) / 1e12, "peak": peak_tops,
-                            "unit": "T FP32-FMA-pipe instructions/s",
+                            "unit": "T FP32 FMA-pipe lane-ops/s",
                             "frac": 6.0 * pc2 / (cavg * 1e-3) / 1e12 / peak_tops,
                             "tflops": fl2 / (cavg * 1e-3) / 1e12,
                             "flop_frac": fl2 / (cavg * 1e-3) / 1e12 / peak_tflops,
@@ -316,7 +316,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "gpu_launches_per_step": launches / args.steps,
         "roofline": {"bound": "alu", "achieved": achieved_ops, "peak": peak_tops,
-                     "unit": "T FP32-FMA-pipe instructions/s", "frac": achieved_ops / peak_tops,
+                     "unit": "T FP32 FMA-pipe lane-ops/s", "frac": achieved_ops / peak_tops,
                      "traffic": TRAFFIC.get((N, ncells)),
                      "kernel": "conv_strip_kernel (step a2)", "avg_launch_ms": conv_avg,
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz (max SM clock)",

@@ -122,13 +122,40 @@ __device__ __forceinline__ void two_sum(float &hi, float &lo, float p)
     lo = __fadd_rn(lo, e);
 }
 
-__device__ __forceinline__ void cmad(float2 &acc, float g, float2 a, float2 b)
+// Complex multiply-add acc += g a b on packed float pairs (f32x2 instructions,
+// half the issue slots of the scalar form): axx = (a.x, a.x), ayy = (a.y, a.y),
+// bs = (-b.y, b.x), gg = (g, g);
+//   t = axx * b = (a.x b.x, a.x b.y);  t += ayy * bs  ->  t = a b;  acc += gg * t.
+__device__ __forceinline__ void cmad2(float2 &acc, float2 gg, float2 axx, float2 ayy, float2 b, float2 bs)
 {
-    const float tr = fmaf(a.x, b.x, -a.y * b.y);
-    const float ti = fmaf(a.x, b.y, a.y * b.x);
-    acc.x = fmaf(g, tr, acc.x);
-    acc.y = fmaf(g, ti, acc.y);
+    float2 t = __fmul2_rn(axx, b);
+    t = __ffma2_rn(ayy, bs, t);
+    acc = __ffma2_rn(gg, t, acc);
 }
+
+__device__ __forceinline__ float2 dup_x(float2 a) { return make_float2(a.x, a.x); }
+__device__ __forceinline__ float2 dup_y(float2 a) { return make_float2(a.y, a.y); }
+__device__ __forceinline__ float2 rot_i(float2 b) { return make_float2(-b.y, b.x); }  // i b
+
+// K consecutive weights from entry e0 (a multiple of 4), read with 128-bit
+// loads, each as the packed pair (w, w) cmad2 takes.  (Storing every weight
+// twice in the table instead measured slower: it doubles the shared-memory
+// reads of the weights.)
+template <int K>
+__device__ __forceinline__ void wrow(const float *g, int e0, float2 (&w)[K])
+{
+    const float4 *p = reinterpret_cast<const float4 *>(g + e0);
+#pragma unroll
+    for (int q = 0; q < K / 4; ++q) {
+        const float4 v = p[q];
+        w[4 * q] = make_float2(v.x, v.x);
+        w[4 * q + 1] = make_float2(v.y, v.y);
+        w[4 * q + 2] = make_float2(v.z, v.z);
+        w[4 * q + 3] = make_float2(v.w, v.w);
+    }
+}
+
+__device__ __forceinline__ float2 wpair(const float *g, int e) { return make_float2(g[e], g[e]); }
 
 // UB uniform rows starting at row m3 = m3b: window value t is the partner at
 // s3 = smin + t; entry (u, j) uses t = j - u + UB - 1.  Weights: UB rows of K.
@@ -137,21 +164,24 @@ __device__ __forceinline__ void uniform_block(const float2 *__restrict__ arow, c
                                               const float *__restrict__ g, int m3b, int smin, int lane,
                                               float2 (&acc)[K])
 {
-    float2 a[UB], bw[UB + K - 1];
-#pragma unroll
-    for (int u = 0; u < UB; ++u) a[u] = arow[(m3b + u) * kGroup + lane];
-#pragma unroll
-    for (int t = 0; t < UB + K - 1; ++t) bw[t] = brow[(smin + t) * kGroup + lane];
+    float2 axx[UB], ayy[UB], bw[UB + K - 1], bs[UB + K - 1];
 #pragma unroll
     for (int u = 0; u < UB; ++u) {
+        const float2 a = arow[(m3b + u) * kGroup + lane];
+        axx[u] = dup_x(a);
+        ayy[u] = dup_y(a);
+    }
 #pragma unroll
-        for (int q = 0; q < K / 4; ++q) {
-            const float4 g4 = reinterpret_cast<const float4 *>(g + u * K)[q];
-            cmad(acc[4 * q + 0], g4.x, a[u], bw[4 * q + 0 - u + UB - 1]);
-            cmad(acc[4 * q + 1], g4.y, a[u], bw[4 * q + 1 - u + UB - 1]);
-            cmad(acc[4 * q + 2], g4.z, a[u], bw[4 * q + 2 - u + UB - 1]);
-            cmad(acc[4 * q + 3], g4.w, a[u], bw[4 * q + 3 - u + UB - 1]);
-        }
+    for (int t = 0; t < UB + K - 1; ++t) {
+        bw[t] = brow[(smin + t) * kGroup + lane];
+        bs[t] = rot_i(bw[t]);
+    }
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+        float2 w[K];
+        wrow<K>(g, u * K, w);
+#pragma unroll
+        for (int j = 0; j < K; ++j) cmad2(acc[j], w[j], axx[u], ayy[u], bw[j - u + UB - 1], bs[j - u + UB - 1]);
     }
 }
 
@@ -163,47 +193,45 @@ __device__ __forceinline__ void uniform_run(const float2 *arow, const float2 *br
     const int nblk = nrows / U;
     int r = 0;
 #pragma unroll 1
-    for (int b = 0; b < nblk; ++b, r += U) uniform_block<K, U>(arow, brow, g + r * K, m3s + r, C - r - (U - 1), lane, acc);
+    for (int b = 0; b < nblk; ++b, r += U)
+        uniform_block<K, U>(arow, brow, g + r * K, m3s + r, C - r - (U - 1), lane, acc);
     if constexpr (R > 0) uniform_block<K, R>(arow, brow, g + r * K, m3s + r, C - r - (R - 1), lane, acc);
 }
 
 // Strip of kind A: uniform rows m3 = 0 .. k0+H (partner s3 = k0+H-m3+j),
 // then the triangle m3 = k0+H+t, t = 1..K-1, outputs j = t..K-1 (s3 = j-t).
 // The last R = (H+1) mod U uniform rows join the triangle in a compile-time
-// tail (partners s3 = 0 .. R+K-2, weights read as float4: R*K + pad(K(K-1)/2)).
+// tail (partners s3 = 0 .. R+K-2).
 template <int N, int K, int U>
 __device__ __forceinline__ void strip_a(const float2 *arow, const float2 *brow, const float *g, int k0, int lane,
                                         float2 (&acc)[K])
 {
     constexpr int H = N / 2;
     constexpr int R = (H + 1) % U;
-    constexpr int TAILG = R * K + strip_round4(strip_tri(K));
     const int lu = k0 + H + 1;
     uniform_run<K, U, 0>(arow, brow, g, 0, k0 + H, lu - R, lane, acc);
     const float *gt = g + (lu - R) * K;
-    float gv[TAILG];
+    float2 b[R + K - 1], bs[R + K - 1];
 #pragma unroll
-    for (int q = 0; q < TAILG / 4; ++q) {
-        const float4 v = reinterpret_cast<const float4 *>(gt)[q];
-        gv[4 * q] = v.x;
-        gv[4 * q + 1] = v.y;
-        gv[4 * q + 2] = v.z;
-        gv[4 * q + 3] = v.w;
+    for (int i = 0; i < R + K - 1; ++i) {
+        b[i] = brow[i * kGroup + lane];
+        bs[i] = rot_i(b[i]);
     }
-    float2 b[R + K - 1];
-#pragma unroll
-    for (int i = 0; i < R + K - 1; ++i) b[i] = brow[i * kGroup + lane];
 #pragma unroll
     for (int i = 0; i < R; ++i) {  // full rows m3 = lu - R + i, s3 = R - 1 - i + j
         const float2 a = arow[(lu - R + i) * kGroup + lane];
+        float2 w[K];
+        wrow<K>(gt, i * K, w);
 #pragma unroll
-        for (int j = 0; j < K; ++j) cmad(acc[j], gv[i * K + j], a, b[R - 1 - i + j]);
+        for (int j = 0; j < K; ++j) cmad2(acc[j], w[j], dup_x(a), dup_y(a), b[R - 1 - i + j], bs[R - 1 - i + j]);
     }
 #pragma unroll
     for (int t = 1; t < K; ++t) {  // triangle
         const float2 a = arow[(k0 + H + t) * kGroup + lane];
 #pragma unroll
-        for (int j = t; j < K; ++j) cmad(acc[j], gv[R * K + strip_tri_a_off(K, t) + j - t], a, b[j - t]);
+        for (int j = t; j < K; ++j)
+            cmad2(acc[j], wpair(gt, R * K + strip_tri_a_off(K, t) + j - t), dup_x(a), dup_y(a), b[j - t],
+                  bs[j - t]);
     }
 }
 
@@ -218,30 +246,29 @@ __device__ __forceinline__ void strip_b(const float2 *arow, const float2 *brow, 
     constexpr int R = (N + H - K) % U;
     constexpr int TRI4 = strip_round4(strip_tri(K));
     constexpr int HEADG = TRI4 + R * K;
-    float gv[HEADG];
-#pragma unroll
-    for (int q = 0; q < HEADG / 4; ++q) {
-        const float4 v = reinterpret_cast<const float4 *>(g)[q];
-        gv[4 * q] = v.x;
-        gv[4 * q + 1] = v.y;
-        gv[4 * q + 2] = v.z;
-        gv[4 * q + 3] = v.w;
-    }
     constexpr int B0 = N - K - R + 1;  // lowest partner index of the head
-    float2 b[K + R - 1];
+    float2 b[K + R - 1], bs[K + R - 1];
 #pragma unroll
-    for (int i = 0; i < K + R - 1; ++i) b[i] = brow[(B0 + i) * kGroup + lane];
+    for (int i = 0; i < K + R - 1; ++i) {
+        b[i] = brow[(B0 + i) * kGroup + lane];
+        bs[i] = rot_i(b[i]);
+    }
 #pragma unroll
     for (int t = 0; t < K - 1; ++t) {  // triangle
         const float2 a = arow[(k0 - H + 1 + t) * kGroup + lane];
 #pragma unroll
-        for (int j = 0; j <= t; ++j) cmad(acc[j], gv[strip_tri_b_off(t) + j], a, b[N - 1 + j - t - B0]);
+        for (int j = 0; j <= t; ++j)
+            cmad2(acc[j], wpair(g, strip_tri_b_off(t) + j), dup_x(a), dup_y(a), b[N - 1 + j - t - B0],
+                  bs[N - 1 + j - t - B0]);
     }
 #pragma unroll
     for (int i = 0; i < R; ++i) {  // first R uniform rows
         const float2 a = arow[(k0 + K - H + i) * kGroup + lane];
+        float2 w[K];
+        wrow<K>(g, TRI4 + i * K, w);
 #pragma unroll
-        for (int j = 0; j < K; ++j) cmad(acc[j], gv[TRI4 + i * K + j], a, b[N - K - i + j - B0]);
+        for (int j = 0; j < K; ++j)
+            cmad2(acc[j], w[j], dup_x(a), dup_y(a), b[N - K - i + j - B0], bs[N - K - i + j - B0]);
     }
     const int lu = N + H - k0 - K;
     uniform_run<K, U, 0>(arow, brow, g + HEADG, k0 + K - H + R, N - K - R, lu - R, lane, acc);
