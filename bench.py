@@ -47,7 +47,7 @@ WORKLOADS = {
 MAX_SM_MHZ = 2070.0
 # DRAM bytes (read + write) per convolution launch from ncu captures of the
 # current kernel (profiles/), keyed by (N, cells); None where not captured
-TRAFFIC = {(16, 128): 18414592, (32, 256): 3027302912 + 64243712}
+TRAFFIC = {(16, 128): 18409472, (32, 256): 2614967296 + 68261376}
 SMS = 152
 FP32_LANES = 128
 
@@ -321,7 +321,9 @@ def run_ours(args):
                      "kernel": "conv_strip_kernel (step a2)", "avg_launch_ms": conv_avg,
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz (max SM clock)",
                      "ops_per_launch": 6.0 * pair_cells, "tflops": achieved,
-                     "flop_frac": achieved / peak_tflops, "autotuned_ms": tuned_ms},
+                     "flop_frac": achieved / peak_tflops, "autotuned_ms": tuned_ms,
+                     "launch": {"groups_per_cta": api.cs_tune_get(h32.ptr, api.CS_TUNE_GROUPS_PER_CTA),
+                                "ctas_per_sm": api.cs_tune_get(h32.ptr, api.CS_TUNE_CTAS_PER_SM)}},
         "stage_ms_per_step": step_stage_ms,
         "fp64": fp64,
         "speedup_vs_fp64": fp64["ms_per_step"] / ms_step if fp64 else None,
@@ -406,6 +408,17 @@ def cpu_baseline(args, api, inputs, torch, device, h32, h64):
     cpu = {"value": reps * nsample * N ** 6 / t_total, "unit": UNIT, "cores": cores, "kind": "oracle",
            "sample": f"{reps} x one collision evaluation of {nsample} random-mixture cells at N={N} "
                      f"(L=6, lambda=1), OpenMP over zeta outputs"}
+    # the same on one core, and one N = 32 cell on all cores (the paper's Tables 1-4
+    # time one evaluation on 1..16 cores)
+    t0 = time.perf_counter()
+    oracle.collide(f0[:4], N, L_BOX, LAM, nthreads=1)
+    cpu["single_thread"] = {"value": 4 * N ** 6 / (time.perf_counter() - t0), "cores": 1,
+                            "sample": f"one evaluation of 4 of the cells at N={N}"}
+    f32 = inputs.random_mixture_cells(32, L_BOX, 1, first_id=5000)
+    t0 = time.perf_counter()
+    oracle.collide(f32, 32, L_BOX, LAM, nthreads=cores)
+    cpu["n32_one_cell"] = {"value": 32 ** 6 / (time.perf_counter() - t0), "cores": cores,
+                           "sample": "one evaluation of one random-mixture cell at N=32"}
     err = {}
     fd = torch.from_numpy(f0).to(device)
     for name, h in (("fp32", h32), ("fp64", h64)):

@@ -284,6 +284,10 @@ int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, double eps, d
 #define CS_TUNE_CTAS_PER_SM 2
 int cs_tune(cs_handle_t h, int param, int value);
 
+/* The current value of a launch choice (0 = automatic).
+ *   value (host, out).  Errors: CS_EINVAL. */
+int cs_tune_get(cs_handle_t h, int param, int *value);
+
 /* Time the convolution's launch choices on ncells synthetic cells on
  * `stream` (synchronising), keep the fastest in the handle and return its
  * time per launch in *ms (may be NULL).  Uses the workspace (cs_reserve).

@@ -72,6 +72,7 @@ _SIGS = {
     "cs_status": (_i, [_vp]),
     "cs_collide_batched": (_i, [ctypes.POINTER(BatchEntry), _i, _d, _i, _vp]),
     "cs_tune": (_i, [_vp, _i, _i]),
+    "cs_tune_get": (_i, [_vp, _i, ctypes.POINTER(_i)]),
     "cs_autotune": (_i, [_vp, _i, _vp, ctypes.POINTER(_d)]),
     "cs_profile": (_i, [_vp, _i]),
     "cs_profile_read": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong), _i]),
@@ -252,6 +253,12 @@ CS_TUNE_CTAS_PER_SM = 2
 
 def cs_tune(h, param: int, value: int):
     _check(lib().cs_tune(h, param, value))
+
+
+def cs_tune_get(h, param: int) -> int:
+    v = _i()
+    _check(lib().cs_tune_get(h, param, ctypes.byref(v)))
+    return v.value
 
 
 def cs_autotune(h, ncells: int, stream=None) -> float:

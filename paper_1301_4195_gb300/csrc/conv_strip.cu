@@ -314,8 +314,15 @@ struct TileWalk {
 // counter, heaviest pencils first, so the tail of the launch holds only the
 // smallest items.  The stage ring runs across items: ring use u sits in
 // slot u % NST, phase u / NST.
+// Resident CTAs per SM the register allocation must allow: at N = 16 the
+// kernel is latency-bound and 128 registers (8 one-group or 4 two-group CTAs
+// per SM) measured faster than the ~134 the compiler picks on its own; for
+// the other N one CTA (no cap) measured best.
+template <int N, int GPC>
+constexpr int strip_min_ctas() { return N == 16 ? (GPC == 1 ? 8 : 4) : 1; }
+
 template <int N, int K, int U, int NST, int GPC, int S>
-__global__ void __launch_bounds__(32 * (N / K) * GPC) conv_strip_kernel(const float *__restrict__ ghat,
+__global__ void __launch_bounds__(32 * (N / K) * GPC, strip_min_ctas<N, GPC>()) conv_strip_kernel(const float *__restrict__ ghat,
                                                                         const int *__restrict__ tile0,
                                                                         const int *__restrict__ order, int nblocks,
                                                                         const float2 *__restrict__ F,

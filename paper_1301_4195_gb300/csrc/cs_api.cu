@@ -708,6 +708,17 @@ int cs_tune(cs_handle_t h, int param, int value)
     return CS_OK;
 }
 
+int cs_tune_get(cs_handle_t h, int param, int *value)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (!value) return set_error(CS_EINVAL, "value is NULL");
+    switch (param) {
+    case CS_TUNE_GROUPS_PER_CTA: *value = h->h.tune_gpc; return CS_OK;
+    case CS_TUNE_CTAS_PER_SM: *value = h->h.tune_ctas; return CS_OK;
+    default: return set_error(CS_EINVAL, "unknown tuning parameter");
+    }
+}
+
 int cs_autotune(cs_handle_t h, int ncells, cudaStream_t s, double *ms)
 {
     if (int rc = check_handle(h)) return rc;
@@ -722,7 +733,8 @@ int cs_autotune(cs_handle_t h, int ncells, cudaStream_t s, double *ms)
         return set_error(CS_ECUDA, "cs_autotune: events");
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, hd.device);
-    const int cand[][2] = {{0, 0}, {1, 0}, {2, 1}, {2, 2}, {2, 3}, {2, 4}, {1, 2}, {1, 3}, {1, 4}, {1, 6}, {1, 8}};
+    const int cand[][2] = {{0, 0}, {1, 0}, {2, 1}, {2, 2}, {2, 3}, {2, 4}, {2, 6}, {1, 2},
+                           {1, 3}, {1, 4}, {1, 6}, {1, 8}, {1, 12}};
     double best = 1e300;
     int bg = 0, bc = 0;
     const int keep_g = hd.tune_gpc, keep_c = hd.tune_ctas;

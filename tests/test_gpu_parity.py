@@ -318,3 +318,29 @@ def test_collide_batched_matches_individual_calls(cs):
         cs.cs_collide_batched([(hs[0].ptr, fs[0], qs[0], 40), (hs[0].ptr, fs[0], qs[1], 24)])  # same handle twice
     for h in hs:
         h.close()
+
+
+def test_launch_choices_give_identical_results(cs):
+    """The convolution's launch shape (groups per CTA, resident CTAs) changes
+    only scheduling: every cell's sum runs in the same order."""
+    N, nc = 16, 128
+    h = cs.Handle(N, L, 1.0, "fp32")
+    f = dev(I.random_mixture_cells(N, L, nc, first_id=900))
+    outs = []
+    for gpc, ctas in ((1, 2), (2, 4), (1, 8), (0, 0)):
+        cs.cs_tune(h.ptr, cs.CS_TUNE_GROUPS_PER_CTA, gpc)
+        cs.cs_tune(h.ptr, cs.CS_TUNE_CTAS_PER_SM, ctas)
+        assert cs.cs_tune_get(h.ptr, cs.CS_TUNE_GROUPS_PER_CTA) == gpc
+        assert cs.cs_tune_get(h.ptr, cs.CS_TUNE_CTAS_PER_SM) == ctas
+        q = torch.empty_like(f)
+        cs.cs_collide(h.ptr, f, nc, 1.0, q, 1)
+        outs.append(host(q))
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    best = cs.cs_autotune(h.ptr, nc)
+    assert best > 0
+    with pytest.raises(cs.CSError):
+        cs.cs_tune(h.ptr, 7, 1)
+    with pytest.raises(cs.CSError):
+        cs.cs_tune_get(h.ptr, 7)
+    h.close()
