@@ -16,7 +16,9 @@
  *     dzeta = pi/L.  A cell's distribution is N^3 doubles in C order, flat
  *     index (k1*N + k2)*N + k3.  A batch of cells is [ncells][N^3].
  *   - Collision kernel B = |u|^lambda / (4 pi) (isotropic, Sec. 2.2),
- *     0 <= lambda <= 1, weight integral cut at r0 = L, beta = 1.
+ *     -3 < lambda <= 1 (soft potentials, Maxwell molecules, variable hard
+ *     potentials, hard spheres; Sec. 2), weight integral cut at r0 = L,
+ *     beta = 1.
  *   - Pointers marked "device" are CUDA device pointers owned by the caller
  *     (e.g. allocated by PyTorch); "host" pointers are ordinary memory.
  *     Device arrays must be 8-byte aligned and must not overlap unless a
@@ -83,7 +85,8 @@ int cs_tile_layout(int N, int precision, int *map, int cap, int *entries);
  * transforms and of the projection (C C^T)^{-1} of Sec. 3.3.
  *   N        even, 4..32
  *   L        > 0, half-width of the velocity cube; r0 = L
- *   lambda   0 <= lambda <= 1
+ *   lambda   -3 < lambda <= 1 (the radial integrand behaves as r^{lambda+4}
+ *            near 0, so the quadrature converges for every such lambda)
  *   stream   the build is enqueued here; the handle is usable on any stream
  *            once the build has completed on this one
  *   out      (host, out) new handle; *out is untouched on error.

@@ -619,7 +619,7 @@ int cs_weights_build(int N, double L, double lambda, int precision, cudaStream_t
 {
     if (N < 4 || N > kMaxN || (N & 1)) return set_error(CS_EINVAL, "N must be even, 4 <= N <= 32");
     if (!(L > 0) || !is_finite(L)) return set_error(CS_EINVAL, "L must be finite and > 0");
-    if (!(lambda >= 0.0 && lambda <= 1.0)) return set_error(CS_EINVAL, "lambda must lie in [0, 1]");
+    if (!(lambda > -3.0 && lambda <= 1.0)) return set_error(CS_EINVAL, "lambda must lie in (-3, 1]");
     if (precision != CS_FP64 && precision != CS_FP32) return set_error(CS_EINVAL, "precision must be CS_FP64 or CS_FP32");
     if (!out) return set_error(CS_EINVAL, "out is NULL");
     cs_handle_s *hs = new (std::nothrow) cs_handle_s();

@@ -58,7 +58,7 @@ def test_launch_count_is_host_side(libcs):
 
 
 @pytest.mark.parametrize("N,L,lam,prec", [(5, 6.0, 1.0, 0), (34, 6.0, 1.0, 0), (2, 6.0, 1.0, 0),
-                                          (8, -1.0, 1.0, 0), (8, 6.0, 1.5, 0), (8, 6.0, -0.1, 0),
+                                          (8, -1.0, 1.0, 0), (8, 6.0, 1.5, 0), (8, 6.0, -3.0, 0),
                                           (8, 6.0, 1.0, 7), (8, float("nan"), 1.0, 0)])
 def test_weights_build_rejects_bad_arguments(libcs, N, L, lam, prec):
     with pytest.raises(libcs.CSError) as e:

@@ -66,9 +66,9 @@ def rinterleave(z):
 
 # ------------------------------------------------------------------ a0: weights
 @pytest.mark.parametrize("N", [4, 8, 16, 32])
-@pytest.mark.parametrize("lam", [0.0, 1.0, 0.5])
+@pytest.mark.parametrize("lam", [0.0, 1.0, 0.5, -1.0, -2.5])
 def test_weights_match_oracle(cs, orc, N, lam):
-    if lam == 0.5 and N == 32:
+    if lam not in (0.0, 1.0) and N == 32:
         pytest.skip("general-lambda quadrature is checked at N <= 16")
     h = handle(cs, N, lam, "fp64")
     rng = np.random.default_rng(N)
@@ -154,7 +154,7 @@ def drift(orc, Q, N):
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
 @pytest.mark.parametrize("N,ncells,lam,kind", [(8, 1, 1.0, "two_stream"), (8, 1, 0.0, "two_stream"),
                                                (12, 37, 1.0, "mix"), (16, 5, 0.0, "mix"), (16, 5, 1.0, "mix"),
-                                               (4, 3, 1.0, "mix")])
+                                               (4, 3, 1.0, "mix"), (8, 3, -1.0, "mix"), (16, 2, -2.5, "mix")])
 def test_collide_matches_oracle(cs, orc, prec, tol, N, ncells, lam, kind):
     f = I.two_stream(N, L)[None] if kind == "two_stream" else I.random_mixture_cells(N, L, ncells, first_id=300)
     h = handle(cs, N, lam, prec)

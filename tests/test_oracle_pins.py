@@ -90,7 +90,9 @@ def test_ghat_closed_form_matches_radial_quadrature(oracle_mod, N, L, lam):
 
 
 def test_ghat_against_mpmath(oracle_mod):
-    """High-precision quadrature of eq. (GHat_calc) at the singular configurations."""
+    """High-precision quadrature of eq. (GHat_calc) at the singular configurations:
+    the closed forms (lambda = 0, 1) and the quadrature route, a variable hard
+    potential (0.5) and soft potentials (-1, -2.5; Sec. 2 admits -3 < lambda)."""
     mpmath = pytest.importorskip("mpmath")
     mpmath.mp.dps = 30
     N, L = 16, 6.0
@@ -101,7 +103,7 @@ def test_ghat_against_mpmath(oracle_mod):
              ([h + 2, h, h], [h + 2, h + 1, h]),    # p = 0
              ([h + 3, h - 2, h + 1], [h - 4, h + 5, h + 2]),
              ([0, 0, 0], [0, 3, 5])]
-    for lam in (0, 1):
+    for lam in (0, 1, 0.5, -1.0, -2.5):
         for k, m in cases:
             kp = np.array(k) - h
             mp_ = np.array(m) - h
@@ -209,7 +211,7 @@ def test_mass_of_qtilde_vanishes_before_projection(oracle_mod):
     """Ghat(xi, 0) = 0 gives Qhat(0) = 0, and the mass of Qt is (2 pi)^{3/2} Re Qhat(0)."""
     N, L = 12, 6.0
     f = I.random_mixture_cells(N, L, 4)
-    for lam in (0.0, 1.0):
+    for lam in (0.0, 1.0, -1.5):
         Qt = oracle_mod.collide(f, N, L, lam, conserve=False)
         scale = np.abs(Qt).max() * (2 * L / N) ** 3 * N ** 3
         assert np.abs(oracle_mod.moments(Qt, N, L)[:, 0]).max() < 1e-14 * scale
