@@ -78,6 +78,15 @@ def _load():
                                                       ctypes.c_double, ctypes.c_int, ctypes.c_int]),
                 "or_transport_rk2": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp,
                                                     ctypes.c_double, _dp, _dp, ctypes.c_double]),
+                "or_transport2d_rhs": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                                      _dp, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp,
+                                                      _dp]),
+                "or_transport2d_rk2": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                                      _dp, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp,
+                                                      ctypes.c_double]),
+                "or_strang_step2d": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                                    ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                                    _dp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int]),
                 "or_transport_rhs_window": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                                            ctypes.c_int, ctypes.c_int, _dp, _dp,
                                                            ctypes.c_double, _dp, _dp, _dp]),
@@ -288,6 +297,49 @@ def strang_step(f: np.ndarray, N: int, L: float, lam: float, dx: np.ndarray, Tw:
     _load().or_strang_step(N, L, lam, fc.shape[0], _d(fc), _d(dxa), Tw, _d(vw), _d(ff), dt, eps,
                            nthreads)
     return fc.reshape(-1, N, N, N)
+
+
+# ---------------------------------------------- two space dimensions
+def _grid2d(f, N, nx, ny):
+    fc = np.ascontiguousarray(f, dtype=np.float64).reshape(nx * ny, N ** 3).copy()
+    return fc
+
+
+def transport2d_rhs(f: np.ndarray, N: int, L: float, nx: int, ny: int, dx: np.ndarray, dy: float, Tw: float,
+                    Vw, ffar: np.ndarray) -> np.ndarray:
+    """Right-hand side of the 2-D transport, f [nx][ny][N,N,N] (x: the wall
+    problem's grid and boundaries, y: periodic, uniform dy)."""
+    fc = _grid2d(f, N, nx, ny)
+    dxa = np.ascontiguousarray(dx, dtype=np.float64)
+    vw = np.ascontiguousarray(Vw, dtype=np.float64)
+    ff = np.ascontiguousarray(ffar, dtype=np.float64).reshape(-1)
+    out = np.empty_like(fc)
+    rc = _load().or_transport2d_rhs(N, L, nx, ny, _d(fc), _d(dxa), dy, Tw, _d(vw), _d(ff), _d(out))
+    if rc != 0:
+        raise ValueError("bad 2-D grid")
+    return out.reshape(nx, ny, N, N, N)
+
+
+def transport2d_rk2(f: np.ndarray, N: int, L: float, nx: int, ny: int, dx: np.ndarray, dy: float, Tw: float,
+                    Vw, ffar: np.ndarray, dt: float) -> np.ndarray:
+    """One Heun step of the 2-D transport."""
+    fc = _grid2d(f, N, nx, ny)
+    dxa = np.ascontiguousarray(dx, dtype=np.float64)
+    vw = np.ascontiguousarray(Vw, dtype=np.float64)
+    ff = np.ascontiguousarray(ffar, dtype=np.float64).reshape(-1)
+    _load().or_transport2d_rk2(N, L, nx, ny, _d(fc), _d(dxa), dy, Tw, _d(vw), _d(ff), dt)
+    return fc.reshape(nx, ny, N, N, N)
+
+
+def strang_step2d(f: np.ndarray, N: int, L: float, lam: float, nx: int, ny: int, dx: np.ndarray, dy: float,
+                  Tw: float, Vw, ffar: np.ndarray, dt: float, eps: float = 1.0, nthreads: int = 0) -> np.ndarray:
+    """Strang step T(dt/2) C(dt) T(dt/2) with the 2-D transport."""
+    fc = _grid2d(f, N, nx, ny)
+    dxa = np.ascontiguousarray(dx, dtype=np.float64)
+    vw = np.ascontiguousarray(Vw, dtype=np.float64)
+    ff = np.ascontiguousarray(ffar, dtype=np.float64).reshape(-1)
+    _load().or_strang_step2d(N, L, lam, nx, ny, _d(fc), _d(dxa), dy, Tw, _d(vw), _d(ff), dt, eps, nthreads)
+    return fc.reshape(nx, ny, N, N, N)
 
 
 # ---------------------------------------------- direct collision integral (Sec. 2)

@@ -755,6 +755,95 @@ int or_strang_step(int N, double L, double lambda, int nc, double *f, const doub
 }
 
 /* ------------------------------------------------------------------------ */
+/* Transport in two space dimensions (the extension Sec. 3.4 says the ideas
+ * carry to): cells (i, j), i = 0..nx-1 across the wall-normal direction x
+ * with widths dx_i and the boundaries of the 1-D problem above, j = 0..ny-1
+ * across a periodic direction y with uniform width dy.  State f[i][j][v]
+ * (cell index i ny + j).  The semi-discrete scheme adds the two directions'
+ * flux differences (no splitting between x and y):
+ *   d f_ij / dt = -(F_{i+1/2,j} - F_{i-1/2,j}) / dx_i - (H_{i,j+1/2} - H_{i,j-1/2}) / dy,
+ * F the x-flux of row j exactly as in 1-D (wall, far end, non-uniform grid),
+ *   H_{j+1/2} = v2 (f_j + dy/2 s_j)           (v2 >= 0)
+ *             = v2 (f_{j+1} - dy/2 s_{j+1})   (v2 <  0),
+ * s_j = minmod of the forward, backward and central quotients in y, indices
+ * taken modulo ny.                                                           */
+static void transport_rhs_2d(int N, double L, int nx, int ny, const double *f, const double *dx,
+                             double dy, double Tw, const double *Vw, const double *ffar, double *rhs)
+{
+    size_t M = (size_t)N * N * N;
+    double dv = or_dv(N, L);
+    double *row = (double *)malloc(sizeof(double) * M * nx);
+    double *rr = (double *)malloc(sizeof(double) * M * nx);
+    /* x: the 1-D right-hand side of every row */
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i)
+            memcpy(row + M * i, f + M * ((size_t)i * ny + j), sizeof(double) * M);
+        transport_rhs(N, L, nx, row, dx, Tw, Vw, ffar, rr);
+        for (int i = 0; i < nx; ++i)
+            memcpy(rhs + M * ((size_t)i * ny + j), rr + M * i, sizeof(double) * M);
+    }
+    /* y: periodic second-order upwind */
+    for (int i = 0; i < nx; ++i) {
+        for (size_t v = 0; v < M; ++v) {
+            double v2 = dv * ((int)((v / N) % N) - N / 2);
+            for (int j = 0; j < ny; ++j) {
+#define FY(jj) f[M * ((size_t)i * ny + (size_t)((((jj) % ny) + ny) % ny)) + v]
+#define SLOPE(jj) minmod3((FY((jj) + 1) - FY(jj)) / dy, (FY(jj) - FY((jj) - 1)) / dy, \
+                          (FY((jj) + 1) - FY((jj) - 1)) / (2.0 * dy))
+                double hp, hm; /* H_{j+1/2}, H_{j-1/2} */
+                if (v2 >= 0) {
+                    hp = v2 * (FY(j) + 0.5 * dy * SLOPE(j));
+                    hm = v2 * (FY(j - 1) + 0.5 * dy * SLOPE(j - 1));
+                } else {
+                    hp = v2 * (FY(j + 1) - 0.5 * dy * SLOPE(j + 1));
+                    hm = v2 * (FY(j) - 0.5 * dy * SLOPE(j));
+                }
+#undef SLOPE
+#undef FY
+                rhs[M * ((size_t)i * ny + j) + v] -= (hp - hm) / dy;
+            }
+        }
+    }
+    free(row);
+    free(rr);
+}
+
+int or_transport2d_rhs(int N, double L, int nx, int ny, const double *f, const double *dx, double dy,
+                       double Tw, const double *Vw, const double *ffar, double *rhs)
+{
+    if (nx < 2 || ny < 1 || !(dy > 0)) return -1;
+    transport_rhs_2d(N, L, nx, ny, f, dx, dy, Tw, Vw, ffar, rhs);
+    return 0;
+}
+
+/* one Heun step of length dt of the 2-D transport */
+int or_transport2d_rk2(int N, double L, int nx, int ny, double *f, const double *dx, double dy,
+                       double Tw, const double *Vw, const double *ffar, double dt)
+{
+    size_t n = (size_t)N * N * N * nx * ny;
+    double *r = (double *)malloc(sizeof(double) * n);
+    double *f1 = (double *)malloc(sizeof(double) * n);
+    transport_rhs_2d(N, L, nx, ny, f, dx, dy, Tw, Vw, ffar, r);
+    for (size_t i = 0; i < n; ++i) f1[i] = f[i] + dt * r[i];
+    transport_rhs_2d(N, L, nx, ny, f1, dx, dy, Tw, Vw, ffar, r);
+    for (size_t i = 0; i < n; ++i) f[i] = 0.5 * (f[i] + f1[i] + dt * r[i]);
+    free(r);
+    free(f1);
+    return 0;
+}
+
+/* Strang step T(dt/2) C(dt) T(dt/2) with the 2-D transport */
+int or_strang_step2d(int N, double L, double lambda, int nx, int ny, double *f, const double *dx,
+                     double dy, double Tw, const double *Vw, const double *ffar, double dt, double eps,
+                     int nthreads)
+{
+    or_transport2d_rk2(N, L, nx, ny, f, dx, dy, Tw, Vw, ffar, 0.5 * dt);
+    or_rk2_homogeneous(N, L, lambda, nx * ny, f, dt, 1, eps, 1, nthreads);
+    or_transport2d_rk2(N, L, nx, ny, f, dx, dy, Tw, Vw, ffar, 0.5 * dt);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Direct quadrature of the collision integral, Sec. 2 ("Q_general") with
  * the collision law "velocity_interact", B = |u|^lambda / (4 pi) and the
  * same cut |u| <= r0 as the weights, for f a sum of Maxwellians
