@@ -303,6 +303,35 @@ def run_ours(args):
                             "traffic": TRAFFIC.get((N2, nc2))}}
         hb.close()
 
+    # the wall problem in two space dimensions (secondary): 32 x-cells by 8
+    # periodic y-cells, the same step with the 2-D transport
+    wall2d = None
+    if args.workload == "wall16" and not args.skip_2d:
+        N2, nx, ny, Y = 16, 32, 8, 2.0
+        hw = api.Handle(N2, L_BOX, LAM, "fp32")
+        hw.reserve(nx * ny)
+        api.cs_autotune(hw.ptr, nx * ny)
+        dx2 = torch.from_numpy(inputs.wall_grid(nx)).to(device)
+        far2 = torch.from_numpy(inputs.maxwellian(N2, L_BOX, 1.0, (0.0, 0.0, 0.0), 1.0)).to(device)
+        f2 = torch.from_numpy(inputs.wall2d_initial(N2, L_BOX, nx, ny, Y)).to(device)
+        for _ in range(3):
+            hw.step2d(f2, dx2, far2, WALL_T, (0.0, 0.0, 0.0), ny, Y / ny, DT)
+        torch.cuda.synchronize()
+        k2, ms2 = max(2, min(args.steps, 10)), 0.0
+        for _ in range(k2):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            hw.step2d(f2, dx2, far2, WALL_T, (0.0, 0.0, 0.0), ny, Y / ny, DT)
+            b.record()
+            b.synchronize()
+            ms2 += a.elapsed_time(b)
+        wall2d = {"workload": f"wall problem in 2-D: N={N2}, {nx} x-cells (dx_j=min(0.125*1.05^j,0.5)) x {ny} "
+                              f"periodic y-cells (Y={Y}), density 1+0.2 sin(2 pi y/Y), one Strang step",
+                  "ms_per_step": ms2 / k2, "value": 2 * nx * ny * N2 ** 6 / (ms2 / k2 * 1e-3), "unit": UNIT}
+        hw.close()
+
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -330,6 +359,8 @@ def run_ours(args):
     }
     if n32:
         out["n32"] = n32
+    if wall2d:
+        out["wall2d"] = wall2d
     if not args.skip_batched and world == 1:
         out["batched"] = batched_run(api, inputs, torch, device, args)
     if not args.skip_serve and world == 1:
@@ -477,6 +508,7 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true", help="omit the double-precision comparison")
     ap.add_argument("--skip-serve", action="store_true", help="omit the serving run")
     ap.add_argument("--skip-batched", action="store_true", help="omit the uneven-N batched run")
+    ap.add_argument("--skip-2d", action="store_true", help="omit the two-dimensional wall problem")
     ap.add_argument("--serve-rate", type=float, default=100.0, help="Poisson arrival rate of the serving run (1/s)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -209,6 +209,38 @@ typedef struct {
 int cs_transport(cs_handle_t h, double *f, int ncells, const cs_domain *dom, double dt,
                  cudaStream_t stream);
 
+/* Transport in two space dimensions (Sec. 3.4 notes the scheme carries over
+ * to higher dimensions): x is the wall-normal direction of the 1-D problem
+ * (cells of width dx, diffusely reflecting wall at x = 0, far-field gas at
+ * the end), y a periodic direction of ny cells of uniform width dy.  The
+ * state is [nx][ny][N^3] (cell (i, j) at index i ny + j).  A stage adds the
+ * flux differences of both directions (no splitting between x and y):
+ *   d f_ij/dt = -(F_{i+1/2,j} - F_{i-1/2,j})/dx_i - (H_{i,j+1/2} - H_{i,j-1/2})/dy,
+ * F the x-flux of cs_transport on row j, H the second-order upwind y-flux
+ * (v2 times the minmod-limited upwind face value).  ny = 1 is the 1-D
+ * problem. */
+typedef struct {
+    const double *dx;    /* device, [nx] cell widths across x */
+    const double *f_far; /* device, [N^3] far-field distribution (x end), used for v1 < 0 */
+    double wall_T;       /* wall temperature T_w > 0 */
+    double wall_V[3];    /* wall velocity V_w */
+    int ny;              /* cells across the periodic y direction, >= 1 */
+    double dy;           /* their width, > 0 */
+} cs_domain2d;
+
+/* One Heun step of length dt of the 2-D transport, in place.
+ *   f (device, in/out) [nx][ny][N^3].  nx >= 2.
+ * Errors: CS_EINVAL, CS_ENOMEM, CS_ECUDA. */
+int cs_transport2d(cs_handle_t h, double *f, int nx, const cs_domain2d *dom, double dt,
+                   cudaStream_t stream);
+
+/* nsteps Strang-split steps with the 2-D transport: transport dt/2,
+ * collision dt (Heun on P_N Qt / eps, every cell), transport dt/2, in place;
+ * captured once as a CUDA graph and replayed like cs_step.
+ * Errors: CS_EINVAL, CS_ENOMEM, CS_ECUDA. */
+int cs_step2d(cs_handle_t h, double *f, int nx, const cs_domain2d *dom, double dt, double eps,
+              int nsteps, cudaStream_t stream);
+
 /* Sharded transport (Sec. 4.2, distributed memory): the x-grid of
  * total_cells cells is split into contiguous shards, one per process (or
  * several per process); the collision step is local to each cell, and the

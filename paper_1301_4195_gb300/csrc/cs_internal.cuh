@@ -126,12 +126,14 @@ struct Handle {
     double *part5 = nullptr;  // per-block partial moments of the projection
     // replayable steps (cs_step, cs_relax): one captured step per argument set
     struct GraphEntry {
-        int kind;  // 1 = Strang step, 2 = homogeneous Heun step
+        int kind;  // 1 = Strang step, 2 = homogeneous Heun step, 3 = Strang step in 2-D
         const void *f, *dx, *ffar;
         int ncells;
         double wall_T, wall_V[3], dt, eps;
         cudaGraphExec_t exec;
         int kernels;  // kernel nodes of the captured step
+        int ny;       // 2-D: cells across y, and their width
+        double dy;
     };
     std::vector<GraphEntry> graphs;
     cudaStream_t cap_stream = nullptr;
@@ -236,6 +238,11 @@ int conserve_parts(int M);  // blocks per cell of the projection
 // transport tables (geometry, wall Maxwellian) for a grid of total_cells cells
 size_t transport_table_doubles(int N, int total_cells);
 int launch_transport_prep(const Handle &hd, int total_cells, const cs_domain &dom, cudaStream_t s);
+// a stage of the transport in two space dimensions: fin, out [nx][ny][N^3],
+// x the wall direction of dom, y periodic with ny cells of width dy
+int launch_transport_stage2d(const Handle &hd, const double *fin, int nx, int ny, double dy, const cs_domain &dom,
+                             double a, const double *x, double b, const double *y, double c, double *out,
+                             cudaStream_t s);
 // one transport stage, out = a x + b y + c rhs(fin), rhs the finite-volume
 // operator, for cells first .. first+ncells-1, read from fin with `ghost`
 // leading ghost cells (0: fin holds exactly the cells; 2: a window); out must

@@ -129,11 +129,24 @@ constexpr int kStageCells = 4;      // cells per block: their 5 faces from 8 loa
 // of the stage input; every such block sums in the same order, so all of them
 // hold the same value.  Reads fin only, writes out only: out must not overlap
 // fin (it may alias x or y, read and written by the same thread).
+//
+// Two space dimensions (Y2D): cell (i, j) of an x-grid of nc cells and a
+// periodic y-row of ny cells is stored at index i ny + j; blockIdx.z = j.  The
+// x-part is the 1-D stage applied to row j (the same arithmetic); the y-part
+// adds -(H_{j+1/2} - H_{j-1/2}) / dy, H the second-order upwind flux on the
+// uniform periodic y-grid with the two-argument minmod (equal to the
+// three-argument one: on a uniform grid the central quotient is the mean of
+// the other two).  Both rows of a y-face evaluate its flux with the same
+// operations on the same values, so the y-fluxes telescope exactly.
+__device__ __forceinline__ double yface(double fu, double hs, double s) { return fma(hs, s, fu); }
+
+template <bool Y2D>
 __global__ void __launch_bounds__(kStageThreads) stage_kernel(Geom g, const double *__restrict__ fin, int first,
                                                               int ncl, int nc, int G, const double *__restrict__ dx,
                                                               const double *__restrict__ ffar,
                                                               const double *__restrict__ scal, double a, const double *x,
-                                                              double b, const double *y, double c, double *out)
+                                                              double b, const double *y, double c, double *out, int ny,
+                                                              double idy, double hdy)
 {
     __shared__ double sh[kStageThreads / 32];
     __shared__ double s_coef[kStageCells];  // c / dx_j of the block's cells
@@ -143,6 +156,9 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(Geom g, const doub
     const int ncb = min(kStageCells, ncl - cl0);  // cells of this block
     const int v = blockIdx.x * kStageThreads + threadIdx.x;
     const int c0 = first + cl0;                   // grid index of the block's first cell and face
+    const int row = Y2D ? (int)blockIdx.z : 0;    // y-row j
+    const size_t XS = (size_t)(Y2D ? ny : 1) * M;  // stride between x-neighbours
+    const size_t R0 = (size_t)row * M;             // offset of the row
 
     // sigma_w enters the wall face of velocities with v1 > 0 only, i.e. index
     // k1 > N/2, v >= (N/2 + 1) N^2 (block-uniform test)
@@ -150,10 +166,10 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(Geom g, const doub
     if (c0 == 0 && (blockIdx.x + 1) * kStageThreads > (g.h + 1) * NN) {
         const int half = g.h * NN;  // velocities with v1 < 0 come first
         const double i01 = t.inv_fwd[0], hx = 0.5 * dx[0];
-        const double *f0p = fin + (size_t)G * M;
+        const double *f0p = fin + (size_t)G * XS + R0;
         double o = 0.0;
         for (int u = threadIdx.x; u < half; u += kStageThreads) {
-            const double f0 = f0p[u], f1 = f0p[(size_t)M + u];
+            const double f0 = f0p[u], f1 = f0p[XS + u];
             o -= t.v1[u / NN] * (f0 - hx * ((f1 - f0) * i01));
         }
 #pragma unroll
@@ -178,9 +194,9 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(Geom g, const doub
         fv[i] = 0.0;
         if (i <= ncb + 3 && j >= 0) {
             if (j < nc)
-                fv[i] = fin[(ptrdiff_t)(j - first + G) * M + v];
+                fv[i] = fin[(ptrdiff_t)(j - first + G) * XS + R0 + v];
             else  // j >= nc only where the block reaches the grid's last cell
-                fv[i] = v1 < 0 ? ffar[v] : fin[(ptrdiff_t)(nc - 1 - first + G) * M + v];
+                fv[i] = v1 < 0 ? ffar[v] : fin[(ptrdiff_t)(nc - 1 - first + G) * XS + R0 + v];
         }
     }
     // forward difference quotients of the loaded cells, d[i] = (f_{j+1} - f_j)
@@ -198,6 +214,34 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(Geom g, const doub
 #pragma unroll
     for (int i = 0; i < kStageCells; ++i) vco[i] = v1 * s_coef[i];
     const bool plain = a == 1.0 && y == nullptr;  // out = x + c R(f): one fused multiply-add per point
+    // y-part of the block's cells: (H_{j-1/2} - H_{j+1/2}) c v2 / dy
+    double ry[kStageCells];
+    if constexpr (Y2D) {
+        const double v2 = t.v1[(v / g.N) % g.N];
+        const double vy = c * v2 * idy;
+        const int jm2 = (row + 2 * ny - 2) % ny, jm1 = (row + ny - 1) % ny;
+        const int jp1 = (row + 1) % ny, jp2 = (row + 2) % ny;
+#pragma unroll
+        for (int i = 0; i < kStageCells; ++i) {
+            ry[i] = 0.0;
+            if (i < ncb) {
+                const double *cell = fin + (ptrdiff_t)(c0 + i - first + G) * XS + v;
+                const double fm2 = cell[(size_t)jm2 * M], fm1 = cell[(size_t)jm1 * M], f0 = fv[i + 2];
+                const double fp1 = cell[(size_t)jp1 * M], fp2 = cell[(size_t)jp2 * M];
+                double hp, hm;
+                if (v2 >= 0) {  // faces j+1/2 and j-1/2 from cells j and j-1
+                    const double e_2 = (fm1 - fm2) * idy, e_1 = (f0 - fm1) * idy, e0 = (fp1 - f0) * idy;
+                    hp = yface(f0, hdy, minmod2(e0, e_1));
+                    hm = yface(fm1, hdy, minmod2(e_1, e_2));
+                } else {  // from cells j+1 and j
+                    const double e_1 = (f0 - fm1) * idy, e0 = (fp1 - f0) * idy, e1 = (fp2 - fp1) * idy;
+                    hp = yface(fp1, -hdy, minmod2(e1, e0));
+                    hm = yface(f0, -hdy, minmod2(e0, e_1));
+                }
+                ry[i] = (hm - hp) * vy;
+            }
+        }
+    }
     double Gprev = 0.0;
 #pragma unroll
     for (int i = 0; i <= kStageCells; ++i) {
@@ -220,9 +264,13 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(Geom g, const doub
             G = right ? fma(hw, sl, fu) : fma(-hw, sl, fu);
         }
         if (i > 0) {  // cell cf-1 = local cl0 + i - 1
-            const size_t idx = (size_t)(cl0 + i - 1) * M + v;
+            const size_t idx = (size_t)(cl0 + i - 1) * XS + R0 + v;
             double o;
-            if (plain && x) {
+            if constexpr (Y2D) {
+                o = fma(Gprev - G, vco[i - 1], ry[i - 1]);
+                if (x) o = fma(a, x[idx], o);
+                if (y) o = fma(b, y[idx], o);
+            } else if (plain && x) {
                 o = fma(Gprev - G, vco[i - 1], x[idx]);
             } else {
                 o = (Gprev - G) * vco[i - 1];
@@ -271,9 +319,21 @@ int launch_transport_stage(const Handle &hd, const double *fin, int ghost, int f
 {
     const dim3 grid((unsigned)((hd.g.M + kStageThreads - 1) / kStageThreads),
                     (unsigned)((ncells + kStageCells - 1) / kStageCells));
-    stage_kernel<<<grid, kStageThreads, 0, s>>>(hd.g, fin, first, ncells, total_cells, ghost, dom.dx, dom.f_far,
-                                                hd.scal, a, x, b, y, c, out);
+    stage_kernel<false><<<grid, kStageThreads, 0, s>>>(hd.g, fin, first, ncells, total_cells, ghost, dom.dx,
+                                                       dom.f_far, hd.scal, a, x, b, y, c, out, 1, 0.0, 0.0);
     CS_LAUNCHED(1, s, "transport stage");
+    return CS_OK;
+}
+
+int launch_transport_stage2d(const Handle &hd, const double *fin, int nx, int ny, double dy, const cs_domain &dom,
+                             double a, const double *x, double b, const double *y, double c, double *out,
+                             cudaStream_t s)
+{
+    const dim3 grid((unsigned)((hd.g.M + kStageThreads - 1) / kStageThreads),
+                    (unsigned)((nx + kStageCells - 1) / kStageCells), (unsigned)ny);
+    stage_kernel<true><<<grid, kStageThreads, 0, s>>>(hd.g, fin, 0, nx, nx, 0, dom.dx, dom.f_far, hd.scal, a, x,
+                                                      b, y, c, out, ny, 1.0 / dy, 0.5 * dy);
+    CS_LAUNCHED(1, s, "transport stage (2-D)");
     return CS_OK;
 }
 

@@ -110,3 +110,13 @@ def wall_profile(N: int, L: float, ncells: int) -> np.ndarray:
         s = j / max(ncells - 1, 1)
         out[j] = maxwellian(N, L, 1.0 + 0.3 * np.sin(3.0 * s), (0.4 * np.cos(5.0 * s), 0.1, 0.0), 1.0 + 0.2 * s)
     return out
+
+
+def wall2d_initial(N: int, L: float, nx: int, ny: int, Y: float) -> np.ndarray:
+    """The wall problem in two space dimensions, [nx][ny][N, N, N]: the unit
+    Maxwellian with density 1 + 0.2 sin(2 pi y / Y) across the periodic
+    direction y (cell centres (j + 1/2) Y / ny), uniform across x."""
+    m = maxwellian(N, L, 1.0, (0.0, 0.0, 0.0), 1.0)
+    y = (np.arange(ny) + 0.5) * Y / ny
+    rho = 1.0 + 0.2 * np.sin(2.0 * np.pi * y / Y)
+    return np.broadcast_to(rho[None, :, None, None, None] * m[None, None], (nx, ny, N, N, N)).copy()
