@@ -11,7 +11,7 @@
  * transport step combined by Strang splitting.
  *
  * Conventions shared by every call
- *   - Velocity grid (Sec. 3.1, "meshpoints"): N even, 4 <= N <= 32, the cube
+ *   - Velocity grid (Sec. 3.1, "meshpoints"): N even, 4 <= N <= 64, the cube
  *     [-L, L]^3, v_k = dv (k - N/2), dv = 2L/N, zeta_k = dzeta (k - N/2),
  *     dzeta = pi/L.  A cell's distribution is N^3 doubles in C order, flat
  *     index (k1*N + k2)*N + k3.  A batch of cells is [ncells][N^3].
@@ -83,7 +83,8 @@ int cs_tile_layout(int N, int precision, int *map, int cap, int *entries);
  * lambda = 0 and 1, radial Gauss-Legendre quadrature otherwise), in double on
  * the device (kept in float for CS_FP32), together with the constants of the
  * transforms and of the projection (C C^T)^{-1} of Sec. 3.3.
- *   N        even, 4..32
+ *   N        even, 4..64 (the float table needs ~0.5 (27 N^6 / 64) 4 bytes:
+ *            0.9 GB at N = 32, 10 GB at 48, 58 GB at 64; cs_weights_bytes)
  *   L        > 0, half-width of the velocity cube; r0 = L
  *   lambda   -3 < lambda <= 1 (the radial integrand behaves as r^{lambda+4}
  *            near 0, so the quadrature converges for every such lambda)

@@ -67,6 +67,8 @@ def _load():
                 "or_ghat_table": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp]),
                 "or_convolve": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                                ctypes.c_int, _dp, _dp, ctypes.c_int]),
+                "or_convolve_at": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                                  ctypes.c_int, _dp, ctypes.c_int, _ip, _dp, ctypes.c_int]),
                 "or_moments": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp]),
                 "or_cct": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, _dp]),
                 "or_conserve": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp]),
@@ -202,6 +204,17 @@ def convolve(fhat: np.ndarray, N: int, L: float, lam: float, nthreads: int = 0) 
     out = np.zeros_like(fi)
     _load().or_convolve(N, L, lam, fh.shape[0], _d(fi), _d(out), nthreads)
     return (out[..., 0] + 1j * out[..., 1]).reshape(fh.shape[0], N, N, N)
+
+
+def convolve_at(fhat: np.ndarray, N: int, L: float, lam: float, kflat, nthreads: int = 0) -> np.ndarray:
+    """The convolution at the flat output indices kflat only: [ncells, len(kflat)]
+    complex, each entry the same sum as convolve() computes there."""
+    fh = np.ascontiguousarray(fhat, dtype=np.complex128).reshape(-1, N ** 3)
+    fi = np.ascontiguousarray(np.stack([fh.real, fh.imag], axis=-1))
+    ks = np.ascontiguousarray(kflat, dtype=np.int32)
+    out = np.zeros((fh.shape[0], ks.shape[0], 2))
+    _load().or_convolve_at(N, L, lam, fh.shape[0], _d(fi), ks.shape[0], _i(ks), _d(out), nthreads)
+    return out[..., 0] + 1j * out[..., 1]
 
 
 # ------------------------------------------------------ conservation (Sec. 3.3)

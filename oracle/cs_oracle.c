@@ -347,11 +347,42 @@ int or_ghat_table(int N, double L, double lambda, double *out)
  * leaves [0, N-1] on some axis.  m runs in lexicographic order.  The weight
  * of each (k, m) is evaluated once and applied to every cell.  OpenMP splits
  * the zeta_k outputs over threads, as in Sec. 4.1.                          */
+/* One output zeta_k of the convolution for ncells cells: acc[2c], acc[2c+1]
+ * receive the real and imaginary sums (before the factor omega).            */
+static void convolve_one(int N, double L, double lambda, const int *k, int ncells, const double *fhat,
+                         double *acc)
+{
+    int M = N * N * N;
+    int h = N / 2;
+    for (int c = 0; c < 2 * ncells; ++c) acc[c] = 0.0;
+    for (int m1 = 0; m1 < N; ++m1) {
+        int s1 = k[0] - m1 + h;
+        if (s1 < 0 || s1 > N - 1) continue;
+        for (int m2 = 0; m2 < N; ++m2) {
+            int s2 = k[1] - m2 + h;
+            if (s2 < 0 || s2 > N - 1) continue;
+            for (int m3 = 0; m3 < N; ++m3) {
+                int s3 = k[2] - m3 + h;
+                if (s3 < 0 || s3 > N - 1) continue;
+                int m[3] = {m1, m2, m3};
+                double g = or_ghat(N, L, lambda, k, m);
+                int im = idx3(N, m1, m2, m3), is = idx3(N, s1, s2, s3);
+                for (int c = 0; c < ncells; ++c) {
+                    const double *F = fhat + (size_t)2 * M * c;
+                    double ar = F[2 * im], ai = F[2 * im + 1];
+                    double br = F[2 * is], bi = F[2 * is + 1];
+                    acc[2 * c] += g * (ar * br - ai * bi);
+                    acc[2 * c + 1] += g * (ar * bi + ai * br);
+                }
+            }
+        }
+    }
+}
+
 int or_convolve(int N, double L, double lambda, int ncells, const double *fhat,
                 double *qhat, int nthreads)
 {
     int M = N * N * N;
-    int h = N / 2;
     double dz = or_dzeta(L);
     double omega = dz * dz * dz;
 #ifdef _OPENMP
@@ -363,32 +394,38 @@ int or_convolve(int N, double L, double lambda, int ncells, const double *fhat,
 #pragma omp for schedule(dynamic, 4)
         for (int kf = 0; kf < M; ++kf) {
             int k[3] = {kf / (N * N), (kf / N) % N, kf % N};
-            for (int c = 0; c < 2 * ncells; ++c) acc[c] = 0.0;
-            for (int m1 = 0; m1 < N; ++m1) {
-                int s1 = k[0] - m1 + h;
-                if (s1 < 0 || s1 > N - 1) continue;
-                for (int m2 = 0; m2 < N; ++m2) {
-                    int s2 = k[1] - m2 + h;
-                    if (s2 < 0 || s2 > N - 1) continue;
-                    for (int m3 = 0; m3 < N; ++m3) {
-                        int s3 = k[2] - m3 + h;
-                        if (s3 < 0 || s3 > N - 1) continue;
-                        int m[3] = {m1, m2, m3};
-                        double g = or_ghat(N, L, lambda, k, m);
-                        int im = idx3(N, m1, m2, m3), is = idx3(N, s1, s2, s3);
-                        for (int c = 0; c < ncells; ++c) {
-                            const double *F = fhat + (size_t)2 * M * c;
-                            double ar = F[2 * im], ai = F[2 * im + 1];
-                            double br = F[2 * is], bi = F[2 * is + 1];
-                            acc[2 * c] += g * (ar * br - ai * bi);
-                            acc[2 * c + 1] += g * (ar * bi + ai * br);
-                        }
-                    }
-                }
-            }
+            convolve_one(N, L, lambda, k, ncells, fhat, acc);
             for (int c = 0; c < ncells; ++c) {
                 qhat[(size_t)2 * M * c + 2 * kf] = omega * acc[2 * c];
                 qhat[(size_t)2 * M * c + 2 * kf + 1] = omega * acc[2 * c + 1];
+            }
+        }
+        free(acc);
+    }
+    return 0;
+}
+
+/* The convolution at nk selected outputs kf[i] (flat indices) only, for
+ * grids too large for the full sum: qhat [ncells][nk][2].  Each output is
+ * the same sum as in or_convolve, bit for bit.                              */
+int or_convolve_at(int N, double L, double lambda, int ncells, const double *fhat, int nk, const int *kf,
+                   double *qhat, int nthreads)
+{
+    double dz = or_dzeta(L);
+    double omega = dz * dz * dz;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel
+    {
+        double *acc = (double *)malloc(sizeof(double) * 2 * (size_t)ncells);
+#pragma omp for schedule(dynamic, 1)
+        for (int i = 0; i < nk; ++i) {
+            int k[3] = {kf[i] / (N * N), (kf[i] / N) % N, kf[i] % N};
+            convolve_one(N, L, lambda, k, ncells, fhat, acc);
+            for (int c = 0; c < ncells; ++c) {
+                qhat[(size_t)2 * nk * c + 2 * i] = omega * acc[2 * c];
+                qhat[(size_t)2 * nk * c + 2 * i + 1] = omega * acc[2 * c + 1];
             }
         }
         free(acc);

@@ -1,4 +1,4 @@
-// K2, strip kernel (float; N in {8, 16, 24, 32}): the weighted convolution of
+// K2, strip kernel (float; N in {8, 16, 24, 32, 48, 64}): the weighted convolution of
 // Sec. 3.2,
 //   Qhat(zeta_k) = dzeta^3 sum_m Ghat(xi_m, zeta_k) fhat(xi_m) fhat(zeta_k - xi_m),
 // over the symmetrised half-tiles of the weight table (weights.cu).
@@ -541,6 +541,8 @@ int launch_strip(const Handle &hd, int ncells, cudaStream_t s)
     case 16: return launch_n<16, 8, 8, 3, 3, 2>(hd, ncells, s);
     case 24: return launch_n<24, 12, 4, 3, 2, 1>(hd, ncells, s);
     case 32: return launch_n<32, 8, 8, 3, 3, 1>(hd, ncells, s);
+    case 48: return launch_n<48, 8, 8, 3, 2, 1>(hd, ncells, s);
+    case 64: return launch_n<64, 8, 8, 3, 2, 1>(hd, ncells, s);
     default: return set_error(CS_ENOTSUP, "strip kernel: unsupported N");
     }
 }

@@ -604,7 +604,7 @@ const char *cs_last_error(void) { return g_last_error.c_str(); }
 
 int cs_weights_bytes(int N, int precision, size_t *bytes)
 {
-    if (N < 4 || N > kMaxN || (N & 1)) return set_error(CS_EINVAL, "N must be even, 4 <= N <= 32");
+    if (N < 4 || N > kMaxN || (N & 1)) return set_error(CS_EINVAL, "N must be even, 4 <= N <= 64");
     if (precision != CS_FP64 && precision != CS_FP32) return set_error(CS_EINVAL, "precision must be CS_FP64 or CS_FP32");
     if (!bytes) return set_error(CS_EINVAL, "bytes is NULL");
     Geom g{};
@@ -617,7 +617,7 @@ int cs_weights_bytes(int N, int precision, size_t *bytes)
 
 int cs_tile_layout(int N, int precision, int *map, int cap, int *entries)
 {
-    if (N < 4 || N > kMaxN || (N & 1)) return set_error(CS_EINVAL, "N must be even, 4 <= N <= 32");
+    if (N < 4 || N > kMaxN || (N & 1)) return set_error(CS_EINVAL, "N must be even, 4 <= N <= 64");
     if (precision != CS_FP64 && precision != CS_FP32) return set_error(CS_EINVAL, "precision must be CS_FP64 or CS_FP32");
     Geom g{};
     fill_geom(g, N, 1.0, 0.0, precision);
@@ -632,7 +632,7 @@ int cs_tile_layout(int N, int precision, int *map, int cap, int *entries)
 
 int cs_weights_build(int N, double L, double lambda, int precision, cudaStream_t stream, cs_handle_t *out)
 {
-    if (N < 4 || N > kMaxN || (N & 1)) return set_error(CS_EINVAL, "N must be even, 4 <= N <= 32");
+    if (N < 4 || N > kMaxN || (N & 1)) return set_error(CS_EINVAL, "N must be even, 4 <= N <= 64");
     if (!(L > 0) || !is_finite(L)) return set_error(CS_EINVAL, "L must be finite and > 0");
     if (!(lambda > -3.0 && lambda <= 1.0)) return set_error(CS_EINVAL, "lambda must lie in (-3, 1]");
     if (precision != CS_FP64 && precision != CS_FP32) return set_error(CS_EINVAL, "precision must be CS_FP64 or CS_FP32");

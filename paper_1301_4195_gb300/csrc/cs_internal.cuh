@@ -21,7 +21,7 @@
 namespace cs {
 
 constexpr int kGroup = 32;  // cells per group (= warp lanes)
-constexpr int kMaxN = 32;
+constexpr int kMaxN = 64;
 
 template <typename T> struct C2;
 template <> struct C2<double> { using type = double2; };
@@ -31,7 +31,7 @@ template <typename T> using c2_t = typename C2<T>::type;
 // Order of the (m3, k3) pairs inside one weight tile.
 //   ROWS:  rows m3 = 0..N-1, each row the valid k3 ascending, padded to a
 //          multiple of 4 entries (generic and pencil kernels).
-//   STRIP: for the strip kernel (float, N in {8, 16, 24, 32}): the k3 range is
+//   STRIP: for the strip kernel (float, N in {8, 16, 24, 32, 48, 64}): the k3 range is
 //          cut into strips of K outputs; each strip's pairs are stored together
 //          (see strip_* below).
 enum Layout { LAYOUT_ROWS = 0, LAYOUT_STRIP = 1 };
@@ -84,7 +84,7 @@ __host__ __device__ constexpr int strip_tri_b_off(int t) { return t * (t + 1) / 
 // strip width used for (N, float); 0 = the strip kernel does not serve N
 __host__ __device__ constexpr int strip_width(int N)
 {
-    return N == 8 ? 4 : N == 16 ? 8 : N == 24 ? 12 : N == 32 ? 8 : 0;
+    return N == 8 ? 4 : N == 16 ? 8 : N == 24 ? 12 : (N == 32 || N == 48 || N == 64) ? 8 : 0;
 }
 
 struct Handle {

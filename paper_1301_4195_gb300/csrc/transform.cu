@@ -11,6 +11,8 @@
 // Inverse:  Qh --axis 1--> X --axis 2--> Y --axis 3 (real part x c_i / eps)--> Qt
 // so the caller-layout arrays are always read and written along contiguous
 // rows.  X, Y, F and Qh use the grouped layout [group][i1][i2][i3][32].
+// A block has 32 min(N, 32) threads; for N > 32 each thread produces the
+// outputs t, t + 32, ... of its line.
 #include "cs_internal.cuh"
 
 namespace cs {
@@ -22,8 +24,10 @@ __device__ __forceinline__ size_t grouped_index(int N, int g, int i1, int i2, in
     return ((((size_t)g * N + i1) * N + i2) * N + i3) * kGroup + lane;
 }
 
+__host__ __device__ inline int line_threads(int N) { return kGroup * (N < 32 ? N : 32); }
+
 // axis-3 transform of the real rows f[c][j1][j2][:]; one block per
-// (group, j1, j2), blockDim = 32 * N.  Cells >= ncells are zero.
+// (group, j1, j2).  Cells >= ncells are zero.
 template <typename T>
 __global__ void forward_rows_kernel(int N, const double *__restrict__ f, int ncells,
                                     const c2_t<T> *__restrict__ tw, c2_t<T> *__restrict__ X)
@@ -34,26 +38,28 @@ __global__ void forward_rows_kernel(int N, const double *__restrict__ f, int nce
     const int j2 = bid % N, j1 = (bid / N) % N, g = bid / (N * N);
     const int tid = threadIdx.x;
     const size_t M = (size_t)N * N * N;
-    {   // consecutive threads read consecutive j3 of one cell's row
-        const int lane = tid / N, j3 = tid % N;
+    for (int e = tid; e < kGroup * N; e += blockDim.x) {  // consecutive threads read consecutive j3 of a row
+        const int lane = e / N, j3 = e % N;
         const int c = g * kGroup + lane;
         T v = T(0);
         if (c < ncells) v = (T)f[(size_t)c * M + ((size_t)j1 * N + j2) * N + j3];
         line[j3 * kGroup + lane] = v;
     }
     __syncthreads();
-    const int lane = tid % kGroup, k3 = tid / kGroup;
-    T re = T(0), im = T(0);
-    for (int j = 0; j < N; ++j) {
-        const c2_t<T> w = tw[k3 * N + j];
-        const T v = line[j * kGroup + lane];
-        re += v * w.x;
-        im += v * w.y;
+    const int lane = tid % kGroup;
+    for (int k3 = tid / kGroup; k3 < N; k3 += blockDim.x / kGroup) {
+        T re = T(0), im = T(0);
+        for (int j = 0; j < N; ++j) {
+            const c2_t<T> w = tw[k3 * N + j];
+            const T v = line[j * kGroup + lane];
+            re += v * w.x;
+            im += v * w.y;
+        }
+        c2_t<T> o;
+        o.x = re;
+        o.y = im;
+        X[grouped_index(N, g, j1, j2, k3, lane)] = o;
     }
-    c2_t<T> o;
-    o.x = re;
-    o.y = im;
-    X[grouped_index(N, g, j1, j2, k3, lane)] = o;
 }
 
 // axis 1 or 2 of a grouped complex array, one block per line (group, a, b);
@@ -67,23 +73,25 @@ __global__ void line_kernel(int N, int axis, int conj, T scale, const c2_t<T> *_
     const int bid = blockIdx.x;
     const int b = bid % N, a = (bid / N) % N, g = bid / (N * N);
     const int tid = threadIdx.x;
-    const int lane = tid % kGroup, t = tid / kGroup;
-    const size_t idx = axis == 1 ? grouped_index(N, g, t, a, b, lane) : grouped_index(N, g, a, t, b, lane);
-    line[t * kGroup + lane] = in[idx];
+    const int lane = tid % kGroup, tstep = blockDim.x / kGroup;
+    auto index = [&](int t) { return axis == 1 ? grouped_index(N, g, t, a, b, lane) : grouped_index(N, g, a, t, b, lane); };
+    for (int t = tid / kGroup; t < N; t += tstep) line[t * kGroup + lane] = in[index(t)];
     __syncthreads();
     const T sgn = conj ? T(-1) : T(1);
-    T re = T(0), im = T(0);
-    for (int j = 0; j < N; ++j) {
-        const c2_t<T> w = tw[t * N + j];
-        const T wy = sgn * w.y;
-        const c2_t<T> v = line[j * kGroup + lane];
-        re += v.x * w.x - v.y * wy;
-        im += v.x * wy + v.y * w.x;
+    for (int t = tid / kGroup; t < N; t += tstep) {
+        T re = T(0), im = T(0);
+        for (int j = 0; j < N; ++j) {
+            const c2_t<T> w = tw[t * N + j];
+            const T wy = sgn * w.y;
+            const c2_t<T> v = line[j * kGroup + lane];
+            re += v.x * w.x - v.y * wy;
+            im += v.x * wy + v.y * w.x;
+        }
+        c2_t<T> o;
+        o.x = scale * re;
+        o.y = scale * im;
+        out[index(t)] = o;
     }
-    c2_t<T> o;
-    o.x = scale * re;
-    o.y = scale * im;
-    out[idx] = o;
 }
 
 // last inverse pass: axis 3, real part, written to the caller layout rows
@@ -98,13 +106,10 @@ __global__ void inverse_rows_kernel(int N, double scale, const c2_t<T> *__restri
     const int j2 = bid % N, j1 = (bid / N) % N, g = bid / (N * N);
     const int tid = threadIdx.x;
     const size_t M = (size_t)N * N * N;
-    {
-        const int lane = tid % kGroup, k3 = tid / kGroup;
-        line[k3 * kGroup + lane] = Y[grouped_index(N, g, j1, j2, k3, lane)];
-    }
+    const int lane = tid % kGroup, tstep = blockDim.x / kGroup;
+    for (int k3 = tid / kGroup; k3 < N; k3 += tstep) line[k3 * kGroup + lane] = Y[grouped_index(N, g, j1, j2, k3, lane)];
     __syncthreads();
-    {
-        const int lane = tid % kGroup, j3 = tid / kGroup;
+    for (int j3 = tid / kGroup; j3 < N; j3 += tstep) {
         T re = T(0);
         // Re sum_k Y_k exp(+i theta_jk) = sum_k (Y.x cos - Y.y * (+sin)); tw holds exp(-i theta)
         for (int k = 0; k < N; ++k) {
@@ -115,10 +120,10 @@ __global__ void inverse_rows_kernel(int N, double scale, const c2_t<T> *__restri
         outl[lane * N + j3] = scale * (double)re;
     }
     __syncthreads();
-    {   // consecutive threads write consecutive j3 of one cell's row
-        const int lane = tid / N, j3 = tid % N;
-        const int c = g * kGroup + lane;
-        if (c < ncells) Qt[(size_t)c * M + ((size_t)j1 * N + j2) * N + j3] = outl[lane * N + j3];
+    for (int e = tid; e < kGroup * N; e += blockDim.x) {  // consecutive threads write consecutive j3 of a row
+        const int ln = e / N, j3 = e % N;
+        const int c = g * kGroup + ln;
+        if (c < ncells) Qt[(size_t)c * M + ((size_t)j1 * N + j2) * N + j3] = outl[ln * N + j3];
     }
 }
 
@@ -167,7 +172,7 @@ int forward_impl(const Handle &hd, const double *f, int ncells, cudaStream_t s)
     const int N = hd.g.N;
     const int ng = ngroups_of(ncells);
     const unsigned blocks = (unsigned)(ng * N * N);
-    const int threads = kGroup * N;
+    const int threads = line_threads(N);
     const c2_t<T> *tw = (const c2_t<T> *)(sizeof(T) == 8 ? (const void *)hd.tw64 : (const void *)hd.tw32);
     const double cf = pow(2.0 * M_PI, -1.5) * hd.g.dv * hd.g.dv * hd.g.dv;
     forward_rows_kernel<T><<<blocks, threads, sizeof(T) * N * kGroup, s>>>(N, f, ncells, tw, (c2_t<T> *)hd.X);
@@ -185,7 +190,7 @@ int inverse_impl(const Handle &hd, int ncells, double eps, double *Qt, cudaStrea
     const int N = hd.g.N;
     const int ng = ngroups_of(ncells);
     const unsigned blocks = (unsigned)(ng * N * N);
-    const int threads = kGroup * N;
+    const int threads = line_threads(N);
     const c2_t<T> *tw = (const c2_t<T> *)(sizeof(T) == 8 ? (const void *)hd.tw64 : (const void *)hd.tw32);
     const double ci = pow(2.0 * M_PI, -1.5) * hd.g.dz * hd.g.dz * hd.g.dz / eps;
     line_kernel<T><<<blocks, threads, sizeof(c2_t<T>) * N * kGroup, s>>>(N, 1, 1, T(1), tw, (const c2_t<T> *)hd.Qh,

@@ -57,7 +57,7 @@ def test_launch_count_is_host_side(libcs):
     assert libcs.lib().cs_launch_count(None, 0) == libcs.CS_EINVAL
 
 
-@pytest.mark.parametrize("N,L,lam,prec", [(5, 6.0, 1.0, 0), (34, 6.0, 1.0, 0), (2, 6.0, 1.0, 0),
+@pytest.mark.parametrize("N,L,lam,prec", [(5, 6.0, 1.0, 0), (66, 6.0, 1.0, 0), (2, 6.0, 1.0, 0),
                                           (8, -1.0, 1.0, 0), (8, 6.0, 1.5, 0), (8, 6.0, -3.0, 0),
                                           (8, 6.0, 1.0, 7), (8, float("nan"), 1.0, 0)])
 def test_weights_build_rejects_bad_arguments(libcs, N, L, lam, prec):
@@ -74,7 +74,7 @@ def test_null_handle_is_rejected(libcs):
     assert lib.cs_weights_bytes(16, 0, None) == libcs.CS_EINVAL
 
 
-@pytest.mark.parametrize("N", list(range(4, 33, 2)))
+@pytest.mark.parametrize("N", list(range(4, 33, 2)) + [40, 48, 64])
 @pytest.mark.parametrize("prec", [0, 1])
 def test_tile_layout_covers_every_valid_pair_once(libcs, N, prec):
     """Sec. 3.2: the pairs (m3, k3) with k3 - m3 + N/2 in [0, N-1]; every one of them

@@ -427,3 +427,15 @@ def test_strang_step_composition(oracle_mod):
     b = oracle_mod.rk2_homogeneous(b, N, L, 1.0, dt, 1)
     b = oracle_mod.transport_rk2(b, N, L, dx, 1.5, (0, 0, 0), far, dt / 2)
     assert np.array_equal(a, b)
+
+
+def test_sampled_convolution_equals_the_full_one(oracle_mod):
+    """convolve_at (used where the full sum is too large) is the same sum."""
+    N, L = 8, 6.0
+    from paper_1301_4195_gb300 import inputs
+    f = inputs.random_mixture_cells(N, L, 2, first_id=70)
+    fh = oracle_mod.dft_forward(f, N, L)
+    full = oracle_mod.convolve(fh, N, L, 1.0).reshape(2, -1)
+    ks = np.array([0, 5, 77, 200, 511, 256])
+    part = oracle_mod.convolve_at(fh, N, L, 1.0, ks)
+    assert np.array_equal(part, full[:, ks])
