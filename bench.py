@@ -47,7 +47,7 @@ WORKLOADS = {
 MAX_SM_MHZ = 2070.0
 # DRAM bytes (read + write) per convolution launch from ncu captures of the
 # current kernel (profiles/), keyed by (N, cells); None where not captured
-TRAFFIC = {(16, 128): 18409472, (32, 256): 2614967296 + 68261376}
+TRAFFIC = {(16, 128): 18410496, (32, 256): 2952739328 + 68189952}
 SMS = 152
 FP32_LANES = 128
 
@@ -303,6 +303,43 @@ def run_ours(args):
                             "traffic": TRAFFIC.get((N2, nc2))}}
         hb.close()
 
+    # N = 64 (the largest grid; a 40 GB float weight table): one collision
+    # evaluation of 32 random-mixture cells, and its convolution's roofline
+    n64 = None
+    if args.workload == "wall16" and not args.skip_n64:
+        N6, nc6 = 64, 32
+        t0 = time.perf_counter()
+        h6 = api.Handle(N6, L_BOX, LAM, "fp32")
+        torch.cuda.synchronize()
+        build_s = time.perf_counter() - t0
+        h6.reserve(nc6)
+        f6 = torch.from_numpy(inputs.random_mixture_cells(N6, L_BOX, nc6, first_id=7000)).to(device)
+        q6 = torch.empty_like(f6)
+        api.cs_collide(h6.ptr, f6, nc6, 1.0, q6, 1)
+        torch.cuda.synchronize()
+        api.cs_profile(h6.ptr, True)
+        api.cs_profile_read(h6.ptr, reset=True)
+        reps6 = 2
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps6):
+            api.cs_collide(h6.ptr, f6, nc6, 1.0, q6, 1)
+        b.record()
+        b.synchronize()
+        p6 = api.cs_profile_read(h6.ptr, reset=True)
+        api.cs_profile(h6.ptr, False)
+        ms6 = a.elapsed_time(b) / reps6
+        c6 = p6["convolve"][0] / max(p6["convolve"][1], 1)
+        pc6 = unique_pairs_per_cell(N6) * nc6
+        n64 = {"workload": f"one collision evaluation, N={N6}, {nc6} random-mixture cells (L=6, lambda=1)",
+               "ms_per_evaluation": ms6, "value": nc6 * N6 ** 6 / (ms6 * 1e-3), "unit": UNIT,
+               "weights_build_s": build_s, "weight_bytes": h6.weight_bytes(), "conv_ms": c6,
+               "roofline": {"bound": "alu", "achieved": 6.0 * pc6 / (c6 * 1e-3) / 1e12, "peak": peak_tops,
+                            "unit": "T FP32 FMA-pipe lane-ops/s",
+                            "frac": 6.0 * pc6 / (c6 * 1e-3) / 1e12 / peak_tops, "traffic": None}}
+        h6.close()
+
     # the wall problem in two space dimensions (secondary): 32 x-cells by 8
     # periodic y-cells, the same step with the 2-D transport
     wall2d = None
@@ -361,6 +398,8 @@ def run_ours(args):
         out["n32"] = n32
     if wall2d:
         out["wall2d"] = wall2d
+    if n64:
+        out["n64"] = n64
     if not args.skip_batched and world == 1:
         out["batched"] = batched_run(api, inputs, torch, device, args)
     if not args.skip_serve and world == 1:
@@ -509,6 +548,7 @@ def main():
     ap.add_argument("--skip-serve", action="store_true", help="omit the serving run")
     ap.add_argument("--skip-batched", action="store_true", help="omit the uneven-N batched run")
     ap.add_argument("--skip-2d", action="store_true", help="omit the two-dimensional wall problem")
+    ap.add_argument("--skip-n64", action="store_true", help="omit the N = 64 collision evaluation")
     ap.add_argument("--serve-rate", type=float, default=100.0, help="Poisson arrival rate of the serving run (1/s)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -83,8 +83,9 @@ int cs_tile_layout(int N, int precision, int *map, int cap, int *entries);
  * lambda = 0 and 1, radial Gauss-Legendre quadrature otherwise), in double on
  * the device (kept in float for CS_FP32), together with the constants of the
  * transforms and of the projection (C C^T)^{-1} of Sec. 3.3.
- *   N        even, 4..64 (the float table needs ~0.5 (27 N^6 / 64) 4 bytes:
- *            0.9 GB at N = 32, 10 GB at 48, 58 GB at 64; cs_weights_bytes)
+ *   N        even, 4..64 (the float table holds about half the 27 N^6 / 64
+ *            valid pairs, 4 bytes each, plus padding: 0.9 GB at N = 32,
+ *            58 GB at N = 64; cs_weights_bytes gives the exact size)
  *   L        > 0, half-width of the velocity cube; r0 = L
  *   lambda   -3 < lambda <= 1 (the radial integrand behaves as r^{lambda+4}
  *            near 0, so the quadrature converges for every such lambda)
