@@ -26,6 +26,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -84,7 +85,9 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the raw samples go to $CS_CLOCKS_DIR when set (kept), else to a temporary folder
+        folder = os.environ.get("CS_CLOCKS_DIR") or tempfile.mkdtemp(prefix="cs_clocks_")
+        self.path = os.path.join(folder, f"clocks_rank{index}.csv")
 
     def start(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)

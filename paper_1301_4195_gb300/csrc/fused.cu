@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kThreads<N>) inverse_project_kernel(
     extern __shared__ float2 X[];  // [N*N][P]; after the transform, reused as double q = c Qt
     __shared__ double vax[N], vsq[N], cv3[N], lbase[N * N];
     __shared__ double red[5][NW];
-    __shared__ double ycoef[5];
+    __shared__ double ycoef[5], mom_s[5];
     const int cell = blockIdx.x;
     const int g = cell / kGroup, lane = cell % kGroup;
     const int tid = threadIdx.x;
@@ -262,21 +262,21 @@ __global__ void __launch_bounds__(kThreads<N>) inverse_project_kernel(
         }
     }
     __syncthreads();
-    if (tid == 0) {
-        const double w3 = dv * dv * dv;
-        double mom[5];
-        for (int i = 0; i < 5; ++i) {
-            double t = 0;
-            if (project)
-                for (int k = 0; k < NW; ++k) t += red[i][k];
-            mom[i] = w3 * t;
-        }
-        for (int i = 0; i < 5; ++i) {
-            double s = 0;
-            if (project)
-                for (int k = 0; k < 5; ++k) s += pj.ainv[5 * i + k] * mom[k];
-            ycoef[i] = w3 * s;  // C^T y = w3 (1, v1, v2, v3, |v|^2) . y
-        }
+    // moments (thread i sums moment i over the warps), then y = (C C^T)^{-1} C q
+    // (thread i takes row i); the same order of operations as one thread would use
+    const double w3 = dv * dv * dv;
+    if (tid < 5) {
+        double t = 0;
+        if (project)
+            for (int k = 0; k < NW; ++k) t += red[tid][k];
+        mom_s[tid] = w3 * t;
+    }
+    __syncthreads();
+    if (tid < 5) {
+        double s = 0;
+        if (project)
+            for (int k = 0; k < 5; ++k) s += pj.ainv[5 * tid + k] * mom_s[k];
+        ycoef[tid] = w3 * s;  // C^T y = w3 (1, v1, v2, v3, |v|^2) . y
     }
     __syncthreads();
     const double y0 = ycoef[0], y1 = ycoef[1], y2 = ycoef[2], y3 = ycoef[3], y4 = ycoef[4];
