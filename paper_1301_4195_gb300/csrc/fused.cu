@@ -1,5 +1,6 @@
-// Whole-cell transforms for float handles with N <= 16, where one cell's
-// spectrum (N^3 complex floats, 32 KB at N = 16) fits in shared memory.
+// Whole-cell transforms for float handles with N <= 24, where one cell's
+// spectrum (N^3 complex floats, 32 KB at N = 16, 113 KB at N = 24) fits in
+// shared memory.
 //
 // forward_fused_kernel: one block per cell.  The cell's f is read once
 // (contiguous), the three axis passes of the forward transform of Sec. 3.2,
@@ -27,7 +28,7 @@
 // only).  The DFT runs in registers as a two-level Cooley-Tukey FFT,
 // N = 4 x (N/4): length-4 and length-N/4 DFTs (2, 3 or 4 points) with
 // twiddles that are compile-time constants (cos and sin of multiples of a
-// 48th of a turn, which covers N = 8, 12, 16).  One thread owns one line, so
+// 48th of a turn, which covers N = 8, 12, 16, 24).  One thread owns one line, so
 // the passes need no synchronisation inside a pass.
 //
 // Shared-memory layout of a cell: element (i1, i2, i3) at (i1 N + i2)(N + 1) + i3;
@@ -133,14 +134,18 @@ __device__ __forceinline__ void line_transform(float2 *X, int base, int stride, 
 }
 
 // one thread per line, rounded up to whole warps (the reductions shuffle over
-// full warps): 64, 160, 256 for N = 8, 12, 16
+// full warps): 64, 160, 256, 576 for N = 8, 12, 16, 24
 template <int N>
 constexpr int kThreads = (N * N + 31) / 32 * 32 < 64 ? 64 : (N * N + 31) / 32 * 32;
 
-// loops over a cell's N^3 points run kPer<N> rounds of the block, unrolled
-// with every global load issued before the first use
+// loops over a cell's N^3 points run kPer<N> rounds of the block, in chunks
+// of kChunk<N> rounds unrolled with every global load of a chunk issued
+// before its first use (one chunk up to N = 16; at N = 24 three chunks of 8,
+// which keeps the registers of a 576-thread block within its share)
 template <int N>
 constexpr int kPer = (N * N * N + kThreads<N> - 1) / kThreads<N>;
+template <int N>
+constexpr int kChunk = kPer<N> <= 16 ? kPer<N> : 8;
 
 struct Proj5 {
     double ainv[25];
@@ -155,16 +160,17 @@ __global__ void __launch_bounds__(kThreads<N>) forward_fused_kernel(const double
     const int cell = blockIdx.x;
     const int tid = threadIdx.x;
     const bool real = cell < ncells;
-    {
-        double fr[kPer<N>];
+    static_assert(kPer<N> % kChunk<N> == 0, "whole chunks");
+    for (int r0 = 0; r0 < kPer<N>; r0 += kChunk<N>) {
+        double fr[kChunk<N>];
 #pragma unroll
-        for (int r = 0; r < kPer<N>; ++r) {
-            const int j = r * NT + tid;
+        for (int r = 0; r < kChunk<N>; ++r) {
+            const int j = (r0 + r) * NT + tid;
             fr[r] = (real && j < M) ? f[(size_t)cell * M + j] : 0.0;
         }
 #pragma unroll
-        for (int r = 0; r < kPer<N>; ++r) {
-            const int j = r * NT + tid;
+        for (int r = 0; r < kChunk<N>; ++r) {
+            const int j = (r0 + r) * NT + tid;
             if (j < M) X[(j / N) * P + j % N] = make_float2((float)fr[r], 0.f);
         }
     }
@@ -202,18 +208,18 @@ __global__ void __launch_bounds__(kThreads<N>) inverse_project_kernel(
         vax[tid] = dv * (tid - H);
         vsq[tid] = vax[tid] * vax[tid];
     }
-    {
-        float2 qa[kPer<N>], qb[kPer<N>];
+    for (int r0 = 0; r0 < kPer<N>; r0 += kChunk<N>) {
+        float2 qa[kChunk<N>], qb[kChunk<N>];
 #pragma unroll
-        for (int r = 0; r < kPer<N>; ++r) {
-            const int k = r * NT + tid;
+        for (int r = 0; r < kChunk<N>; ++r) {
+            const int k = (r0 + r) * NT + tid;
             const size_t i = ((size_t)g * M + (k < M ? k : 0)) * kGroup + lane;
             qa[r] = Qh[i];
             qb[r] = Qh2 ? Qh2[i] : make_float2(0.f, 0.f);
         }
 #pragma unroll
-        for (int r = 0; r < kPer<N>; ++r) {  // two partial sums of the convolution, added in a fixed order
-            const int k = r * NT + tid;
+        for (int r = 0; r < kChunk<N>; ++r) {  // two partial sums of the convolution, added in a fixed order
+            const int k = (r0 + r) * NT + tid;
             if (k < M) X[(k / N) * P + k % N] = Qh2 ? make_float2(qa[r].x + qb[r].x, qa[r].y + qb[r].y) : qa[r];
         }
     }
@@ -288,35 +294,48 @@ __global__ void __launch_bounds__(kThreads<N>) inverse_project_kernel(
     if (tid < N) cv3[tid] = vax[tid] * fma(y4, vax[tid], y3);
     __syncthreads();
     const size_t base = (size_t)cell * M;
-    // x and y may alias out (same index only): all loads before any store
-    double xr[kPer<N>], yr[kPer<N>];
+    // x and y may alias out (same index, same thread only): a chunk's loads
+    // come before its stores
+    for (int r0 = 0; r0 < kPer<N>; r0 += kChunk<N>) {
+        double xr[kChunk<N>], yr[kChunk<N>];
 #pragma unroll
-    for (int r = 0; r < kPer<N>; ++r) {
-        const int j = r * NT + tid;
-        xr[r] = (x && j < M) ? x[base + j] : 0.0;
-        yr[r] = (y && j < M) ? y[base + j] : 0.0;
-    }
+        for (int r = 0; r < kChunk<N>; ++r) {
+            const int j = (r0 + r) * NT + tid;
+            xr[r] = (x && j < M) ? x[base + j] : 0.0;
+            yr[r] = (y && j < M) ? y[base + j] : 0.0;
+        }
 #pragma unroll
-    for (int r = 0; r < kPer<N>; ++r) {
-        const int j = r * NT + tid;
-        if (j >= M) break;
-        const int jl = j / N, j3 = j % N;
-        double o = Qd[jl * P + j3];
-        if (project) o -= lbase[jl] + cv3[j3];
-        if (x) o = fma(a, xr[r], o);
-        if (y) o = fma(b, yr[r], o);
-        out[base + j] = o;
+        for (int r = 0; r < kChunk<N>; ++r) {
+            const int j = (r0 + r) * NT + tid;
+            if (j >= M) break;
+            const int jl = j / N, j3 = j % N;
+            double o = Qd[jl * P + j3];
+            if (project) o -= lbase[jl] + cv3[j3];
+            if (x) o = fma(a, xr[r], o);
+            if (y) o = fma(b, yr[r], o);
+            out[base + j] = o;
+        }
     }
 }
 
 template <int N>
 size_t fused_smem() { return sizeof(float2) * (size_t)N * N * (N + 1); }
 
+// dynamic shared memory above the default 48 KB needs the kernel's opt-in
+template <typename Kern>
+int allow_smem(Kern kern, size_t bytes, const char *what)
+{
+    if (bytes <= 48 * 1024) return CS_OK;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return e == cudaSuccess ? CS_OK : cuda_error(e, what);
+}
+
 template <int N>
 int forward_n(const Handle &hd, const double *f, int ncells, cudaStream_t s)
 {
     const float cf = (float)(pow(2.0 * M_PI, -1.5) * hd.g.dv * hd.g.dv * hd.g.dv);
     const unsigned blocks = (unsigned)(ngroups_of(ncells) * kGroup);
+    if (int rc = allow_smem(forward_fused_kernel<N>, fused_smem<N>(), "fused forward: shared-memory attribute")) return rc;
     forward_fused_kernel<N><<<blocks, kThreads<N>, fused_smem<N>(), s>>>(f, ncells, cf, (float2 *)hd.F);
     CS_LAUNCHED(1, s, "forward transform (fused)");
     return CS_OK;
@@ -330,6 +349,8 @@ int inverse_n(const Handle &hd, int ncells, double eps, int project, double a, c
     for (int i = 0; i < 25; ++i) pj.ainv[i] = hd.cct_inv[i];
     // the scale of the last inverse pass, times the step factor c
     const float cic = (float)(c * pow(2.0 * M_PI, -1.5) * hd.g.dz * hd.g.dz * hd.g.dz / eps);
+    if (int rc = allow_smem(inverse_project_kernel<N>, fused_smem<N>(), "fused inverse: shared-memory attribute"))
+        return rc;
     inverse_project_kernel<N><<<ncells, kThreads<N>, fused_smem<N>(), s>>>(
         (const float2 *)hd.Qh, (const float2 *)qh2, cic, hd.g.dv, project, pj, a, x, b, y, out);
     CS_LAUNCHED(1, s, "inverse transform and projection (fused)");
@@ -340,7 +361,7 @@ int inverse_n(const Handle &hd, int ncells, double eps, int project, double a, c
 
 bool fused_available(const Handle &hd)
 {
-    return hd.precision == CS_FP32 && (hd.g.N == 8 || hd.g.N == 12 || hd.g.N == 16);
+    return hd.precision == CS_FP32 && (hd.g.N == 8 || hd.g.N == 12 || hd.g.N == 16 || hd.g.N == 24);
 }
 
 int launch_forward_fused(const Handle &hd, const double *f, int ncells, cudaStream_t s)
@@ -349,6 +370,7 @@ int launch_forward_fused(const Handle &hd, const double *f, int ncells, cudaStre
     case 8: return forward_n<8>(hd, f, ncells, s);
     case 12: return forward_n<12>(hd, f, ncells, s);
     case 16: return forward_n<16>(hd, f, ncells, s);
+    case 24: return forward_n<24>(hd, f, ncells, s);
     default: return set_error(CS_ENOTSUP, "fused forward transform: unsupported N");
     }
 }
@@ -360,6 +382,7 @@ int launch_inverse_project(const Handle &hd, int ncells, double eps, int project
     case 8: return inverse_n<8>(hd, ncells, eps, project, a, x, b, y, c, out, qh2, s);
     case 12: return inverse_n<12>(hd, ncells, eps, project, a, x, b, y, c, out, qh2, s);
     case 16: return inverse_n<16>(hd, ncells, eps, project, a, x, b, y, c, out, qh2, s);
+    case 24: return inverse_n<24>(hd, ncells, eps, project, a, x, b, y, c, out, qh2, s);
     default: return set_error(CS_ENOTSUP, "fused inverse transform: unsupported N");
     }
 }

@@ -87,7 +87,7 @@ def test_weights_match_oracle(cs, orc, N, lam):
 
 # ------------------------------------------------------------------ a1: forward transform
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
-@pytest.mark.parametrize("N,ncells", [(4, 1), (8, 33), (12, 5), (16, 2), (32, 1)])
+@pytest.mark.parametrize("N,ncells", [(4, 1), (8, 33), (12, 5), (16, 2), (24, 3), (32, 1)])
 def test_transform_matches_oracle(cs, orc, prec, tol, N, ncells):
     f = I.random_mixture_cells(N, L, ncells)
     h = handle(cs, N, 1.0, prec)
@@ -111,7 +111,7 @@ def test_convolution_matches_oracle(cs, orc, prec, tol, N, ncells, lam):
 
 # ------------------------------------------------------------------ a3: inverse transform
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
-@pytest.mark.parametrize("N,ncells", [(8, 3), (12, 33), (32, 1)])
+@pytest.mark.parametrize("N,ncells", [(8, 3), (12, 33), (24, 3), (32, 1)])
 def test_inverse_matches_oracle(cs, orc, prec, tol, N, ncells):
     f = I.random_mixture_cells(N, L, ncells, first_id=200)
     qh = orc.convolve(orc.dft_forward(f, N, L), N, L, 1.0) if N <= 12 else orc.dft_forward(f, N, L)
@@ -154,7 +154,8 @@ def drift(orc, Q, N):
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
 @pytest.mark.parametrize("N,ncells,lam,kind", [(8, 1, 1.0, "two_stream"), (8, 1, 0.0, "two_stream"),
                                                (12, 37, 1.0, "mix"), (16, 5, 0.0, "mix"), (16, 5, 1.0, "mix"),
-                                               (4, 3, 1.0, "mix"), (8, 3, -1.0, "mix"), (16, 2, -2.5, "mix")])
+                                               (4, 3, 1.0, "mix"), (8, 3, -1.0, "mix"), (16, 2, -2.5, "mix"),
+                                               (24, 2, 1.0, "mix")])
 def test_collide_matches_oracle(cs, orc, prec, tol, N, ncells, lam, kind):
     f = I.two_stream(N, L)[None] if kind == "two_stream" else I.random_mixture_cells(N, L, ncells, first_id=300)
     h = handle(cs, N, lam, prec)
