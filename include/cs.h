@@ -160,14 +160,19 @@ typedef struct {
     int ncells;
 } cs_batch_entry;
 
-/* The collision operator for n entries of possibly different N and lambda,
- * as one replayable unit: the first call with a given list of entries
- * captures every entry's kernels into one CUDA graph with one parallel
- * branch per entry (so entries overlap on the device), later calls with the
- * same entries, eps and conserve replay it with a single graph launch on
- * `stream`.  Each entry's result equals cs_collide on that entry.  Every
- * entry needs its own handle; handles must not be used elsewhere while the
- * call runs.  Cached graphs are dropped when one of their handles is
+/* The collision operator for n <= 16 entries of possibly different N and
+ * lambda, as one replayable unit: the first call with a given list of
+ * entries captures every entry's kernels into one CUDA graph, later calls
+ * with the same entries, eps and conserve replay it with a single graph
+ * launch on `stream`.  When two or more entries have float handles with N in
+ * {8, 16, 24, 32}, their convolutions (the O(N^6) step) run as ONE persistent
+ * kernel launch that takes the items of all of them from one queue, heaviest
+ * first; their transforms and projections, and the whole evaluation of every
+ * other entry, run on one parallel graph branch per entry.  Each entry's
+ * result is bit-identical to cs_collide on that entry.  Every entry needs its
+ * own handle; handles must not be used elsewhere while the call runs.  The
+ * workspace of a float handle in a shared launch is padded to whole 64-cell
+ * blocks (N < 32).  Cached graphs are dropped when one of their handles is
  * destroyed or its workspace grows.
  * Errors: CS_EINVAL (NULL, duplicate handle, bad sizes), CS_ENOMEM, CS_ECUDA. */
 int cs_collide_batched(const cs_batch_entry *entries, int n, double eps, int conserve, cudaStream_t stream);

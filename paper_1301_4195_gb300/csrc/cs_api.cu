@@ -258,7 +258,23 @@ int timed_transport(Handle &hd, const double *fin, int ncells, const cs_domain &
 // One collision evaluation written as out = a x + b y + c P(Qt(f)/eps)
 // (P = projection if project): forward transform, convolution, inverse
 // transform, projection and combination.  With whole-cell kernels (float,
-// N <= 16) the last three steps are one launch, timed as the inverse stage.
+// N <= 24) the last three steps are one launch, timed as the inverse stage.
+// collide_back: the steps after the convolution (hd.Qh -> out)
+int collide_back(Handle &hd, int ncells, double eps, int project, double a, const double *x, double b,
+                 const double *y, double c, double *out, cudaStream_t s)
+{
+    if (fused_available(hd)) {
+        StageTimer t(hd, CS_K_INVERSE, s);
+        return launch_inverse_project(hd, ncells, eps, project, a, x, b, y, c, out, conv_second(hd), s);
+    }
+    const bool direct = (x == nullptr && y == nullptr && c == 1.0);
+    double *qt = direct ? out : hd.Qt;
+    int rc = timed_inverse(hd, ncells, eps, qt, s);
+    if (rc) return rc;
+    if (!project && direct) return CS_OK;
+    return timed_conserve(hd, qt, ncells, project, a, x, b, y, c, out, nullptr, s);
+}
+
 int collide_combine(Handle &hd, const double *f, int ncells, double eps, int project, double a, const double *x,
                     double b, const double *y, double c, double *out, cudaStream_t s)
 {
@@ -266,16 +282,7 @@ int collide_combine(Handle &hd, const double *f, int ncells, double eps, int pro
     if (rc) return rc;
     rc = timed_convolve(hd, ncells, s);
     if (rc) return rc;
-    if (fused_available(hd)) {
-        StageTimer t(hd, CS_K_INVERSE, s);
-        return launch_inverse_project(hd, ncells, eps, project, a, x, b, y, c, out, conv_second(hd), s);
-    }
-    const bool direct = (x == nullptr && y == nullptr && c == 1.0);
-    double *qt = direct ? out : hd.Qt;
-    rc = timed_inverse(hd, ncells, eps, qt, s);
-    if (rc) return rc;
-    if (!project && direct) return CS_OK;
-    return timed_conserve(hd, qt, ncells, project, a, x, b, y, c, out, nullptr, s);
+    return collide_back(hd, ncells, eps, project, a, x, b, y, c, out, s);
 }
 
 // one Heun step of df/dt = P Qt(f) / eps, in place
@@ -510,7 +517,18 @@ int cs_collide_batched(const cs_batch_entry *entries, int n, double eps, int con
         if ((const char *)e.f < (const char *)e.Q + bytes && (const char *)e.Q < (const char *)e.f + bytes)
             return set_error(CS_EINVAL, "entry f and Q overlap");
         if (e.handle->h.prof) return set_error(CS_EINVAL, "stage timing must be off for batched calls");
-        if (int rc = ensure_workspace(e.handle->h, e.ncells)) return rc;
+    }
+    // float strip handles share one persistent convolution launch when the
+    // call has two or more of them; their cells are padded to whole CTA groups
+    int nmix = 0;
+    for (int i = 0; i < n; ++i) nmix += entries[i].ncells > 0 && strip_mixable(entries[i].handle->h);
+    const bool mixed = nmix >= 2;
+    for (int i = 0; i < n; ++i) {
+        const cs_batch_entry &e = entries[i];
+        if (e.ncells == 0) continue;
+        Handle &hd = e.handle->h;
+        const int cells = mixed && strip_mixable(hd) ? strip_mixed_cells(hd, e.ncells) : e.ncells;
+        if (int rc = ensure_workspace(hd, cells)) return rc;
     }
     std::lock_guard<std::mutex> lock(g_batch_mutex);
     cudaGraphExec_t exec = nullptr;
@@ -534,7 +552,7 @@ int cs_collide_batched(const cs_batch_entry *entries, int n, double eps, int con
                 return set_error(CS_ECUDA, "cs_collide_batched: stream creation failed");
             }
         cudaStream_t root = g_batch_streams[0];
-        std::vector<cudaEvent_t> ev(n + 1, nullptr);
+        std::vector<cudaEvent_t> ev(2 * n + 2, nullptr);
         for (auto &e : ev)
             if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
                 cudaGetLastError();
@@ -546,15 +564,46 @@ int cs_collide_batched(const cs_batch_entry *entries, int n, double eps, int con
         int rc = CS_OK;
         cudaError_t e = cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
+            // one branch per entry; with a mixed convolution the graph is
+            // fork (forward transforms; other entries whole) -> join -> the
+            // mixed convolution -> fork (inverse + projection) -> join
+            const int project = conserve ? 1 : 0;
+            auto in_mix = [&](int i) { return mixed && entries[i].ncells > 0 && strip_mixable(entries[i].handle->h); };
             cudaEventRecord(ev[0], root);
             for (int i = 0; i < n && rc == CS_OK; ++i) {
                 cudaStream_t br = g_batch_streams[i + 1];
                 cudaStreamWaitEvent(br, ev[0], 0);
-                if (entries[i].ncells > 0)
-                    rc = collide_combine(entries[i].handle->h, entries[i].f, entries[i].ncells, eps, conserve ? 1 : 0,
-                                         0.0, nullptr, 0.0, nullptr, 1.0, entries[i].Q, br);
+                Handle &hd = entries[i].handle->h;
+                if (in_mix(i))
+                    rc = fused_available(hd)
+                             ? launch_forward_fused(hd, entries[i].f, entries[i].ncells, br,
+                                                    strip_mixed_cells(hd, entries[i].ncells))
+                             : launch_forward(hd, entries[i].f, entries[i].ncells, br);
+                else if (entries[i].ncells > 0)
+                    rc = collide_combine(hd, entries[i].f, entries[i].ncells, eps, project, 0.0, nullptr, 0.0,
+                                         nullptr, 1.0, entries[i].Q, br);
                 cudaEventRecord(ev[i + 1], br);
                 cudaStreamWaitEvent(root, ev[i + 1], 0);
+            }
+            if (mixed && rc == CS_OK) {
+                std::vector<const Handle *> hs;
+                std::vector<int> cells;
+                for (int i = 0; i < n; ++i)
+                    if (in_mix(i)) {
+                        hs.push_back(&entries[i].handle->h);
+                        cells.push_back(entries[i].ncells);
+                    }
+                rc = launch_strip_mixed(hs.data(), cells.data(), (int)hs.size(), root);
+                cudaEventRecord(ev[n + 1], root);
+                for (int i = 0; i < n && rc == CS_OK; ++i) {
+                    if (!in_mix(i)) continue;
+                    cudaStream_t br = g_batch_streams[i + 1];
+                    cudaStreamWaitEvent(br, ev[n + 1], 0);
+                    rc = collide_back(entries[i].handle->h, entries[i].ncells, eps, project, 0.0, nullptr, 0.0,
+                                      nullptr, 1.0, entries[i].Q, br);
+                    cudaEventRecord(ev[n + 2 + i], br);
+                    cudaStreamWaitEvent(root, ev[n + 2 + i], 0);
+                }
             }
             e = cudaStreamEndCapture(root, &graph);
         }

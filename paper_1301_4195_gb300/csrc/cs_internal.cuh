@@ -207,9 +207,11 @@ int launch_spectral_to_natural(const Handle &hd, const void *src, int ncells, do
                                const void *src2 = nullptr);
 int launch_natural_to_spectral(const Handle &hd, const double *src, int ncells, void *dst, cudaStream_t s);
 
-// ---- fused.cu (float, N <= 16: whole-cell transforms in shared memory)
+// ---- fused.cu (float, N <= 24: whole-cell transforms in shared memory)
 bool fused_available(const Handle &hd);
-int launch_forward_fused(const Handle &hd, const double *f, int ncells, cudaStream_t s);
+// fhat of cells 0 .. ncells-1, zeros for the cells up to max(ncells, grid_cells)
+// rounded up to whole 32-cell groups
+int launch_forward_fused(const Handle &hd, const double *f, int ncells, cudaStream_t s, int grid_cells = 0);
 // out = a x + b y + P(c Qt), Qt the inverse transform of hd.Qh (+ qh2 if not
 // NULL), P the projection if project (else the identity)
 int launch_inverse_project(const Handle &hd, int ncells, double eps, int project, double a, const double *x,
@@ -222,6 +224,11 @@ int launch_convolve(const Handle &hd, int ncells, cudaStream_t s);  // hd.F -> h
 int conv_parts(const Handle &hd);
 inline const void *conv_second(const Handle &hd) { return conv_parts(hd) == 2 ? hd.Qh2 : nullptr; }
 int launch_strip(const Handle &hd, int ncells, cudaStream_t s);     // float, LAYOUT_STRIP
+
+// ---- conv_mixed.cu: the convolutions of several float strip handles in one launch
+bool strip_mixable(const Handle &hd);              // float, LAYOUT_STRIP, N in {8, 16, 24, 32}
+int strip_mixed_cells(const Handle &hd, int ncells);  // cells its workspace and forward transform must cover
+int launch_strip_mixed(const Handle *const *hds, const int *ncells, int n, cudaStream_t s);
 
 // ---- conserve.cu
 // out = a*x + b*y + c*(P Qt)   (P = projection if project, else identity), per cell

@@ -33,6 +33,8 @@
 //
 // Shared-memory layout of a cell: element (i1, i2, i3) at (i1 N + i2)(N + 1) + i3;
 // the +1 pad keeps the three line directions free of bank conflicts.
+#include <algorithm>
+
 #include "cs_internal.cuh"
 
 namespace cs {
@@ -331,10 +333,10 @@ int allow_smem(Kern kern, size_t bytes, const char *what)
 }
 
 template <int N>
-int forward_n(const Handle &hd, const double *f, int ncells, cudaStream_t s)
+int forward_n(const Handle &hd, const double *f, int ncells, int grid_cells, cudaStream_t s)
 {
     const float cf = (float)(pow(2.0 * M_PI, -1.5) * hd.g.dv * hd.g.dv * hd.g.dv);
-    const unsigned blocks = (unsigned)(ngroups_of(ncells) * kGroup);
+    const unsigned blocks = (unsigned)(ngroups_of(std::max(ncells, grid_cells)) * kGroup);
     if (int rc = allow_smem(forward_fused_kernel<N>, fused_smem<N>(), "fused forward: shared-memory attribute")) return rc;
     forward_fused_kernel<N><<<blocks, kThreads<N>, fused_smem<N>(), s>>>(f, ncells, cf, (float2 *)hd.F);
     CS_LAUNCHED(1, s, "forward transform (fused)");
@@ -364,13 +366,13 @@ bool fused_available(const Handle &hd)
     return hd.precision == CS_FP32 && (hd.g.N == 8 || hd.g.N == 12 || hd.g.N == 16 || hd.g.N == 24);
 }
 
-int launch_forward_fused(const Handle &hd, const double *f, int ncells, cudaStream_t s)
+int launch_forward_fused(const Handle &hd, const double *f, int ncells, cudaStream_t s, int grid_cells)
 {
     switch (hd.g.N) {
-    case 8: return forward_n<8>(hd, f, ncells, s);
-    case 12: return forward_n<12>(hd, f, ncells, s);
-    case 16: return forward_n<16>(hd, f, ncells, s);
-    case 24: return forward_n<24>(hd, f, ncells, s);
+    case 8: return forward_n<8>(hd, f, ncells, grid_cells, s);
+    case 12: return forward_n<12>(hd, f, ncells, grid_cells, s);
+    case 16: return forward_n<16>(hd, f, ncells, grid_cells, s);
+    case 24: return forward_n<24>(hd, f, ncells, grid_cells, s);
     default: return set_error(CS_ENOTSUP, "fused forward transform: unsupported N");
     }
 }

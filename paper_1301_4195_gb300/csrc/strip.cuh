@@ -1,0 +1,522 @@
+// Device building blocks of the strip convolution (conv_strip.cu: one
+// handle per launch; conv_mixed.cu: several handles of different N in one
+// persistent launch): mbarrier and bulk-copy wrappers with bounded waits,
+// the packed complex multiply-add, the strip bodies of kinds A and B, the
+// tile walk of a pencil, and one work item on a CTA's stage ring.
+#pragma once
+
+#include <cstdint>
+
+#include "cs_internal.cuh"
+
+namespace cs {
+
+namespace {
+
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bulk copy global -> shared, completion counted on bar (bytes and addresses 16-byte multiples)
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// wait for the phase of parity `parity`; false if the CTA aborted or the wait
+// exceeded its time limit (then the CTA is told to abort and *err is set)
+__device__ bool wait_phase(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *err, unsigned long long limit)
+{
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    for (unsigned it = 1;; ++it) {
+        if (mbar_test(bar, parity)) return true;
+        if ((it & 63) == 0) {
+            if (*abort_flag) return false;
+            if (globaltimer() - t0 > limit) {
+                *abort_flag = 1;
+                atomicOr(err, 1);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void two_sum(float &hi, float &lo, float p)
+{
+    const float s = __fadd_rn(hi, p);
+    const float bp = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
+// Complex multiply-add acc += g a b on packed float pairs (f32x2 instructions,
+// half the issue slots of the scalar form): axx = (a.x, a.x), ayy = (a.y, a.y),
+// bs = (-b.y, b.x), gg = (g, g);
+//   t = axx * b = (a.x b.x, a.x b.y);  t += ayy * bs  ->  t = a b;  acc += gg * t.
+__device__ __forceinline__ void cmad2(float2 &acc, float2 gg, float2 axx, float2 ayy, float2 b, float2 bs)
+{
+    float2 t = __fmul2_rn(axx, b);
+    t = __ffma2_rn(ayy, bs, t);
+    acc = __ffma2_rn(gg, t, acc);
+}
+
+__device__ __forceinline__ float2 dup_x(float2 a) { return make_float2(a.x, a.x); }
+__device__ __forceinline__ float2 dup_y(float2 a) { return make_float2(a.y, a.y); }
+__device__ __forceinline__ float2 rot_i(float2 b) { return make_float2(-b.y, b.x); }  // i b
+
+// K consecutive weights from entry e0 (a multiple of 4), read with 128-bit
+// loads, each as the packed pair (w, w) cmad2 takes.  (Storing every weight
+// twice in the table instead measured slower: it doubles the shared-memory
+// reads of the weights.)
+template <int K>
+__device__ __forceinline__ void wrow(const float *g, int e0, float2 (&w)[K])
+{
+    const float4 *p = reinterpret_cast<const float4 *>(g + e0);
+#pragma unroll
+    for (int q = 0; q < K / 4; ++q) {
+        const float4 v = p[q];
+        w[4 * q] = make_float2(v.x, v.x);
+        w[4 * q + 1] = make_float2(v.y, v.y);
+        w[4 * q + 2] = make_float2(v.z, v.z);
+        w[4 * q + 3] = make_float2(v.w, v.w);
+    }
+}
+
+__device__ __forceinline__ float2 wpair(const float *g, int e) { return make_float2(g[e], g[e]); }
+
+// UB uniform rows starting at row m3 = m3b: window value t is the partner at
+// s3 = smin + t; entry (u, j) uses t = j - u + UB - 1.  Weights: UB rows of K.
+template <int K, int UB>
+__device__ __forceinline__ void uniform_block(const float2 *__restrict__ arow, const float2 *__restrict__ brow,
+                                              const float *__restrict__ g, int m3b, int smin, int lane,
+                                              float2 (&acc)[K])
+{
+    float2 axx[UB], ayy[UB], bw[UB + K - 1], bs[UB + K - 1];
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+        const float2 a = arow[(m3b + u) * kGroup + lane];
+        axx[u] = dup_x(a);
+        ayy[u] = dup_y(a);
+    }
+#pragma unroll
+    for (int t = 0; t < UB + K - 1; ++t) {
+        bw[t] = brow[(smin + t) * kGroup + lane];
+        bs[t] = rot_i(bw[t]);
+    }
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+        float2 w[K];
+        wrow<K>(g, u * K, w);
+#pragma unroll
+        for (int j = 0; j < K; ++j) cmad2(acc[j], w[j], axx[u], ayy[u], bw[j - u + UB - 1], bs[j - u + UB - 1]);
+    }
+}
+
+// the uniform run: nrows rows from m3 = m3s, partner s3 = C - r + j for row r
+template <int K, int U, int R>
+__device__ __forceinline__ void uniform_run(const float2 *arow, const float2 *brow, const float *g, int m3s, int C,
+                                            int nrows, int lane, float2 (&acc)[K])
+{
+    const int nblk = nrows / U;
+    int r = 0;
+#pragma unroll 1
+    for (int b = 0; b < nblk; ++b, r += U)
+        uniform_block<K, U>(arow, brow, g + r * K, m3s + r, C - r - (U - 1), lane, acc);
+    if constexpr (R > 0) uniform_block<K, R>(arow, brow, g + r * K, m3s + r, C - r - (R - 1), lane, acc);
+}
+
+// Strip of kind A: uniform rows m3 = 0 .. k0+H (partner s3 = k0+H-m3+j),
+// then the triangle m3 = k0+H+t, t = 1..K-1, outputs j = t..K-1 (s3 = j-t).
+// The last R = (H+1) mod U uniform rows join the triangle in a compile-time
+// tail (partners s3 = 0 .. R+K-2).
+template <int N, int K, int U>
+__device__ __forceinline__ void strip_a(const float2 *arow, const float2 *brow, const float *g, int k0, int lane,
+                                        float2 (&acc)[K])
+{
+    constexpr int H = N / 2;
+    constexpr int R = (H + 1) % U;
+    const int lu = k0 + H + 1;
+    uniform_run<K, U, 0>(arow, brow, g, 0, k0 + H, lu - R, lane, acc);
+    const float *gt = g + (lu - R) * K;
+    float2 b[R + K - 1], bs[R + K - 1];
+#pragma unroll
+    for (int i = 0; i < R + K - 1; ++i) {
+        b[i] = brow[i * kGroup + lane];
+        bs[i] = rot_i(b[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i) {  // full rows m3 = lu - R + i, s3 = R - 1 - i + j
+        const float2 a = arow[(lu - R + i) * kGroup + lane];
+        float2 w[K];
+        wrow<K>(gt, i * K, w);
+#pragma unroll
+        for (int j = 0; j < K; ++j) cmad2(acc[j], w[j], dup_x(a), dup_y(a), b[R - 1 - i + j], bs[R - 1 - i + j]);
+    }
+#pragma unroll
+    for (int t = 1; t < K; ++t) {  // triangle
+        const float2 a = arow[(k0 + H + t) * kGroup + lane];
+#pragma unroll
+        for (int j = t; j < K; ++j)
+            cmad2(acc[j], wpair(gt, R * K + strip_tri_a_off(K, t) + j - t), dup_x(a), dup_y(a), b[j - t],
+                  bs[j - t]);
+    }
+}
+
+// Strip of kind B: triangle m3 = k0-H+1+t, t = 0..K-2, outputs j = 0..t
+// (s3 = N-1+j-t), then uniform rows m3 = k0+K-H+r (s3 = N-K-r+j).  The first
+// R = (N+H-K) mod U uniform rows join the triangle in a compile-time head.
+template <int N, int K, int U>
+__device__ __forceinline__ void strip_b(const float2 *arow, const float2 *brow, const float *g, int k0, int lane,
+                                        float2 (&acc)[K])
+{
+    constexpr int H = N / 2;
+    constexpr int R = (N + H - K) % U;
+    constexpr int TRI4 = strip_round4(strip_tri(K));
+    constexpr int HEADG = TRI4 + R * K;
+    constexpr int B0 = N - K - R + 1;  // lowest partner index of the head
+    float2 b[K + R - 1], bs[K + R - 1];
+#pragma unroll
+    for (int i = 0; i < K + R - 1; ++i) {
+        b[i] = brow[(B0 + i) * kGroup + lane];
+        bs[i] = rot_i(b[i]);
+    }
+#pragma unroll
+    for (int t = 0; t < K - 1; ++t) {  // triangle
+        const float2 a = arow[(k0 - H + 1 + t) * kGroup + lane];
+#pragma unroll
+        for (int j = 0; j <= t; ++j)
+            cmad2(acc[j], wpair(g, strip_tri_b_off(t) + j), dup_x(a), dup_y(a), b[N - 1 + j - t - B0],
+                  bs[N - 1 + j - t - B0]);
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i) {  // first R uniform rows
+        const float2 a = arow[(k0 + K - H + i) * kGroup + lane];
+        float2 w[K];
+        wrow<K>(g, TRI4 + i * K, w);
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            cmad2(acc[j], w[j], dup_x(a), dup_y(a), b[N - K - i + j - B0], bs[N - K - i + j - B0]);
+    }
+    const int lu = N + H - k0 - K;
+    uniform_run<K, U, 0>(arow, brow, g + HEADG, k0 + K - H + R, N - K - R, lu - R, lane, acc);
+}
+
+// Tile coordinates of one pencil, advanced in the order of the weight table:
+// m1 = lo1 .. K1/2; m2 = lo2 .. hi2, except m2 = lo2 .. K2/2 when 2 m1 = K1.
+struct TileWalk {
+    int m1, m2, m2end, lo2, hi2, K1, K2;
+    __device__ void start(int lo1, int lo2_, int hi2_, int K1_, int K2_)
+    {
+        lo2 = lo2_;
+        hi2 = hi2_;
+        K1 = K1_;
+        K2 = K2_;
+        m1 = lo1;
+        m2 = lo2;
+        m2end = (2 * m1 < K1) ? hi2 : K2 / 2;
+    }
+    __device__ void next()
+    {
+        if (++m2 > m2end) {
+            ++m1;
+            m2 = lo2;
+            m2end = (2 * m1 < K1) ? hi2 : K2 / 2;
+        }
+    }
+};
+
+// The compensated sums (hi, lo) of a strip's K outputs, folded once per m1
+// slab: in registers, or (LOCAL) in local memory, where the volatile array
+// keeps them out of the register file; at N = 24 that frees 48 registers a
+// thread and lets three CTAs share an SM instead of two.  Both forms run the
+// same operations in the same order.
+template <int K, bool LOCAL>
+struct CompSum;
+
+template <int K>
+struct CompSum<K, false> {
+    float2 hi[K], lo[K];
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            hi[j] = make_float2(0.f, 0.f);
+            lo[j] = make_float2(0.f, 0.f);
+        }
+    }
+    __device__ __forceinline__ void add(int j, float2 p)
+    {
+        two_sum(hi[j].x, lo[j].x, p.x);
+        two_sum(hi[j].y, lo[j].y, p.y);
+    }
+    __device__ __forceinline__ float2 value(int j) const { return make_float2(hi[j].x + lo[j].x, hi[j].y + lo[j].y); }
+};
+
+template <int K>
+struct CompSum<K, true> {
+    volatile float v[4 * K];  // (hi.x, hi.y, lo.x, lo.y) per output
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int i = 0; i < 4 * K; ++i) v[i] = 0.f;
+    }
+    __device__ __forceinline__ void add(int j, float2 p)
+    {
+        float hx = v[4 * j], hy = v[4 * j + 1], lx = v[4 * j + 2], ly = v[4 * j + 3];
+        two_sum(hx, lx, p.x);
+        two_sum(hy, ly, p.y);
+        v[4 * j] = hx;
+        v[4 * j + 1] = hy;
+        v[4 * j + 2] = lx;
+        v[4 * j + 3] = ly;
+    }
+    __device__ __forceinline__ float2 value(int j) const
+    {
+        return make_float2(v[4 * j] + v[4 * j + 2], v[4 * j + 1] + v[4 * j + 3]);
+    }
+};
+
+// where a strip keeps its compensated sums (measured: local memory wins at
+// N = 24 only; at N = 16 and 32 it cost 1-2 %)
+template <int N>
+constexpr bool strip_comp_local() { return N == 24; }
+
+// One problem of a strip launch: a handle's weights, tile tables and
+// workspace.  A mixed launch carries several (of different N), each owning
+// the items first .. first + N^2 nblocks S - 1 of the launch's item space.
+struct StripJob {
+    const float *ghat;
+    const int *tile0, *order;
+    const float2 *F;
+    float2 *Qh, *Qh2;
+    int *err;  // the handle's status word
+    float omega;
+    int nblocks, N, first;
+};
+
+// A persistent CTA's stage ring: barriers and the abort word at the front of
+// the dynamic shared memory, then the stages.  The use counters run across
+// items: ring use u sits in slot u % NST, phase u / NST.  Between items every
+// use has landed and been consumed, so the stage size may change from one
+// item to the next (a mixed launch); the slot and phase arithmetic may not,
+// so one launch has one NST.
+constexpr int kRingHead = 128;
+
+struct Ring {
+    unsigned char *stages;
+    uint64_t *full, *empty;
+    volatile int *abort_flag;
+    int *err;         // status word of the item in flight
+    uint32_t tt;      // ring uses consumed by this CTA before the current item
+    uint32_t issued;  // ring uses issued (thread 0)
+};
+
+template <int N, int K, int U, int NST, int GPC>
+struct StripCfg {
+    static constexpr int W = N / K;
+    static constexpr int WARPS = W * GPC;
+    static constexpr int M = N * N * N;
+    static constexpr int TSV = strip_stride(N, K);
+    static constexpr uint32_t ROWB = N * kGroup * sizeof(float2);
+    static constexpr uint32_t GB = TSV * sizeof(float);
+    static constexpr uint32_t STAGE = (2 * GPC * ROWB + GB + 127) / 128 * 128;
+    static constexpr size_t SMEM = kRingHead + (size_t)NST * STAGE;
+};
+
+template <int NST, int WARPS>
+__device__ __forceinline__ Ring ring_init(unsigned char *smem, int *err)
+{
+    static_assert(2 * NST * sizeof(uint64_t) + sizeof(int) <= kRingHead, "ring head");
+    Ring r;
+    r.full = reinterpret_cast<uint64_t *>(smem);
+    r.empty = r.full + NST;
+    r.abort_flag = reinterpret_cast<volatile int *>(r.empty + NST);
+    r.stages = smem + kRingHead;
+    r.err = err;
+    r.tt = 0;
+    r.issued = 0;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(&r.full[s], 1);
+            mbar_init(&r.empty[s], WARPS);
+        }
+        *r.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    return r;
+}
+
+// after an abort: give the copies thread 0 issued a bounded time to land
+// before the CTA exits
+template <int NST>
+__device__ __forceinline__ void ring_drain(const Ring &r, bool ok)
+{
+    if (threadIdx.x == 0 && (!ok || *r.abort_flag)) {
+        for (uint32_t u = r.tt; u < r.issued; ++u) {
+            volatile int dummy = 0;
+            wait_phase(&r.full[u % NST], (u / NST) & 1u, &dummy, r.err, kWaitNs / 20);
+        }
+    }
+}
+
+// One work item of job jb (item numbered within the job): a (pencil, group
+// block) pair, or half of its tiles when S = 2.  Thread 0 produces the
+// pencil's tiles into the ring, NST ahead of the warps; every warp sums its
+// strip.  Returns false (CTA-uniform) if a wait expired or the CTA aborted.
+template <int N, int K, int U, int NST, int GPC, int S>
+__device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &rg)
+{
+    using C = StripCfg<N, K, U, NST, GPC>;
+    constexpr int H = N / 2;
+    const int warp_id = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gl = warp_id / C::W, warp = warp_id % C::W;  // group within the CTA, strip
+    const int k0 = warp * K;
+    const bool kind_a = k0 < H;
+    const int seg = strip_seg_off(N, K, warp);
+    const int nblocks = jb.nblocks;
+    rg.err = jb.err;
+
+    const int part = item % S, rest = item / S;
+    const int pencil = jb.order[rest / nblocks];
+    const int gblk = rest % nblocks;
+    const int grp = gblk * GPC + gl;
+    const int k1 = pencil / N, k2 = pencil % N;
+    const int K1 = k1 + H, K2 = k2 + H;
+    const int lo1 = max(0, K1 - N + 1);
+    const int lo2 = max(0, K2 - N + 1), hi2 = min(N - 1, K2);
+    const int Tall = jb.tile0[pencil + 1] - jb.tile0[pencil];
+    const int tb = part == 0 ? 0 : (Tall + 1) / 2;  // this part's tiles: tb .. te-1
+    const int te = (S == 1 || part == 1) ? Tall : (Tall + 1) / 2;
+    const int T = te - tb;
+    const float2 *Fb0 = jb.F + (size_t)gblk * GPC * C::M * kGroup;
+    const float *Gp = jb.ghat + (size_t)(jb.tile0[pencil] + tb) * C::TSV;
+    float2 *Qout = part == 0 ? jb.Qh : jb.Qh2;
+    bool ok = true;
+
+    TileWalk pw;  // producer's walk (thread 0), NST tiles ahead of the consumers
+    int pt = 0;
+    auto issue_next = [&]() -> bool {
+        const uint32_t u = rg.tt + pt;
+        const int s = u % NST;
+        if (u >= NST && !wait_phase(&rg.empty[s], ((u / NST) + 1) & 1u, rg.abort_flag, rg.err, kWaitNs))
+            return false;
+        unsigned char *st = rg.stages + s * C::STAGE;
+        mbar_arrive_expect_tx(&rg.full[s], 2 * GPC * C::ROWB + C::GB);
+#pragma unroll
+        for (int q = 0; q < GPC; ++q) {
+            const float2 *Fq = Fb0 + (size_t)q * C::M * kGroup;
+            bulk_copy(st + q * C::ROWB, Fq + (size_t)(pw.m1 * N + pw.m2) * N * kGroup, C::ROWB, &rg.full[s]);
+            bulk_copy(st + (GPC + q) * C::ROWB, Fq + (size_t)((K1 - pw.m1) * N + (K2 - pw.m2)) * N * kGroup,
+                      C::ROWB, &rg.full[s]);
+        }
+        bulk_copy(st + 2 * GPC * C::ROWB, Gp + (size_t)pt * C::TSV, C::GB, &rg.full[s]);
+        ++pt;
+        ++rg.issued;
+        pw.next();
+        return true;
+    };
+    if (threadIdx.x == 0) {
+        pw.start(lo1, lo2, hi2, K1, K2);
+        for (int i = 0; i < tb; ++i) pw.next();
+        while (pt < NST && pt < T)
+            if (!issue_next()) {
+                ok = false;
+                break;
+            }
+    }
+
+    float2 acc[K];
+    CompSum<K, strip_comp_local<N>()> cs;
+#pragma unroll
+    for (int j = 0; j < K; ++j) acc[j] = make_float2(0.f, 0.f);
+    cs.zero();
+    TileWalk cw;
+    cw.start(lo1, lo2, hi2, K1, K2);
+    for (int i = 0; i < tb; ++i) cw.next();
+    int cur_m1 = cw.m1;
+    for (int t = 0; t < T && ok; ++t) {
+        const uint32_t u = rg.tt + t;
+        const int s = u % NST;
+        if (!wait_phase(&rg.full[s], (u / NST) & 1u, rg.abort_flag, rg.err, kWaitNs)) {
+            ok = false;
+            break;
+        }
+        if (cw.m1 != cur_m1) {  // new m1 slab: fold the finished one
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                cs.add(j, acc[j]);
+                acc[j] = make_float2(0.f, 0.f);
+            }
+            cur_m1 = cw.m1;
+        }
+        const unsigned char *st = rg.stages + s * C::STAGE;
+        const float2 *arow = reinterpret_cast<const float2 *>(st + gl * C::ROWB);
+        const float2 *brow = reinterpret_cast<const float2 *>(st + (GPC + gl) * C::ROWB);
+        const float *gt = reinterpret_cast<const float *>(st + 2 * GPC * C::ROWB) + seg;
+        if (kind_a)
+            strip_a<N, K, U>(arow, brow, gt, k0, lane, acc);
+        else
+            strip_b<N, K, U>(arow, brow, gt, k0, lane, acc);
+        cw.next();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&rg.empty[s]);
+        if (threadIdx.x == 0 && pt < T)
+            if (!issue_next()) ok = false;
+        __syncwarp();
+    }
+    if (__syncthreads_or(!ok || *rg.abort_flag)) return false;  // CTA-uniform
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        cs.add(j, acc[j]);
+        const float2 v = cs.value(j);
+        Qout[((size_t)grp * C::M + (size_t)pencil * N + k0 + j) * kGroup + lane] =
+            make_float2(jb.omega * v.x, jb.omega * v.y);
+    }
+    rg.tt += T;
+    return true;
+}
+
+}  // namespace
+
+}  // namespace cs

@@ -298,23 +298,33 @@ def test_graph_replay_matches_direct_launches(cs, prec):
 
 
 def test_collide_batched_matches_individual_calls(cs):
-    """Uneven N and lambda in one replayed graph: every entry equals cs_collide."""
-    specs = [(16, 0.0, 40), (16, 1.0, 24), (24, 0.0, 8), (24, 1.0, 33), (8, 1.0, 1)]
-    hs = [cs.Handle(N, L, lam, "fp32") for N, lam, _ in specs]
-    fs = [dev(I.random_mixture_cells(N, L, n, first_id=600 + 50 * i)) for i, (N, _, n) in enumerate(specs)]
+    """Uneven N and lambda in one replayed graph: every entry equals cs_collide
+    bit for bit.  The float strip entries (N = 8, 16, 24, 32; group counts odd
+    and even) share one persistent convolution launch; the N = 12 and double
+    entries run whole on their own branches."""
+    specs = [(16, 0.0, 40, "fp32"), (16, 1.0, 24, "fp32"), (24, 0.0, 8, "fp32"), (24, 1.0, 33, "fp32"),
+             (8, 1.0, 1, "fp32"), (32, 1.0, 3, "fp32"), (12, 1.0, 5, "fp32"), (8, 0.0, 7, "fp64")]
+    hs = [cs.Handle(N, L, lam, prec) for N, lam, _, prec in specs]
+    fs = [dev(I.random_mixture_cells(N, L, n, first_id=600 + 50 * i)) for i, (N, _, n, _) in enumerate(specs)]
     qs = [torch.empty_like(f) for f in fs]
-    refs = []
-    for h, f, (N, lam, n) in zip(hs, fs, specs):
+    refs, alone = [], 0
+    for h, f, (N, lam, n, _) in zip(hs, fs, specs):
         q = torch.empty_like(f)
+        cs.cs_launch_count(reset=True)
         cs.cs_collide(h.ptr, f, n, 1.0, q, 1)
+        alone += cs.cs_launch_count(reset=True)
         refs.append(host(q))
-    entries = [(h.ptr, f, q, n) for h, f, q, (_, _, n) in zip(hs, fs, qs, specs)]
+    entries = [(h.ptr, f, q, n) for h, f, q, (_, _, n, _) in zip(hs, fs, qs, specs)]
     for _ in range(2):  # capture, then replay
         for q in qs:
             q.fill_(float("nan"))
+        cs.cs_launch_count(reset=True)
         cs.cs_collide_batched(entries)
+        # six strip convolutions became one launch
+        assert cs.cs_launch_count(reset=True) == alone - 5
         for q, r in zip(qs, refs):
             assert np.array_equal(host(q), r)
+    cs.cs_status(hs[0].ptr)  # no bounded device wait expired
     with pytest.raises(cs.CSError):
         cs.cs_collide_batched([(hs[0].ptr, fs[0], qs[0], 40), (hs[0].ptr, fs[0], qs[1], 24)])  # same handle twice
     for h in hs:
