@@ -1,6 +1,11 @@
-// Whole-cell transforms for float handles with N <= 24, where one cell's
-// spectrum (N^3 complex floats, 32 KB at N = 16, 113 KB at N = 24) fits in
-// shared memory.
+// Whole-cell transforms for float handles with N in {8, 12, 16, 24, 32}.
+// Up to N = 24 one cell's spectrum (N^3 complex floats, 32 KB at N = 16,
+// 113 KB at N = 24) fits in one block's shared memory.  At N = 32 (256 KB) a
+// cell takes a cluster of two blocks on two SMs: block r holds the v1-planes
+// 16r .. 16r+15 (132 KB), the passes along axes 2 and 3 stay inside a block,
+// and the pass along axis 1 reads and writes the partner's half through
+// distributed shared memory; the projection's moments are summed over the
+// pair the same way.
 //
 // forward_fused_kernel: one block per cell.  The cell's f is read once
 // (contiguous), the three axis passes of the forward transform of Sec. 3.2,
@@ -28,12 +33,16 @@
 // only).  The DFT runs in registers as a two-level Cooley-Tukey FFT,
 // N = 4 x (N/4): length-4 and length-N/4 DFTs (2, 3 or 4 points) with
 // twiddles that are compile-time constants (cos and sin of multiples of a
-// 48th of a turn, which covers N = 8, 12, 16, 24).  One thread owns one line, so
+// 96th of a turn, which covers N = 8, 12, 16, 24, 32).  One thread owns one line, so
 // the passes need no synchronisation inside a pass.
 //
-// Shared-memory layout of a cell: element (i1, i2, i3) at (i1 N + i2)(N + 1) + i3;
-// the +1 pad keeps the three line directions free of bank conflicts.
+// Shared-memory layout of a block's planes: element (i1, i2, i3) at
+// (p N + i2)(N + 1) + i3 in the block of rank i1 / PL, p = i1 mod PL (PL = N
+// planes per block, or N/2 in a cluster pair); the +1 pad keeps the three
+// line directions free of bank conflicts.
 #include <algorithm>
+
+#include <cooperative_groups.h>
 
 #include "cs_internal.cuh"
 
@@ -41,42 +50,36 @@ namespace cs {
 
 namespace {
 
-// cos(2 pi e / 48) for e = 0 .. 12 (a quarter turn); other angles by symmetry
-__host__ __device__ constexpr float cos48q(int e)
+// cos(2 pi e / 96) for e = 0 .. 24 (a quarter turn); other angles by symmetry
+__host__ __device__ constexpr float cos96q(int e)
 {
-    return e == 0    ? 1.0f
-           : e == 1  ? 0.991444861f
-           : e == 2  ? 0.965925826f
-           : e == 3  ? 0.923879533f
-           : e == 4  ? 0.866025404f
-           : e == 5  ? 0.793353340f
-           : e == 6  ? 0.707106781f
-           : e == 7  ? 0.608761429f
-           : e == 8  ? 0.5f
-           : e == 9  ? 0.382683432f
-           : e == 10 ? 0.258819045f
-           : e == 11 ? 0.130526192f
-                     : 0.0f;
+    constexpr float c[25] = {1.0f,         0.997858923f, 0.991444861f, 0.980785280f, 0.965925826f,
+                             0.946930129f, 0.923879533f, 0.896872742f, 0.866025404f, 0.831469612f,
+                             0.793353340f, 0.751839807f, 0.707106781f, 0.659345815f, 0.608761429f,
+                             0.555570233f, 0.5f,         0.442288690f, 0.382683432f, 0.321439465f,
+                             0.258819045f, 0.195090322f, 0.130526192f, 0.065403129f, 0.0f};
+    return c[e];
 }
 
-__host__ __device__ constexpr float cos48(int e)
+__host__ __device__ constexpr float cos96(int e)
 {
-    return e <= 12 ? cos48q(e) : e <= 24 ? -cos48q(24 - e) : e <= 36 ? -cos48q(e - 24) : cos48q(48 - e);
+    return e <= 24 ? cos96q(e) : e <= 48 ? -cos96q(48 - e) : e <= 72 ? -cos96q(e - 48) : cos96q(96 - e);
 }
 
-__host__ __device__ constexpr float sin48(int e) { return cos48((e + 36) % 48); }  // sin t = cos(t - quarter turn)
+__host__ __device__ constexpr float sin96(int e) { return cos96((e + 72) % 96); }  // sin t = cos(t - quarter turn)
 
 // x * w^m with w = exp(-2 pi i / R) (forward) or exp(+2 pi i / R) (inverse),
 // m a compile-time value after unrolling; quarter turns are exact swaps
 template <int R, bool INV>
 __device__ __forceinline__ float2 rot(float2 x, int m)
 {
-    const int e = (m % R) * (48 / R);
+    static_assert(96 % R == 0, "twiddles in 96ths of a turn");
+    const int e = (m % R) * (96 / R);
     if (e == 0) return x;
-    if (e == 24) return make_float2(-x.x, -x.y);
-    if (e == 12) return INV ? make_float2(-x.y, x.x) : make_float2(x.y, -x.x);
-    if (e == 36) return INV ? make_float2(x.y, -x.x) : make_float2(-x.y, x.x);
-    const float c = cos48(e), s = INV ? sin48(e) : -sin48(e);
+    if (e == 48) return make_float2(-x.x, -x.y);
+    if (e == 24) return INV ? make_float2(-x.y, x.x) : make_float2(x.y, -x.x);
+    if (e == 72) return INV ? make_float2(x.y, -x.x) : make_float2(-x.y, x.x);
+    const float c = cos96(e), s = INV ? sin96(e) : -sin96(e);
     return make_float2(fmaf(x.x, c, -x.y * s), fmaf(x.x, s, x.y * c));
 }
 
@@ -135,17 +138,26 @@ __device__ __forceinline__ void line_transform(float2 *X, int base, int stride, 
     }
 }
 
-// one thread per line, rounded up to whole warps (the reductions shuffle over
-// full warps): 64, 160, 256, 576 for N = 8, 12, 16, 24
+// Blocks per cell (a cluster pair at N = 32), v1-planes per block, lines a
+// block transforms per pass (one per thread, rounded up to whole warps for
+// the shuffled reductions: 64, 160, 256, 576, 512 for N = 8, 12, 16, 24, 32)
 template <int N>
-constexpr int kThreads = (N * N + 31) / 32 * 32 < 64 ? 64 : (N * N + 31) / 32 * 32;
+constexpr int kCL = N == 32 ? 2 : 1;
+template <int N>
+constexpr int kPL = N / kCL<N>;
+template <int N>
+constexpr int kLines = kPL<N> * N;
+template <int N>
+constexpr int kThreads = (kLines<N> + 31) / 32 * 32 < 64 ? 64 : (kLines<N> + 31) / 32 * 32;
 
-// loops over a cell's N^3 points run kPer<N> rounds of the block, in chunks
-// of kChunk<N> rounds unrolled with every global load of a chunk issued
-// before its first use (one chunk up to N = 16; at N = 24 three chunks of 8,
-// which keeps the registers of a 576-thread block within its share)
+// loops over a block's kPts<N> points run kPer<N> rounds of the block, in
+// chunks of kChunk<N> rounds unrolled with every global load of a chunk issued
+// before its first use (one chunk up to N = 16; chunks of 8 at N = 24 and 32,
+// which keeps the registers of a 576- or 512-thread block within its share)
 template <int N>
-constexpr int kPer = (N * N * N + kThreads<N> - 1) / kThreads<N>;
+constexpr int kPts = kPL<N> * N * N;
+template <int N>
+constexpr int kPer = (kPts<N> + kThreads<N> - 1) / kThreads<N>;
 template <int N>
 constexpr int kChunk = kPer<N> <= 16 ? kPer<N> : 8;
 
@@ -153,27 +165,85 @@ struct Proj5 {
     double ainv[25];
 };
 
+namespace cg = cooperative_groups;
+
+// every block of the cell's cluster has finished its accesses to shared memory
+// (its own and, through the cluster, the partner's) before any goes on
+template <int N>
+__device__ __forceinline__ void cell_sync()
+{
+    if constexpr (kCL<N> == 2)
+        cg::this_cluster().sync();
+    else
+        __syncthreads();
+}
+
+template <int N>
+__device__ __forceinline__ int cell_rank()
+{
+    if constexpr (kCL<N> == 2)
+        return (int)cg::this_cluster().block_rank();
+    else
+        return 0;
+}
+
+// the shared array X of every block of the cell, by rank
+template <int N>
+__device__ __forceinline__ void cell_arrays(float2 *X, int rank, float2 *(&Xr)[kCL<N>])
+{
+    if constexpr (kCL<N> == 2) {
+        float2 *peer = cg::this_cluster().map_shared_rank(X, rank ^ 1);
+        Xr[rank] = X;
+        Xr[rank ^ 1] = peer;
+    } else {
+        Xr[0] = X;
+    }
+}
+
+// the transform along axis 1 of line l of block `rank`: (i2, i3) =
+// (rank PL + l / N, l mod N); element i1 sits in block i1 / PL
+template <int N, bool INV>
+__device__ __forceinline__ void axis1_transform(float2 *const (&Xr)[kCL<N>], int rank, int l, float scale)
+{
+    constexpr int P = N + 1, PL = kPL<N>;
+    const int i2 = rank * PL + l / N, i3 = l % N;
+    float2 v[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        const float2 t = Xr[j / PL][((j % PL) * N + i2) * P + i3];
+        v[j] = (j & 1) ? make_float2(-t.x, -t.y) : t;
+    }
+    fft<N, INV>(v);
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const float sk = (k & 1) ? -scale : scale;
+        Xr[k / PL][((k % PL) * N + i2) * P + i3] = make_float2(sk * v[k].x, sk * v[k].y);
+    }
+}
+
 template <int N>
 __global__ void __launch_bounds__(kThreads<N>) forward_fused_kernel(const double *__restrict__ f, int ncells, float cf,
                                                                     float2 *__restrict__ F)
 {
-    constexpr int M = N * N * N, P = N + 1, NT = kThreads<N>, LINES = N * N;
-    extern __shared__ float2 X[];  // [N*N][P]
-    const int cell = blockIdx.x;
+    constexpr int M = N * N * N, P = N + 1, NT = kThreads<N>, LINES = kLines<N>, PTS = kPts<N>;
+    extern __shared__ float2 X[];  // [PL*N][P]
+    const int cell = blockIdx.x / kCL<N>;
+    const int rank = cell_rank<N>();
     const int tid = threadIdx.x;
     const bool real = cell < ncells;
+    const size_t gbase = (size_t)cell * M + (size_t)rank * PTS;  // the block's planes in f
     static_assert(kPer<N> % kChunk<N> == 0, "whole chunks");
     for (int r0 = 0; r0 < kPer<N>; r0 += kChunk<N>) {
         double fr[kChunk<N>];
 #pragma unroll
         for (int r = 0; r < kChunk<N>; ++r) {
             const int j = (r0 + r) * NT + tid;
-            fr[r] = (real && j < M) ? f[(size_t)cell * M + j] : 0.0;
+            fr[r] = (real && j < PTS) ? f[gbase + j] : 0.0;
         }
 #pragma unroll
         for (int r = 0; r < kChunk<N>; ++r) {
             const int j = (r0 + r) * NT + tid;
-            if (j < M) X[(j / N) * P + j % N] = make_float2((float)fr[r], 0.f);
+            if (j < PTS) X[(j / N) * P + j % N] = make_float2((float)fr[r], 0.f);
         }
     }
     __syncthreads();
@@ -181,14 +251,19 @@ __global__ void __launch_bounds__(kThreads<N>) forward_fused_kernel(const double
     if (l < LINES) line_transform<N, false>(X, l * P, 1, 1.f);  // axis 3
     __syncthreads();
     if (l < LINES) line_transform<N, false>(X, (l / N) * N * P + l % N, P, 1.f);  // axis 2
-    __syncthreads();
-    if (l < LINES) line_transform<N, false>(X, (l / N) * P + l % N, N * P, cf);  // axis 1
-    __syncthreads();
+    cell_sync<N>();
+    {
+        float2 *Xr[kCL<N>];
+        cell_arrays<N>(X, rank, Xr);
+        if (l < LINES) axis1_transform<N, false>(Xr, rank, l, cf);  // axis 1
+    }
+    cell_sync<N>();
     const int g = cell / kGroup, lane = cell % kGroup;
+    const size_t fbase = (size_t)g * M + (size_t)rank * PTS;
 #pragma unroll
     for (int r = 0; r < kPer<N>; ++r) {
         const int k = r * NT + tid;
-        if (k < M) F[((size_t)g * M + k) * kGroup + lane] = X[(k / N) * P + k % N];
+        if (k < PTS) F[(fbase + k) * kGroup + lane] = X[(k / N) * P + k % N];
     }
 }
 
@@ -197,38 +272,45 @@ __global__ void __launch_bounds__(kThreads<N>) inverse_project_kernel(
     const float2 *__restrict__ Qh, const float2 *__restrict__ Qh2, float cic, double dv, int project, Proj5 pj,
     double a, const double *x, double b, const double *y, double *out)
 {
-    constexpr int M = N * N * N, P = N + 1, LINES = N * N, H = N / 2, NT = kThreads<N>, NW = NT / 32;
+    constexpr int M = N * N * N, P = N + 1, LINES = kLines<N>, PL = kPL<N>, PTS = kPts<N>, H = N / 2;
+    constexpr int NT = kThreads<N>, NW = NT / 32;
     static_assert(NT % 32 == 0, "whole warps");
-    extern __shared__ float2 X[];  // [N*N][P]; after the transform, reused as double q = c Qt
-    __shared__ double vax[N], vsq[N], cv3[N], lbase[N * N];
+    extern __shared__ float2 X[];  // [PL*N][P]; after the transform, reused as double q = c Qt
+    __shared__ double vax[N], vsq[N], cv3[N], lbase[LINES];
     __shared__ double red[5][NW];
-    __shared__ double ycoef[5], mom_s[5];
-    const int cell = blockIdx.x;
+    __shared__ double ycoef[5], mom_s[5], part[5];
+    const int cell = blockIdx.x / kCL<N>;
+    const int rank = cell_rank<N>();
     const int g = cell / kGroup, lane = cell % kGroup;
     const int tid = threadIdx.x;
     if (tid < N) {
         vax[tid] = dv * (tid - H);
         vsq[tid] = vax[tid] * vax[tid];
     }
+    const size_t fbase = (size_t)g * M + (size_t)rank * PTS;  // the block's planes in Qh
     for (int r0 = 0; r0 < kPer<N>; r0 += kChunk<N>) {
         float2 qa[kChunk<N>], qb[kChunk<N>];
 #pragma unroll
         for (int r = 0; r < kChunk<N>; ++r) {
             const int k = (r0 + r) * NT + tid;
-            const size_t i = ((size_t)g * M + (k < M ? k : 0)) * kGroup + lane;
+            const size_t i = (fbase + (k < PTS ? k : 0)) * kGroup + lane;
             qa[r] = Qh[i];
             qb[r] = Qh2 ? Qh2[i] : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int r = 0; r < kChunk<N>; ++r) {  // two partial sums of the convolution, added in a fixed order
             const int k = (r0 + r) * NT + tid;
-            if (k < M) X[(k / N) * P + k % N] = Qh2 ? make_float2(qa[r].x + qb[r].x, qa[r].y + qb[r].y) : qa[r];
+            if (k < PTS) X[(k / N) * P + k % N] = Qh2 ? make_float2(qa[r].x + qb[r].x, qa[r].y + qb[r].y) : qa[r];
         }
     }
-    __syncthreads();
+    cell_sync<N>();
     const int l = tid;
-    if (l < LINES) line_transform<N, true>(X, (l / N) * P + l % N, N * P, 1.f);  // axis 1
-    __syncthreads();
+    {
+        float2 *Xr[kCL<N>];
+        cell_arrays<N>(X, rank, Xr);
+        if (l < LINES) axis1_transform<N, true>(Xr, rank, l, 1.f);  // axis 1
+    }
+    cell_sync<N>();
     if (l < LINES) line_transform<N, true>(X, (l / N) * N * P + l % N, P, 1.f);  // axis 2
     __syncthreads();
     // axis 3: c times the real part, as a double in the same slot (one thread
@@ -243,7 +325,8 @@ __global__ void __launch_bounds__(kThreads<N>) inverse_project_kernel(
             v[j] = (j & 1) ? make_float2(-t.x, -t.y) : t;
         }
         fft<N, true>(v);
-        // moments of the line (j1, j2) = l: S0 = sum q, S3 = sum v3 q, S33 = sum v3^2 q
+        // moments of the line (j1, j2) = (rank PL + l / N, l mod N): S0 = sum q,
+        // S3 = sum v3 q, S33 = sum v3^2 q
         double s0 = 0, s3 = 0, s33 = 0;
 #pragma unroll
         for (int k = 0; k < N; ++k) {
@@ -253,11 +336,12 @@ __global__ void __launch_bounds__(kThreads<N>) inverse_project_kernel(
             s3 = fma(vax[k], qq, s3);
             s33 = fma(vsq[k], qq, s33);
         }
+        const int j1 = rank * PL + l / N, j2 = l % N;
         m[0] = s0;
-        m[1] = vax[l / N] * s0;
-        m[2] = vax[l % N] * s0;
+        m[1] = vax[j1] * s0;
+        m[2] = vax[j2] * s0;
         m[3] = s3;
-        m[4] = fma(vsq[l / N] + vsq[l % N], s0, s33);
+        m[4] = fma(vsq[j1] + vsq[j2], s0, s33);
     }
     if (project) {
         const int w = tid >> 5, ln = tid & 31;
@@ -270,16 +354,28 @@ __global__ void __launch_bounds__(kThreads<N>) inverse_project_kernel(
         }
     }
     __syncthreads();
-    // moments (thread i sums moment i over the warps), then y = (C C^T)^{-1} C q
-    // (thread i takes row i); the same order of operations as one thread would use
+    // moments (thread i sums moment i over the warps, then over the cluster's
+    // blocks in rank order), then y = (C C^T)^{-1} C q (thread i takes row
+    // i); every block of the cell gets the same doubles
     const double w3 = dv * dv * dv;
     if (tid < 5) {
         double t = 0;
         if (project)
             for (int k = 0; k < NW; ++k) t += red[tid][k];
-        mom_s[tid] = w3 * t;
+        part[tid] = t;
     }
-    __syncthreads();
+    if constexpr (kCL<N> == 2) {
+        cg::cluster_group cl = cg::this_cluster();
+        cl.sync();
+        if (tid < 5) {
+            const double *p0 = cl.map_shared_rank(part, 0), *p1 = cl.map_shared_rank(part, 1);
+            mom_s[tid] = w3 * (p0[tid] + p1[tid]);
+        }
+        cl.sync();  // both blocks have read the partner's partial sums
+    } else {
+        if (tid < 5) mom_s[tid] = w3 * part[tid];
+        __syncthreads();
+    }
     if (tid < 5) {
         double s = 0;
         if (project)
@@ -288,14 +384,14 @@ __global__ void __launch_bounds__(kThreads<N>) inverse_project_kernel(
     }
     __syncthreads();
     const double y0 = ycoef[0], y1 = ycoef[1], y2 = ycoef[2], y3 = ycoef[3], y4 = ycoef[4];
-    // correction C^T y at (v1, v2, v3) = lbase(v1, v2) + cv3(v3)
+    // correction C^T y at (v1, v2, v3) = lbase(v1, v2) + cv3(v3), for the block's lines
     for (int i = tid; i < LINES; i += NT) {
-        const double v1 = vax[i / N], v2 = vax[i % N];
-        lbase[i] = fma(y4, vsq[i / N] + vsq[i % N], fma(y2, v2, fma(y1, v1, y0)));
+        const int j1 = rank * PL + i / N, j2 = i % N;
+        lbase[i] = fma(y4, vsq[j1] + vsq[j2], fma(y2, vax[j2], fma(y1, vax[j1], y0)));
     }
     if (tid < N) cv3[tid] = vax[tid] * fma(y4, vax[tid], y3);
     __syncthreads();
-    const size_t base = (size_t)cell * M;
+    const size_t base = (size_t)cell * M + (size_t)rank * PTS;
     // x and y may alias out (same index, same thread only): a chunk's loads
     // come before its stores
     for (int r0 = 0; r0 < kPer<N>; r0 += kChunk<N>) {
@@ -303,13 +399,13 @@ __global__ void __launch_bounds__(kThreads<N>) inverse_project_kernel(
 #pragma unroll
         for (int r = 0; r < kChunk<N>; ++r) {
             const int j = (r0 + r) * NT + tid;
-            xr[r] = (x && j < M) ? x[base + j] : 0.0;
-            yr[r] = (y && j < M) ? y[base + j] : 0.0;
+            xr[r] = (x && j < PTS) ? x[base + j] : 0.0;
+            yr[r] = (y && j < PTS) ? y[base + j] : 0.0;
         }
 #pragma unroll
         for (int r = 0; r < kChunk<N>; ++r) {
             const int j = (r0 + r) * NT + tid;
-            if (j >= M) break;
+            if (j >= PTS) break;
             const int jl = j / N, j3 = j % N;
             double o = Qd[jl * P + j3];
             if (project) o -= lbase[jl] + cv3[j3];
@@ -321,7 +417,7 @@ __global__ void __launch_bounds__(kThreads<N>) inverse_project_kernel(
 }
 
 template <int N>
-size_t fused_smem() { return sizeof(float2) * (size_t)N * N * (N + 1); }
+size_t fused_smem() { return sizeof(float2) * (size_t)kPL<N> * N * (N + 1); }
 
 // dynamic shared memory above the default 48 KB needs the kernel's opt-in
 template <typename Kern>
@@ -332,13 +428,33 @@ int allow_smem(Kern kern, size_t bytes, const char *what)
     return e == cudaSuccess ? CS_OK : cuda_error(e, what);
 }
 
+// launch with kCL<N> blocks per cell, as a cluster when there are two
+template <int N, typename... Args>
+cudaError_t launch_cells(void (*kern)(Args...), unsigned cells, cudaStream_t s, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cells * kCL<N>);
+    cfg.blockDim = dim3(kThreads<N>);
+    cfg.dynamicSmemBytes = fused_smem<N>();
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kCL<N>;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = kCL<N> > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 template <int N>
 int forward_n(const Handle &hd, const double *f, int ncells, int grid_cells, cudaStream_t s)
 {
     const float cf = (float)(pow(2.0 * M_PI, -1.5) * hd.g.dv * hd.g.dv * hd.g.dv);
-    const unsigned blocks = (unsigned)(ngroups_of(std::max(ncells, grid_cells)) * kGroup);
+    const unsigned cells = (unsigned)(ngroups_of(std::max(ncells, grid_cells)) * kGroup);
     if (int rc = allow_smem(forward_fused_kernel<N>, fused_smem<N>(), "fused forward: shared-memory attribute")) return rc;
-    forward_fused_kernel<N><<<blocks, kThreads<N>, fused_smem<N>(), s>>>(f, ncells, cf, (float2 *)hd.F);
+    cudaError_t e = launch_cells<N>(forward_fused_kernel<N>, cells, s, f, ncells, cf, (float2 *)hd.F);
+    if (e != cudaSuccess) return cuda_error(e, "fused forward transform launch");
     CS_LAUNCHED(1, s, "forward transform (fused)");
     return CS_OK;
 }
@@ -353,8 +469,9 @@ int inverse_n(const Handle &hd, int ncells, double eps, int project, double a, c
     const float cic = (float)(c * pow(2.0 * M_PI, -1.5) * hd.g.dz * hd.g.dz * hd.g.dz / eps);
     if (int rc = allow_smem(inverse_project_kernel<N>, fused_smem<N>(), "fused inverse: shared-memory attribute"))
         return rc;
-    inverse_project_kernel<N><<<ncells, kThreads<N>, fused_smem<N>(), s>>>(
-        (const float2 *)hd.Qh, (const float2 *)qh2, cic, hd.g.dv, project, pj, a, x, b, y, out);
+    cudaError_t e = launch_cells<N>(inverse_project_kernel<N>, (unsigned)ncells, s, (const float2 *)hd.Qh,
+                                    (const float2 *)qh2, cic, hd.g.dv, project, pj, a, x, b, y, out);
+    if (e != cudaSuccess) return cuda_error(e, "fused inverse transform launch");
     CS_LAUNCHED(1, s, "inverse transform and projection (fused)");
     return CS_OK;
 }
@@ -363,7 +480,8 @@ int inverse_n(const Handle &hd, int ncells, double eps, int project, double a, c
 
 bool fused_available(const Handle &hd)
 {
-    return hd.precision == CS_FP32 && (hd.g.N == 8 || hd.g.N == 12 || hd.g.N == 16 || hd.g.N == 24);
+    const int N = hd.g.N;
+    return hd.precision == CS_FP32 && (N == 8 || N == 12 || N == 16 || N == 24 || N == 32);
 }
 
 int launch_forward_fused(const Handle &hd, const double *f, int ncells, cudaStream_t s, int grid_cells)
@@ -373,6 +491,7 @@ int launch_forward_fused(const Handle &hd, const double *f, int ncells, cudaStre
     case 12: return forward_n<12>(hd, f, ncells, grid_cells, s);
     case 16: return forward_n<16>(hd, f, ncells, grid_cells, s);
     case 24: return forward_n<24>(hd, f, ncells, grid_cells, s);
+    case 32: return forward_n<32>(hd, f, ncells, grid_cells, s);
     default: return set_error(CS_ENOTSUP, "fused forward transform: unsupported N");
     }
 }
@@ -385,6 +504,7 @@ int launch_inverse_project(const Handle &hd, int ncells, double eps, int project
     case 12: return inverse_n<12>(hd, ncells, eps, project, a, x, b, y, c, out, qh2, s);
     case 16: return inverse_n<16>(hd, ncells, eps, project, a, x, b, y, c, out, qh2, s);
     case 24: return inverse_n<24>(hd, ncells, eps, project, a, x, b, y, c, out, qh2, s);
+    case 32: return inverse_n<32>(hd, ncells, eps, project, a, x, b, y, c, out, qh2, s);
     default: return set_error(CS_ENOTSUP, "fused inverse transform: unsupported N");
     }
 }
