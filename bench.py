@@ -127,6 +127,28 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def conv_ms_in_mode(api, torch, h, f, n, mode, reps=5):
+    """Average convolution launch (ms) of cs_collide on n cells with the
+    weights read from the stored tiles (mode 1) or rebuilt from the radius
+    tables (mode 2), the launch shape left as tuned."""
+    keep = api.cs_tune_get(h.ptr, api.CS_TUNE_WEIGHTS)
+    api.cs_tune(h.ptr, api.CS_TUNE_WEIGHTS, mode)
+    q = torch.empty_like(f)
+    api.cs_collide(h.ptr, f, n, 1.0, q, 1)
+    api.cs_profile(h.ptr, True)
+    api.cs_profile_read(h.ptr, reset=True)
+    for _ in range(reps):
+        api.cs_collide(h.ptr, f, n, 1.0, q, 1)
+    torch.cuda.synchronize()
+    p = api.cs_profile_read(h.ptr, reset=True)
+    api.cs_profile(h.ptr, False)
+    api.cs_tune(h.ptr, api.CS_TUNE_WEIGHTS, keep)
+    return p["convolve"][0] / max(p["convolve"][1], 1)
+
+
+WEIGHT_MODES = {0: "automatic", 1: "stored tiles", 2: "radius tables"}
+
+
 def max_over_ranks(x: float, device) -> float:
     """The largest of every rank's x (the job's time is its slowest rank's)."""
     import torch
@@ -272,6 +294,12 @@ def run_ours(args):
     e2e = {"value": world * pairs_step * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
            "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes}
 
+    # store versus recompute: the convolution with stored weight tiles and with
+    # tiles rebuilt from the radius tables (the autotuner keeps the faster)
+    weights = {"chosen": WEIGHT_MODES[api.cs_tune_get(h32.ptr, api.CS_TUNE_WEIGHTS)],
+               "stored_conv_ms": conv_ms_in_mode(api, torch, h32, fd, ncells, 1),
+               "radius_conv_ms": conv_ms_in_mode(api, torch, h32, fd, ncells, 2)}
+
     # the same step in double precision (the plain FP64 GPU form)
     h64, fp64 = None, None
     if not args.skip_fp64:
@@ -298,6 +326,8 @@ def run_ours(args):
         pc2 = unique_pairs_per_cell(N2) * nc2
         n32 = {"workload": describe("wall32"), "value": 2 * nc2 * N2 ** 6 / (msb / kb * 1e-3),
                "ms_per_step": msb / kb, "conv_ms": cavg,
+               "weights": {"chosen": WEIGHT_MODES[api.cs_tune_get(hb.ptr, api.CS_TUNE_WEIGHTS)],
+                           "stored_conv_ms": cavg, "radius_conv_ms": conv_ms_in_mode(api, torch, hb, fb, nc2, 2, 2)},
                "roofline": {"bound": "alu", "achieved": 6.0 * pc2 / (cavg * 1e-3) / 1e12, "peak": peak_tops,
                             "unit": "T FP32 FMA-pipe lane-ops/s",
                             "frac": 6.0 * pc2 / (cavg * 1e-3) / 1e12 / peak_tops,
@@ -341,6 +371,13 @@ def run_ours(args):
                "roofline": {"bound": "alu", "achieved": 6.0 * pc6 / (c6 * 1e-3) / 1e12, "peak": peak_tops,
                             "unit": "T FP32 FMA-pipe lane-ops/s",
                             "frac": 6.0 * pc6 / (c6 * 1e-3) / 1e12 / peak_tops, "traffic": None}}
+        h6.close()
+        # the same evaluation from a handle holding the radius tables only
+        t0 = time.perf_counter()
+        h6 = api.Handle(N6, L_BOX, LAM, "fp32-radius")
+        torch.cuda.synchronize()
+        n64["radius_only"] = {"weights_build_s": time.perf_counter() - t0, "weight_bytes": h6.weight_bytes(),
+                              "conv_ms": conv_ms_in_mode(api, torch, h6, f6, nc6, 2, 2)}
         h6.close()
 
     # the wall problem in two space dimensions (secondary): 32 x-cells by 8
@@ -394,6 +431,7 @@ def run_ours(args):
                      "launch": {"groups_per_cta": api.cs_tune_get(h32.ptr, api.CS_TUNE_GROUPS_PER_CTA),
                                 "ctas_per_sm": api.cs_tune_get(h32.ptr, api.CS_TUNE_CTAS_PER_SM)}},
         "stage_ms_per_step": step_stage_ms,
+        "weights": weights,
         "fp64": fp64,
         "speedup_vs_fp64": fp64["ms_per_step"] / ms_step if fp64 else None,
     }

@@ -55,6 +55,14 @@ extern "C" {
 #define CS_FP64 0 /* every step in double precision */
 #define CS_FP32 1 /* transforms and convolution in float (compensated sum over xi),
                      weights built in double, moments and projection in double */
+/* OR'd into the precision of cs_weights_build / cs_weights_bytes (CS_FP32,
+ * N in {8, 16, 24, 32, 48, 64} only): build the radius tables alone, not the
+ * table of every pair.  Ghat(xi_m, zeta_k) depends on the pair only through
+ * |k'|^2, |2m' - k'|^2 and |m'|^2 (k' = k - N/2, m' = m - N/2; Sec. 2.2, eq.
+ * GHat_calc: a = |zeta|/2, b = |xi - zeta/2|, c = |xi|), and splits into
+ * A(|k'|^2, |2m'-k'|^2) - B(|m'|^2); the convolution then rebuilds every
+ * weight tile from A and B (146 MB at N = 64 instead of 58 GB). */
+#define CS_WEIGHTS_RADIUS 16
 
 typedef struct cs_handle_s *cs_handle_t;
 
@@ -65,10 +73,12 @@ int cs_version(void);
  * The pointer stays valid until the thread's next failing call. */
 const char *cs_last_error(void);
 
-/* Bytes of device memory cs_weights_build will hold for the weight table of
- * grid size N in the given precision (admission planning).  The table stores
- * the symmetrised weights Ghat(xi, zeta) + Ghat(zeta - xi, zeta) for the
- * lexicographically lower half of the valid (xi, zeta) pairs, Sec. 3.2.
+/* Bytes of device memory cs_weights_build will hold for the weights of grid
+ * size N in the given precision (admission planning).  The table stores the
+ * symmetrised weights Ghat(xi, zeta) + Ghat(zeta - xi, zeta) for the
+ * lexicographically lower half of the valid (xi, zeta) pairs, Sec. 3.2; a
+ * float handle served by the strip kernel also holds the radius tables (see
+ * CS_WEIGHTS_RADIUS, which leaves the table out).
  *   bytes (host, out).  Errors: CS_EINVAL. */
 int cs_weights_bytes(int N, int precision, size_t *bytes);
 
@@ -82,7 +92,10 @@ int cs_tile_layout(int N, int precision, int *map, int cap, int *entries);
 /* Build the convolution weights of Sec. 2.2 (eq. GHat_calc; closed forms for
  * lambda = 0 and 1, radial Gauss-Legendre quadrature otherwise), in double on
  * the device (kept in float for CS_FP32), together with the constants of the
- * transforms and of the projection (C C^T)^{-1} of Sec. 3.3.
+ * transforms and of the projection (C C^T)^{-1} of Sec. 3.3.  Float handles
+ * with N in {8, 16, 24, 32, 48, 64} also get the radius tables, so the
+ * convolution can read stored tiles or rebuild them (CS_TUNE_WEIGHTS);
+ * precision CS_FP32 | CS_WEIGHTS_RADIUS builds the radius tables only.
  *   N        even, 4..64 (the float table holds about half the 27 N^6 / 64
  *            valid pairs, 4 bytes each, plus padding: 0.9 GB at N = 32,
  *            58 GB at N = 64; cs_weights_bytes gives the exact size)
@@ -321,9 +334,14 @@ int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, double eps, d
  *                           in shared memory (2 needs an even group count)
  *   CS_TUNE_CTAS_PER_SM     resident CTAs per SM of the persistent kernel
  *                           (capped by what fits)
- * value 0 restores the automatic choice.  Errors: CS_EINVAL. */
+ *   CS_TUNE_WEIGHTS         1: read the stored weight tiles; 2: rebuild each
+ *                           tile from the radius tables (float strip handles;
+ *                           results agree to float rounding of the weights)
+ * value 0 restores the automatic choice (stored tiles where the handle has
+ * them).  Errors: CS_EINVAL, CS_ENOTSUP (a weight mode the handle lacks). */
 #define CS_TUNE_GROUPS_PER_CTA 1
 #define CS_TUNE_CTAS_PER_SM 2
+#define CS_TUNE_WEIGHTS 3
 int cs_tune(cs_handle_t h, int param, int value);
 
 /* The current value of a launch choice (0 = automatic).
@@ -332,7 +350,10 @@ int cs_tune_get(cs_handle_t h, int param, int *value);
 
 /* Time the convolution's launch choices on ncells synthetic cells on
  * `stream` (synchronising), keep the fastest in the handle and return its
- * time per launch in *ms (may be NULL).  Uses the workspace (cs_reserve).
+ * time per launch in *ms (may be NULL).  The choices are the launch shapes
+ * times the weight modes the handle has (stored tiles, radius tables): the
+ * store-versus-recompute choice of the weights is timed, not assumed.  Uses
+ * the workspace (cs_reserve).
  * Errors: CS_EINVAL, CS_ENOMEM, CS_ECUDA. */
 int cs_autotune(cs_handle_t h, int ncells, cudaStream_t stream, double *ms);
 

@@ -24,6 +24,7 @@ CS_ETIMEOUT = -5
 CS_ENONFINITE = -6
 CS_FP64 = 0
 CS_FP32 = 1
+CS_WEIGHTS_RADIUS = 16  # OR'd into the precision: radius tables only, no table of every pair
 
 _LIB_PATH = pathlib.Path(__file__).resolve().parent / "_build" / "libcs.so"
 _lib = None
@@ -268,6 +269,7 @@ def cs_transport_shard_stage(h, f_win, ncells, first_cell, total_cells, dom: Dom
 
 
 CS_TUNE_GROUPS_PER_CTA = 1
+CS_TUNE_WEIGHTS = 3
 CS_TUNE_CTAS_PER_SM = 2
 
 
@@ -322,7 +324,8 @@ class Handle:
     """Owns one cs_handle_t (weights for one (N, L, lambda, precision))."""
 
     def __init__(self, N: int, L: float, lam: float, precision: str | int = "fp64", stream=None):
-        p = precision if isinstance(precision, int) else {"fp64": CS_FP64, "fp32": CS_FP32}[precision]
+        p = precision if isinstance(precision, int) else {
+            "fp64": CS_FP64, "fp32": CS_FP32, "fp32-radius": CS_FP32 | CS_WEIGHTS_RADIUS}[precision]
         self.N, self.L, self.lam, self.precision = int(N), float(L), float(lam), p
         self._h = cs_weights_build(self.N, self.L, self.lam, p, stream)
 

@@ -108,7 +108,8 @@ int groups_per_cta(int N) { return N == 32 ? 1 : 2; }
 bool strip_mixable(const Handle &hd)
 {
     const int N = hd.g.N;
-    return hd.precision == CS_FP32 && hd.g.layout == LAYOUT_STRIP && (N == 8 || N == 16 || N == 24 || N == 32);
+    return hd.precision == CS_FP32 && hd.g.layout == LAYOUT_STRIP && (N == 8 || N == 16 || N == 24 || N == 32) &&
+           hd.has_table && !strip_uses_radius(hd);
 }
 
 int strip_mixed_cells(const Handle &hd, int ncells)

@@ -653,14 +653,20 @@ const char *cs_last_error(void) { return g_last_error.c_str(); }
 
 int cs_weights_bytes(int N, int precision, size_t *bytes)
 {
+    const bool radius_only = (precision & CS_WEIGHTS_RADIUS) != 0;
+    precision &= ~CS_WEIGHTS_RADIUS;
     if (N < 4 || N > kMaxN || (N & 1)) return set_error(CS_EINVAL, "N must be even, 4 <= N <= 64");
     if (precision != CS_FP64 && precision != CS_FP32) return set_error(CS_EINVAL, "precision must be CS_FP64 or CS_FP32");
+    if (radius_only && !(precision == CS_FP32 && strip_width(N)))
+        return set_error(CS_EINVAL, "CS_WEIGHTS_RADIUS needs CS_FP32 and N in {8, 16, 24, 32, 48, 64}");
     if (!bytes) return set_error(CS_EINVAL, "bytes is NULL");
     Geom g{};
     fill_geom(g, N, 1.0, 0.0, precision);
     const long long tiles = count_tiles(N, nullptr);
-    *bytes = (size_t)tiles * g.TSp * elem_bytes(precision) + sizeof(int) * (N * N + 1) +
-             (size_t)N * N * (sizeof(double2) + sizeof(float2));
+    size_t b = sizeof(int) * (2 * N * N + 1) + (size_t)N * N * (sizeof(double2) + sizeof(float2));
+    if (!radius_only) b += (size_t)tiles * g.TSp * elem_bytes(precision);
+    if (g.layout == LAYOUT_STRIP) b += radius_bytes(N);
+    *bytes = b;
     return CS_OK;
 }
 
@@ -681,16 +687,21 @@ int cs_tile_layout(int N, int precision, int *map, int cap, int *entries)
 
 int cs_weights_build(int N, double L, double lambda, int precision, cudaStream_t stream, cs_handle_t *out)
 {
+    const bool radius_only = (precision & CS_WEIGHTS_RADIUS) != 0;
+    precision &= ~CS_WEIGHTS_RADIUS;
     if (N < 4 || N > kMaxN || (N & 1)) return set_error(CS_EINVAL, "N must be even, 4 <= N <= 64");
     if (!(L > 0) || !is_finite(L)) return set_error(CS_EINVAL, "L must be finite and > 0");
     if (!(lambda > -3.0 && lambda <= 1.0)) return set_error(CS_EINVAL, "lambda must lie in (-3, 1]");
     if (precision != CS_FP64 && precision != CS_FP32) return set_error(CS_EINVAL, "precision must be CS_FP64 or CS_FP32");
+    if (radius_only && !(precision == CS_FP32 && strip_width(N)))
+        return set_error(CS_EINVAL, "CS_WEIGHTS_RADIUS needs CS_FP32 and N in {8, 16, 24, 32, 48, 64}");
     if (!out) return set_error(CS_EINVAL, "out is NULL");
     cs_handle_s *hs = new (std::nothrow) cs_handle_s();
     if (!hs) return set_error(CS_ENOMEM, "host allocation of the handle failed");
     Handle &hd = hs->h;
     cudaGetDevice(&hd.device);
     hd.precision = precision;
+    hd.has_table = !radius_only;
     fill_geom(hd.g, N, L, lambda, precision);
     // twiddles exp(-i 2 pi ((k-h)(j-h) mod N) / N)
     std::vector<double2> t64(N * N);
@@ -738,6 +749,7 @@ int cs_weights_build(int N, double L, double lambda, int precision, cudaStream_t
         return rc;
     }
     int rc = build_weights(hd, stream);
+    if (rc == CS_OK && hd.g.layout == LAYOUT_STRIP) rc = build_radius_tables(hd, stream);
     if (rc == CS_OK) {
         // host vectors above must outlive the async copies
         e = cudaStreamSynchronize(stream);
@@ -766,6 +778,12 @@ int cs_tune(cs_handle_t h, int param, int value)
         if (value < 0 || value > 64) return set_error(CS_EINVAL, "CTAs per SM must be in 0..64");
         hd.tune_ctas = value;
         break;
+    case CS_TUNE_WEIGHTS:
+        if (value < 0 || value > 2) return set_error(CS_EINVAL, "weights must be 0, 1 (stored) or 2 (radius tables)");
+        if (value == 1 && !hd.has_table) return set_error(CS_ENOTSUP, "the handle was built without the stored table");
+        if (value == 2 && !hd.radA) return set_error(CS_ENOTSUP, "the handle has no radius tables");
+        hd.tune_weights = value;
+        break;
     default: return set_error(CS_EINVAL, "unknown tuning parameter");
     }
     drop_graphs(hd);  // captured steps hold the old launch configuration
@@ -779,6 +797,7 @@ int cs_tune_get(cs_handle_t h, int param, int *value)
     switch (param) {
     case CS_TUNE_GROUPS_PER_CTA: *value = h->h.tune_gpc; return CS_OK;
     case CS_TUNE_CTAS_PER_SM: *value = h->h.tune_ctas; return CS_OK;
+    case CS_TUNE_WEIGHTS: *value = h->h.tune_weights; return CS_OK;
     default: return set_error(CS_EINVAL, "unknown tuning parameter");
     }
 }
@@ -799,11 +818,18 @@ int cs_autotune(cs_handle_t h, int ncells, cudaStream_t s, double *ms)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, hd.device);
     const int cand[][2] = {{0, 0}, {1, 0}, {2, 1}, {2, 2}, {2, 3}, {2, 4}, {2, 6}, {1, 2},
                            {1, 3}, {1, 4}, {1, 6}, {1, 8}, {1, 12}};
+    // weight modes to time: the stored tiles and the radius tables, where the handle has both
+    std::vector<int> modes;
+    if (hd.has_table) modes.push_back(1);
+    if (hd.radA) modes.push_back(2);
+    if (modes.empty()) modes.push_back(0);
     double best = 1e300;
-    int bg = 0, bc = 0;
-    const int keep_g = hd.tune_gpc, keep_c = hd.tune_ctas;
+    int bg = 0, bc = 0, bw = 0;
+    const int keep_g = hd.tune_gpc, keep_c = hd.tune_ctas, keep_w = hd.tune_weights;
     int rc = CS_OK;
-    for (const auto &c : cand) {
+    for (size_t ci = 0; ci < modes.size() * (sizeof(cand) / sizeof(cand[0])) && rc == CS_OK; ++ci) {
+        const auto &c = cand[ci % (sizeof(cand) / sizeof(cand[0]))];
+        hd.tune_weights = modes[ci / (sizeof(cand) / sizeof(cand[0]))];
         hd.tune_gpc = c[0];
         hd.tune_ctas = c[1];
         if ((rc = launch_convolve(hd, ncells, s)) != CS_OK) break;  // warm-up
@@ -822,6 +848,7 @@ int cs_autotune(cs_handle_t h, int ncells, cudaStream_t s, double *ms)
             best = t / 3.0;
             bg = c[0];
             bc = c[1];
+            bw = hd.tune_weights;
         }
     }
     cudaEventDestroy(a);
@@ -829,10 +856,12 @@ int cs_autotune(cs_handle_t h, int ncells, cudaStream_t s, double *ms)
     if (rc != CS_OK) {
         hd.tune_gpc = keep_g;
         hd.tune_ctas = keep_c;
+        hd.tune_weights = keep_w;
         return rc;
     }
     hd.tune_gpc = bg;
     hd.tune_ctas = bc;
+    hd.tune_weights = bw;
     drop_graphs(hd);
     if (ms) *ms = best;
     (void)sms;
@@ -901,6 +930,9 @@ int cs_handle_destroy(cs_handle_t h)
     drop_graphs(hd);
     if (hd.cap_stream) cudaStreamDestroy(hd.cap_stream);
     cudaFree(hd.ghat);
+    cudaFree(hd.radA);
+    cudaFree(hd.radB);
+    cudaFree(hd.emap);
     cudaFree(hd.pencil_tile0);
     cudaFree(hd.pencil_order);
     cudaFree(hd.err);
@@ -919,7 +951,9 @@ int cs_handle_info(cs_handle_t h, int *N, double *L, double *lambda, int *precis
     if (L) *L = hd.g.L;
     if (lambda) *lambda = hd.g.lambda;
     if (precision) *precision = hd.precision;
-    if (weight_bytes) *weight_bytes = hd.ghat_bytes;
+    if (weight_bytes)
+        *weight_bytes = hd.ghat_bytes + hd.rad_bytes + sizeof(int) * (2 * hd.g.N * hd.g.N + 1) +
+                        (size_t)hd.g.N * hd.g.N * (sizeof(double2) + sizeof(float2));
     return CS_OK;
 }
 

@@ -98,6 +98,13 @@ struct Handle {
     int *pencil_tile0 = nullptr;  // device int[N*N + 1]: first tile of each pencil
     int *pencil_order = nullptr;  // device int[N*N]: pencils by decreasing tile count
     std::vector<int> order_host;
+    // radius tables (float strip handles): A[|k'|^2][|2m'-k'|^2], B[|m'|^2], and
+    // the tile entry map; the strip kernel rebuilds weight tiles from them
+    float *radA = nullptr, *radB = nullptr;
+    int *emap = nullptr;
+    int rad_bb = 0;               // row length of A
+    size_t rad_bytes = 0;
+    bool has_table = true;        // false: built with CS_WEIGHTS_RADIUS (no stored tiles)
     int *err = nullptr;           // device word: bit 0 set when a bounded device wait expired
     int *counter = nullptr;       // device word: work counter of the persistent convolution (err + 32)
     // transforms: twiddles exp(-i 2 pi ((k-h)(j-h) mod N) / N), [k][j]
@@ -141,6 +148,7 @@ struct Handle {
     // convolution launch choices (0 = automatic), set by cs_tune / cs_autotune
     int tune_gpc = 0;     // cell groups per CTA of the strip kernel (1 or 2)
     int tune_ctas = 0;    // resident CTAs per SM of the persistent strip kernel
+    int tune_weights = 0; // 1 = stored tiles, 2 = tiles rebuilt from the radius tables
     // stage timing (cs_profile)
     bool prof = false;
     struct Rec {
@@ -195,6 +203,11 @@ void tile_entry_map(const Geom &g, std::vector<int> &map);
 // ---- weights.cu
 long long count_tiles(int N, int *pencil_tile0_host /* may be null, size N*N+1 */);
 int build_weights(Handle &hd, cudaStream_t s);
+// radius tables of a float strip handle: dimensions, bytes (0 where the strip
+// kernel does not serve N), build
+void radius_dims(int N, int *KK, int *BB, int *MM);
+size_t radius_bytes(int N);
+int build_radius_tables(Handle &hd, cudaStream_t s);
 int sample_weights(Handle &hd, const int *km_host, int n, double *out_host);
 
 // ---- transform.cu
@@ -224,6 +237,8 @@ int launch_convolve(const Handle &hd, int ncells, cudaStream_t s);  // hd.F -> h
 int conv_parts(const Handle &hd);
 inline const void *conv_second(const Handle &hd) { return conv_parts(hd) == 2 ? hd.Qh2 : nullptr; }
 int launch_strip(const Handle &hd, int ncells, cudaStream_t s);     // float, LAYOUT_STRIP
+int launch_strip_radius(const Handle &hd, int ncells, cudaStream_t s);  // conv_radius.cu
+bool strip_uses_radius(const Handle &hd);  // the handle's strip launches rebuild tiles from the radius tables
 
 // ---- conv_mixed.cu: the convolutions of several float strip handles in one launch
 bool strip_mixable(const Handle &hd);              // float, LAYOUT_STRIP, N in {8, 16, 24, 32}

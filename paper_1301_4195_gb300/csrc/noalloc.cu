@@ -69,6 +69,12 @@ Handle view_of(const Handle &hd)
     v.total_tiles = hd.total_tiles;
     v.pencil_tile0 = hd.pencil_tile0;
     v.pencil_order = hd.pencil_order;
+    v.radA = hd.radA;
+    v.radB = hd.radB;
+    v.emap = hd.emap;
+    v.rad_bb = hd.rad_bb;
+    v.has_table = hd.has_table;
+    v.tune_weights = hd.tune_weights;
     v.err = hd.err;
     v.counter = hd.counter;
     v.tw64 = hd.tw64;

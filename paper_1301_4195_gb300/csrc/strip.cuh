@@ -331,6 +331,11 @@ struct StripJob {
     int *err;  // the handle's status word
     float omega;
     int nblocks, N, first;
+    // radius tables (launches that rebuild the weight tiles): A, B, the tile
+    // entry map and the row length of A
+    const float *radA = nullptr, *radB = nullptr;
+    const int *emap = nullptr;
+    int bbn = 0;
 };
 
 // A persistent CTA's stage ring: barriers and the abort word at the front of
@@ -350,7 +355,18 @@ struct Ring {
     uint32_t issued;  // ring uses issued (thread 0)
 };
 
-template <int N, int K, int U, int NST, int GPC>
+__host__ __device__ constexpr int strip_seg_max(int N, int K)
+{
+    int m = 0;
+    for (int w = 0; w < N / K; ++w) m = strip_seg_size(N, K, w) > m ? strip_seg_size(N, K, w) : m;
+    return m;
+}
+
+// Shared memory of a strip CTA: the ring head, NST stages (two f-hat rows per
+// group, plus the weight tile unless RAD), and with RAD one weight segment
+// per warp rebuilt from the radius tables, the tile entry map and the table
+// B (both copied in once per CTA).
+template <int N, int K, int U, int NST, int GPC, bool RAD = false>
 struct StripCfg {
     static constexpr int W = N / K;
     static constexpr int WARPS = W * GPC;
@@ -358,9 +374,48 @@ struct StripCfg {
     static constexpr int TSV = strip_stride(N, K);
     static constexpr uint32_t ROWB = N * kGroup * sizeof(float2);
     static constexpr uint32_t GB = TSV * sizeof(float);
-    static constexpr uint32_t STAGE = (2 * GPC * ROWB + GB + 127) / 128 * 128;
-    static constexpr size_t SMEM = kRingHead + (size_t)NST * STAGE;
+    static constexpr uint32_t STAGE = (2 * GPC * ROWB + (RAD ? 0 : GB) + 127) / 128 * 128;
+    static constexpr int WBUF = RAD ? strip_round4(strip_seg_max(N, K)) : 0;  // floats per warp
+    static constexpr int NB = RAD ? 3 * (N / 2) * (N / 2) + 1 : 0;              // entries of B
+    static constexpr size_t SMEM = kRingHead + (size_t)NST * STAGE +
+                                   sizeof(float) * ((size_t)WARPS * WBUF + (RAD ? TSV : 0) + strip_round4(NB));
 };
+
+// RAD: the per-CTA copies of the tile entry map and of B, after the warps'
+// weight segments
+
+
+// The weight segment of strip w (entries seg .. seg+nseg-1 of the tile
+// layout) of tile (m1, m2) of pencil (k1, k2), rebuilt from the radius
+// tables: entry (m3, k3) gets 2 A - B(|m'|^2) - B(|s'|^2), the centre tile
+// A - B(|m'|^2), zero where k' = 0 and in the padding.  Lanes take every
+// 32nd entry.
+template <int N>
+__device__ __forceinline__ void radius_segment(const StripJob &jb, const int *emap, const float *radB, int seg,
+                                               int nseg, int k1, int k2, int m1, int m2, float *wb, int lane)
+{
+    constexpr int h = N / 2;
+    const int k1p = k1 - h, k2p = k2 - h, m1p = m1 - h, m2p = m2 - h;
+    const int s1p = k1p - m1p, s2p = k2p - m2p, d1 = 2 * m1p - k1p, d2 = 2 * m2p - k2p;
+    const bool centre = s1p == m1p && s2p == m2p;
+    const int kk12 = k1p * k1p + k2p * k2p, bb12 = d1 * d1 + d2 * d2;
+    const int mm12 = m1p * m1p + m2p * m2p, ss12 = s1p * s1p + s2p * s2p;
+    for (int p = lane; p < nseg; p += 32) {
+        const int e = emap[seg + p];
+        float w = 0.f;
+        if (e >= 0) {
+            const int m3p = (e >> 8) - h, k3p = (e & 255) - h;
+            const int kk = kk12 + k3p * k3p;
+            if (kk != 0) {
+                const int d3 = 2 * m3p - k3p, s3p = k3p - m3p;
+                const float A = __ldg(jb.radA + (size_t)kk * jb.bbn + bb12 + d3 * d3);
+                w = A - radB[mm12 + m3p * m3p];
+                if (!centre) w += A - radB[ss12 + s3p * s3p];
+            }
+        }
+        wb[p] = w;
+    }
+}
 
 template <int NST, int WARPS>
 __device__ __forceinline__ Ring ring_init(unsigned char *smem, int *err)
@@ -404,10 +459,10 @@ __device__ __forceinline__ void ring_drain(const Ring &r, bool ok)
 // block) pair, or half of its tiles when S = 2.  Thread 0 produces the
 // pencil's tiles into the ring, NST ahead of the warps; every warp sums its
 // strip.  Returns false (CTA-uniform) if a wait expired or the CTA aborted.
-template <int N, int K, int U, int NST, int GPC, int S>
+template <int N, int K, int U, int NST, int GPC, int S, bool RAD = false>
 __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &rg)
 {
-    using C = StripCfg<N, K, U, NST, GPC>;
+    using C = StripCfg<N, K, U, NST, GPC, RAD>;
     constexpr int H = N / 2;
     const int warp_id = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gl = warp_id / C::W, warp = warp_id % C::W;  // group within the CTA, strip
@@ -442,7 +497,7 @@ __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &r
         if (u >= NST && !wait_phase(&rg.empty[s], ((u / NST) + 1) & 1u, rg.abort_flag, rg.err, kWaitNs))
             return false;
         unsigned char *st = rg.stages + s * C::STAGE;
-        mbar_arrive_expect_tx(&rg.full[s], 2 * GPC * C::ROWB + C::GB);
+        mbar_arrive_expect_tx(&rg.full[s], 2 * GPC * C::ROWB + (RAD ? 0 : C::GB));
 #pragma unroll
         for (int q = 0; q < GPC; ++q) {
             const float2 *Fq = Fb0 + (size_t)q * C::M * kGroup;
@@ -450,7 +505,7 @@ __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &r
             bulk_copy(st + (GPC + q) * C::ROWB, Fq + (size_t)((K1 - pw.m1) * N + (K2 - pw.m2)) * N * kGroup,
                       C::ROWB, &rg.full[s]);
         }
-        bulk_copy(st + 2 * GPC * C::ROWB, Gp + (size_t)pt * C::TSV, C::GB, &rg.full[s]);
+        if constexpr (!RAD) bulk_copy(st + 2 * GPC * C::ROWB, Gp + (size_t)pt * C::TSV, C::GB, &rg.full[s]);
         ++pt;
         ++rg.issued;
         pw.next();
@@ -475,9 +530,22 @@ __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &r
     cw.start(lo1, lo2, hi2, K1, K2);
     for (int i = 0; i < tb; ++i) cw.next();
     int cur_m1 = cw.m1;
+    float *wb = nullptr;  // RAD: this warp's weight segment, the entry map and B
+    const int *s_emap = nullptr;
+    const float *s_radB = nullptr;
+    if constexpr (RAD) {
+        float *r = reinterpret_cast<float *>(rg.stages + NST * C::STAGE);
+        wb = r + warp_id * C::WBUF;
+        s_emap = reinterpret_cast<const int *>(r + C::WARPS * C::WBUF);
+        s_radB = r + C::WARPS * C::WBUF + C::TSV;
+    }
     for (int t = 0; t < T && ok; ++t) {
         const uint32_t u = rg.tt + t;
         const int s = u % NST;
+        if constexpr (RAD) {  // before the wait: the gathers overlap the tile's copies
+            radius_segment<N>(jb, s_emap, s_radB, seg, strip_seg_size(N, K, warp), k1, k2, cw.m1, cw.m2, wb, lane);
+            __syncwarp();
+        }
         if (!wait_phase(&rg.full[s], (u / NST) & 1u, rg.abort_flag, rg.err, kWaitNs)) {
             ok = false;
             break;
@@ -493,7 +561,7 @@ __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &r
         const unsigned char *st = rg.stages + s * C::STAGE;
         const float2 *arow = reinterpret_cast<const float2 *>(st + gl * C::ROWB);
         const float2 *brow = reinterpret_cast<const float2 *>(st + (GPC + gl) * C::ROWB);
-        const float *gt = reinterpret_cast<const float *>(st + 2 * GPC * C::ROWB) + seg;
+        const float *gt = RAD ? wb : reinterpret_cast<const float *>(st + 2 * GPC * C::ROWB) + seg;
         if (kind_a)
             strip_a<N, K, U>(arow, brow, gt, k0, lane, acc);
         else
@@ -515,6 +583,122 @@ __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &r
     }
     rg.tt += T;
     return true;
+}
+
+
+// Persistent kernel: CTAs take (pencil, group block) items from an atomic
+// counter, heaviest pencils first, so the tail of the launch holds only the
+// smallest items.
+// Resident CTAs per SM the register allocation must allow: at N = 16 the
+// kernel is latency-bound and 128 registers (8 one-group or 4 two-group CTAs
+// per SM) measured faster than the ~134 the compiler picks on its own; for
+// the other N one CTA (no cap) measured best.
+template <int N, int GPC>
+constexpr int strip_min_ctas() { return N == 16 ? (GPC == 1 ? 8 : 4) : 1; }
+
+template <int N, int K, int U, int NST, int GPC, int S, bool RAD>
+__global__ void __launch_bounds__(32 * (N / K) * GPC, strip_min_ctas<N, GPC>())
+    conv_strip_kernel(StripJob jb, int *counter)
+{
+    using C = StripCfg<N, K, U, NST, GPC, RAD>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int s_item;
+    Ring rg = ring_init<NST, C::WARPS>(smem, jb.err);
+    if constexpr (RAD) {  // the entry map and B into shared memory, once per CTA
+        float *r = reinterpret_cast<float *>(rg.stages + NST * C::STAGE) + C::WARPS * C::WBUF;
+        int *se = reinterpret_cast<int *>(r);
+        for (int i = threadIdx.x; i < C::TSV; i += blockDim.x) se[i] = jb.emap[i];
+        for (int i = threadIdx.x; i < C::NB; i += blockDim.x) r[C::TSV + i] = jb.radB[i];
+        __syncthreads();
+    }
+    const int nitems = N * N * jb.nblocks * S;
+    bool ok = true;
+    for (;;) {
+        // thread 0 decides for the whole CTA, so every thread leaves the loop together
+        if (threadIdx.x == 0) s_item = *rg.abort_flag ? nitems : atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= nitems) break;
+        if (!strip_item<N, K, U, NST, GPC, S, RAD>(jb, item, rg)) {
+            ok = false;
+            break;
+        }
+    }
+    ring_drain<NST>(rg, ok);
+}
+
+template <int N, int K, int U, int NST, int GPC, int S, bool RAD>
+int launch_cfg(const Handle &hd, int ncells, cudaStream_t s)
+{
+    using C = StripCfg<N, K, U, NST, GPC, RAD>;
+    static_assert(K % 4 == 0 && (N / 2) % K == 0, "strip width must divide N/2 and be a multiple of 4");
+    static_assert(C::STAGE % 16 == 0 && C::ROWB % 16 == 0 && C::GB % 16 == 0, "bulk copies need 16-byte units");
+    auto kern = conv_strip_kernel<N, K, U, NST, GPC, S, RAD>;
+    if (C::SMEM > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        if (e != cudaSuccess) return cuda_error(e, "strip kernel shared-memory attribute");
+    }
+    const int ng = ngroups_of(ncells);
+    const int nblocks = ng / GPC;  // callers pick GPC dividing ng
+    const int nitems = N * N * nblocks * S;
+    static int per_sm[2] = {0, 0};  // resident CTAs per SM, per GPC variant
+    int &occ = per_sm[GPC - 1];
+    if (occ == 0) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, 32 * C::WARPS, C::SMEM) != cudaSuccess || v < 1) {
+            cudaGetLastError();
+            v = 1;
+        }
+        occ = v;
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, hd.device);
+    // automatic: about two items per resident CTA, so the queue can balance
+    // pencils of unequal size (measured best at N = 16, 128 cells)
+    const int autoper = std::max(1, std::min(occ, (int)((nitems + 2 * sms - 1) / (2 * std::max(1, sms)))));
+    const int per = hd.tune_ctas > 0 ? std::min(hd.tune_ctas, occ) : autoper;
+    const int grid = std::min(nitems, std::max(1, sms) * per);
+    const float omega = (float)(hd.g.dz * hd.g.dz * hd.g.dz);
+    cudaError_t e = cudaMemsetAsync(hd.counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return cuda_error(e, "strip kernel work counter");
+    StripJob jb{(const float *)hd.ghat, hd.pencil_tile0, hd.pencil_order, (const float2 *)hd.F,
+                (float2 *)hd.Qh, (float2 *)hd.Qh2, hd.err, omega, nblocks, N, 0};
+    if constexpr (RAD) {
+        jb.radA = hd.radA;
+        jb.radB = hd.radB;
+        jb.emap = hd.emap;
+        jb.bbn = hd.rad_bb;
+    }
+    kern<<<grid, 32 * C::WARPS, C::SMEM, s>>>(jb, hd.counter);
+    CS_LAUNCHED(1, s, RAD ? "convolution (strip kernel, radius tables)" : "convolution (strip kernel)");
+    return CS_OK;
+}
+
+template <int N, int K, int U, int NST1, int NST2, int S, bool RAD>
+int launch_n(const Handle &hd, int ncells, cudaStream_t s)
+{
+    const bool even = ngroups_of(ncells) % 2 == 0;
+    const bool two = hd.tune_gpc == 2 || (hd.tune_gpc == 0 && N <= 16);  // measured: 1 group per CTA wins at N = 32
+    if (even && two) return launch_cfg<N, K, U, NST2, 2, S, RAD>(hd, ncells, s);
+    return launch_cfg<N, K, U, NST1, 1, S, RAD>(hd, ncells, s);
+}
+
+// the strip launch of every N, with stored weight tiles or (RAD) tiles
+// rebuilt from the radius tables; conv_strip.cu and conv_radius.cu each
+// instantiate one
+template <bool RAD>
+int launch_strip_mode(const Handle &hd, int ncells, cudaStream_t s)
+{
+    switch (hd.g.N) {
+    case 8: return launch_n<8, 4, 4, 4, 4, 1, RAD>(hd, ncells, s);
+    case 16: return launch_n<16, 8, 8, 3, 3, 2, RAD>(hd, ncells, s);
+    case 24: return launch_n<24, 12, 4, 3, 2, 1, RAD>(hd, ncells, s);
+    case 32: return launch_n<32, 8, 8, 3, 3, 1, RAD>(hd, ncells, s);
+    case 48: return launch_n<48, 8, 8, 3, 2, 1, RAD>(hd, ncells, s);
+    case 64: return launch_n<64, 8, 8, 3, 2, 1, RAD>(hd, ncells, s);
+    default: return set_error(CS_ENOTSUP, "strip kernel: unsupported N");
+    }
 }
 
 }  // namespace

@@ -20,6 +20,21 @@
 // each row (one m3) is padded with zeros to a multiple of 4 entries so rows
 // start on 16-byte boundaries.  Tiles of one pencil are consecutive, pencils
 // in (k1, k2) order.
+//
+// Radius tables (the alternative to storing every pair).  Ghat depends on the
+// pair only through three integer squared radii, with k' = k - N/2 and
+// m' = m - N/2:  a = dz |k'| / 2,  b = dz |2m' - k'| / 2,  c = dz |m'|, and
+// splits into two one- and two-index integrals,
+//   Ghat(m, k) = A(|k'|^2, |2m' - k'|^2) - B(|m'|^2),
+//   A = sqrt(2/pi) int_0^{r0} r^{lambda+2} sinc(r a) sinc(r b) dr,
+//   B = sqrt(2/pi) int_0^{r0} r^{lambda+2} sinc(r c) dr,
+// (Ghat = 0 when k' = 0).  For the mirror partner s' = k' - m' the middle
+// radius is the same, so the symmetrised weight of a tile entry is
+// 2 A - B(|m'|^2) - B(|s'|^2).  A holds (3 h^2 + 1) x (3 (N-1)^2 + 1) floats
+// (h = N/2: 9 MB at N = 32, 146 MB at N = 64), B 3 h^2 + 1; both are
+// evaluated in double (the same closed forms and quadrature as the table) and
+// kept in float.  The strip kernel can rebuild each weight tile from them in
+// shared memory instead of reading the stored tile (conv_strip.cu).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -237,6 +252,78 @@ __global__ void build_table_kernel(Geom g, QuadRule q, const int *__restrict__ t
     }
 }
 
+// int_0^r0 r^{lambda+2} sinc(a r) sinc(b r) dr by composite Gauss-Legendre,
+// the panels as in radial_bracket_quad (b = 0 gives the one-radius integral)
+__device__ double radial_pair_quad(double a, double b, double r0, double lam, const QuadRule &q)
+{
+    const int np = (int)ceil((a + b) * r0 / 3.0) + 2;
+    const double hw = r0 / np;
+    double total = 0.0;
+    for (int p = 0; p < np; ++p) {
+        const int nsub = (p == 0) ? 12 : 1;
+        for (int sidx = 0; sidx < nsub; ++sidx) {
+            double lo, hi;
+            if (p == 0) {
+                hi = hw * exp2(-(double)(nsub - 1 - sidx));
+                lo = (sidx == 0) ? 0.0 : hw * exp2(-(double)(nsub - sidx));
+            } else {
+                lo = p * hw;
+                hi = (p + 1) * hw;
+            }
+            const double mid = 0.5 * (lo + hi), half = 0.5 * (hi - lo);
+            for (int i = 0; i < kQuadNodes; ++i) {
+                const double r = mid + half * q.x[i];
+                total += half * q.w[i] * pow(r, lam + 2.0) * (dsinc(a * r) * dsinc(b * r));
+            }
+        }
+    }
+    return total;
+}
+
+// A(kk, bb) for kk = 1 .. KK-1, bb = 0 .. BB-1 (row kk = 0 is never read: Ghat(xi, 0) = 0)
+__global__ void radius_a_kernel(Geom g, QuadRule q, int KK, int BB, float *__restrict__ A)
+{
+    const long long n = (long long)KK * BB;
+    const double dz = g.dz, r0 = g.L, lam = g.lambda;
+    const double pref = 0.79788456080286535588;  // sqrt(2 / pi)
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int kk = (int)(i / BB), bb = (int)(i % BB);
+        double v = 0.0;
+        if (kk > 0) {
+            const double a = 0.5 * dz * sqrt((double)kk), b = 0.5 * dz * sqrt((double)bb);
+            if (lam == 0.0 || lam == 1.0) {
+                const int il = (int)lam;
+                if (bb == 0) {
+                    v = sinc_moment(a, r0, il);
+                } else {
+                    // a^2 - b^2 = dz^2 (kk - bb) / 4 = dz^2 (m'.k' - |m'|^2), an integer multiple
+                    const double qv = a + b;
+                    const double pv = dz * dz * (0.25 * (double)(kk - bb)) / qv;
+                    v = (cos_moment(pv, r0, il) - cos_moment(qv, r0, il)) / (2.0 * a * b);
+                }
+            } else {
+                v = radial_pair_quad(a, b, r0, lam, q);
+            }
+        }
+        A[i] = (float)(pref * v);
+    }
+}
+
+// B(mm) for mm = 0 .. MM-1
+__global__ void radius_b_kernel(Geom g, QuadRule q, int MM, float *__restrict__ B)
+{
+    const int mm = blockIdx.x * blockDim.x + threadIdx.x;
+    if (mm >= MM) return;
+    const double c = g.dz * sqrt((double)mm), r0 = g.L, lam = g.lambda;
+    const double pref = 0.79788456080286535588;
+    double v;
+    if (lam == 0.0 || lam == 1.0)
+        v = sinc_moment(mm == 0 ? 0.0 : c, r0, (int)lam);
+    else
+        v = radial_pair_quad(c, 0.0, r0, lam, q);
+    B[mm] = (float)(pref * v);
+}
+
 __global__ void sample_kernel(Geom g, QuadRule q, const int *__restrict__ km, int n, double *__restrict__ out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -264,6 +351,58 @@ long long count_tiles(int N, int *pencil_tile0)
     return total;
 }
 
+void radius_dims(int N, int *KK, int *BB, int *MM)
+{
+    const int h = N / 2;
+    *KK = 3 * h * h + 1;            // |k'|^2, k'_i in [-h, h-1]
+    *BB = 3 * (N - 1) * (N - 1) + 1;  // |2m' - k'|^2, components in [-(N-1), N-1] for valid pairs
+    *MM = 3 * h * h + 1;            // |m'|^2 and |k' - m'|^2
+}
+
+size_t radius_bytes(int N)
+{
+    const int K = strip_width(N);
+    if (K == 0) return 0;
+    int KK, BB, MM;
+    radius_dims(N, &KK, &BB, &MM);
+    const int TSp = strip_stride(N, K);
+    return sizeof(float) * ((size_t)KK * BB + MM) + sizeof(int) * (size_t)TSp;
+}
+
+int build_radius_tables(Handle &hd, cudaStream_t s)
+{
+    const Geom &g = hd.g;
+    if (g.layout != LAYOUT_STRIP) return set_error(CS_ENOTSUP, "radius tables serve the float strip kernel only");
+    int KK, BB, MM;
+    radius_dims(g.N, &KK, &BB, &MM);
+    hd.rad_bb = BB;
+    cudaError_t e = cudaMalloc(&hd.radA, sizeof(float) * (size_t)KK * BB);
+    if (e == cudaSuccess) e = cudaMalloc(&hd.radB, sizeof(float) * (size_t)MM);
+    if (e == cudaSuccess) e = cudaMalloc(&hd.emap, sizeof(int) * (size_t)g.TSp);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(CS_ENOMEM, "cudaMalloc of the radius tables failed");
+    }
+    std::vector<int> emap;
+    tile_entry_map(g, emap);
+    e = cudaMemcpyAsync(hd.emap, emap.data(), sizeof(int) * emap.size(), cudaMemcpyHostToDevice, s);
+    const QuadRule q = make_rule();
+    if (e == cudaSuccess) {
+        const long long n = (long long)KK * BB;
+        const unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 65536);
+        radius_a_kernel<<<blocks, 256, 0, s>>>(g, q, KK, BB, hd.radA);
+        radius_b_kernel<<<(MM + 127) / 128, 128, 0, s>>>(g, q, MM, hd.radB);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) note_kernels(s, 2);
+    }
+    // the host map behind the async copy must outlive it
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(e, "radius table build");
+    if (e2 != cudaSuccess) return cuda_error(e2, "radius table build");
+    hd.rad_bytes = radius_bytes(g.N);
+    return CS_OK;
+}
+
 int build_weights(Handle &hd, cudaStream_t s)
 {
     const Geom &g = hd.g;
@@ -289,6 +428,7 @@ int build_weights(Handle &hd, cudaStream_t s)
     // the host copies above are read asynchronously: keep tile0 alive until the stream passes
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_error(e, "copy of the pencil index");
+    if (!hd.has_table) return CS_OK;  // radius tables only
     hd.ghat_bytes = (size_t)hd.total_tiles * g.TSp * elem_bytes(hd.precision);
     e = cudaMalloc(&hd.ghat, hd.ghat_bytes);
     if (e != cudaSuccess) {

@@ -51,6 +51,27 @@ def test_host_only_queries(libcs):
     assert libcs.cs_weights_bytes(32, libcs.CS_FP64) > 1.9 * b32
 
 
+def test_radius_table_bytes(libcs):
+    """CS_WEIGHTS_RADIUS: A has (3 (N/2)^2 + 1) x (3 (N-1)^2 + 1) floats and
+    B 3 (N/2)^2 + 1; the flag leaves the table of every pair out, and needs a
+    float handle of the strip kernel."""
+    R = libcs.CS_WEIGHTS_RADIUS
+    for N in (16, 32, 64):
+        full = libcs.cs_weights_bytes(N, libcs.CS_FP32)
+        rad = libcs.cs_weights_bytes(N, libcs.CS_FP32 | R)
+        KK, BB = 3 * (N // 2) ** 2 + 1, 3 * (N - 1) ** 2 + 1
+        assert 4 * (KK * BB + KK) <= rad < 4 * (KK * BB + KK) + 1e6
+        assert full > rad
+    assert libcs.cs_weights_bytes(64, libcs.CS_FP32 | R) < 2e8 < 5e10 < libcs.cs_weights_bytes(64, libcs.CS_FP32)
+    for N, prec in ((16, libcs.CS_FP64 | R), (12, libcs.CS_FP32 | R)):
+        with pytest.raises(libcs.CSError) as e:
+            libcs.cs_weights_bytes(N, prec)
+        assert e.value.code == libcs.CS_EINVAL
+        with pytest.raises(libcs.CSError) as e:
+            libcs.cs_weights_build(N, 6.0, 1.0, prec, stream=0)
+        assert e.value.code == libcs.CS_EINVAL
+
+
 def test_launch_count_is_host_side(libcs):
     libcs.cs_launch_count(reset=True)
     assert libcs.cs_launch_count() == 0
