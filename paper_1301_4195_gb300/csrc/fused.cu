@@ -138,28 +138,31 @@ __device__ __forceinline__ void line_transform(float2 *X, int base, int stride, 
     }
 }
 
-// Blocks per cell (a cluster pair at N = 32), v1-planes per block, lines a
-// block transforms per pass (one per thread, rounded up to whole warps for
-// the shuffled reductions: 64, 160, 256, 576, 512 for N = 8, 12, 16, 24, 32)
+// Blocks per cell CL (a cluster pair at N = 32, where a cell does not fit
+// one SM; splitting smaller cells over a pair as well measured slower, even
+// at 128 cells where one block per cell leaves SMs idle), v1-planes per
+// block, lines a block transforms per pass (one per thread, rounded up to
+// whole warps for the shuffled reductions: 64, 160, 256, 576, 512 for
+// N = 8, 12, 16, 24, 32)
 template <int N>
 constexpr int kCL = N == 32 ? 2 : 1;
-template <int N>
-constexpr int kPL = N / kCL<N>;
-template <int N>
-constexpr int kLines = kPL<N> * N;
-template <int N>
-constexpr int kThreads = (kLines<N> + 31) / 32 * 32 < 64 ? 64 : (kLines<N> + 31) / 32 * 32;
+template <int N, int CL>
+constexpr int kPL = N / CL;
+template <int N, int CL>
+constexpr int kLines = kPL<N, CL> * N;
+template <int N, int CL>
+constexpr int kThreads = (kLines<N, CL> + 31) / 32 * 32 < 64 ? 64 : (kLines<N, CL> + 31) / 32 * 32;
 
-// loops over a block's kPts<N> points run kPer<N> rounds of the block, in
-// chunks of kChunk<N> rounds unrolled with every global load of a chunk issued
-// before its first use (one chunk up to N = 16; chunks of 8 at N = 24 and 32,
+// loops over a block's kPts points run kPer rounds of the block, in chunks
+// of kChunk rounds unrolled with every global load of a chunk issued before
+// its first use (one chunk up to 16 rounds; chunks of 8 at N = 24 and 32,
 // which keeps the registers of a 576- or 512-thread block within its share)
-template <int N>
-constexpr int kPts = kPL<N> * N * N;
-template <int N>
-constexpr int kPer = (kPts<N> + kThreads<N> - 1) / kThreads<N>;
-template <int N>
-constexpr int kChunk = kPer<N> <= 16 ? kPer<N> : 8;
+template <int N, int CL>
+constexpr int kPts = kPL<N, CL> * N * N;
+template <int N, int CL>
+constexpr int kPer = (kPts<N, CL> + kThreads<N, CL> - 1) / kThreads<N, CL>;
+template <int N, int CL>
+constexpr int kChunk = kPer<N, CL> <= 16 ? kPer<N, CL> : 8;
 
 struct Proj5 {
     double ainv[25];
@@ -169,29 +172,29 @@ namespace cg = cooperative_groups;
 
 // every block of the cell's cluster has finished its accesses to shared memory
 // (its own and, through the cluster, the partner's) before any goes on
-template <int N>
+template <int CL>
 __device__ __forceinline__ void cell_sync()
 {
-    if constexpr (kCL<N> == 2)
+    if constexpr (CL == 2)
         cg::this_cluster().sync();
     else
         __syncthreads();
 }
 
-template <int N>
+template <int CL>
 __device__ __forceinline__ int cell_rank()
 {
-    if constexpr (kCL<N> == 2)
+    if constexpr (CL == 2)
         return (int)cg::this_cluster().block_rank();
     else
         return 0;
 }
 
 // the shared array X of every block of the cell, by rank
-template <int N>
-__device__ __forceinline__ void cell_arrays(float2 *X, int rank, float2 *(&Xr)[kCL<N>])
+template <int CL>
+__device__ __forceinline__ void cell_arrays(float2 *X, int rank, float2 *(&Xr)[CL])
 {
-    if constexpr (kCL<N> == 2) {
+    if constexpr (CL == 2) {
         float2 *peer = cg::this_cluster().map_shared_rank(X, rank ^ 1);
         Xr[rank] = X;
         Xr[rank ^ 1] = peer;
@@ -202,10 +205,10 @@ __device__ __forceinline__ void cell_arrays(float2 *X, int rank, float2 *(&Xr)[k
 
 // the transform along axis 1 of line l of block `rank`: (i2, i3) =
 // (rank PL + l / N, l mod N); element i1 sits in block i1 / PL
-template <int N, bool INV>
-__device__ __forceinline__ void axis1_transform(float2 *const (&Xr)[kCL<N>], int rank, int l, float scale)
+template <int N, bool INV, int CL>
+__device__ __forceinline__ void axis1_transform(float2 *const (&Xr)[CL], int rank, int l, float scale)
 {
-    constexpr int P = N + 1, PL = kPL<N>;
+    constexpr int P = N + 1, PL = kPL<N, CL>;
     const int i2 = rank * PL + l / N, i3 = l % N;
     float2 v[N];
 #pragma unroll
@@ -221,27 +224,28 @@ __device__ __forceinline__ void axis1_transform(float2 *const (&Xr)[kCL<N>], int
     }
 }
 
-template <int N>
-__global__ void __launch_bounds__(kThreads<N>) forward_fused_kernel(const double *__restrict__ f, int ncells, float cf,
-                                                                    float2 *__restrict__ F)
+template <int N, int CL>
+__global__ void __launch_bounds__(kThreads<N, CL>) forward_fused_kernel(const double *__restrict__ f, int ncells,
+                                                                        float cf, float2 *__restrict__ F)
 {
-    constexpr int M = N * N * N, P = N + 1, NT = kThreads<N>, LINES = kLines<N>, PTS = kPts<N>;
+    constexpr int M = N * N * N, P = N + 1, NT = kThreads<N, CL>, LINES = kLines<N, CL>, PTS = kPts<N, CL>;
+    constexpr int PER = kPer<N, CL>, CHUNK = kChunk<N, CL>;
     extern __shared__ float2 X[];  // [PL*N][P]
-    const int cell = blockIdx.x / kCL<N>;
-    const int rank = cell_rank<N>();
+    const int cell = blockIdx.x / CL;
+    const int rank = cell_rank<CL>();
     const int tid = threadIdx.x;
     const bool real = cell < ncells;
     const size_t gbase = (size_t)cell * M + (size_t)rank * PTS;  // the block's planes in f
-    static_assert(kPer<N> % kChunk<N> == 0, "whole chunks");
-    for (int r0 = 0; r0 < kPer<N>; r0 += kChunk<N>) {
-        double fr[kChunk<N>];
+    static_assert(PER % CHUNK == 0, "whole chunks");
+    for (int r0 = 0; r0 < PER; r0 += CHUNK) {
+        double fr[CHUNK];
 #pragma unroll
-        for (int r = 0; r < kChunk<N>; ++r) {
+        for (int r = 0; r < CHUNK; ++r) {
             const int j = (r0 + r) * NT + tid;
             fr[r] = (real && j < PTS) ? f[gbase + j] : 0.0;
         }
 #pragma unroll
-        for (int r = 0; r < kChunk<N>; ++r) {
+        for (int r = 0; r < CHUNK; ++r) {
             const int j = (r0 + r) * NT + tid;
             if (j < PTS) X[(j / N) * P + j % N] = make_float2((float)fr[r], 0.f);
         }
@@ -251,36 +255,36 @@ __global__ void __launch_bounds__(kThreads<N>) forward_fused_kernel(const double
     if (l < LINES) line_transform<N, false>(X, l * P, 1, 1.f);  // axis 3
     __syncthreads();
     if (l < LINES) line_transform<N, false>(X, (l / N) * N * P + l % N, P, 1.f);  // axis 2
-    cell_sync<N>();
+    cell_sync<CL>();
     {
-        float2 *Xr[kCL<N>];
-        cell_arrays<N>(X, rank, Xr);
-        if (l < LINES) axis1_transform<N, false>(Xr, rank, l, cf);  // axis 1
+        float2 *Xr[CL];
+        cell_arrays<CL>(X, rank, Xr);
+        if (l < LINES) axis1_transform<N, false, CL>(Xr, rank, l, cf);  // axis 1
     }
-    cell_sync<N>();
+    cell_sync<CL>();
     const int g = cell / kGroup, lane = cell % kGroup;
     const size_t fbase = (size_t)g * M + (size_t)rank * PTS;
 #pragma unroll
-    for (int r = 0; r < kPer<N>; ++r) {
+    for (int r = 0; r < PER; ++r) {
         const int k = r * NT + tid;
         if (k < PTS) F[(fbase + k) * kGroup + lane] = X[(k / N) * P + k % N];
     }
 }
 
-template <int N>
-__global__ void __launch_bounds__(kThreads<N>) inverse_project_kernel(
+template <int N, int CL>
+__global__ void __launch_bounds__(kThreads<N, CL>) inverse_project_kernel(
     const float2 *__restrict__ Qh, const float2 *__restrict__ Qh2, float cic, double dv, int project, Proj5 pj,
     double a, const double *x, double b, const double *y, double *out)
 {
-    constexpr int M = N * N * N, P = N + 1, LINES = kLines<N>, PL = kPL<N>, PTS = kPts<N>, H = N / 2;
-    constexpr int NT = kThreads<N>, NW = NT / 32;
+    constexpr int M = N * N * N, P = N + 1, LINES = kLines<N, CL>, PL = kPL<N, CL>, PTS = kPts<N, CL>, H = N / 2;
+    constexpr int NT = kThreads<N, CL>, NW = NT / 32, PER = kPer<N, CL>, CHUNK = kChunk<N, CL>;
     static_assert(NT % 32 == 0, "whole warps");
     extern __shared__ float2 X[];  // [PL*N][P]; after the transform, reused as double q = c Qt
     __shared__ double vax[N], vsq[N], cv3[N], lbase[LINES];
     __shared__ double red[5][NW];
     __shared__ double ycoef[5], mom_s[5], part[5];
-    const int cell = blockIdx.x / kCL<N>;
-    const int rank = cell_rank<N>();
+    const int cell = blockIdx.x / CL;
+    const int rank = cell_rank<CL>();
     const int g = cell / kGroup, lane = cell % kGroup;
     const int tid = threadIdx.x;
     if (tid < N) {
@@ -288,29 +292,29 @@ __global__ void __launch_bounds__(kThreads<N>) inverse_project_kernel(
         vsq[tid] = vax[tid] * vax[tid];
     }
     const size_t fbase = (size_t)g * M + (size_t)rank * PTS;  // the block's planes in Qh
-    for (int r0 = 0; r0 < kPer<N>; r0 += kChunk<N>) {
-        float2 qa[kChunk<N>], qb[kChunk<N>];
+    for (int r0 = 0; r0 < PER; r0 += CHUNK) {
+        float2 qa[CHUNK], qb[CHUNK];
 #pragma unroll
-        for (int r = 0; r < kChunk<N>; ++r) {
+        for (int r = 0; r < CHUNK; ++r) {
             const int k = (r0 + r) * NT + tid;
             const size_t i = (fbase + (k < PTS ? k : 0)) * kGroup + lane;
             qa[r] = Qh[i];
             qb[r] = Qh2 ? Qh2[i] : make_float2(0.f, 0.f);
         }
 #pragma unroll
-        for (int r = 0; r < kChunk<N>; ++r) {  // two partial sums of the convolution, added in a fixed order
+        for (int r = 0; r < CHUNK; ++r) {  // two partial sums of the convolution, added in a fixed order
             const int k = (r0 + r) * NT + tid;
             if (k < PTS) X[(k / N) * P + k % N] = Qh2 ? make_float2(qa[r].x + qb[r].x, qa[r].y + qb[r].y) : qa[r];
         }
     }
-    cell_sync<N>();
+    cell_sync<CL>();
     const int l = tid;
     {
-        float2 *Xr[kCL<N>];
-        cell_arrays<N>(X, rank, Xr);
-        if (l < LINES) axis1_transform<N, true>(Xr, rank, l, 1.f);  // axis 1
+        float2 *Xr[CL];
+        cell_arrays<CL>(X, rank, Xr);
+        if (l < LINES) axis1_transform<N, true, CL>(Xr, rank, l, 1.f);  // axis 1
     }
-    cell_sync<N>();
+    cell_sync<CL>();
     if (l < LINES) line_transform<N, true>(X, (l / N) * N * P + l % N, P, 1.f);  // axis 2
     __syncthreads();
     // axis 3: c times the real part, as a double in the same slot (one thread
@@ -364,7 +368,7 @@ __global__ void __launch_bounds__(kThreads<N>) inverse_project_kernel(
             for (int k = 0; k < NW; ++k) t += red[tid][k];
         part[tid] = t;
     }
-    if constexpr (kCL<N> == 2) {
+    if constexpr (CL == 2) {
         cg::cluster_group cl = cg::this_cluster();
         cl.sync();
         if (tid < 5) {
@@ -394,16 +398,16 @@ __global__ void __launch_bounds__(kThreads<N>) inverse_project_kernel(
     const size_t base = (size_t)cell * M + (size_t)rank * PTS;
     // x and y may alias out (same index, same thread only): a chunk's loads
     // come before its stores
-    for (int r0 = 0; r0 < kPer<N>; r0 += kChunk<N>) {
-        double xr[kChunk<N>], yr[kChunk<N>];
+    for (int r0 = 0; r0 < PER; r0 += CHUNK) {
+        double xr[CHUNK], yr[CHUNK];
 #pragma unroll
-        for (int r = 0; r < kChunk<N>; ++r) {
+        for (int r = 0; r < CHUNK; ++r) {
             const int j = (r0 + r) * NT + tid;
             xr[r] = (x && j < PTS) ? x[base + j] : 0.0;
             yr[r] = (y && j < PTS) ? y[base + j] : 0.0;
         }
 #pragma unroll
-        for (int r = 0; r < kChunk<N>; ++r) {
+        for (int r = 0; r < CHUNK; ++r) {
             const int j = (r0 + r) * NT + tid;
             if (j >= PTS) break;
             const int jl = j / N, j3 = j % N;
@@ -416,8 +420,8 @@ __global__ void __launch_bounds__(kThreads<N>) inverse_project_kernel(
     }
 }
 
-template <int N>
-size_t fused_smem() { return sizeof(float2) * (size_t)kPL<N> * N * (N + 1); }
+template <int N, int CL>
+size_t fused_smem() { return sizeof(float2) * (size_t)kPL<N, CL> * N * (N + 1); }
 
 // dynamic shared memory above the default 48 KB needs the kernel's opt-in
 template <typename Kern>
@@ -428,23 +432,34 @@ int allow_smem(Kern kern, size_t bytes, const char *what)
     return e == cudaSuccess ? CS_OK : cuda_error(e, what);
 }
 
-// launch with kCL<N> blocks per cell, as a cluster when there are two
-template <int N, typename... Args>
+// launch with CL blocks per cell, as a cluster when there are two
+template <int N, int CL, typename... Args>
 cudaError_t launch_cells(void (*kern)(Args...), unsigned cells, cudaStream_t s, Args... args)
 {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(cells * kCL<N>);
-    cfg.blockDim = dim3(kThreads<N>);
-    cfg.dynamicSmemBytes = fused_smem<N>();
+    cfg.gridDim = dim3(cells * CL);
+    cfg.blockDim = dim3(kThreads<N, CL>);
+    cfg.dynamicSmemBytes = fused_smem<N, CL>();
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = kCL<N>;
+    attr[0].val.clusterDim.x = CL;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = kCL<N> > 1 ? 1 : 0;
+    cfg.numAttrs = CL > 1 ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+template <int N, int CL>
+int forward_cl(const Handle &hd, const double *f, int ncells, unsigned cells, float cf, cudaStream_t s)
+{
+    if (int rc = allow_smem(forward_fused_kernel<N, CL>, fused_smem<N, CL>(), "fused forward: shared-memory attribute"))
+        return rc;
+    cudaError_t e = launch_cells<N, CL>(forward_fused_kernel<N, CL>, cells, s, f, ncells, cf, (float2 *)hd.F);
+    if (e != cudaSuccess) return cuda_error(e, "fused forward transform launch");
+    CS_LAUNCHED(1, s, "forward transform (fused)");
+    return CS_OK;
 }
 
 template <int N>
@@ -452,10 +467,19 @@ int forward_n(const Handle &hd, const double *f, int ncells, int grid_cells, cud
 {
     const float cf = (float)(pow(2.0 * M_PI, -1.5) * hd.g.dv * hd.g.dv * hd.g.dv);
     const unsigned cells = (unsigned)(ngroups_of(std::max(ncells, grid_cells)) * kGroup);
-    if (int rc = allow_smem(forward_fused_kernel<N>, fused_smem<N>(), "fused forward: shared-memory attribute")) return rc;
-    cudaError_t e = launch_cells<N>(forward_fused_kernel<N>, cells, s, f, ncells, cf, (float2 *)hd.F);
-    if (e != cudaSuccess) return cuda_error(e, "fused forward transform launch");
-    CS_LAUNCHED(1, s, "forward transform (fused)");
+    return forward_cl<N, kCL<N>>(hd, f, ncells, cells, cf, s);
+}
+
+template <int N, int CL>
+int inverse_cl(const Handle &hd, int ncells, float cic, int project, const Proj5 &pj, double a, const double *x,
+               double b, const double *y, double *out, const void *qh2, cudaStream_t s)
+{
+    if (int rc = allow_smem(inverse_project_kernel<N, CL>, fused_smem<N, CL>(), "fused inverse: shared-memory attribute"))
+        return rc;
+    cudaError_t e = launch_cells<N, CL>(inverse_project_kernel<N, CL>, (unsigned)ncells, s, (const float2 *)hd.Qh,
+                                        (const float2 *)qh2, cic, hd.g.dv, project, pj, a, x, b, y, out);
+    if (e != cudaSuccess) return cuda_error(e, "fused inverse transform launch");
+    CS_LAUNCHED(1, s, "inverse transform and projection (fused)");
     return CS_OK;
 }
 
@@ -467,13 +491,7 @@ int inverse_n(const Handle &hd, int ncells, double eps, int project, double a, c
     for (int i = 0; i < 25; ++i) pj.ainv[i] = hd.cct_inv[i];
     // the scale of the last inverse pass, times the step factor c
     const float cic = (float)(c * pow(2.0 * M_PI, -1.5) * hd.g.dz * hd.g.dz * hd.g.dz / eps);
-    if (int rc = allow_smem(inverse_project_kernel<N>, fused_smem<N>(), "fused inverse: shared-memory attribute"))
-        return rc;
-    cudaError_t e = launch_cells<N>(inverse_project_kernel<N>, (unsigned)ncells, s, (const float2 *)hd.Qh,
-                                    (const float2 *)qh2, cic, hd.g.dv, project, pj, a, x, b, y, out);
-    if (e != cudaSuccess) return cuda_error(e, "fused inverse transform launch");
-    CS_LAUNCHED(1, s, "inverse transform and projection (fused)");
-    return CS_OK;
+    return inverse_cl<N, kCL<N>>(hd, ncells, cic, project, pj, a, x, b, y, out, qh2, s);
 }
 
 }  // namespace
