@@ -387,33 +387,73 @@ struct StripCfg {
 
 // The weight segment of strip w (entries seg .. seg+nseg-1 of the tile
 // layout) of tile (m1, m2) of pencil (k1, k2), rebuilt from the radius
-// tables: entry (m3, k3) gets 2 A - B(|m'|^2) - B(|s'|^2), the centre tile
-// A - B(|m'|^2), zero where k' = 0 and in the padding.  Lanes take every
-// 32nd entry.
+// tables: entry (m3, k3) gets (A - B(|m'|^2)) + (A - B(|s'|^2)), the centre
+// tile A - B(|m'|^2), zero where k' = 0 and in the padding.  Lane l takes
+// entries l, l + 32, ...  In two steps, so the loads from A (the only ones
+// from global memory; the entry map and B are in shared memory) can be
+// issued a tile ahead: radius_gather loads A into registers, radius_combine
+// forms the weights into the warp's buffer.
+struct RadiusTile {
+    int kk12, bb12, mm12, ss12;
+    bool centre;
+};
+
 template <int N>
-__device__ __forceinline__ void radius_segment(const StripJob &jb, const int *emap, const float *radB, int seg,
-                                               int nseg, int k1, int k2, int m1, int m2, float *wb, int lane)
+__device__ __forceinline__ RadiusTile radius_tile(int k1, int k2, int m1, int m2)
 {
     constexpr int h = N / 2;
     const int k1p = k1 - h, k2p = k2 - h, m1p = m1 - h, m2p = m2 - h;
     const int s1p = k1p - m1p, s2p = k2p - m2p, d1 = 2 * m1p - k1p, d2 = 2 * m2p - k2p;
-    const bool centre = s1p == m1p && s2p == m2p;
-    const int kk12 = k1p * k1p + k2p * k2p, bb12 = d1 * d1 + d2 * d2;
-    const int mm12 = m1p * m1p + m2p * m2p, ss12 = s1p * s1p + s2p * s2p;
-    for (int p = lane; p < nseg; p += 32) {
-        const int e = emap[seg + p];
-        float w = 0.f;
-        if (e >= 0) {
-            const int m3p = (e >> 8) - h, k3p = (e & 255) - h;
-            const int kk = kk12 + k3p * k3p;
-            if (kk != 0) {
-                const int d3 = 2 * m3p - k3p, s3p = k3p - m3p;
-                const float A = __ldg(jb.radA + (size_t)kk * jb.bbn + bb12 + d3 * d3);
-                w = A - radB[mm12 + m3p * m3p];
-                if (!centre) w += A - radB[ss12 + s3p * s3p];
+    RadiusTile r;
+    r.centre = s1p == m1p && s2p == m2p;
+    r.kk12 = k1p * k1p + k2p * k2p;
+    r.bb12 = d1 * d1 + d2 * d2;
+    r.mm12 = m1p * m1p + m2p * m2p;
+    r.ss12 = s1p * s1p + s2p * s2p;
+    return r;
+}
+
+template <int N, int EPL>
+__device__ __forceinline__ void radius_gather(const StripJob &jb, const int *emap, int seg, int nseg,
+                                              const RadiusTile &rt, int lane, float (&pa)[EPL])
+{
+    constexpr int h = N / 2;
+#pragma unroll
+    for (int i = 0; i < EPL; ++i) {
+        const int p = lane + 32 * i;
+        pa[i] = 0.f;
+        if (p < nseg) {
+            const int e = emap[seg + p];
+            if (e >= 0) {
+                const int m3p = (e >> 8) - h, k3p = (e & 255) - h;
+                const int kk = rt.kk12 + k3p * k3p, d3 = 2 * m3p - k3p;
+                if (kk != 0) pa[i] = __ldg(jb.radA + (size_t)kk * jb.bbn + rt.bb12 + d3 * d3);
             }
         }
-        wb[p] = w;
+    }
+}
+
+template <int N, int EPL>
+__device__ __forceinline__ void radius_combine(const int *emap, const float *radB, int seg, int nseg,
+                                               const RadiusTile &rt, int lane, const float (&pa)[EPL], float *wb)
+{
+    constexpr int h = N / 2;
+#pragma unroll
+    for (int i = 0; i < EPL; ++i) {
+        const int p = lane + 32 * i;
+        if (p < nseg) {
+            const int e = emap[seg + p];
+            float w = 0.f;
+            if (e >= 0) {
+                const int m3p = (e >> 8) - h, k3p = (e & 255) - h;
+                if (rt.kk12 + k3p * k3p != 0) {
+                    const int s3p = k3p - m3p;
+                    w = pa[i] - radB[rt.mm12 + m3p * m3p];
+                    if (!rt.centre) w += pa[i] - radB[rt.ss12 + s3p * s3p];
+                }
+            }
+            wb[p] = w;
+        }
     }
 }
 
@@ -533,18 +573,27 @@ __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &r
     float *wb = nullptr;  // RAD: this warp's weight segment, the entry map and B
     const int *s_emap = nullptr;
     const float *s_radB = nullptr;
+    constexpr int EPL = RAD ? (C::WBUF + 31) / 32 : 1;  // segment entries per lane
+    float pa[EPL];                                      // A of the next tile's entries, loaded a tile ahead
+    const int nseg = strip_seg_size(N, K, warp);
     if constexpr (RAD) {
         float *r = reinterpret_cast<float *>(rg.stages + NST * C::STAGE);
         wb = r + warp_id * C::WBUF;
         s_emap = reinterpret_cast<const int *>(r + C::WARPS * C::WBUF);
         s_radB = r + C::WARPS * C::WBUF + C::TSV;
+        if (T > 0) radius_gather<N, EPL>(jb, s_emap, seg, nseg, radius_tile<N>(k1, k2, cw.m1, cw.m2), lane, pa);
     }
     for (int t = 0; t < T && ok; ++t) {
         const uint32_t u = rg.tt + t;
         const int s = u % NST;
-        if constexpr (RAD) {  // before the wait: the gathers overlap the tile's copies
-            radius_segment<N>(jb, s_emap, s_radB, seg, strip_seg_size(N, K, warp), k1, k2, cw.m1, cw.m2, wb, lane);
+        if constexpr (RAD) {  // this tile's weights from the loads issued a tile ago, then the next tile's loads
+            radius_combine<N, EPL>(s_emap, s_radB, seg, nseg, radius_tile<N>(k1, k2, cw.m1, cw.m2), lane, pa, wb);
             __syncwarp();
+            if (t + 1 < T) {
+                TileWalk nw = cw;
+                nw.next();
+                radius_gather<N, EPL>(jb, s_emap, seg, nseg, radius_tile<N>(k1, k2, nw.m1, nw.m2), lane, pa);
+            }
         }
         if (!wait_phase(&rg.full[s], (u / NST) & 1u, rg.abort_flag, rg.err, kWaitNs)) {
             ok = false;
