@@ -786,7 +786,8 @@ int cs_tune(cs_handle_t h, int param, int value)
         break;
     default: return set_error(CS_EINVAL, "unknown tuning parameter");
     }
-    drop_graphs(hd);  // captured steps hold the old launch configuration
+    drop_graphs(hd);  // captured steps and batches hold the old launch configuration
+    drop_batch_graphs_of(h);
     return CS_OK;
 }
 
@@ -863,6 +864,7 @@ int cs_autotune(cs_handle_t h, int ncells, cudaStream_t s, double *ms)
     hd.tune_ctas = bc;
     hd.tune_weights = bw;
     drop_graphs(hd);
+    drop_batch_graphs_of(h);
     if (ms) *ms = best;
     (void)sms;
     return CS_OK;

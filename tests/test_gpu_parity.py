@@ -324,6 +324,17 @@ def test_collide_batched_matches_individual_calls(cs):
         assert cs.cs_launch_count(reset=True) == alone - 5
         for q, r in zip(qs, refs):
             assert np.array_equal(host(q), r)
+    # a launch choice changed after the capture holds at the next call: entry 0
+    # rebuilds its weights from the radius tables and leaves the shared launch
+    cs.cs_tune(hs[0].ptr, cs.CS_TUNE_WEIGHTS, 2)
+    q0 = torch.empty_like(fs[0])
+    cs.cs_collide(hs[0].ptr, fs[0], specs[0][2], 1.0, q0, 1)
+    cs.cs_launch_count(reset=True)
+    cs.cs_collide_batched(entries)
+    assert cs.cs_launch_count(reset=True) == alone - 4
+    assert np.array_equal(host(qs[0]), host(q0))
+    for q, r in zip(qs[1:], refs[1:]):
+        assert np.array_equal(host(q), r)
     cs.cs_status(hs[0].ptr)  # no bounded device wait expired
     with pytest.raises(cs.CSError):
         cs.cs_collide_batched([(hs[0].ptr, fs[0], qs[0], 40), (hs[0].ptr, fs[0], qs[1], 24)])  # same handle twice
