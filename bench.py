@@ -541,6 +541,20 @@ def cpu_baseline(args, api, inputs, torch, device, h32, h64):
     oracle.collide(f32, 32, L_BOX, LAM, nthreads=cores)
     cpu["n32_one_cell"] = {"value": 32 ** 6 / (time.perf_counter() - t0), "cores": cores,
                            "sample": "one evaluation of one random-mixture cell at N=32"}
+    # the space-homogeneous two-stream case whole: N = 8, one cell, 100 Heun steps
+    # of dt = 0.01 (200 evaluations), one core, and the GPU's Heun steps beside it
+    f8 = inputs.two_stream(8, L_BOX)[None]
+    t0 = time.perf_counter()
+    r8 = oracle.rk2_homogeneous(f8, 8, L_BOX, 1.0, 0.01, 100, nthreads=1)
+    t8 = time.perf_counter() - t0
+    h8 = api.Handle(8, L_BOX, 1.0, "fp64")
+    g8 = torch.from_numpy(f8.copy()).to(device)
+    h8.relax(g8, 0.01, 100)
+    torch.cuda.synchronize()
+    cpu["two_stream_n8"] = {"value": 200 * 8 ** 6 / t8, "cores": 1, "seconds": t8,
+                            "sample": "N=8, one two-stream cell, 100 Heun steps of dt=0.01 (200 evaluations)",
+                            "gpu_fp64_error": float(np.abs(g8.cpu().numpy() - r8).max() / np.abs(r8).max())}
+    h8.close()
     err = {}
     fd = torch.from_numpy(f0).to(device)
     for name, h in (("fp32", h32), ("fp64", h64)):
