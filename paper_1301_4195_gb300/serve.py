@@ -9,7 +9,9 @@ a horizon t_end, in Heun steps of dt (cs_relax).  The server
   dense device buffer of the active requests' states;
 * admits waiting requests at iteration boundaries while the device-memory
   budget allows (weight table of a new class + per-cell state and
-  workspace), in arrival order;
+  workspace), in arrival order; a float class whose table of every pair
+  does not fit is built from the radius tables alone (CS_WEIGHTS_RADIUS:
+  9 MB instead of 0.9 GB at N = 32), slower per step but admitted;
 * per iteration advances every active request of every class by one Heun
   step: one cs_relax call per class on its stream, so classes overlap on the
   device and requests that arrive while others run join the next iteration;
@@ -57,9 +59,9 @@ class Request:
 class _Class:
     """Requests of one (N, lambda): handle, stream, dense state buffer."""
 
-    def __init__(self, N: int, lam: float, L: float, precision: str, device, capacity: int):
-        self.N, self.lam = N, lam
-        self.handle = api.Handle(N, L, lam, precision)
+    def __init__(self, N: int, lam: float, L: float, precision: str, device, capacity: int, radius: bool = False):
+        self.N, self.lam, self.radius = N, lam, radius
+        self.handle = api.Handle(N, L, lam, "fp32-radius" if radius else precision)
         self.stream = torch.cuda.Stream(device=device)
         self.capacity = capacity
         self.buf = torch.empty((capacity, N, N, N), dtype=torch.float64, device=device)
@@ -82,8 +84,10 @@ class Server:
     """Continuous batching over (N, lambda) classes; see the module docstring."""
 
     def __init__(self, L: float = 6.0, dt: float = 0.01, eps: float = 1.0, precision: str = "fp32",
-                 mem_budget: Optional[int] = None, device=None, max_cells_per_class: int = 4096):
+                 mem_budget: Optional[int] = None, device=None, max_cells_per_class: int = 4096,
+                 radius_fallback: bool = True):
         self.L, self.dt, self.eps, self.precision = L, dt, eps, precision
+        self.radius_fallback = radius_fallback
         self.device = torch.device(device or "cuda")
         if mem_budget is None:
             free, _ = torch.cuda.mem_get_info(self.device)
@@ -103,13 +107,17 @@ class Server:
         es = 8 if self.precision == "fp64" else 4
         return N ** 3 * (8 + 4 * 2 * es + 2 * 8) + 4096
 
-    def _class_bytes(self, N: int) -> int:
-        return api.cs_weights_bytes(N, api.CS_FP64 if self.precision == "fp64" else api.CS_FP32)
+    def _class_bytes(self, N: int, radius: bool = False) -> int:
+        p = api.CS_FP64 if self.precision == "fp64" else api.CS_FP32
+        return api.cs_weights_bytes(N, p | (api.CS_WEIGHTS_RADIUS if radius else 0))
+
+    def _radius_possible(self, N: int) -> bool:
+        return self.radius_fallback and self.precision == "fp32" and N in (8, 16, 24, 32, 48, 64)
 
     def used_bytes(self) -> int:
         total = 0
         for (N, _), c in self.classes.items():
-            total += self._class_bytes(N) + c.capacity * self._cell_bytes(N)
+            total += self._class_bytes(N, c.radius) + c.capacity * self._cell_bytes(N)
         return total
 
     # ------------------------------------------------------------ requests
@@ -136,18 +144,23 @@ class Server:
             _, _, r = self.waiting[0]
             key = (r.N, float(r.lam))
             c = self.classes.get(key)
-            extra = 0
+            extra, radius = 0, False
             if c is None:
                 extra += self._class_bytes(r.N) + 32 * self._cell_bytes(r.N)
             elif len(c.reqs) + 1 > c.capacity:
                 extra += c.capacity * self._cell_bytes(r.N)  # capacity doubles
             if c is None and self.used_bytes() + extra > self.mem_budget:
                 self._evict_idle()
+            if c is None and self.used_bytes() + extra > self.mem_budget and self._radius_possible(r.N):
+                # the table of every pair does not fit: the radius tables alone
+                rx = self._class_bytes(r.N, True) + 32 * self._cell_bytes(r.N)
+                if self.used_bytes() + rx <= self.mem_budget:
+                    extra, radius = rx, True
             if self.used_bytes() + extra > self.mem_budget or (c is not None and len(c.reqs) >= self.max_cells):
                 break  # head of line waits until memory frees up (arrival order kept)
             heapq.heappop(self.waiting)
             if c is None:
-                c = _Class(r.N, r.lam, self.L, self.precision, self.device, 32)
+                c = _Class(r.N, r.lam, self.L, self.precision, self.device, 32, radius)
                 self.classes[key] = c
             if len(c.reqs) + 1 > c.capacity:
                 c.grow(2 * c.capacity)

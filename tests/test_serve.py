@@ -70,7 +70,7 @@ def test_maxwell_molecule_request_follows_bkw(srv):
 
 
 def test_admission_waits_for_memory_and_evicts_idle_classes(srv):
-    s = srv.Server(L=L)
+    s = srv.Server(L=L, radius_fallback=False)
     one = {N: s._class_bytes(N) + 32 * s._cell_bytes(N) for N in (16, 24)}
     s.mem_budget = int(1.01 * max(one.values()))  # room for one class at a time
     assert sum(one.values()) > s.mem_budget
@@ -84,6 +84,24 @@ def test_admission_waits_for_memory_and_evicts_idle_classes(srv):
     assert first24 >= last16
     assert len(s.classes) <= 1
     s.close()
+
+
+def test_class_without_room_for_its_table_runs_from_the_radius_tables(srv):
+    """An N = 32 class whose 0.9 GB table does not fit the budget is admitted
+    with the radius tables alone; its result equals a direct relaxation by a
+    handle built the same way, bit for bit."""
+    from paper_1301_4195_gb300 import api
+    s = srv.Server(L=L)
+    s.mem_budget = s._class_bytes(32, True) + 64 * s._cell_bytes(32)
+    assert s._class_bytes(32) > s.mem_budget
+    r = s.run([_req(srv, 0, 32, 1.0, 0.02, first_id=9)])[0]
+    assert s.classes[(32, 1.0)].radius
+    s.close()
+    h = api.Handle(32, L, 1.0, "fp32-radius")
+    f = torch.from_numpy(I.random_mixture_cells(32, L, 1, first_id=9)).cuda()
+    h.relax(f, 0.01, r.steps_total)
+    assert np.array_equal(f.cpu().numpy()[0], r.result)
+    h.close()
 
 
 def test_poisson_run_reports_latencies(srv):
