@@ -190,6 +190,25 @@ typedef struct {
  * Errors: CS_EINVAL (NULL, duplicate handle, bad sizes), CS_ENOMEM, CS_ECUDA. */
 int cs_collide_batched(const cs_batch_entry *entries, int n, double eps, int conserve, cudaStream_t stream);
 
+/* One entry of a batched relaxation: a handle and its cells' states. */
+typedef struct {
+    cs_handle_t handle; /* weights and workspace of this entry (N, L, lambda, precision) */
+    double *f;          /* device, [ncells][N^3], advanced in place */
+    int ncells;
+} cs_relax_entry;
+
+/* nsteps Heun steps (Sec. 3.1) of df/dt = P_N Qt(f) / eps (Sec. 3.3) for
+ * n <= 16 entries of possibly different N and lambda: cs_relax on each, as
+ * one captured graph per step (cached like cs_collide_batched, replayed
+ * nsteps times on `stream`).  Each of the step's two collision evaluations
+ * runs the convolutions of the float entries with N in {8, 16, 24, 32} as
+ * ONE persistent launch.  Each entry's result is bit-identical to cs_relax
+ * on that entry.  The entries' states must not overlap; every entry needs
+ * its own handle (its workspace holds the intermediate stage).
+ * Errors: CS_EINVAL (NULL, duplicate handle, overlap, bad sizes, dt, eps),
+ * CS_ENOMEM, CS_ECUDA. */
+int cs_relax_batched(const cs_relax_entry *entries, int n, double dt, double eps, int nsteps, cudaStream_t stream);
+
 /* Step a4, the conservation projection of Sec. 3.3, in place, in double:
  *   Q <- Q - C^T (C C^T)^{-1} C Q,  C = dv^3 (1, v1, v2, v3, |v|^2) (5 x N^3).
  *   Q        (device, in/out) [ncells][N^3]

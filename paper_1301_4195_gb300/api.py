@@ -55,6 +55,11 @@ class BatchEntry(ctypes.Structure):
     _fields_ = [("handle", _vp), ("f", _vp), ("Q", _vp), ("ncells", _i)]
 
 
+class RelaxEntry(ctypes.Structure):
+    """cs_relax_entry: handle, f (device, advanced in place), ncells."""
+    _fields_ = [("handle", _vp), ("f", _vp), ("ncells", _i)]
+
+
 _SIGS = {
     "cs_version": (_i, []),
     "cs_last_error": (ctypes.c_char_p, []),
@@ -77,6 +82,7 @@ _SIGS = {
     "cs_tile_layout": (_i, [_i, _i, ctypes.POINTER(_i), _i, ctypes.POINTER(_i)]),
     "cs_status": (_i, [_vp]),
     "cs_collide_batched": (_i, [ctypes.POINTER(BatchEntry), _i, _d, _i, _vp]),
+    "cs_relax_batched": (_i, [ctypes.POINTER(RelaxEntry), _i, _d, _d, _i, _vp]),
     "cs_tune": (_i, [_vp, _i, _i]),
     "cs_tune_get": (_i, [_vp, _i, ctypes.POINTER(_i)]),
     "cs_autotune": (_i, [_vp, _i, _vp, ctypes.POINTER(_d)]),
@@ -217,6 +223,14 @@ def cs_collide_batched(entries, eps=1.0, conserve=1, stream=None):
     for i, (h, f, Q, n) in enumerate(entries):
         arr[i] = BatchEntry(h, _dptr(f, "f"), _dptr(Q, "Q"), int(n))
     _check(lib().cs_collide_batched(arr, len(entries), eps, int(conserve), _stream(stream)))
+
+
+def cs_relax_batched(entries, dt, nsteps=1, eps=1.0, stream=None):
+    """entries: list of (handle_ptr, f, ncells) with device state tensors f, advanced in place."""
+    arr = (RelaxEntry * max(1, len(entries)))()
+    for i, (h, f, n) in enumerate(entries):
+        arr[i] = RelaxEntry(h, _dptr(f, "f"), int(n))
+    _check(lib().cs_relax_batched(arr, len(entries), dt, eps, int(nsteps), _stream(stream)))
 
 
 def cs_conserve(h, Q, ncells, moments=None, stream=None):

@@ -458,15 +458,16 @@ int graph_kernel_nodes(cudaGraph_t g)
     return k;
 }
 
-// ---- batched collision graphs (library-wide cache)
+// ---- batched calls (library-wide cache of captured graphs)
 namespace {
 
 struct BatchGraph {
+    int kind;  // 1 = collision evaluation (cs_collide_batched), 2 = Heun step (cs_relax_batched)
     std::vector<cs_handle_t> handles;
     std::vector<unsigned> generations;
     std::vector<const void *> f, q;
     std::vector<int> ncells;
-    double eps;
+    double eps, dt;
     int conserve;
     cudaGraphExec_t exec;
     int kernels = 0;  // kernel nodes of the graph
@@ -491,6 +492,204 @@ void drop_batch_graphs_of(cs_handle_t h)
     }
 }
 
+// One collision evaluation of every entry, written as
+//   out_i = a x_i + b y_i + c P(Qt(src_i) / eps)
+// (P the projection if project), enqueued on the capture root and one
+// branch stream per entry.  With `mixed` the float strip entries' forward
+// transforms run on their branches, their convolutions as one persistent
+// launch on the root, and their inverse + projection on their branches
+// again; every other entry runs its whole evaluation on its branch.
+struct EvalSpec {
+    const double *src;
+    double a;
+    const double *x;
+    double b;
+    const double *y;
+    double c;
+    double *out;
+};
+
+int capture_evaluation(const std::vector<Handle *> &hs, const std::vector<int> &cells,
+                       const std::vector<EvalSpec> &sp, bool mixed, double eps, int project, cudaStream_t root,
+                       cudaStream_t *br, const std::vector<cudaEvent_t> &ev)
+{
+    const int n = (int)hs.size();
+    auto in_mix = [&](int i) { return mixed && cells[i] > 0 && strip_mixable(*hs[i]); };
+    int rc = CS_OK;
+    cudaEventRecord(ev[0], root);
+    for (int i = 0; i < n && rc == CS_OK; ++i) {
+        cudaStreamWaitEvent(br[i], ev[0], 0);
+        Handle &hd = *hs[i];
+        if (in_mix(i))
+            rc = fused_available(hd) ? launch_forward_fused(hd, sp[i].src, cells[i], br[i], strip_mixed_cells(hd, cells[i]))
+                                     : launch_forward(hd, sp[i].src, cells[i], br[i]);
+        else if (cells[i] > 0)
+            rc = collide_combine(hd, sp[i].src, cells[i], eps, project, sp[i].a, sp[i].x, sp[i].b, sp[i].y, sp[i].c,
+                                 sp[i].out, br[i]);
+        cudaEventRecord(ev[i + 1], br[i]);
+        cudaStreamWaitEvent(root, ev[i + 1], 0);
+    }
+    if (!mixed || rc != CS_OK) return rc;
+    std::vector<const Handle *> mh;
+    std::vector<int> mc;
+    for (int i = 0; i < n; ++i)
+        if (in_mix(i)) {
+            mh.push_back(hs[i]);
+            mc.push_back(cells[i]);
+        }
+    rc = launch_strip_mixed(mh.data(), mc.data(), (int)mh.size(), root);
+    cudaEventRecord(ev[n + 1], root);
+    for (int i = 0; i < n && rc == CS_OK; ++i) {
+        if (!in_mix(i)) continue;
+        cudaStreamWaitEvent(br[i], ev[n + 1], 0);
+        rc = collide_back(*hs[i], cells[i], eps, project, sp[i].a, sp[i].x, sp[i].b, sp[i].y, sp[i].c, sp[i].out,
+                          br[i]);
+        cudaEventRecord(ev[n + 2 + i], br[i]);
+        cudaStreamWaitEvent(root, ev[n + 2 + i], 0);
+    }
+    return rc;
+}
+
+// Validation, workspace, the graph cache and the replay shared by the
+// batched calls.  kind 1: one collision evaluation, f[i] -> q[i]; kind 2:
+// Heun steps of df/dt = P Qt(f) / eps on the states f[i] (q unused),
+// nsteps replays of one captured step.
+int batched_call(int kind, const std::vector<cs_handle_t> &handles, const std::vector<const double *> &f,
+                 const std::vector<double *> &q, const std::vector<int> &ncells, double eps, double dt,
+                 int conserve, int nsteps, cudaStream_t stream)
+{
+    const int n = (int)handles.size();
+    if (n > 16) return set_error(CS_EINVAL, "at most 16 entries per batched call");
+    if (!(eps > 0) || !is_finite(eps)) return set_error(CS_EINVAL, "eps must be finite and > 0");
+    if (kind == 2 && !is_finite(dt)) return set_error(CS_EINVAL, "dt must be finite");
+    if (nsteps < 0) return set_error(CS_EINVAL, "nsteps < 0");
+    for (int i = 0; i < n; ++i) {
+        if (int rc = check_handle(handles[i])) return rc;
+        if (int rc = check_cells(ncells[i])) return rc;
+        for (int j = 0; j < i; ++j)
+            if (handles[j] == handles[i]) return set_error(CS_EINVAL, "each batch entry needs its own handle");
+        if (ncells[i] == 0) continue;
+        if (int rc = check_device_ptr(f[i], "entry f")) return rc;
+        const size_t bytes = (size_t)ncells[i] * handles[i]->h.g.M * sizeof(double);
+        if (kind == 1) {
+            if (int rc = check_device_ptr(q[i], "entry Q")) return rc;
+            if ((const char *)f[i] < (const char *)q[i] + bytes && (const char *)q[i] < (const char *)f[i] + bytes)
+                return set_error(CS_EINVAL, "entry f and Q overlap");
+        } else {
+            for (int j = 0; j < i; ++j) {
+                if (ncells[j] == 0) continue;
+                const size_t bj = (size_t)ncells[j] * handles[j]->h.g.M * sizeof(double);
+                if ((const char *)f[i] < (const char *)f[j] + bj && (const char *)f[j] < (const char *)f[i] + bytes)
+                    return set_error(CS_EINVAL, "the states of two entries overlap");
+            }
+        }
+        if (handles[i]->h.prof) return set_error(CS_EINVAL, "stage timing must be off for batched calls");
+    }
+    if (n == 0 || nsteps == 0) return CS_OK;
+    // float strip handles share one persistent convolution launch when the
+    // call has two or more of them; their cells are padded to whole CTA groups
+    int nmix = 0;
+    for (int i = 0; i < n; ++i) nmix += ncells[i] > 0 && strip_mixable(handles[i]->h);
+    const bool mixed = nmix >= 2;
+    for (int i = 0; i < n; ++i) {
+        if (ncells[i] == 0) continue;
+        Handle &hd = handles[i]->h;
+        const int cells = mixed && strip_mixable(hd) ? strip_mixed_cells(hd, ncells[i]) : ncells[i];
+        if (int rc = ensure_workspace(hd, cells)) return rc;
+    }
+    std::lock_guard<std::mutex> lock(g_batch_mutex);
+    cudaGraphExec_t exec = nullptr;
+    int kernels_of_exec = 0;
+    for (auto &g : g_batch_graphs) {
+        if (g.kind != kind || (int)g.handles.size() != n || g.eps != eps || g.conserve != conserve ||
+            (kind == 2 && g.dt != dt))
+            continue;
+        bool same = true;
+        for (int i = 0; i < n && same; ++i)
+            same = g.handles[i] == handles[i] && g.generations[i] == handles[i]->h.ws_generation && g.f[i] == f[i] &&
+                   g.q[i] == (kind == 1 ? (const void *)q[i] : nullptr) && g.ncells[i] == ncells[i];
+        if (same) {
+            exec = g.exec;
+            kernels_of_exec = g.kernels;
+        }
+    }
+    if (!exec) {
+        for (int i = 0; i <= n; ++i)
+            if (!g_batch_streams[i] &&
+                cudaStreamCreateWithFlags(&g_batch_streams[i], cudaStreamNonBlocking) != cudaSuccess) {
+                cudaGetLastError();
+                return set_error(CS_ECUDA, "batched call: stream creation failed");
+            }
+        cudaStream_t root = g_batch_streams[0];
+        const int nev = (kind == 2 ? 2 : 1) * (2 * n + 2);
+        std::vector<cudaEvent_t> ev(nev, nullptr);
+        for (auto &e : ev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                for (auto x : ev)
+                    if (x) cudaEventDestroy(x);
+                return set_error(CS_ECUDA, "batched call: event creation failed");
+            }
+        std::vector<Handle *> hs(n);
+        for (int i = 0; i < n; ++i) hs[i] = &handles[i]->h;
+        cudaGraph_t graph = nullptr;
+        int rc = CS_OK;
+        cudaError_t e = cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const int project = conserve ? 1 : 0;
+            std::vector<EvalSpec> sp(n);
+            if (kind == 1) {
+                for (int i = 0; i < n; ++i) sp[i] = EvalSpec{f[i], 0.0, nullptr, 0.0, nullptr, 1.0, q[i]};
+                rc = capture_evaluation(hs, ncells, sp, mixed, eps, project, root, g_batch_streams + 1, ev);
+            } else {
+                // Heun: f1 = f + dt P Q(f); f = f/2 + (f1 + dt P Q(f1))/2, each entry's f1 in its workspace
+                std::vector<cudaEvent_t> ev1(ev.begin(), ev.begin() + (2 * n + 2));
+                std::vector<cudaEvent_t> ev2(ev.begin() + (2 * n + 2), ev.end());
+                for (int i = 0; i < n; ++i) sp[i] = EvalSpec{f[i], 1.0, f[i], 0.0, nullptr, dt, hs[i]->f1};
+                rc = capture_evaluation(hs, ncells, sp, mixed, eps, project, root, g_batch_streams + 1, ev1);
+                for (int i = 0; i < n; ++i)
+                    sp[i] = EvalSpec{hs[i]->f1, 0.5, f[i], 0.5, hs[i]->f1, 0.5 * dt, const_cast<double *>(f[i])};
+                if (rc == CS_OK)
+                    rc = capture_evaluation(hs, ncells, sp, mixed, eps, project, root, g_batch_streams + 1, ev2);
+            }
+            e = cudaStreamEndCapture(root, &graph);
+        }
+        if (e == cudaSuccess && rc == CS_OK) e = cudaGraphInstantiate(&exec, graph, 0);
+        int kernels = 0;
+        if (e == cudaSuccess && rc == CS_OK) kernels = graph_kernel_nodes(graph);
+        if (graph) cudaGraphDestroy(graph);
+        for (auto x : ev) cudaEventDestroy(x);
+        if (rc != CS_OK) return rc;
+        if (e != cudaSuccess) return cuda_error(e, "batched call: graph capture");
+        if (g_batch_graphs.size() >= 16) {
+            cudaGraphExecDestroy(g_batch_graphs.front().exec);
+            g_batch_graphs.erase(g_batch_graphs.begin());
+        }
+        BatchGraph bg;
+        bg.kind = kind;
+        for (int i = 0; i < n; ++i) {
+            bg.handles.push_back(handles[i]);
+            bg.generations.push_back(handles[i]->h.ws_generation);
+            bg.f.push_back(f[i]);
+            bg.q.push_back(kind == 1 ? (const void *)q[i] : nullptr);
+            bg.ncells.push_back(ncells[i]);
+        }
+        bg.eps = eps;
+        bg.dt = kind == 2 ? dt : 0.0;
+        bg.conserve = conserve;
+        bg.exec = exec;
+        bg.kernels = kernels;
+        kernels_of_exec = kernels;
+        g_batch_graphs.push_back(bg);
+    }
+    for (int r = 0; r < (kind == 2 ? nsteps : 1); ++r) {
+        cudaError_t e = cudaGraphLaunch(exec, stream);
+        if (e != cudaSuccess) return cuda_error(e, "batched call: replay");
+        note_replay(kernels_of_exec);
+    }
+    return CS_OK;
+}
+
 }  // namespace
 
 }  // namespace cs
@@ -502,141 +701,33 @@ extern "C" {
 int cs_collide_batched(const cs_batch_entry *entries, int n, double eps, int conserve, cudaStream_t stream)
 {
     if (n < 0 || (n > 0 && !entries)) return set_error(CS_EINVAL, "bad entry list");
-    if (n > 16) return set_error(CS_EINVAL, "at most 16 entries per batched call");
-    if (!(eps > 0) || !is_finite(eps)) return set_error(CS_EINVAL, "eps must be finite and > 0");
+    std::vector<cs_handle_t> hs;
+    std::vector<const double *> f;
+    std::vector<double *> q;
+    std::vector<int> nc;
     for (int i = 0; i < n; ++i) {
-        const cs_batch_entry &e = entries[i];
-        if (int rc = check_handle(e.handle)) return rc;
-        if (int rc = check_cells(e.ncells)) return rc;
-        for (int j = 0; j < i; ++j)
-            if (entries[j].handle == e.handle) return set_error(CS_EINVAL, "each batch entry needs its own handle");
-        if (e.ncells == 0) continue;
-        if (int rc = check_device_ptr(e.f, "entry f")) return rc;
-        if (int rc = check_device_ptr(e.Q, "entry Q")) return rc;
-        const size_t bytes = (size_t)e.ncells * e.handle->h.g.M * sizeof(double);
-        if ((const char *)e.f < (const char *)e.Q + bytes && (const char *)e.Q < (const char *)e.f + bytes)
-            return set_error(CS_EINVAL, "entry f and Q overlap");
-        if (e.handle->h.prof) return set_error(CS_EINVAL, "stage timing must be off for batched calls");
+        hs.push_back(entries[i].handle);
+        f.push_back(entries[i].f);
+        q.push_back(entries[i].Q);
+        nc.push_back(entries[i].ncells);
     }
-    // float strip handles share one persistent convolution launch when the
-    // call has two or more of them; their cells are padded to whole CTA groups
-    int nmix = 0;
-    for (int i = 0; i < n; ++i) nmix += entries[i].ncells > 0 && strip_mixable(entries[i].handle->h);
-    const bool mixed = nmix >= 2;
+    return batched_call(1, hs, f, q, nc, eps, 0.0, conserve, 1, stream);
+}
+
+int cs_relax_batched(const cs_relax_entry *entries, int n, double dt, double eps, int nsteps, cudaStream_t stream)
+{
+    if (n < 0 || (n > 0 && !entries)) return set_error(CS_EINVAL, "bad entry list");
+    std::vector<cs_handle_t> hs;
+    std::vector<const double *> f;
+    std::vector<double *> q;
+    std::vector<int> nc;
     for (int i = 0; i < n; ++i) {
-        const cs_batch_entry &e = entries[i];
-        if (e.ncells == 0) continue;
-        Handle &hd = e.handle->h;
-        const int cells = mixed && strip_mixable(hd) ? strip_mixed_cells(hd, e.ncells) : e.ncells;
-        if (int rc = ensure_workspace(hd, cells)) return rc;
+        hs.push_back(entries[i].handle);
+        f.push_back(entries[i].f);
+        q.push_back(nullptr);
+        nc.push_back(entries[i].ncells);
     }
-    std::lock_guard<std::mutex> lock(g_batch_mutex);
-    cudaGraphExec_t exec = nullptr;
-    int kernels_of_exec = 0;
-    for (auto &g : g_batch_graphs) {
-        if ((int)g.handles.size() != n || g.eps != eps || g.conserve != conserve) continue;
-        bool same = true;
-        for (int i = 0; i < n && same; ++i)
-            same = g.handles[i] == entries[i].handle && g.generations[i] == entries[i].handle->h.ws_generation &&
-                   g.f[i] == entries[i].f && g.q[i] == entries[i].Q && g.ncells[i] == entries[i].ncells;
-        if (same) {
-            exec = g.exec;
-            kernels_of_exec = g.kernels;
-        }
-    }
-    if (!exec) {
-        for (int i = 0; i <= n; ++i)
-            if (!g_batch_streams[i] &&
-                cudaStreamCreateWithFlags(&g_batch_streams[i], cudaStreamNonBlocking) != cudaSuccess) {
-                cudaGetLastError();
-                return set_error(CS_ECUDA, "cs_collide_batched: stream creation failed");
-            }
-        cudaStream_t root = g_batch_streams[0];
-        std::vector<cudaEvent_t> ev(2 * n + 2, nullptr);
-        for (auto &e : ev)
-            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
-                cudaGetLastError();
-                for (auto x : ev)
-                    if (x) cudaEventDestroy(x);
-                return set_error(CS_ECUDA, "cs_collide_batched: event creation failed");
-            }
-        cudaGraph_t graph = nullptr;
-        int rc = CS_OK;
-        cudaError_t e = cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            // one branch per entry; with a mixed convolution the graph is
-            // fork (forward transforms; other entries whole) -> join -> the
-            // mixed convolution -> fork (inverse + projection) -> join
-            const int project = conserve ? 1 : 0;
-            auto in_mix = [&](int i) { return mixed && entries[i].ncells > 0 && strip_mixable(entries[i].handle->h); };
-            cudaEventRecord(ev[0], root);
-            for (int i = 0; i < n && rc == CS_OK; ++i) {
-                cudaStream_t br = g_batch_streams[i + 1];
-                cudaStreamWaitEvent(br, ev[0], 0);
-                Handle &hd = entries[i].handle->h;
-                if (in_mix(i))
-                    rc = fused_available(hd)
-                             ? launch_forward_fused(hd, entries[i].f, entries[i].ncells, br,
-                                                    strip_mixed_cells(hd, entries[i].ncells))
-                             : launch_forward(hd, entries[i].f, entries[i].ncells, br);
-                else if (entries[i].ncells > 0)
-                    rc = collide_combine(hd, entries[i].f, entries[i].ncells, eps, project, 0.0, nullptr, 0.0,
-                                         nullptr, 1.0, entries[i].Q, br);
-                cudaEventRecord(ev[i + 1], br);
-                cudaStreamWaitEvent(root, ev[i + 1], 0);
-            }
-            if (mixed && rc == CS_OK) {
-                std::vector<const Handle *> hs;
-                std::vector<int> cells;
-                for (int i = 0; i < n; ++i)
-                    if (in_mix(i)) {
-                        hs.push_back(&entries[i].handle->h);
-                        cells.push_back(entries[i].ncells);
-                    }
-                rc = launch_strip_mixed(hs.data(), cells.data(), (int)hs.size(), root);
-                cudaEventRecord(ev[n + 1], root);
-                for (int i = 0; i < n && rc == CS_OK; ++i) {
-                    if (!in_mix(i)) continue;
-                    cudaStream_t br = g_batch_streams[i + 1];
-                    cudaStreamWaitEvent(br, ev[n + 1], 0);
-                    rc = collide_back(entries[i].handle->h, entries[i].ncells, eps, project, 0.0, nullptr, 0.0,
-                                      nullptr, 1.0, entries[i].Q, br);
-                    cudaEventRecord(ev[n + 2 + i], br);
-                    cudaStreamWaitEvent(root, ev[n + 2 + i], 0);
-                }
-            }
-            e = cudaStreamEndCapture(root, &graph);
-        }
-        if (e == cudaSuccess && rc == CS_OK) e = cudaGraphInstantiate(&exec, graph, 0);
-        int kernels = 0;
-        if (e == cudaSuccess && rc == CS_OK) kernels = graph_kernel_nodes(graph);
-        if (graph) cudaGraphDestroy(graph);
-        for (auto x : ev) cudaEventDestroy(x);
-        if (rc != CS_OK) return rc;
-        if (e != cudaSuccess) return cuda_error(e, "cs_collide_batched: graph capture");
-        if (g_batch_graphs.size() >= 16) {
-            cudaGraphExecDestroy(g_batch_graphs.front().exec);
-            g_batch_graphs.erase(g_batch_graphs.begin());
-        }
-        BatchGraph bg;
-        for (int i = 0; i < n; ++i) {
-            bg.handles.push_back(entries[i].handle);
-            bg.generations.push_back(entries[i].handle->h.ws_generation);
-            bg.f.push_back(entries[i].f);
-            bg.q.push_back(entries[i].Q);
-            bg.ncells.push_back(entries[i].ncells);
-        }
-        bg.eps = eps;
-        bg.conserve = conserve;
-        bg.exec = exec;
-        bg.kernels = kernels;
-        kernels_of_exec = kernels;
-        g_batch_graphs.push_back(bg);
-    }
-    cudaError_t e = cudaGraphLaunch(exec, stream);
-    if (e != cudaSuccess) return cuda_error(e, "cs_collide_batched: replay");
-    note_replay(kernels_of_exec);
-    return CS_OK;
+    return batched_call(2, hs, f, q, nc, eps, dt, 1, nsteps, stream);
 }
 
 int cs_launch_count(long long *kernels, int reset)

@@ -13,8 +13,11 @@ a horizon t_end, in Heun steps of dt (cs_relax).  The server
   does not fit is built from the radius tables alone (CS_WEIGHTS_RADIUS:
   9 MB instead of 0.9 GB at N = 32), slower per step but admitted;
 * per iteration advances every active request of every class by one Heun
-  step: one cs_relax call per class on its stream, so classes overlap on the
-  device and requests that arrive while others run join the next iteration;
+  step: one cs_relax_batched call over all active classes (a replayed graph
+  with one branch per class, so classes overlap on the device, and the
+  float classes' convolutions as one persistent launch per evaluation), or
+  with batched=False one cs_relax per class on its own stream; requests that
+  arrive while others run join the next iteration;
 * retires finished requests (their final state is copied out) and compacts
   the class buffer by moving the last active state into the freed slot.
 
@@ -59,10 +62,11 @@ class Request:
 class _Class:
     """Requests of one (N, lambda): handle, stream, dense state buffer."""
 
-    def __init__(self, N: int, lam: float, L: float, precision: str, device, capacity: int, radius: bool = False):
+    def __init__(self, N: int, lam: float, L: float, precision: str, device, capacity: int, radius: bool = False,
+                 stream=None):
         self.N, self.lam, self.radius = N, lam, radius
         self.handle = api.Handle(N, L, lam, "fp32-radius" if radius else precision)
-        self.stream = torch.cuda.Stream(device=device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=device)
         self.capacity = capacity
         self.buf = torch.empty((capacity, N, N, N), dtype=torch.float64, device=device)
         self.reqs: List[Request] = []
@@ -85,10 +89,13 @@ class Server:
 
     def __init__(self, L: float = 6.0, dt: float = 0.01, eps: float = 1.0, precision: str = "fp32",
                  mem_budget: Optional[int] = None, device=None, max_cells_per_class: int = 4096,
-                 radius_fallback: bool = True):
+                 radius_fallback: bool = True, batched: bool = True):
         self.L, self.dt, self.eps, self.precision = L, dt, eps, precision
         self.radius_fallback = radius_fallback
+        self.batched = batched
         self.device = torch.device(device or "cuda")
+        # batched: every class works on one stream, the batched call's
+        self.stream = torch.cuda.Stream(device=self.device) if batched else None
         if mem_budget is None:
             free, _ = torch.cuda.mem_get_info(self.device)
             mem_budget = int(0.8 * free)
@@ -130,7 +137,8 @@ class Server:
         for N, lam in classes:
             key = (int(N), float(lam))
             if key not in self.classes:
-                self.classes[key] = _Class(int(N), float(lam), self.L, self.precision, self.device, capacity)
+                self.classes[key] = _Class(int(N), float(lam), self.L, self.precision, self.device, capacity,
+                                           stream=self.stream)
         torch.cuda.synchronize(self.device)
         self.t0 = time.perf_counter()
 
@@ -160,7 +168,7 @@ class Server:
                 break  # head of line waits until memory frees up (arrival order kept)
             heapq.heappop(self.waiting)
             if c is None:
-                c = _Class(r.N, r.lam, self.L, self.precision, self.device, 32, radius)
+                c = _Class(r.N, r.lam, self.L, self.precision, self.device, 32, radius, stream=self.stream)
                 self.classes[key] = c
             if len(c.reqs) + 1 > c.capacity:
                 c.grow(2 * c.capacity)
@@ -203,9 +211,16 @@ class Server:
         active = [c for c in self.classes.values() if c.reqs]
         if not active and not self.waiting:
             return False
+        if self.batched and active:
+            for k in range(0, len(active), 16):  # at most 16 entries per batched call
+                part = active[k:k + 16]
+                api.cs_relax_batched([(c.handle.ptr, c.buf[:len(c.reqs)], len(c.reqs)) for c in part], self.dt,
+                                     1, self.eps, stream=self.stream)
+        else:
+            for c in active:
+                n = len(c.reqs)
+                api.cs_relax(c.handle.ptr, c.buf[:n], n, self.dt, self.eps, 1, stream=c.stream)
         for c in active:
-            n = len(c.reqs)
-            api.cs_relax(c.handle.ptr, c.buf[:n], n, self.dt, self.eps, 1, stream=c.stream)
             for r in c.reqs:
                 r.steps_done += 1
         for c in active:

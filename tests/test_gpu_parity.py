@@ -342,6 +342,35 @@ def test_collide_batched_matches_individual_calls(cs):
         h.close()
 
 
+def test_relax_batched_matches_individual_calls(cs):
+    """Heun steps of uneven entries in one replayed graph per step: each entry
+    equals cs_relax on it bit for bit, and each of a step's two evaluations
+    runs the four float strip entries' convolutions as one launch."""
+    specs = [(16, 0.0, 40, "fp32"), (24, 1.0, 9, "fp32"), (8, 1.0, 3, "fp32"), (32, 0.0, 2, "fp32"),
+             (12, 1.0, 5, "fp32"), (8, 0.0, 4, "fp64")]
+    hs = [cs.Handle(N, L, lam, prec) for N, lam, _, prec in specs]
+    f0 = [I.random_mixture_cells(N, L, n, first_id=700 + 40 * i) for i, (N, _, n, _) in enumerate(specs)]
+    refs, alone = [], 0
+    for h, f, (N, lam, n, _) in zip(hs, f0, specs):
+        fd = dev(f)
+        cs.cs_launch_count(reset=True)
+        cs.cs_relax(h.ptr, fd, n, 0.01, 1.0, 3)
+        alone += cs.cs_launch_count(reset=True)
+        refs.append(host(fd))
+    for _ in range(2):  # capture, then replay
+        fs = [dev(f) for f in f0]
+        cs.cs_launch_count(reset=True)
+        cs.cs_relax_batched([(h.ptr, f, n) for h, f, (_, _, n, _) in zip(hs, fs, specs)], 0.01, nsteps=3)
+        assert cs.cs_launch_count(reset=True) == alone - 3 * 2 * 3
+        for f, r in zip(fs, refs):
+            assert np.array_equal(host(f), r)
+    with pytest.raises(cs.CSError):  # the same state twice
+        cs.cs_relax_batched([(hs[0].ptr, fs[0], 40), (hs[1].ptr, fs[0], 9)], 0.01)
+    cs.cs_status(hs[0].ptr)
+    for h in hs:
+        h.close()
+
+
 def test_launch_choices_give_identical_results(cs):
     """The convolution's launch shape (groups per CTA, resident CTAs) changes
     only scheduling: every cell's sum runs in the same order."""

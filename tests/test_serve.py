@@ -43,6 +43,19 @@ def test_result_is_the_same_alone_and_in_the_mix(srv):
     assert np.array_equal(done[0].result, a)
 
 
+def test_batched_and_per_class_iterations_agree(srv):
+    """One cs_relax_batched per iteration (float classes' convolutions in one
+    launch) and one cs_relax per class on its own stream give the same
+    states bit for bit."""
+    reqs = lambda: [_req(srv, i, (12, 16, 24, 32)[i % 4], float(i % 2), 0.02 + 0.01 * (i % 3),
+                         arrival=0.0003 * i, first_id=300 + i) for i in range(12)]
+    a = {r.rid: r.result for r in srv.Server(L=L, batched=True).run(reqs())}
+    b = {r.rid: r.result for r in srv.Server(L=L, batched=False).run(reqs())}
+    assert sorted(a) == sorted(b) == list(range(12))
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
 def test_served_result_equals_direct_relaxation(srv):
     from paper_1301_4195_gb300 import api
     s = srv.Server(L=L)
