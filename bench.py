@@ -294,6 +294,11 @@ def run_ours(args):
     e2e = {"value": world * pairs_step * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
            "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes}
 
+    # measured pipe peaks beside the derived one (lane operations per second)
+    probe = {"ffma_tlane_ops": api.cs_fma_probe(0) / 1e12, "ffma2_tlane_ops": api.cs_fma_probe(1) / 1e12,
+             "dfma_tlane_ops": api.cs_fma_probe(2) / 1e12}
+    probe["frac_of_best_fp32_probe"] = achieved_ops / max(probe["ffma_tlane_ops"], probe["ffma2_tlane_ops"])
+
     # store versus recompute: the convolution with stored weight tiles and with
     # tiles rebuilt from the radius tables (the autotuner keeps the faster)
     weights = {"chosen": WEIGHT_MODES[api.cs_tune_get(h32.ptr, api.CS_TUNE_WEIGHTS)],
@@ -431,7 +436,8 @@ def run_ours(args):
                      "ops_per_launch": 6.0 * pair_cells, "tflops": achieved,
                      "flop_frac": achieved / peak_tflops, "autotuned_ms": tuned_ms,
                      "launch": {"groups_per_cta": api.cs_tune_get(h32.ptr, api.CS_TUNE_GROUPS_PER_CTA),
-                                "ctas_per_sm": api.cs_tune_get(h32.ptr, api.CS_TUNE_CTAS_PER_SM)}},
+                                "ctas_per_sm": api.cs_tune_get(h32.ptr, api.CS_TUNE_CTAS_PER_SM)},
+                     "probe": probe},
         "stage_ms_per_step": step_stage_ms,
         "weights": weights,
         "fp64": fp64,

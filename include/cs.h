@@ -367,6 +367,14 @@ int cs_tune(cs_handle_t h, int param, int value);
  *   value (host, out).  Errors: CS_EINVAL. */
 int cs_tune_get(cs_handle_t h, int param, int *value);
 
+/* Measured peak of one arithmetic pipe (diagnostics, no counterpart in the
+ * paper): kind 0 scalar FP32 fused multiply-adds, 1 packed f32x2 ones (the
+ * convolution's instructions), 2 FP64 ones; every SM full of independent
+ * chains, best of three timed launches on `stream` (synchronising).
+ *   lane_ops_per_s (host, out): lane operations per second (a packed f32x2
+ *   instruction counts two).  Errors: CS_EINVAL, CS_ENOMEM, CS_ECUDA. */
+int cs_fma_probe(int kind, cudaStream_t stream, double *lane_ops_per_s);
+
 /* Time the convolution's launch choices on ncells synthetic cells on
  * `stream` (synchronising), keep the fastest in the handle and return its
  * time per launch in *ms (may be NULL).  The choices are the launch shapes

@@ -83,6 +83,7 @@ _SIGS = {
     "cs_status": (_i, [_vp]),
     "cs_collide_batched": (_i, [ctypes.POINTER(BatchEntry), _i, _d, _i, _vp]),
     "cs_relax_batched": (_i, [ctypes.POINTER(RelaxEntry), _i, _d, _d, _i, _vp]),
+    "cs_fma_probe": (_i, [_i, _vp, ctypes.POINTER(_d)]),
     "cs_tune": (_i, [_vp, _i, _i]),
     "cs_tune_get": (_i, [_vp, _i, ctypes.POINTER(_i)]),
     "cs_autotune": (_i, [_vp, _i, _vp, ctypes.POINTER(_d)]),
@@ -302,6 +303,13 @@ def cs_autotune(h, ncells: int, stream=None) -> float:
     ms = _d()
     _check(lib().cs_autotune(h, ncells, _stream(stream), ctypes.byref(ms)))
     return ms.value
+
+
+def cs_fma_probe(kind: int, stream=None) -> float:
+    """Measured lane operations per second of FFMA (0), packed FFMA2 (1) or DFMA (2)."""
+    out = _d()
+    _check(lib().cs_fma_probe(int(kind), _stream(stream), ctypes.byref(out)))
+    return out.value
 
 
 def cs_profile(h, enable: bool):

@@ -395,3 +395,14 @@ def test_launch_choices_give_identical_results(cs):
     with pytest.raises(cs.CSError):
         cs.cs_tune_get(h.ptr, 7)
     h.close()
+
+
+def test_fma_probe_rates_are_plausible(cs):
+    """The pipe probes land between a quarter of and just above the rates the
+    unit counts give at the maximum clock (152 SMs x 128 FP32 lanes x 2.07 GHz
+    = 40.3 T lane-ops/s; FP64 at 1/64 of that)."""
+    ffma, ffma2, dfma = (cs.cs_fma_probe(k) / 1e12 for k in (0, 1, 2))
+    assert 10.0 < ffma < 42.0 and 10.0 < ffma2 < 42.0, (ffma, ffma2)
+    assert 0.1 < dfma < 1.5, dfma
+    with pytest.raises(cs.CSError):
+        cs.cs_fma_probe(3)
