@@ -48,7 +48,7 @@ WORKLOADS = {
 MAX_SM_MHZ = 2070.0
 # DRAM bytes (read + write) per convolution launch from ncu captures of the
 # current kernel (profiles/), keyed by (N, cells); None where not captured
-TRAFFIC = {(16, 128): 18410496, (32, 256): 2951102208 + 68633088}
+TRAFFIC = {(16, 128): 18411008, (32, 256): 2991451648 + 68178176}
 SMS = 152
 FP32_LANES = 128
 
