@@ -333,7 +333,7 @@ int cs_step(cs_handle_t h, double *f, int ncells, const cs_domain *dom, double d
  *   Arguments, layouts and results are those of cs_collide (same kernels).
  *   Size limit: the three spectral intermediates must fit in 64 MiB, i.e.
  *   at most 64 cells at N = 32 in CS_FP32, 32 cells at N = 32 in CS_FP64,
- *   672 cells at N = 16 in CS_FP32; larger ncells returns CS_EINVAL and a
+ *   384 cells at N = 16 in CS_FP32; larger ncells returns CS_EINVAL and a
  *   message with the limit for the handle's N and precision.
  *   Every GPU that loads the library holds the 64 MiB array until the
  *   process exits.  All calls on a device share it and it keeps the last

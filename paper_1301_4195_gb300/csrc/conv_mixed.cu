@@ -36,7 +36,7 @@ struct MixedShape<8> {
 };
 template <>
 struct MixedShape<16> {
-    static constexpr int K = 8, U = 8, GPC = 2, S = 2;
+    static constexpr int K = 8, U = 8, GPC = 2, S = 4;
 };
 template <>
 struct MixedShape<24> {
@@ -135,11 +135,12 @@ int launch_strip_mixed(const Handle *const *hds, const int *ncells, int n, cudaS
     for (int k = 0; k < n; ++k) {
         const Handle &hd = *hds[idx[k]];
         const int N = hd.g.N, gpc = groups_per_cta(N);
-        const int parts = N == 16 ? 2 : 1;
+        const int parts = N == 16 ? 4 : 1;
         if (parts != conv_parts(hd)) return set_error(CS_ENOTSUP, "mixed convolution: split differs from the handle's");
         const int nblocks = strip_mixed_cells(hd, ncells[idx[k]]) / kGroup / gpc;
         js.j[k] = StripJob{(const float *)hd.ghat, hd.pencil_tile0, hd.pencil_order, (const float2 *)hd.F,
-                           (float2 *)hd.Qh, (float2 *)hd.Qh2, hd.err, (float)(hd.g.dz * hd.g.dz * hd.g.dz),
+                           (float2 *)hd.Qh, (float2 *)hd.Qh2, (float2 *)hd.Qh3, (float2 *)hd.Qh4, hd.err,
+                           (float)(hd.g.dz * hd.g.dz * hd.g.dz),
                            nblocks, N, (int)first};
         first += (long long)N * N * nblocks * parts;
     }

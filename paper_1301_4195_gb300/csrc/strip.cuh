@@ -327,7 +327,7 @@ struct StripJob {
     const float *ghat;
     const int *tile0, *order;
     const float2 *F;
-    float2 *Qh, *Qh2;
+    float2 *Qh, *Qh2, *Qh3, *Qh4;  // partial sums of tile ranges 0, 1, 2, 3
     int *err;  // the handle's status word
     float omega;
     int nblocks, N, first;
@@ -496,7 +496,7 @@ __device__ __forceinline__ void ring_drain(const Ring &r, bool ok)
 }
 
 // One work item of job jb (item numbered within the job): a (pencil, group
-// block) pair, or half of its tiles when S = 2.  Thread 0 produces the
+// block) pair, or the part-th of S ranges of its tiles.  Thread 0 produces the
 // pencil's tiles into the ring, NST ahead of the warps; every warp sums its
 // strip.  Returns false (CTA-uniform) if a wait expired or the CTA aborted.
 template <int N, int K, int U, int NST, int GPC, int S, bool RAD = false>
@@ -521,12 +521,12 @@ __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &r
     const int lo1 = max(0, K1 - N + 1);
     const int lo2 = max(0, K2 - N + 1), hi2 = min(N - 1, K2);
     const int Tall = jb.tile0[pencil + 1] - jb.tile0[pencil];
-    const int tb = part == 0 ? 0 : (Tall + 1) / 2;  // this part's tiles: tb .. te-1
-    const int te = (S == 1 || part == 1) ? Tall : (Tall + 1) / 2;
+    const int tb = (part * Tall + S - 1) / S;  // this part's tiles: tb .. te-1
+    const int te = ((part + 1) * Tall + S - 1) / S;
     const int T = te - tb;
     const float2 *Fb0 = jb.F + (size_t)gblk * GPC * C::M * kGroup;
     const float *Gp = jb.ghat + (size_t)(jb.tile0[pencil] + tb) * C::TSV;
-    float2 *Qout = part == 0 ? jb.Qh : jb.Qh2;
+    float2 *Qout = part == 0 ? jb.Qh : part == 1 ? jb.Qh2 : part == 2 ? jb.Qh3 : jb.Qh4;
     bool ok = true;
 
     TileWalk pw;  // producer's walk (thread 0), NST tiles ahead of the consumers
@@ -712,7 +712,7 @@ int launch_cfg(const Handle &hd, int ncells, cudaStream_t s)
     cudaError_t e = cudaMemsetAsync(hd.counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return cuda_error(e, "strip kernel work counter");
     StripJob jb{(const float *)hd.ghat, hd.pencil_tile0, hd.pencil_order, (const float2 *)hd.F,
-                (float2 *)hd.Qh, (float2 *)hd.Qh2, hd.err, omega, nblocks, N, 0};
+                (float2 *)hd.Qh, (float2 *)hd.Qh2, (float2 *)hd.Qh3, (float2 *)hd.Qh4, hd.err, omega, nblocks, N, 0};
     if constexpr (RAD) {
         jb.radA = hd.radA;
         jb.radB = hd.radB;
@@ -741,7 +741,7 @@ int launch_strip_mode(const Handle &hd, int ncells, cudaStream_t s)
 {
     switch (hd.g.N) {
     case 8: return launch_n<8, 4, 4, 4, 4, 1, RAD>(hd, ncells, s);
-    case 16: return launch_n<16, 8, 8, 3, 3, 2, RAD>(hd, ncells, s);
+    case 16: return launch_n<16, 8, 8, 3, 3, 4, RAD>(hd, ncells, s);
     case 24: return launch_n<24, 12, 4, 3, 2, 1, RAD>(hd, ncells, s);
     case 32: return launch_n<32, 8, 8, 3, 3, 1, RAD>(hd, ncells, s);
     case 48: return launch_n<48, 8, 8, 3, 2, 1, RAD>(hd, ncells, s);
