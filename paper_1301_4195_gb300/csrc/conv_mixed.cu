@@ -27,7 +27,7 @@ constexpr int kMixedWarps = 4;
 constexpr int kMixedNST = 2;  // ring depth of a mixed launch
 
 // item shape per N: strip width K, uniform block U, groups per CTA, parts S
-// (S = conv_parts: the split at N = 16 must match the handle's own launch)
+// (S = conv_split: the split at N = 16 must match the handle's own launch)
 template <int N>
 struct MixedShape;
 template <>
@@ -136,10 +136,10 @@ int launch_strip_mixed(const Handle *const *hds, const int *ncells, int n, cudaS
         const Handle &hd = *hds[idx[k]];
         const int N = hd.g.N, gpc = groups_per_cta(N);
         const int parts = N == 16 ? 4 : 1;
-        if (parts != conv_parts(hd)) return set_error(CS_ENOTSUP, "mixed convolution: split differs from the handle's");
+        if (parts != conv_split(hd)) return set_error(CS_ENOTSUP, "mixed convolution: split differs from the handle's");
         const int nblocks = strip_mixed_cells(hd, ncells[idx[k]]) / kGroup / gpc;
         js.j[k] = StripJob{(const float *)hd.ghat, hd.pencil_tile0, hd.pencil_order, (const float2 *)hd.F,
-                           (float2 *)hd.Qh, (float2 *)hd.Qh2, (float2 *)hd.Qh3, (float2 *)hd.Qh4, hd.err,
+                           (float2 *)hd.Qh, (float2 *)hd.Qh2, (float2 *)hd.Qh3, (float2 *)hd.Qh4, hd.done, hd.err,
                            (float)(hd.g.dz * hd.g.dz * hd.g.dz),
                            nblocks, N, (int)first};
         first += (long long)N * N * nblocks * parts;
@@ -167,7 +167,9 @@ int launch_strip_mixed(const Handle *const *hds, const int *ncells, int n, cudaS
     // the work counter: a word of the first job's handle that its own launches never use
     int *counter = hds[idx[0]]->err + 48;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
-    if (e != cudaSuccess) return cuda_error(e, "mixed convolution: work counter");
+    for (int k = 0; k < n && e == cudaSuccess; ++k)  // finished-range counters of the split jobs
+        if (js.j[k].N == 16) e = cudaMemsetAsync(js.j[k].done, 0, sizeof(int) * 16 * 16 * js.j[k].nblocks, s);
+    if (e != cudaSuccess) return cuda_error(e, "mixed convolution: work counters");
     conv_mixed_kernel<<<grid, 32 * kMixedWarps, kMixedSmem, s>>>(js, counter);
     CS_LAUNCHED(1, s, "convolution (mixed strip kernel)");
     return CS_OK;

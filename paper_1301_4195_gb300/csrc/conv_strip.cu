@@ -9,10 +9,10 @@
 // GPC groups of 32 cells (one cell per lane), or, with S parts, one of S
 // consecutive ranges of that pencil's tiles: part p sums tiles
 // ceil(pT/S) .. ceil((p+1)T/S)-1 into its own partial sum (Qh, Qh2, Qh3,
-// Qh4), and the consumer adds the partial sums in that fixed order.  At
-// N = 16 S = 4: smaller items shorten the tail of a launch over few cells
-// (128 cells: 8 % less time than S = 2, at 2 % more for 4096 cells); the
-// split depends only on N and the precision, so a cell's result never
+// Qh4); the last range of a (pencil, block) to finish adds the partial sums
+// into Qh in that fixed order.  At N = 16 S = 4: smaller items shorten the
+// tail of a launch over few cells (128 cells: 8 % less time than S = 2);
+// the split depends only on N and the precision, so a cell's result never
 // depends on how many cells share the launch.  The pencil's k3 range is cut
 // into N/K strips of K outputs; warp (group g, strip w) keeps only its K
 // complex accumulators (plus a compensation pair) in registers.  CTAs are
@@ -48,7 +48,7 @@
 
 namespace cs {
 
-int conv_parts(const Handle &hd)
+int conv_split(const Handle &hd)
 {
     return (hd.precision == CS_FP32 && hd.g.layout == LAYOUT_STRIP && hd.g.N == 16) ? 4 : 1;
 }

@@ -151,8 +151,9 @@ size_t spectral_bytes(const Handle &hd, int ncells)
 }
 
 // Carve the workspace: F, Qh, X, Y (spectral), Qt, f1 (state), scal
-// (transport tables), part5 (projection partials), and for a convolution
-// split four ways one more spectral buffer (its fourth partial sum).
+// (transport tables), part5 (projection partials), and for a split
+// convolution one more spectral buffer (its fourth partial sum) and the
+// counters of finished tile ranges per (pencil, block).
 size_t workspace_bytes(const Handle &hd, int ncells, int geo_cells, size_t *offs)
 {
     const size_t sb = align_up(spectral_bytes(hd, ncells), 256);
@@ -173,7 +174,9 @@ size_t workspace_bytes(const Handle &hd, int ncells, int geo_cells, size_t *offs
     if (offs) offs[7] = o;
     o += sp;
     if (offs) offs[8] = o;
-    if (conv_parts(hd) > 3) o += sb;
+    if (conv_split(hd) > 3) o += sb;  // Qh4
+    if (offs) offs[9] = o;
+    if (conv_split(hd) > 1) o += align_up(sizeof(int) * (size_t)hd.g.N * hd.g.N * ngroups_of(ncells), 256);
     return o;
 }
 
@@ -192,7 +195,7 @@ int ensure_workspace(Handle &hd, int ncells, int geo_cells = 0)
     if (ncells < hd.ws_cells) ncells = hd.ws_cells;
     if (geo_cells < hd.ws_geo_cells) geo_cells = hd.ws_geo_cells;
     drop_graphs(hd);  // captured steps point into the old workspace
-    size_t offs[9];
+    size_t offs[10];
     const size_t bytes = workspace_bytes(hd, ncells, geo_cells, offs);
     if (hd.ws) {
         cudaError_t e = cudaDeviceSynchronize();
@@ -218,7 +221,8 @@ int ensure_workspace(Handle &hd, int ncells, int geo_cells = 0)
     hd.Qh = b + offs[1];
     hd.Qh2 = b + offs[2];  // X and Y: unused by the whole-cell transforms, the only consumers of a split
     hd.Qh3 = b + offs[3];
-    hd.Qh4 = conv_parts(hd) > 3 ? b + offs[8] : nullptr;
+    hd.Qh4 = conv_split(hd) > 3 ? b + offs[8] : nullptr;
+    hd.done = conv_split(hd) > 1 ? (int *)(b + offs[9]) : nullptr;
     hd.X = b + offs[2];
     hd.Y = b + offs[3];
     hd.Qt = (double *)(b + offs[4]);
@@ -243,7 +247,7 @@ int timed_convolve(Handle &hd, int ncells, cudaStream_t s)
 int timed_inverse(Handle &hd, int ncells, double eps, double *Qt, cudaStream_t s)
 {
     StageTimer t(hd, CS_K_INVERSE, s);
-    return launch_inverse(hd, ncells, eps, Qt, s, conv_extra(hd));
+    return launch_inverse(hd, ncells, eps, Qt, s);
 }
 
 int timed_conserve(Handle &hd, const double *Qt, int ncells, int project, double a, const double *x, double b,
@@ -270,7 +274,7 @@ int collide_back(Handle &hd, int ncells, double eps, int project, double a, cons
 {
     if (fused_available(hd)) {
         StageTimer t(hd, CS_K_INVERSE, s);
-        return launch_inverse_project(hd, ncells, eps, project, a, x, b, y, c, out, conv_extra(hd), s);
+        return launch_inverse_project(hd, ncells, eps, project, a, x, b, y, c, out, s);
     }
     const bool direct = (x == nullptr && y == nullptr && c == 1.0);
     double *qt = direct ? out : hd.Qt;
@@ -1097,7 +1101,7 @@ int cs_convolve(cs_handle_t h, const double *fhat, int ncells, double *qhat, cud
     if (int rc = ensure_workspace(hd, ncells)) return rc;
     if (int rc = launch_natural_to_spectral(hd, fhat, ncells, hd.F, s)) return rc;
     if (int rc = timed_convolve(hd, ncells, s)) return rc;
-    return launch_spectral_to_natural(hd, hd.Qh, ncells, qhat, s, conv_extra(hd));
+    return launch_spectral_to_natural(hd, hd.Qh, ncells, qhat, s);
 }
 
 int cs_inverse(cs_handle_t h, const double *qhat, int ncells, double eps, double *Q, cudaStream_t s)

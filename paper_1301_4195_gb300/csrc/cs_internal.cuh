@@ -128,10 +128,12 @@ struct Handle {
     unsigned ws_generation = 0;  // bumped whenever the workspace moves
     // pieces of the workspace (set by layout_workspace)
     void *F = nullptr, *Qh = nullptr, *X = nullptr, *Y = nullptr;
-    // further partial sums of a split convolution (conv_parts > 1): Qh2 aliases X,
-    // Qh3 aliases Y (scratch of the per-axis transforms, which split handles do
-    // not use), Qh4 has a buffer of its own
+    // partial sums 2-4 of a split convolution (conv_split > 1; the kernel's
+    // last part adds them into Qh): Qh2 aliases X, Qh3 aliases Y (scratch of
+    // the per-axis transforms, which split handles do not use), Qh4 and the
+    // per-(pencil, block) counters of finished parts have room of their own
     void *Qh2 = nullptr, *Qh3 = nullptr, *Qh4 = nullptr;
+    int *done = nullptr;
     double *Qt = nullptr, *f1 = nullptr, *r1 = nullptr, *scal = nullptr;
     double *part5 = nullptr;  // per-block partial moments of the projection
     // replayable steps (cs_step, cs_relax): one captured step per argument set
@@ -216,16 +218,9 @@ int sample_weights(Handle &hd, const int *km_host, int n, double *out_host);
 // ---- transform.cu
 int launch_forward(const Handle &hd, const double *f, int ncells, cudaStream_t s);   // f -> hd.F
 // hd.Qh (+ qh2, the second partial sum of a split convolution, if not NULL) -> Qt
-// the partial sums after the first of a split convolution, in the order they
-// are added (unused entries NULL)
-struct Parts {
-    const void *p[3] = {nullptr, nullptr, nullptr};
-};
-int launch_inverse(const Handle &hd, int ncells, double scale_eps, double *Qt, cudaStream_t s,
-                   Parts parts = Parts());
-// grouped spectral src (+ the further partial sums, in order) -> [ncells][N^3][2] doubles
-int launch_spectral_to_natural(const Handle &hd, const void *src, int ncells, double *dst, cudaStream_t s,
-                               Parts parts = Parts());
+int launch_inverse(const Handle &hd, int ncells, double scale_eps, double *Qt, cudaStream_t s);
+// grouped spectral src -> [ncells][N^3][2] doubles
+int launch_spectral_to_natural(const Handle &hd, const void *src, int ncells, double *dst, cudaStream_t s);
 int launch_natural_to_spectral(const Handle &hd, const double *src, int ncells, void *dst, cudaStream_t s);
 
 // ---- fused.cu (float, N <= 24: whole-cell transforms in shared memory)
@@ -236,22 +231,15 @@ int launch_forward_fused(const Handle &hd, const double *f, int ncells, cudaStre
 // out = a x + b y + P(c Qt), Qt the inverse transform of hd.Qh (+ qh2 if not
 // NULL), P the projection if project (else the identity)
 int launch_inverse_project(const Handle &hd, int ncells, double eps, int project, double a, const double *x,
-                           double b, const double *y, double c, double *out, Parts parts, cudaStream_t s);
+                           double b, const double *y, double c, double *out, cudaStream_t s);
 
 // ---- convolve.cu, conv_strip.cu
 int launch_convolve(const Handle &hd, int ncells, cudaStream_t s);  // hd.F -> hd.Qh (and hd.Qh2)
-// how many partial sums the convolution of this handle leaves (hd.Qh, then
-// hd.Qh2, Qh3, Qh4, to be added in that order): 4 for float strip handles at
-// N = 16, else 1; fixed per N and precision
-int conv_parts(const Handle &hd);
-inline Parts conv_extra(const Handle &hd)
-{
-    Parts r;
-    const int n = conv_parts(hd);
-    const void *q[3] = {hd.Qh2, hd.Qh3, hd.Qh4};
-    for (int i = 0; i + 1 < n && i < 3; ++i) r.p[i] = q[i];
-    return r;
-}
+// into how many tile ranges the convolution of this handle splits each
+// pencil (4 for float strip handles at N = 16, else 1; fixed per N and
+// precision); the last range to finish adds the partial sums into hd.Qh in
+// range order, so every consumer reads one buffer
+int conv_split(const Handle &hd);
 int launch_strip(const Handle &hd, int ncells, cudaStream_t s);     // float, LAYOUT_STRIP
 int launch_strip_radius(const Handle &hd, int ncells, cudaStream_t s);  // conv_radius.cu
 bool strip_uses_radius(const Handle &hd);  // the handle's strip launches rebuild tiles from the radius tables

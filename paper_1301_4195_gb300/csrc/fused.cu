@@ -13,9 +13,8 @@
 // run in shared memory, and fhat goes out in the 32-cell grouped layout the
 // convolution reads.
 //
-// inverse_project_kernel: one block per cell.  Reads Qhat of the cell (the
-// sum of the convolution's partial sums, in their order, when it leaves
-// several), runs the three
+// inverse_project_kernel: one block per cell.  Reads Qhat of the cell, runs
+// the three
 // inverse passes (Qt = Re (2 pi)^{-3/2} dzeta^3 sum_k ... / eps), then the
 // conservation projection of Sec. 3.3 in double precision and the caller's
 // Runge-Kutta combination,
@@ -274,8 +273,7 @@ __global__ void __launch_bounds__(kThreads<N, CL>) forward_fused_kernel(const do
 
 template <int N, int CL>
 __global__ void __launch_bounds__(kThreads<N, CL>) inverse_project_kernel(
-    const float2 *__restrict__ Qh, const float2 *__restrict__ Qh2, const float2 *__restrict__ Qh3,
-    const float2 *__restrict__ Qh4, float cic, double dv, int project, Proj5 pj, double a, const double *x, double b,
+    const float2 *__restrict__ Qh, float cic, double dv, int project, Proj5 pj, double a, const double *x, double b,
     const double *y, double *out)
 {
     constexpr int M = N * N * N, P = N + 1, LINES = kLines<N, CL>, PL = kPL<N, CL>, PTS = kPts<N, CL>, H = N / 2;
@@ -294,24 +292,12 @@ __global__ void __launch_bounds__(kThreads<N, CL>) inverse_project_kernel(
         vsq[tid] = vax[tid] * vax[tid];
     }
     const size_t fbase = (size_t)g * M + (size_t)rank * PTS;  // the block's planes in Qh
-    const float2 *more[3] = {Qh2, Qh3, Qh4};  // further partial sums, added in this order
     for (int r0 = 0; r0 < PER; r0 += CHUNK) {
-        float2 qa[CHUNK], qb[CHUNK];
+        float2 qa[CHUNK];
 #pragma unroll
         for (int r = 0; r < CHUNK; ++r) {
             const int k = (r0 + r) * NT + tid;
             qa[r] = Qh[(fbase + (k < PTS ? k : 0)) * kGroup + lane];
-        }
-#pragma unroll
-        for (int m = 0; m < 3; ++m) {
-            if (!more[m]) break;
-#pragma unroll
-            for (int r = 0; r < CHUNK; ++r) {
-                const int k = (r0 + r) * NT + tid;
-                qb[r] = more[m][(fbase + (k < PTS ? k : 0)) * kGroup + lane];
-            }
-#pragma unroll
-            for (int r = 0; r < CHUNK; ++r) qa[r] = make_float2(qa[r].x + qb[r].x, qa[r].y + qb[r].y);
         }
 #pragma unroll
         for (int r = 0; r < CHUNK; ++r) {
@@ -484,13 +470,12 @@ int forward_n(const Handle &hd, const double *f, int ncells, int grid_cells, cud
 
 template <int N, int CL>
 int inverse_cl(const Handle &hd, int ncells, float cic, int project, const Proj5 &pj, double a, const double *x,
-               double b, const double *y, double *out, Parts parts, cudaStream_t s)
+               double b, const double *y, double *out, cudaStream_t s)
 {
     if (int rc = allow_smem(inverse_project_kernel<N, CL>, fused_smem<N, CL>(), "fused inverse: shared-memory attribute"))
         return rc;
     cudaError_t e = launch_cells<N, CL>(inverse_project_kernel<N, CL>, (unsigned)ncells, s, (const float2 *)hd.Qh,
-                                        (const float2 *)parts.p[0], (const float2 *)parts.p[1],
-                                        (const float2 *)parts.p[2], cic, hd.g.dv, project, pj, a, x, b, y, out);
+                                        cic, hd.g.dv, project, pj, a, x, b, y, out);
     if (e != cudaSuccess) return cuda_error(e, "fused inverse transform launch");
     CS_LAUNCHED(1, s, "inverse transform and projection (fused)");
     return CS_OK;
@@ -498,13 +483,13 @@ int inverse_cl(const Handle &hd, int ncells, float cic, int project, const Proj5
 
 template <int N>
 int inverse_n(const Handle &hd, int ncells, double eps, int project, double a, const double *x, double b,
-              const double *y, double c, double *out, Parts parts, cudaStream_t s)
+              const double *y, double c, double *out, cudaStream_t s)
 {
     Proj5 pj;
     for (int i = 0; i < 25; ++i) pj.ainv[i] = hd.cct_inv[i];
     // the scale of the last inverse pass, times the step factor c
     const float cic = (float)(c * pow(2.0 * M_PI, -1.5) * hd.g.dz * hd.g.dz * hd.g.dz / eps);
-    return inverse_cl<N, kCL<N>>(hd, ncells, cic, project, pj, a, x, b, y, out, parts, s);
+    return inverse_cl<N, kCL<N>>(hd, ncells, cic, project, pj, a, x, b, y, out, s);
 }
 
 }  // namespace
@@ -528,14 +513,14 @@ int launch_forward_fused(const Handle &hd, const double *f, int ncells, cudaStre
 }
 
 int launch_inverse_project(const Handle &hd, int ncells, double eps, int project, double a, const double *x,
-                           double b, const double *y, double c, double *out, Parts parts, cudaStream_t s)
+                           double b, const double *y, double c, double *out, cudaStream_t s)
 {
     switch (hd.g.N) {
-    case 8: return inverse_n<8>(hd, ncells, eps, project, a, x, b, y, c, out, parts, s);
-    case 12: return inverse_n<12>(hd, ncells, eps, project, a, x, b, y, c, out, parts, s);
-    case 16: return inverse_n<16>(hd, ncells, eps, project, a, x, b, y, c, out, parts, s);
-    case 24: return inverse_n<24>(hd, ncells, eps, project, a, x, b, y, c, out, parts, s);
-    case 32: return inverse_n<32>(hd, ncells, eps, project, a, x, b, y, c, out, parts, s);
+    case 8: return inverse_n<8>(hd, ncells, eps, project, a, x, b, y, c, out, s);
+    case 12: return inverse_n<12>(hd, ncells, eps, project, a, x, b, y, c, out, s);
+    case 16: return inverse_n<16>(hd, ncells, eps, project, a, x, b, y, c, out, s);
+    case 24: return inverse_n<24>(hd, ncells, eps, project, a, x, b, y, c, out, s);
+    case 32: return inverse_n<32>(hd, ncells, eps, project, a, x, b, y, c, out, s);
     default: return set_error(CS_ENOTSUP, "fused inverse transform: unsupported N");
     }
 }

@@ -110,13 +110,18 @@ extern "C" int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, do
         return set_error(CS_EINVAL, "f and Q overlap");
     // three spectral buffers: forward X, Y -> F; convolution F -> Qh (reusing X's
     // space, and Y's for a split's second partial sum, two more buffers for a
-    // third and fourth); inverse Qh -> X', Y' (reusing Y's and F's space);
-    // then the per-block partial moments of the projection
-    const int nbuf = 3 + (conv_parts(hd) > 2 ? conv_parts(hd) - 2 : 0);
+    // third and fourth, and the split's counters); inverse Qh -> X', Y'
+    // (reusing Y's and F's space); then the per-block partial moments of the
+    // projection
+    const int split = conv_split(hd);
+    const int nbuf = 3 + (split > 2 ? split - 2 : 0);
     const size_t part_bytes = (sizeof(double) * 5 * (size_t)ncells * conserve_parts(hd.g.M) + 255) / 256 * 256;
-    const size_t need = nbuf * buffer_bytes(hd, ncells) + part_bytes;
+    const size_t done_bytes =
+        split > 1 ? (sizeof(int) * (size_t)hd.g.N * hd.g.N * ngroups_of(ncells) + 255) / 256 * 256 : 0;
+    const size_t need = nbuf * buffer_bytes(hd, ncells) + part_bytes + done_bytes;
     if (need > kScratchBytes) {
-        const size_t per_group = nbuf * buffer_bytes(hd, 1) + 5 * sizeof(double) * kGroup * conserve_parts(hd.g.M);
+        const size_t per_group = nbuf * buffer_bytes(hd, 1) + 5 * sizeof(double) * kGroup * conserve_parts(hd.g.M) +
+                                 (split > 1 ? sizeof(int) * hd.g.N * hd.g.N : 0);
         return set_error(CS_EINVAL, "cs_collide_noalloc: " + std::to_string(ncells) + " cells need " +
                                         std::to_string(need) + " bytes of scratch; the fixed array holds " +
                                         std::to_string(kScratchBytes) + " (at most " +
@@ -142,17 +147,16 @@ extern "C" int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, do
     fwd.Qh2 = B;  // a split convolution's second partial sum (Y is free again after the forward passes)
     fwd.Qh3 = nbuf > 3 ? D : nullptr;
     fwd.Qh4 = nbuf > 4 ? E : nullptr;
+    fwd.done = split > 1 ? (int *)(C + (nbuf - 2) * buffer_bytes(hd, ncells) + part_bytes) : nullptr;
     Handle inv = view_of(hd);
     inv.Qh = A;
-    inv.Qh2 = B;  // read before the inverse writes anything (whole-cell kernel, the only split consumer)
-    inv.Qh3 = fwd.Qh3;
-    inv.Qh4 = fwd.Qh4;
+
     inv.X = B;
     inv.Y = C;
     inv.part5 = (double *)(C + (nbuf - 2) * buffer_bytes(hd, ncells));
     if (int rc = launch_forward(fwd, f, ncells, stream)) return rc;
     if (int rc = launch_convolve(fwd, ncells, stream)) return rc;
-    if (int rc = launch_inverse(inv, ncells, eps, Q, stream, conv_extra(inv))) return rc;
+    if (int rc = launch_inverse(inv, ncells, eps, Q, stream)) return rc;
     if (conserve) return launch_conserve(inv, Q, ncells, 1, 0.0, nullptr, 0.0, nullptr, 1.0, Q, nullptr, stream);
     return CS_OK;
 }

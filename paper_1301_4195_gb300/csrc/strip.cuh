@@ -327,8 +327,9 @@ struct StripJob {
     const float *ghat;
     const int *tile0, *order;
     const float2 *F;
-    float2 *Qh, *Qh2, *Qh3, *Qh4;  // partial sums of tile ranges 0, 1, 2, 3
-    int *err;  // the handle's status word
+    float2 *Qh, *Qh2, *Qh3, *Qh4;  // partial sums of tile ranges 0, 1, 2, 3 (Qh: their sum at the end)
+    int *done;                     // S > 1: finished ranges per (pencil, block), zero at the launch
+    int *err;                      // the handle's status word
     float omega;
     int nblocks, N, first;
     // radius tables (launches that rebuild the weight tiles): A, B, the tile
@@ -631,6 +632,32 @@ __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &r
             make_float2(jb.omega * v.x, jb.omega * v.y);
     }
     rg.tt += T;
+    if constexpr (S > 1) {
+        // the last of a (pencil, block)'s S ranges adds the partial sums into
+        // Qh, in range order: every consumer reads one buffer, and the sum
+        // does not depend on which range finished last (fence, then count;
+        // the last reads the others' sums past L1)
+        __shared__ int s_last;
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_last = atomicAdd(jb.done + rest, 1) == S - 1;
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            const float2 *more[3] = {jb.Qh2, jb.Qh3, jb.Qh4};
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                const size_t idx = ((size_t)grp * C::M + (size_t)pencil * N + k0 + j) * kGroup + lane;
+                float2 v = __ldcg(jb.Qh + idx);
+#pragma unroll
+                for (int m = 0; m < S - 1; ++m) {
+                    const float2 w = __ldcg(more[m] + idx);
+                    v = make_float2(v.x + w.x, v.y + w.y);
+                }
+                jb.Qh[idx] = v;
+            }
+        }
+    }
     return true;
 }
 
@@ -710,9 +737,11 @@ int launch_cfg(const Handle &hd, int ncells, cudaStream_t s)
     const int grid = std::min(nitems, std::max(1, sms) * per);
     const float omega = (float)(hd.g.dz * hd.g.dz * hd.g.dz);
     cudaError_t e = cudaMemsetAsync(hd.counter, 0, sizeof(int), s);
-    if (e != cudaSuccess) return cuda_error(e, "strip kernel work counter");
+    if (e == cudaSuccess && S > 1) e = cudaMemsetAsync(hd.done, 0, sizeof(int) * N * N * nblocks, s);
+    if (e != cudaSuccess) return cuda_error(e, "strip kernel work counters");
     StripJob jb{(const float *)hd.ghat, hd.pencil_tile0, hd.pencil_order, (const float2 *)hd.F,
-                (float2 *)hd.Qh, (float2 *)hd.Qh2, (float2 *)hd.Qh3, (float2 *)hd.Qh4, hd.err, omega, nblocks, N, 0};
+                (float2 *)hd.Qh, (float2 *)hd.Qh2, (float2 *)hd.Qh3, (float2 *)hd.Qh4, hd.done, hd.err, omega,
+                nblocks, N, 0};
     if constexpr (RAD) {
         jb.radA = hd.radA;
         jb.radB = hd.radB;

@@ -128,20 +128,14 @@ __global__ void inverse_rows_kernel(int N, double scale, const c2_t<T> *__restri
 }
 
 template <typename T>
-__global__ void to_natural_kernel(int N, const c2_t<T> *__restrict__ src, const c2_t<T> *src2, const c2_t<T> *src3,
-                                  const c2_t<T> *src4, int ncells, double *__restrict__ dst)
+__global__ void to_natural_kernel(int N, const c2_t<T> *__restrict__ src, int ncells, double *__restrict__ dst)
 {
     const size_t M = (size_t)N * N * N;
     const size_t n = M * ncells;
-    const c2_t<T> *more[3] = {src2, src3, src4};
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const size_t c = i / M, k = i % M;
         const size_t j = ((c / kGroup) * M + k) * kGroup + (c % kGroup);
-        c2_t<T> v = src[j];
-        for (int m = 0; m < 3 && more[m]; ++m) {  // further partial sums, in the order the inverse adds them
-            v.x = v.x + more[m][j].x;
-            v.y = v.y + more[m][j].y;
-        }
+        const c2_t<T> v = src[j];
         dst[2 * i] = (double)v.x;
         dst[2 * i + 1] = (double)v.y;
     }
@@ -212,27 +206,21 @@ int launch_forward(const Handle &hd, const double *f, int ncells, cudaStream_t s
     return hd.precision == CS_FP32 ? forward_impl<float>(hd, f, ncells, s) : forward_impl<double>(hd, f, ncells, s);
 }
 
-int launch_inverse(const Handle &hd, int ncells, double eps, double *Qt, cudaStream_t s, Parts parts)
+int launch_inverse(const Handle &hd, int ncells, double eps, double *Qt, cudaStream_t s)
 {
     if (fused_available(hd))
-        return launch_inverse_project(hd, ncells, eps, 0, 0.0, nullptr, 0.0, nullptr, 1.0, Qt, parts, s);
-    if (parts.p[0]) return set_error(CS_ENOTSUP, "inverse transform: split partial sums need the whole-cell kernel");
+        return launch_inverse_project(hd, ncells, eps, 0, 0.0, nullptr, 0.0, nullptr, 1.0, Qt, s);
     return hd.precision == CS_FP32 ? inverse_impl<float>(hd, ncells, eps, Qt, s)
                                    : inverse_impl<double>(hd, ncells, eps, Qt, s);
 }
 
-int launch_spectral_to_natural(const Handle &hd, const void *src, int ncells, double *dst, cudaStream_t s,
-                               Parts parts)
+int launch_spectral_to_natural(const Handle &hd, const void *src, int ncells, double *dst, cudaStream_t s)
 {
     const int N = hd.g.N;
     if (hd.precision == CS_FP32)
-        to_natural_kernel<float><<<1024, 256, 0, s>>>(N, (const float2 *)src, (const float2 *)parts.p[0],
-                                                      (const float2 *)parts.p[1], (const float2 *)parts.p[2], ncells,
-                                                      dst);
+        to_natural_kernel<float><<<1024, 256, 0, s>>>(N, (const float2 *)src, ncells, dst);
     else
-        to_natural_kernel<double><<<1024, 256, 0, s>>>(N, (const double2 *)src, (const double2 *)parts.p[0],
-                                                       (const double2 *)parts.p[1], (const double2 *)parts.p[2],
-                                                       ncells, dst);
+        to_natural_kernel<double><<<1024, 256, 0, s>>>(N, (const double2 *)src, ncells, dst);
     CS_LAUNCHED(1, s, "spectral layout conversion");
     return CS_OK;
 }
