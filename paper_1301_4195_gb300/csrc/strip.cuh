@@ -635,15 +635,19 @@ __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &r
     if constexpr (S > 1) {
         // the last of a (pencil, block)'s S ranges adds the partial sums into
         // Qh, in range order: every consumer reads one buffer, and the sum
-        // does not depend on which range finished last (fence, then count;
-        // the last reads the others' sums past L1)
+        // does not depend on which range finished last.  The CTA's stores
+        // are ordered before thread 0's count by the barrier and the count's
+        // release; the last CTA's reads after it by the count's acquire and
+        // the barrier, and they bypass L1
         __shared__ int s_last;
-        __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) s_last = atomicAdd(jb.done + rest, 1) == S - 1;
+        if (threadIdx.x == 0) {
+            int old;
+            asm volatile("atom.add.acq_rel.gpu.s32 %0, [%1], 1;" : "=r"(old) : "l"(jb.done + rest) : "memory");
+            s_last = old == S - 1;
+        }
         __syncthreads();
         if (s_last) {
-            __threadfence();
             const float2 *more[3] = {jb.Qh2, jb.Qh3, jb.Qh4};
 #pragma unroll
             for (int j = 0; j < K; ++j) {
