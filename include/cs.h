@@ -349,6 +349,12 @@ int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, double eps, d
                        cudaStream_t stream);
 
 /* Launch choices of the convolution (autotuner parameters).
+ *   CS_TUNE_SPLIT           float handles at N = 16: 2 or 4 tile ranges per
+ *                           output pencil (4 shortens the tail of a launch
+ *                           over few cells); the ranges' partial sums are
+ *                           added in a fixed order, so a choice changes the
+ *                           rounding of the sum, not its terms, and holds
+ *                           for every call on the handle
  *   CS_TUNE_GROUPS_PER_CTA  1 or 2 groups of 32 cells share each weight tile
  *                           in shared memory (2 needs an even group count)
  *   CS_TUNE_CTAS_PER_SM     resident CTAs per SM of the persistent kernel
@@ -361,6 +367,7 @@ int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, double eps, d
 #define CS_TUNE_GROUPS_PER_CTA 1
 #define CS_TUNE_CTAS_PER_SM 2
 #define CS_TUNE_WEIGHTS 3
+#define CS_TUNE_SPLIT 4
 int cs_tune(cs_handle_t h, int param, int value);
 
 /* The current value of a launch choice (0 = automatic).
@@ -379,7 +386,8 @@ int cs_fma_probe(int kind, cudaStream_t stream, double *lane_ops_per_s);
  * `stream` (synchronising), keep the fastest in the handle and return its
  * time per launch in *ms (may be NULL).  The choices are the launch shapes
  * times the weight modes the handle has (stored tiles, radius tables): the
- * store-versus-recompute choice of the weights is timed, not assumed.  Uses
+ * store-versus-recompute choice of the weights is timed, not assumed; at
+ * N = 16 in float times the two splits as well.  Uses
  * the workspace (cs_reserve).
  * Errors: CS_EINVAL, CS_ENOMEM, CS_ECUDA. */
 int cs_autotune(cs_handle_t h, int ncells, cudaStream_t stream, double *ms);

@@ -285,6 +285,7 @@ def cs_transport_shard_stage(h, f_win, ncells, first_cell, total_cells, dom: Dom
 
 CS_TUNE_GROUPS_PER_CTA = 1
 CS_TUNE_WEIGHTS = 3
+CS_TUNE_SPLIT = 4
 CS_TUNE_CTAS_PER_SM = 2
 
 

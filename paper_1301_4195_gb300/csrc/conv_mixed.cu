@@ -36,7 +36,7 @@ struct MixedShape<8> {
 };
 template <>
 struct MixedShape<16> {
-    static constexpr int K = 8, U = 8, GPC = 2, S = 4;
+    static constexpr int K = 8, U = 8, GPC = 2, S = 4;  // or 2: the handle's split (StripJob::S)
 };
 template <>
 struct MixedShape<24> {
@@ -60,12 +60,12 @@ struct StripJobs {
     int n, nitems;
 };
 
-template <int N>
+template <int N, int SPLIT = MixedShape<N>::S>
 __device__ __forceinline__ bool mixed_item(const StripJob &jb, int item, Ring &rg)
 {
     using S = MixedShape<N>;
     static_assert(MixedCfg<N>::WARPS == kMixedWarps, "one CTA shape for every N");
-    return strip_item<N, S::K, S::U, kMixedNST, S::GPC, S::S>(jb, item, rg);
+    return strip_item<N, S::K, S::U, kMixedNST, S::GPC, SPLIT>(jb, item, rg);
 }
 
 __global__ void __launch_bounds__(32 * kMixedWarps) conv_mixed_kernel(StripJobs js, int *counter)
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(32 * kMixedWarps) conv_mixed_kernel(StripJobs 
         bool r = false;
         switch (jb.N) {  // CTA-uniform
         case 8: r = mixed_item<8>(jb, it, rg); break;
-        case 16: r = mixed_item<16>(jb, it, rg); break;
+        case 16: r = jb.S == 2 ? mixed_item<16, 2>(jb, it, rg) : mixed_item<16, 4>(jb, it, rg); break;
         case 24: r = mixed_item<24>(jb, it, rg); break;
         case 32: r = mixed_item<32>(jb, it, rg); break;
         default: break;
@@ -135,13 +135,15 @@ int launch_strip_mixed(const Handle *const *hds, const int *ncells, int n, cudaS
     for (int k = 0; k < n; ++k) {
         const Handle &hd = *hds[idx[k]];
         const int N = hd.g.N, gpc = groups_per_cta(N);
-        const int parts = N == 16 ? 4 : 1;
-        if (parts != conv_split(hd)) return set_error(CS_ENOTSUP, "mixed convolution: split differs from the handle's");
+        const int parts = conv_split(hd);  // 2 or 4 at N = 16 (the handle's choice), else 1
+        if (N == 16 ? (parts != 2 && parts != 4) : parts != 1)
+            return set_error(CS_ENOTSUP, "mixed convolution: split differs from the handle's");
         const int nblocks = strip_mixed_cells(hd, ncells[idx[k]]) / kGroup / gpc;
         js.j[k] = StripJob{(const float *)hd.ghat, hd.pencil_tile0, hd.pencil_order, (const float2 *)hd.F,
                            (float2 *)hd.Qh, (float2 *)hd.Qh2, (float2 *)hd.Qh3, (float2 *)hd.Qh4, hd.done, hd.err,
                            (float)(hd.g.dz * hd.g.dz * hd.g.dz),
                            nblocks, N, (int)first};
+        js.j[k].S = parts;
         first += (long long)N * N * nblocks * parts;
     }
     if (first > 0x7fffffff) return set_error(CS_EINVAL, "mixed convolution: too many items");

@@ -10,10 +10,12 @@
 // consecutive ranges of that pencil's tiles: part p sums tiles
 // ceil(pT/S) .. ceil((p+1)T/S)-1 into its own partial sum (Qh, Qh2, Qh3,
 // Qh4); the last range of a (pencil, block) to finish adds the partial sums
-// into Qh in that fixed order.  At N = 16 S = 4: smaller items shorten the
-// tail of a launch over few cells (128 cells: 8 % less time than S = 2);
-// the split depends only on N and the precision, so a cell's result never
-// depends on how many cells share the launch.  The pencil's k3 range is cut
+// into Qh in that fixed order.  At N = 16 S is 4 or 2, a handle's tuning
+// choice (CS_TUNE_SPLIT): smaller items shorten the tail of a launch over
+// few cells (128 cells: 3 % less time with 4), fewer save the combining at
+// many (2048 cells: 5 % less with 2).  The split belongs to the handle, not
+// to a call, so a cell's result never depends on how many cells share the
+// launch.  The pencil's k3 range is cut
 // into N/K strips of K outputs; warp (group g, strip w) keeps only its K
 // complex accumulators (plus a compensation pair) in registers.  CTAs are
 // persistent and take items from an atomic counter, heaviest pencils first.
@@ -48,9 +50,15 @@
 
 namespace cs {
 
-int conv_split(const Handle &hd)
+int conv_split_max(const Handle &hd)
 {
     return (hd.precision == CS_FP32 && hd.g.layout == LAYOUT_STRIP && hd.g.N == 16) ? 4 : 1;
+}
+
+int conv_split(const Handle &hd)
+{
+    if (conv_split_max(hd) == 1) return 1;
+    return hd.tune_split == 2 ? 2 : 4;
 }
 
 bool strip_uses_radius(const Handle &hd)

@@ -174,9 +174,9 @@ size_t workspace_bytes(const Handle &hd, int ncells, int geo_cells, size_t *offs
     if (offs) offs[7] = o;
     o += sp;
     if (offs) offs[8] = o;
-    if (conv_split(hd) > 3) o += sb;  // Qh4
+    if (conv_split_max(hd) > 3) o += sb;  // Qh4
     if (offs) offs[9] = o;
-    if (conv_split(hd) > 1) o += align_up(sizeof(int) * (size_t)hd.g.N * hd.g.N * ngroups_of(ncells), 256);
+    if (conv_split_max(hd) > 1) o += align_up(sizeof(int) * (size_t)hd.g.N * hd.g.N * ngroups_of(ncells), 256);
     return o;
 }
 
@@ -221,8 +221,8 @@ int ensure_workspace(Handle &hd, int ncells, int geo_cells = 0)
     hd.Qh = b + offs[1];
     hd.Qh2 = b + offs[2];  // X and Y: unused by the whole-cell transforms, the only consumers of a split
     hd.Qh3 = b + offs[3];
-    hd.Qh4 = conv_split(hd) > 3 ? b + offs[8] : nullptr;
-    hd.done = conv_split(hd) > 1 ? (int *)(b + offs[9]) : nullptr;
+    hd.Qh4 = conv_split_max(hd) > 3 ? b + offs[8] : nullptr;
+    hd.done = conv_split_max(hd) > 1 ? (int *)(b + offs[9]) : nullptr;
     hd.X = b + offs[2];
     hd.Y = b + offs[3];
     hd.Qt = (double *)(b + offs[4]);
@@ -878,6 +878,10 @@ int cs_tune(cs_handle_t h, int param, int value)
         if (value < 0 || value > 64) return set_error(CS_EINVAL, "CTAs per SM must be in 0..64");
         hd.tune_ctas = value;
         break;
+    case CS_TUNE_SPLIT:
+        if (value != 0 && value != 2 && value != 4) return set_error(CS_EINVAL, "split must be 0, 2 or 4");
+        hd.tune_split = value;
+        break;
     case CS_TUNE_WEIGHTS:
         if (value < 0 || value > 2) return set_error(CS_EINVAL, "weights must be 0, 1 (stored) or 2 (radius tables)");
         if (value == 1 && !hd.has_table) return set_error(CS_ENOTSUP, "the handle was built without the stored table");
@@ -899,6 +903,7 @@ int cs_tune_get(cs_handle_t h, int param, int *value)
     case CS_TUNE_GROUPS_PER_CTA: *value = h->h.tune_gpc; return CS_OK;
     case CS_TUNE_CTAS_PER_SM: *value = h->h.tune_ctas; return CS_OK;
     case CS_TUNE_WEIGHTS: *value = h->h.tune_weights; return CS_OK;
+    case CS_TUNE_SPLIT: *value = h->h.tune_split; return CS_OK;
     default: return set_error(CS_EINVAL, "unknown tuning parameter");
     }
 }
@@ -924,13 +929,17 @@ int cs_autotune(cs_handle_t h, int ncells, cudaStream_t s, double *ms)
     if (hd.has_table) modes.push_back(1);
     if (hd.radA) modes.push_back(2);
     if (modes.empty()) modes.push_back(0);
+    // and the tile split where the handle has one (float, N = 16)
+    std::vector<int> splits = conv_split_max(hd) > 1 ? std::vector<int>{4, 2} : std::vector<int>{0};
+    const size_t nc = sizeof(cand) / sizeof(cand[0]);
     double best = 1e300;
-    int bg = 0, bc = 0, bw = 0;
-    const int keep_g = hd.tune_gpc, keep_c = hd.tune_ctas, keep_w = hd.tune_weights;
+    int bg = 0, bc = 0, bw = 0, bs = 0;
+    const int keep_g = hd.tune_gpc, keep_c = hd.tune_ctas, keep_w = hd.tune_weights, keep_s = hd.tune_split;
     int rc = CS_OK;
-    for (size_t ci = 0; ci < modes.size() * (sizeof(cand) / sizeof(cand[0])) && rc == CS_OK; ++ci) {
-        const auto &c = cand[ci % (sizeof(cand) / sizeof(cand[0]))];
-        hd.tune_weights = modes[ci / (sizeof(cand) / sizeof(cand[0]))];
+    for (size_t ci = 0; ci < splits.size() * modes.size() * nc && rc == CS_OK; ++ci) {
+        const auto &c = cand[ci % nc];
+        hd.tune_weights = modes[(ci / nc) % modes.size()];
+        hd.tune_split = splits[ci / (nc * modes.size())];
         hd.tune_gpc = c[0];
         hd.tune_ctas = c[1];
         if ((rc = launch_convolve(hd, ncells, s)) != CS_OK) break;  // warm-up
@@ -950,6 +959,7 @@ int cs_autotune(cs_handle_t h, int ncells, cudaStream_t s, double *ms)
             bg = c[0];
             bc = c[1];
             bw = hd.tune_weights;
+            bs = hd.tune_split;
         }
     }
     cudaEventDestroy(a);
@@ -958,11 +968,13 @@ int cs_autotune(cs_handle_t h, int ncells, cudaStream_t s, double *ms)
         hd.tune_gpc = keep_g;
         hd.tune_ctas = keep_c;
         hd.tune_weights = keep_w;
+        hd.tune_split = keep_s;
         return rc;
     }
     hd.tune_gpc = bg;
     hd.tune_ctas = bc;
     hd.tune_weights = bw;
+    hd.tune_split = bs;
     drop_graphs(hd);
     drop_batch_graphs_of(h);
     if (ms) *ms = best;

@@ -75,6 +75,9 @@ Handle view_of(const Handle &hd)
     v.rad_bb = hd.rad_bb;
     v.has_table = hd.has_table;
     v.tune_weights = hd.tune_weights;
+    v.tune_split = hd.tune_split;
+    v.tune_gpc = hd.tune_gpc;
+    v.tune_ctas = hd.tune_ctas;
     v.err = hd.err;
     v.counter = hd.counter;
     v.tw64 = hd.tw64;
@@ -113,7 +116,7 @@ extern "C" int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, do
     // third and fourth, and the split's counters); inverse Qh -> X', Y'
     // (reusing Y's and F's space); then the per-block partial moments of the
     // projection
-    const int split = conv_split(hd);
+    const int split = conv_split_max(hd);
     const int nbuf = 3 + (split > 2 ? split - 2 : 0);
     const size_t part_bytes = (sizeof(double) * 5 * (size_t)ncells * conserve_parts(hd.g.M) + 255) / 256 * 256;
     const size_t done_bytes =

@@ -332,6 +332,7 @@ struct StripJob {
     int *err;                      // the handle's status word
     float omega;
     int nblocks, N, first;
+    int S = 1;  // tile ranges per pencil (the mixed kernel dispatches on it at N = 16)
     // radius tables (launches that rebuild the weight tiles): A, B, the tile
     // entry map and the row length of A
     const float *radA = nullptr, *radB = nullptr;
@@ -774,7 +775,9 @@ int launch_strip_mode(const Handle &hd, int ncells, cudaStream_t s)
 {
     switch (hd.g.N) {
     case 8: return launch_n<8, 4, 4, 4, 4, 1, RAD>(hd, ncells, s);
-    case 16: return launch_n<16, 8, 8, 3, 3, 4, RAD>(hd, ncells, s);
+    case 16:
+        return conv_split(hd) == 2 ? launch_n<16, 8, 8, 3, 3, 2, RAD>(hd, ncells, s)
+                                   : launch_n<16, 8, 8, 3, 3, 4, RAD>(hd, ncells, s);
     case 24: return launch_n<24, 12, 4, 3, 2, 1, RAD>(hd, ncells, s);
     case 32: return launch_n<32, 8, 8, 3, 3, 1, RAD>(hd, ncells, s);
     case 48: return launch_n<48, 8, 8, 3, 2, 1, RAD>(hd, ncells, s);

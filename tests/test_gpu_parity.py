@@ -305,6 +305,7 @@ def test_collide_batched_matches_individual_calls(cs):
     specs = [(16, 0.0, 40, "fp32"), (16, 1.0, 24, "fp32"), (24, 0.0, 8, "fp32"), (24, 1.0, 33, "fp32"),
              (8, 1.0, 1, "fp32"), (32, 1.0, 3, "fp32"), (12, 1.0, 5, "fp32"), (8, 0.0, 7, "fp64")]
     hs = [cs.Handle(N, L, lam, prec) for N, lam, _, prec in specs]
+    cs.cs_tune(hs[1].ptr, cs.CS_TUNE_SPLIT, 2)  # the two N = 16 entries split their pencils differently
     fs = [dev(I.random_mixture_cells(N, L, n, first_id=600 + 50 * i)) for i, (N, _, n, _) in enumerate(specs)]
     qs = [torch.empty_like(f) for f in fs]
     refs, alone = [], 0
@@ -369,6 +370,28 @@ def test_relax_batched_matches_individual_calls(cs):
     cs.cs_status(hs[0].ptr)
     for h in hs:
         h.close()
+
+
+def test_tile_split_choices_agree(cs, orc):
+    """N = 16 in float: 2 or 4 tile ranges per pencil add the same terms in
+    a different grouping; both match the oracle and each other to float
+    rounding, and each is the same for any number of cells in the call."""
+    N = 16
+    f = I.random_mixture_cells(N, L, 40, first_id=950)
+    h = cs.Handle(N, L, 1.0, "fp32")
+    got = {}
+    for split in (2, 4):
+        cs.cs_tune(h.ptr, cs.CS_TUNE_SPLIT, split)
+        assert cs.cs_tune_get(h.ptr, cs.CS_TUNE_SPLIT) == split
+        got[split] = host(h.collide(dev(f)))
+        assert np.array_equal(host(h.collide(dev(f[:3]))), got[split][:3])  # fewer cells, same sums
+    ref = orc.collide(f[:4], N, L, 1.0)
+    for split in (2, 4):
+        assert rel(got[split][:4], ref) < 1e-5
+    assert rel(got[2], got[4]) < 1e-6
+    with pytest.raises(cs.CSError):
+        cs.cs_tune(h.ptr, cs.CS_TUNE_SPLIT, 3)
+    h.close()
 
 
 def test_launch_choices_give_identical_results(cs):
