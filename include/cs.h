@@ -349,12 +349,14 @@ int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, double eps, d
                        cudaStream_t stream);
 
 /* Launch choices of the convolution (autotuner parameters).
- *   CS_TUNE_SPLIT           float handles at N = 16: 2 or 4 tile ranges per
- *                           output pencil (4 shortens the tail of a launch
- *                           over few cells); the ranges' partial sums are
- *                           added in a fixed order, so a choice changes the
- *                           rounding of the sum, not its terms, and holds
- *                           for every call on the handle
+ *   CS_TUNE_SPLIT           float handles at N = 16: 2 (default) or 4 tile
+ *                           ranges per output pencil (4 shortens the tail of
+ *                           a launch over few cells); the ranges' partial
+ *                           sums are added in a fixed order, so a choice
+ *                           changes the rounding of the sum, not its terms,
+ *                           and holds for every call on the handle; handles
+ *                           split 4 ways stay out of cs_collide_batched's
+ *                           shared convolution launch
  *   CS_TUNE_GROUPS_PER_CTA  1 or 2 groups of 32 cells share each weight tile
  *                           in shared memory (2 needs an even group count)
  *   CS_TUNE_CTAS_PER_SM     resident CTAs per SM of the persistent kernel

@@ -58,7 +58,7 @@ int conv_split_max(const Handle &hd)
 int conv_split(const Handle &hd)
 {
     if (conv_split_max(hd) == 1) return 1;
-    return hd.tune_split == 2 ? 2 : 4;
+    return hd.tune_split == 4 ? 4 : 2;
 }
 
 bool strip_uses_radius(const Handle &hd)

@@ -154,7 +154,7 @@ struct Handle {
     int tune_gpc = 0;     // cell groups per CTA of the strip kernel (1 or 2)
     int tune_ctas = 0;    // resident CTAs per SM of the persistent strip kernel
     int tune_weights = 0; // 1 = stored tiles, 2 = tiles rebuilt from the radius tables
-    int tune_split = 0;   // tile ranges per pencil at N = 16 (2 or 4; 0 = 4)
+    int tune_split = 0;   // tile ranges per pencil at N = 16 (2 or 4; 0 = 2)
     // stage timing (cs_profile)
     bool prof = false;
     struct Rec {
@@ -238,7 +238,7 @@ int launch_inverse_project(const Handle &hd, int ncells, double eps, int project
 int launch_convolve(const Handle &hd, int ncells, cudaStream_t s);  // hd.F -> hd.Qh (and hd.Qh2)
 // into how many tile ranges the convolution of this handle splits each
 // pencil: 2 or 4 for float strip handles at N = 16 (CS_TUNE_SPLIT, default
-// 4), else 1; the last range to finish adds the partial sums into hd.Qh in
+// 2), else 1; the last range to finish adds the partial sums into hd.Qh in
 // range order, so every consumer reads one buffer.  The split fixes the
 // summation order, so it is a property of the handle, never of a call.
 int conv_split(const Handle &hd);

@@ -300,12 +300,12 @@ def test_graph_replay_matches_direct_launches(cs, prec):
 def test_collide_batched_matches_individual_calls(cs):
     """Uneven N and lambda in one replayed graph: every entry equals cs_collide
     bit for bit.  The float strip entries (N = 8, 16, 24, 32; group counts odd
-    and even) share one persistent convolution launch; the N = 12 and double
-    entries run whole on their own branches."""
+    and even) share one persistent convolution launch; the N = 12, the double
+    and the four-way split N = 16 entries run whole on their own branches."""
     specs = [(16, 0.0, 40, "fp32"), (16, 1.0, 24, "fp32"), (24, 0.0, 8, "fp32"), (24, 1.0, 33, "fp32"),
              (8, 1.0, 1, "fp32"), (32, 1.0, 3, "fp32"), (12, 1.0, 5, "fp32"), (8, 0.0, 7, "fp64")]
     hs = [cs.Handle(N, L, lam, prec) for N, lam, _, prec in specs]
-    cs.cs_tune(hs[1].ptr, cs.CS_TUNE_SPLIT, 2)  # the two N = 16 entries split their pencils differently
+    cs.cs_tune(hs[1].ptr, cs.CS_TUNE_SPLIT, 4)  # split four ways: runs outside the shared launch
     fs = [dev(I.random_mixture_cells(N, L, n, first_id=600 + 50 * i)) for i, (N, _, n, _) in enumerate(specs)]
     qs = [torch.empty_like(f) for f in fs]
     refs, alone = [], 0
@@ -321,8 +321,8 @@ def test_collide_batched_matches_individual_calls(cs):
             q.fill_(float("nan"))
         cs.cs_launch_count(reset=True)
         cs.cs_collide_batched(entries)
-        # six strip convolutions became one launch
-        assert cs.cs_launch_count(reset=True) == alone - 5
+        # five strip convolutions became one launch
+        assert cs.cs_launch_count(reset=True) == alone - 4
         for q, r in zip(qs, refs):
             assert np.array_equal(host(q), r)
     # a launch choice changed after the capture holds at the next call: entry 0
@@ -332,7 +332,7 @@ def test_collide_batched_matches_individual_calls(cs):
     cs.cs_collide(hs[0].ptr, fs[0], specs[0][2], 1.0, q0, 1)
     cs.cs_launch_count(reset=True)
     cs.cs_collide_batched(entries)
-    assert cs.cs_launch_count(reset=True) == alone - 4
+    assert cs.cs_launch_count(reset=True) == alone - 3
     assert np.array_equal(host(qs[0]), host(q0))
     for q, r in zip(qs[1:], refs[1:]):
         assert np.array_equal(host(q), r)
