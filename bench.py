@@ -436,7 +436,8 @@ def run_ours(args):
                      "ops_per_launch": 6.0 * pair_cells, "tflops": achieved,
                      "flop_frac": achieved / peak_tflops, "autotuned_ms": tuned_ms,
                      "launch": {"groups_per_cta": api.cs_tune_get(h32.ptr, api.CS_TUNE_GROUPS_PER_CTA),
-                                "ctas_per_sm": api.cs_tune_get(h32.ptr, api.CS_TUNE_CTAS_PER_SM)},
+                                "ctas_per_sm": api.cs_tune_get(h32.ptr, api.CS_TUNE_CTAS_PER_SM),
+                                "tile_split": api.cs_tune_get(h32.ptr, api.CS_TUNE_SPLIT)},
                      "probe": probe},
         "stage_ms_per_step": step_stage_ms,
         "weights": weights,
