@@ -48,7 +48,7 @@ WORKLOADS = {
 MAX_SM_MHZ = 2070.0
 # DRAM bytes (read + write) per convolution launch from ncu captures of the
 # current kernel (profiles/), keyed by (N, cells); None where not captured
-TRAFFIC = {(16, 128): 18411008, (32, 256): 2991451648 + 68178176}
+TRAFFIC = {(16, 128): 18415616, (32, 256): 3028994304 + 67706112}
 SMS = 152
 FP32_LANES = 128
 
@@ -223,7 +223,13 @@ def run_ours(args):
 
     h32 = api.Handle(N, L_BOX, LAM, "fp32")
     h32.reserve(ncells)
-    tuned_ms = api.cs_autotune(h32.ptr, ncells)  # launch shape of the convolution (outside the timed region)
+    if args.tune:  # fixed launch choices (profiling runs: timings under a profiler would mislead the autotuner)
+        for param, v in zip((api.CS_TUNE_GROUPS_PER_CTA, api.CS_TUNE_CTAS_PER_SM, api.CS_TUNE_SPLIT,
+                             api.CS_TUNE_WEIGHTS), (int(x) for x in args.tune.split(","))):
+            api.cs_tune(h32.ptr, param, v)
+        tuned_ms = None
+    else:
+        tuned_ms = api.cs_autotune(h32.ptr, ncells)  # launch shape of the convolution (outside the timed region)
     f0, fd, dxd, fard = make_state(api, inputs, torch, N, ncells, device)
 
     # warm-up + timed region (barrier and synchronize on both sides, max over ranks)
@@ -619,6 +625,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="wall16")
     ap.add_argument("--cells", type=int, default=0, help="override the workload's cell count (profiling runs)")
+    ap.add_argument("--tune", default="", help="fixed launch choices instead of the autotuner: "
+                    "groups_per_cta,ctas_per_sm,tile_split,weights (profiling runs)")
     ap.add_argument("--skip-n32", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true", help="omit the double-precision comparison")
