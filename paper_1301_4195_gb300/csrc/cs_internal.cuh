@@ -218,7 +218,7 @@ int sample_weights(Handle &hd, const int *km_host, int n, double *out_host);
 
 // ---- transform.cu
 int launch_forward(const Handle &hd, const double *f, int ncells, cudaStream_t s);   // f -> hd.F
-// hd.Qh (+ qh2, the second partial sum of a split convolution, if not NULL) -> Qt
+// hd.Qh -> Qt
 int launch_inverse(const Handle &hd, int ncells, double scale_eps, double *Qt, cudaStream_t s);
 // grouped spectral src -> [ncells][N^3][2] doubles
 int launch_spectral_to_natural(const Handle &hd, const void *src, int ncells, double *dst, cudaStream_t s);

@@ -147,7 +147,7 @@ extern "C" int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, do
     fwd.Y = B;
     fwd.F = C;
     fwd.Qh = A;
-    fwd.Qh2 = B;  // a split convolution's second partial sum (Y is free again after the forward passes)
+    fwd.Qh2 = B;  // a split convolution's further partial sums (Y is free again after the forward passes)
     fwd.Qh3 = nbuf > 3 ? D : nullptr;
     fwd.Qh4 = nbuf > 4 ? E : nullptr;
     fwd.done = split > 1 ? (int *)(C + (nbuf - 2) * buffer_bytes(hd, ncells) + part_bytes) : nullptr;
