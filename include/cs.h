@@ -7,8 +7,10 @@
  * for the Boltzmann equation" (arXiv:1301.4195): per spatial cell a forward
  * transform of f on an N^3 velocity grid, the weighted Fourier convolution
  * with the precomputed weights Ghat, an inverse transform and the
- * conservation projection; plus Heun time stepping and a 1-D finite-volume
- * transport step combined by Strang splitting.
+ * conservation projection; plus Heun time stepping and a finite-volume
+ * transport step (one space dimension, or two with a periodic second one)
+ * combined by Strang splitting, sharded transport stages for domain
+ * decomposition, and batched calls over handles of different N.
  *
  * Conventions shared by every call
  *   - Velocity grid (Sec. 3.1, "meshpoints"): N even, 4 <= N <= 64, the cube
@@ -29,8 +31,9 @@
  *     a message for cs_last_error().  Arguments are checked on the host
  *     before anything is enqueued; no call traps, asserts or aborts.
  *   - No call allocates device memory except cs_weights_build (the weight
- *     table) and cs_reserve / the first call that needs more workspace than
- *     the handle holds.  Call cs_reserve before capturing a CUDA graph.
+ *     table), cs_reserve / the first call that needs more workspace than
+ *     the handle holds, and cs_fma_probe (one word, freed before it
+ *     returns).  Call cs_reserve before capturing a CUDA graph.
  *   - A handle is not thread-safe: calls on one handle must be serialised by
  *     the caller (one stream, or external synchronisation).
  */
