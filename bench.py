@@ -305,6 +305,24 @@ def run_ours(args):
              "dfma_tlane_ops": api.cs_fma_probe(2) / 1e12}
     probe["frac_of_best_fp32_probe"] = achieved_ops / max(probe["ffma_tlane_ops"], probe["ffma2_tlane_ops"])
 
+    # the operator alone (t_Q = forward transform + convolution + inverse +
+    # projection, one cs_collide on the workload's state), graph-free direct launches
+    qd = torch.empty_like(fd)
+    for _ in range(3):
+        api.cs_collide(h32.ptr, fd, ncells, 1.0, qd, 1)
+    torch.cuda.synchronize()
+    ta, tb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nq = 20
+    ta.record()
+    for _ in range(nq):
+        api.cs_collide(h32.ptr, fd, ncells, 1.0, qd, 1)
+    tb.record()
+    tb.synchronize()
+    tq = ta.elapsed_time(tb) / nq
+    q_eval = {"ms_per_evaluation": tq, "value": world * ncells * N ** 6 / (tq * 1e-3), "unit": UNIT,
+              "note": "one collision evaluation Q(f) of the workload's cells (t_Q: transforms, convolution, "
+                      "projection), L2 not flushed between evaluations"}
+
     # store versus recompute: the convolution with stored weight tiles and with
     # tiles rebuilt from the radius tables (the autotuner keeps the faster)
     weights = {"chosen": WEIGHT_MODES[api.cs_tune_get(h32.ptr, api.CS_TUNE_WEIGHTS)],
@@ -446,6 +464,7 @@ def run_ours(args):
                                 "tile_split": api.cs_tune_get(h32.ptr, api.CS_TUNE_SPLIT)},
                      "probe": probe},
         "stage_ms_per_step": step_stage_ms,
+        "q_eval": q_eval,
         "weights": weights,
         "fp64": fp64,
         "speedup_vs_fp64": fp64["ms_per_step"] / ms_step if fp64 else None,
