@@ -270,11 +270,11 @@ int timed_transport(Handle &hd, const double *fin, int ncells, const cs_domain &
 // N <= 24) the last three steps are one launch, timed as the inverse stage.
 // collide_back: the steps after the convolution (hd.Qh -> out)
 int collide_back(Handle &hd, int ncells, double eps, int project, double a, const double *x, double b,
-                 const double *y, double c, double *out, cudaStream_t s)
+                 const double *y, double c, double *out, cudaStream_t s, bool fwd_next = false)
 {
     if (fused_available(hd)) {
         StageTimer t(hd, CS_K_INVERSE, s);
-        return launch_inverse_project(hd, ncells, eps, project, a, x, b, y, c, out, s);
+        return launch_inverse_project(hd, ncells, eps, project, a, x, b, y, c, out, s, fwd_next ? hd.F : nullptr);
     }
     const bool direct = (x == nullptr && y == nullptr && c == 1.0);
     double *qt = direct ? out : hd.Qt;
@@ -284,22 +284,28 @@ int collide_back(Handle &hd, int ncells, double eps, int project, double a, cons
     return timed_conserve(hd, qt, ncells, project, a, x, b, y, c, out, nullptr, s);
 }
 
+// fwd_next: the inverse launch also transforms out forward into hd.F (the
+// next evaluation's input); have_F: hd.F already holds f's transform
 int collide_combine(Handle &hd, const double *f, int ncells, double eps, int project, double a, const double *x,
-                    double b, const double *y, double c, double *out, cudaStream_t s)
+                    double b, const double *y, double c, double *out, cudaStream_t s, bool fwd_next = false,
+                    bool have_F = false)
 {
-    int rc = timed_forward(hd, f, ncells, s);
+    int rc = have_F ? CS_OK : timed_forward(hd, f, ncells, s);
     if (rc) return rc;
     rc = timed_convolve(hd, ncells, s);
     if (rc) return rc;
-    return collide_back(hd, ncells, eps, project, a, x, b, y, c, out, s);
+    return collide_back(hd, ncells, eps, project, a, x, b, y, c, out, s, fwd_next);
 }
 
 // one Heun step of df/dt = P Qt(f) / eps, in place
+// (with whole-cell kernels the first evaluation's inverse launch also
+// transforms f1 forward, so the second starts at the convolution)
 int heun_collision(Handle &hd, double *f, int ncells, double dt, double eps, cudaStream_t s)
 {
-    int rc = collide_combine(hd, f, ncells, eps, 1, 1.0, f, 0.0, nullptr, dt, hd.f1, s);
+    const bool fuse = fused_forward_next(hd);
+    int rc = collide_combine(hd, f, ncells, eps, 1, 1.0, f, 0.0, nullptr, dt, hd.f1, s, fuse);
     if (rc) return rc;
-    return collide_combine(hd, hd.f1, ncells, eps, 1, 0.5, f, 0.5, hd.f1, 0.5 * dt, f, s);
+    return collide_combine(hd, hd.f1, ncells, eps, 1, 0.5, f, 0.5, hd.f1, 0.5 * dt, f, s, false, fuse);
 }
 
 // one Heun step of the transport in two space dimensions, f [nx][ny][N^3]
@@ -518,9 +524,13 @@ struct EvalSpec {
     double *out;
 };
 
+// fwd_next / have_F: as in collide_combine, for the entries whose inverse
+// launch can transform forward (fused_forward_next), so each entry runs the
+// same kernels as its own cs_relax.
 int capture_evaluation(const std::vector<Handle *> &hs, const std::vector<int> &cells,
                        const std::vector<EvalSpec> &sp, bool mixed, double eps, int project, cudaStream_t root,
-                       cudaStream_t *br, const std::vector<cudaEvent_t> &ev)
+                       cudaStream_t *br, const std::vector<cudaEvent_t> &ev, bool fwd_next = false,
+                       bool have_F = false)
 {
     const int n = (int)hs.size();
     auto in_mix = [&](int i) { return mixed && cells[i] > 0 && strip_mixable(*hs[i]); };
@@ -529,12 +539,16 @@ int capture_evaluation(const std::vector<Handle *> &hs, const std::vector<int> &
     for (int i = 0; i < n && rc == CS_OK; ++i) {
         cudaStreamWaitEvent(br[i], ev[0], 0);
         Handle &hd = *hs[i];
-        if (in_mix(i))
-            rc = fused_available(hd) ? launch_forward_fused(hd, sp[i].src, cells[i], br[i], strip_mixed_cells(hd, cells[i]))
-                                     : launch_forward(hd, sp[i].src, cells[i], br[i]);
-        else if (cells[i] > 0)
+        const bool ffn = fused_forward_next(hd);
+        if (in_mix(i)) {
+            if (!(have_F && ffn))
+                rc = fused_available(hd)
+                         ? launch_forward_fused(hd, sp[i].src, cells[i], br[i], strip_mixed_cells(hd, cells[i]))
+                         : launch_forward(hd, sp[i].src, cells[i], br[i]);
+        } else if (cells[i] > 0) {
             rc = collide_combine(hd, sp[i].src, cells[i], eps, project, sp[i].a, sp[i].x, sp[i].b, sp[i].y, sp[i].c,
-                                 sp[i].out, br[i]);
+                                 sp[i].out, br[i], fwd_next && ffn, have_F && ffn);
+        }
         cudaEventRecord(ev[i + 1], br[i]);
         cudaStreamWaitEvent(root, ev[i + 1], 0);
     }
@@ -552,7 +566,7 @@ int capture_evaluation(const std::vector<Handle *> &hs, const std::vector<int> &
         if (!in_mix(i)) continue;
         cudaStreamWaitEvent(br[i], ev[n + 1], 0);
         rc = collide_back(*hs[i], cells[i], eps, project, sp[i].a, sp[i].x, sp[i].b, sp[i].y, sp[i].c, sp[i].out,
-                          br[i]);
+                          br[i], fwd_next && fused_forward_next(*hs[i]));
         cudaEventRecord(ev[n + 2 + i], br[i]);
         cudaStreamWaitEvent(root, ev[n + 2 + i], 0);
     }
@@ -655,11 +669,12 @@ int batched_call(int kind, const std::vector<cs_handle_t> &handles, const std::v
                 std::vector<cudaEvent_t> ev1(ev.begin(), ev.begin() + (2 * n + 2));
                 std::vector<cudaEvent_t> ev2(ev.begin() + (2 * n + 2), ev.end());
                 for (int i = 0; i < n; ++i) sp[i] = EvalSpec{f[i], 1.0, f[i], 0.0, nullptr, dt, hs[i]->f1};
-                rc = capture_evaluation(hs, ncells, sp, mixed, eps, project, root, g_batch_streams + 1, ev1);
+                rc = capture_evaluation(hs, ncells, sp, mixed, eps, project, root, g_batch_streams + 1, ev1, true);
                 for (int i = 0; i < n; ++i)
                     sp[i] = EvalSpec{hs[i]->f1, 0.5, f[i], 0.5, hs[i]->f1, 0.5 * dt, const_cast<double *>(f[i])};
                 if (rc == CS_OK)
-                    rc = capture_evaluation(hs, ncells, sp, mixed, eps, project, root, g_batch_streams + 1, ev2);
+                    rc = capture_evaluation(hs, ncells, sp, mixed, eps, project, root, g_batch_streams + 1, ev2,
+                                            false, true);
             }
             e = cudaStreamEndCapture(root, &graph);
         }

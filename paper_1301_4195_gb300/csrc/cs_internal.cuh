@@ -231,8 +231,13 @@ bool fused_available(const Handle &hd);
 int launch_forward_fused(const Handle &hd, const double *f, int ncells, cudaStream_t s, int grid_cells = 0);
 // out = a x + b y + P(c Qt), Qt the inverse transform of hd.Qh (+ qh2 if not
 // NULL), P the projection if project (else the identity)
+// With fnext (not NULL; only where fused_forward_next) the same launch then
+// transforms `out` forward into fnext, in the grouped layout the convolution
+// reads: the forward transform of a Heun step's second evaluation.
 int launch_inverse_project(const Handle &hd, int ncells, double eps, int project, double a, const double *x,
-                           double b, const double *y, double c, double *out, cudaStream_t s);
+                           double b, const double *y, double c, double *out, cudaStream_t s,
+                           void *fnext = nullptr);
+bool fused_forward_next(const Handle &hd);  // one block per cell: float, N in {8, 12, 16, 24}
 
 // ---- convolve.cu, conv_strip.cu
 int launch_convolve(const Handle &hd, int ncells, cudaStream_t s);  // hd.F -> hd.Qh (and hd.Qh2)

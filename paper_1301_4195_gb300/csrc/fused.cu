@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kThreads<N, CL>) forward_fused_kernel(const do
 template <int N, int CL>
 __global__ void __launch_bounds__(kThreads<N, CL>) inverse_project_kernel(
     const float2 *__restrict__ Qh, float cic, double dv, int project, Proj5 pj, double a, const double *x, double b,
-    const double *y, double *out)
+    const double *y, double *out, float2 *__restrict__ Fnext, float cf)
 {
     constexpr int M = N * N * N, P = N + 1, LINES = kLines<N, CL>, PL = kPL<N, CL>, PTS = kPts<N, CL>, H = N / 2;
     constexpr int NT = kThreads<N, CL>, NW = NT / 32, PER = kPer<N, CL>, CHUNK = kChunk<N, CL>;
@@ -414,6 +414,27 @@ __global__ void __launch_bounds__(kThreads<N, CL>) inverse_project_kernel(
             if (x) o = fma(a, xr[r], o);
             if (y) o = fma(b, yr[r], o);
             out[base + j] = o;
+            // the slot just read, reused for the forward transform of out (same thread)
+            if (Fnext) X[jl * P + j3] = make_float2((float)o, 0.f);
+        }
+    }
+    if constexpr (CL == 1) {
+        // the forward transform of out, as forward_fused_kernel computes it from
+        // the same values (the next Heun evaluation's input; padding lanes of
+        // the last group keep the zeros the previous forward wrote)
+        if (Fnext) {
+            __syncthreads();
+            if (l < LINES) line_transform<N, false>(X, l * P, 1, 1.f);  // axis 3
+            __syncthreads();
+            if (l < LINES) line_transform<N, false>(X, (l / N) * N * P + l % N, P, 1.f);  // axis 2
+            __syncthreads();
+            if (l < LINES) line_transform<N, false>(X, (l / N) * P + l % N, N * P, cf);  // axis 1
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < PER; ++r) {
+                const int k = r * NT + tid;
+                if (k < PTS) Fnext[((size_t)g * M + k) * kGroup + lane] = X[(k / N) * P + k % N];
+            }
         }
     }
 }
@@ -470,12 +491,14 @@ int forward_n(const Handle &hd, const double *f, int ncells, int grid_cells, cud
 
 template <int N, int CL>
 int inverse_cl(const Handle &hd, int ncells, float cic, int project, const Proj5 &pj, double a, const double *x,
-               double b, const double *y, double *out, cudaStream_t s)
+               double b, const double *y, double *out, void *fnext, cudaStream_t s)
 {
     if (int rc = allow_smem(inverse_project_kernel<N, CL>, fused_smem<N, CL>(), "fused inverse: shared-memory attribute"))
         return rc;
+    const float cf = (float)(pow(2.0 * M_PI, -1.5) * hd.g.dv * hd.g.dv * hd.g.dv);
     cudaError_t e = launch_cells<N, CL>(inverse_project_kernel<N, CL>, (unsigned)ncells, s, (const float2 *)hd.Qh,
-                                        cic, hd.g.dv, project, pj, a, x, b, y, out);
+                                        cic, hd.g.dv, project, pj, a, x, b, y, out,
+                                        CL == 1 ? (float2 *)fnext : (float2 *)nullptr, cf);
     if (e != cudaSuccess) return cuda_error(e, "fused inverse transform launch");
     CS_LAUNCHED(1, s, "inverse transform and projection (fused)");
     return CS_OK;
@@ -483,16 +506,18 @@ int inverse_cl(const Handle &hd, int ncells, float cic, int project, const Proj5
 
 template <int N>
 int inverse_n(const Handle &hd, int ncells, double eps, int project, double a, const double *x, double b,
-              const double *y, double c, double *out, cudaStream_t s)
+              const double *y, double c, double *out, void *fnext, cudaStream_t s)
 {
     Proj5 pj;
     for (int i = 0; i < 25; ++i) pj.ainv[i] = hd.cct_inv[i];
     // the scale of the last inverse pass, times the step factor c
     const float cic = (float)(c * pow(2.0 * M_PI, -1.5) * hd.g.dz * hd.g.dz * hd.g.dz / eps);
-    return inverse_cl<N, kCL<N>>(hd, ncells, cic, project, pj, a, x, b, y, out, s);
+    return inverse_cl<N, kCL<N>>(hd, ncells, cic, project, pj, a, x, b, y, out, fnext, s);
 }
 
 }  // namespace
+
+bool fused_forward_next(const Handle &hd) { return fused_available(hd) && hd.g.N != 32; }
 
 bool fused_available(const Handle &hd)
 {
@@ -513,14 +538,15 @@ int launch_forward_fused(const Handle &hd, const double *f, int ncells, cudaStre
 }
 
 int launch_inverse_project(const Handle &hd, int ncells, double eps, int project, double a, const double *x,
-                           double b, const double *y, double c, double *out, cudaStream_t s)
+                           double b, const double *y, double c, double *out, cudaStream_t s, void *fnext)
 {
+    if (fnext && !fused_forward_next(hd)) return set_error(CS_ENOTSUP, "fused inverse: no forward transform at this N");
     switch (hd.g.N) {
-    case 8: return inverse_n<8>(hd, ncells, eps, project, a, x, b, y, c, out, s);
-    case 12: return inverse_n<12>(hd, ncells, eps, project, a, x, b, y, c, out, s);
-    case 16: return inverse_n<16>(hd, ncells, eps, project, a, x, b, y, c, out, s);
-    case 24: return inverse_n<24>(hd, ncells, eps, project, a, x, b, y, c, out, s);
-    case 32: return inverse_n<32>(hd, ncells, eps, project, a, x, b, y, c, out, s);
+    case 8: return inverse_n<8>(hd, ncells, eps, project, a, x, b, y, c, out, fnext, s);
+    case 12: return inverse_n<12>(hd, ncells, eps, project, a, x, b, y, c, out, fnext, s);
+    case 16: return inverse_n<16>(hd, ncells, eps, project, a, x, b, y, c, out, fnext, s);
+    case 24: return inverse_n<24>(hd, ncells, eps, project, a, x, b, y, c, out, fnext, s);
+    case 32: return inverse_n<32>(hd, ncells, eps, project, a, x, b, y, c, out, fnext, s);
     default: return set_error(CS_ENOTSUP, "fused inverse transform: unsupported N");
     }
 }

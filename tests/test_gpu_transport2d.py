@@ -116,7 +116,7 @@ def test_step2d_graph_replay_matches_direct_launches(cs):
     cs.cs_profile(h.ptr, False)
     cs.cs_profile_read(h.ptr, reset=True)
     assert np.array_equal(host(fa), host(fb))
-    assert replayed == direct == 3 * 11
+    assert replayed == direct == 3 * 10
     cs.cs_status(h.ptr)
     h.close()
 
