@@ -95,6 +95,28 @@ def test_null_handle_is_rejected(libcs):
     assert lib.cs_weights_bytes(16, 0, None) == libcs.CS_EINVAL
 
 
+def test_batched_calls_and_probe_check_arguments_on_the_host(libcs):
+    """Refused before any device work: too many or negative entries, a NULL
+    list, bad eps/dt/nsteps, an unknown probe kind, tuning a NULL handle."""
+    lib = libcs.lib()
+    ent = (libcs.BatchEntry * 17)()
+    rel = (libcs.RelaxEntry * 17)()
+    assert lib.cs_collide_batched(ent, 17, 1.0, 1, None) == libcs.CS_EINVAL
+    assert lib.cs_collide_batched(None, 2, 1.0, 1, None) == libcs.CS_EINVAL
+    assert lib.cs_collide_batched(ent, -1, 1.0, 1, None) == libcs.CS_EINVAL
+    assert lib.cs_collide_batched(ent, 0, 0.0, 1, None) == libcs.CS_EINVAL
+    assert lib.cs_collide_batched(ent, 0, 1.0, 1, None) == libcs.CS_OK  # nothing to do
+    assert lib.cs_relax_batched(rel, 17, 0.01, 1.0, 1, None) == libcs.CS_EINVAL
+    assert lib.cs_relax_batched(rel, 0, float("nan"), 1.0, 1, None) == libcs.CS_EINVAL
+    assert lib.cs_relax_batched(rel, 0, 0.01, 1.0, -1, None) == libcs.CS_EINVAL
+    assert lib.cs_relax_batched(rel, 0, 0.01, 1.0, 5, None) == libcs.CS_OK
+    out = libcs._d()
+    assert lib.cs_fma_probe(3, None, libcs.ctypes.byref(out)) == libcs.CS_EINVAL
+    assert lib.cs_fma_probe(0, None, None) == libcs.CS_EINVAL
+    assert lib.cs_tune(None, libcs.CS_TUNE_SPLIT, 4) == libcs.CS_EINVAL
+    assert lib.cs_last_error().decode()
+
+
 @pytest.mark.parametrize("N", list(range(4, 33, 2)) + [40, 48, 64])
 @pytest.mark.parametrize("prec", [0, 1])
 def test_tile_layout_covers_every_valid_pair_once(libcs, N, prec):
