@@ -128,6 +128,8 @@ int cs_reserve(cs_handle_t h, int ncells);
 /* Device-side status of h: synchronises the device, then returns CS_ETIMEOUT
  * if a bounded wait inside one of h's kernels expired since the last call
  * (the results of that call are invalid; no kernel traps or hangs instead),
+ * else CS_ENONFINITE if the input scan (CS_TUNE_CHECK_INPUT) found a
+ * non-finite value (or, in mode 2, a negative one; the message says which),
  * else CS_OK, and clears the status.  Errors: CS_EINVAL, CS_ECUDA. */
 int cs_status(cs_handle_t h);
 
@@ -367,12 +369,43 @@ int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, double eps, d
  *   CS_TUNE_WEIGHTS         1: read the stored weight tiles; 2: rebuild each
  *                           tile from the radius tables (float strip handles;
  *                           results agree to float rounding of the weights)
+ * Settings of the handle's checks and of its Heun steps (no counterpart in
+ * the paper; failure detection and test plumbing):
+ *   CS_TUNE_WAIT_US         limit of every bounded device-side wait of the
+ *                           convolution, in microseconds (1 .. 10^7; 0 = the
+ *                           default of 2 s).  A wait that runs out makes the
+ *                           kernel record the expiry, wait (at most 0.1 s, a
+ *                           limit this setting does not change) for the copies
+ *                           it issued, and return; cs_status then reports
+ *                           CS_ETIMEOUT
+ *   CS_TUNE_TEST_STALL      1: in every convolution launch of the handle the
+ *                           first CTA issues no copy for its first work item,
+ *                           so its waits run out after CS_TUNE_WAIT_US (the
+ *                           way a test makes the timeout path run without
+ *                           faulting or hanging the GPU); 0 (default): off.
+ *                           The results of such a launch are invalid
+ *   CS_TUNE_CHECK_INPUT     1: every cs_collide, cs_relax, cs_step and
+ *                           cs_step2d call (each step of the latter three)
+ *                           first scans the distribution it is given on the
+ *                           device and records non-finite values; 2: non-finite
+ *                           or negative values; 0 (default): no scan.
+ *                           cs_status then reports CS_ENONFINITE
+ *   CS_TUNE_FORWARD_NEXT    float handles at N <= 24: 1 (default, 0 = 1): the
+ *                           inverse launch of a Heun step's first evaluation
+ *                           also transforms its result forward for the second
+ *                           evaluation; 2: a separate forward launch does it
+ *                           (the same values: a test checks both agree bit for
+ *                           bit)
  * value 0 restores the automatic choice (stored tiles where the handle has
  * them).  Errors: CS_EINVAL, CS_ENOTSUP (a weight mode the handle lacks). */
 #define CS_TUNE_GROUPS_PER_CTA 1
 #define CS_TUNE_CTAS_PER_SM 2
 #define CS_TUNE_WEIGHTS 3
 #define CS_TUNE_SPLIT 4
+#define CS_TUNE_WAIT_US 5
+#define CS_TUNE_TEST_STALL 6
+#define CS_TUNE_CHECK_INPUT 7
+#define CS_TUNE_FORWARD_NEXT 8
 int cs_tune(cs_handle_t h, int param, int value);
 
 /* The current value of a launch choice (0 = automatic).

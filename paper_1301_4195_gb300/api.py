@@ -287,6 +287,10 @@ CS_TUNE_GROUPS_PER_CTA = 1
 CS_TUNE_WEIGHTS = 3
 CS_TUNE_SPLIT = 4
 CS_TUNE_CTAS_PER_SM = 2
+CS_TUNE_WAIT_US = 5        # limit of the convolution's bounded waits, microseconds (0: 2 s)
+CS_TUNE_TEST_STALL = 6     # 1: the first CTA of each convolution launch issues no copy (its waits run out)
+CS_TUNE_CHECK_INPUT = 7    # 1: scan inputs for non-finite values, 2: also for negative ones
+CS_TUNE_FORWARD_NEXT = 8   # 2: a Heun step's second forward transform in a launch of its own
 
 
 def cs_tune(h, param: int, value: int):

@@ -5,6 +5,8 @@
 // reduced with warp shuffles, the 5x5 product is done by one thread, and the
 // correction is applied together with the Runge-Kutta combination of the
 // caller (out = a x + b y + c Q), so a Heun stage costs no extra pass.
+#include <algorithm>
+
 #include "cs_internal.cuh"
 
 namespace cs {
@@ -160,7 +162,37 @@ __global__ void __launch_bounds__(kThreads) moments_kernel(Geom g, const double 
         for (int i = 0; i < 5; ++i) out[5 * (size_t)cell + i] = mom[i];
 }
 
+// The input scan of CS_TUNE_CHECK_INPUT (failure detection, no counterpart
+// in the paper): one pass over the distribution; a warp that meets a
+// non-finite value sets bit 1 of the handle's status word, with `negative`
+// a negative value bit 2.  Grid-stride loop, one atomic per warp at most.
+__global__ void __launch_bounds__(kThreads) input_check_kernel(const double *__restrict__ f, long long count,
+                                                               int negative, int *err)
+{
+    int bits = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double v = f[i];
+        if (!isfinite(v)) bits |= 2;
+        else if (negative && v < 0.0) bits |= 4;
+    }
+    bits = __reduce_or_sync(0xffffffffu, bits);
+    if (bits && (threadIdx.x & 31) == 0) atomicOr(err, bits);
+}
+
 }  // namespace
+
+int launch_input_check(const Handle &hd, const double *f, long long count, cudaStream_t s)
+{
+    if (hd.check_input == 0 || count <= 0) return CS_OK;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, hd.device);
+    const long long want = (count + kThreads - 1) / kThreads;
+    const int blocks = (int)std::min<long long>(want, 4LL * std::max(1, sms));
+    input_check_kernel<<<blocks, kThreads, 0, s>>>(f, count, hd.check_input == 2, hd.err);
+    CS_LAUNCHED(1, s, "input scan");
+    return CS_OK;
+}
 
 int conserve_parts(int M) { return M >= 32768 ? 8 : M >= 4096 ? 4 : 1; }
 

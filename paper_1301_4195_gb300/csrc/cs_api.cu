@@ -903,6 +903,22 @@ int cs_tune(cs_handle_t h, int param, int value)
         if (value == 2 && !hd.radA) return set_error(CS_ENOTSUP, "the handle has no radius tables");
         hd.tune_weights = value;
         break;
+    case CS_TUNE_WAIT_US:
+        if (value < 0 || value > 10000000) return set_error(CS_EINVAL, "wait limit must be 0 .. 10^7 microseconds");
+        hd.wait_ns = 1000ull * (unsigned long long)value;
+        break;
+    case CS_TUNE_TEST_STALL:
+        if (value < 0 || value > 1) return set_error(CS_EINVAL, "test stall must be 0 or 1");
+        hd.test_stall = value;
+        break;
+    case CS_TUNE_CHECK_INPUT:
+        if (value < 0 || value > 2) return set_error(CS_EINVAL, "input check must be 0, 1 or 2");
+        hd.check_input = value;
+        break;
+    case CS_TUNE_FORWARD_NEXT:
+        if (value < 0 || value > 2) return set_error(CS_EINVAL, "forward-next must be 0, 1 or 2");
+        hd.tune_fwd_next = value;
+        break;
     default: return set_error(CS_EINVAL, "unknown tuning parameter");
     }
     drop_graphs(hd);  // captured steps and batches hold the old launch configuration
@@ -919,6 +935,10 @@ int cs_tune_get(cs_handle_t h, int param, int *value)
     case CS_TUNE_CTAS_PER_SM: *value = h->h.tune_ctas; return CS_OK;
     case CS_TUNE_WEIGHTS: *value = h->h.tune_weights; return CS_OK;
     case CS_TUNE_SPLIT: *value = h->h.tune_split; return CS_OK;
+    case CS_TUNE_WAIT_US: *value = (int)(h->h.wait_ns / 1000ull); return CS_OK;
+    case CS_TUNE_TEST_STALL: *value = h->h.test_stall; return CS_OK;
+    case CS_TUNE_CHECK_INPUT: *value = h->h.check_input; return CS_OK;
+    case CS_TUNE_FORWARD_NEXT: *value = h->h.tune_fwd_next; return CS_OK;
     default: return set_error(CS_EINVAL, "unknown tuning parameter");
     }
 }
@@ -1007,7 +1027,9 @@ int cs_status(cs_handle_t h)
     e = cudaMemcpy(&word, hd.err, sizeof(int), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemset(hd.err, 0, sizeof(int));
     if (e != cudaSuccess) return cuda_error(e, "cs_status: read");
-    if (word) return set_error(CS_ETIMEOUT, "a bounded wait inside a kernel expired; its results are invalid");
+    if (word & 1) return set_error(CS_ETIMEOUT, "a bounded wait inside a kernel expired; its results are invalid");
+    if (word & 2) return set_error(CS_ENONFINITE, "the input scan found a non-finite value in a distribution");
+    if (word & 4) return set_error(CS_ENONFINITE, "the input scan found a negative value in a distribution");
     return CS_OK;
 }
 
@@ -1159,6 +1181,7 @@ int cs_collide(cs_handle_t h, const double *f, int ncells, double eps, double *Q
     if ((const char *)f < (const char *)Q + bytes && (const char *)Q < (const char *)f + bytes)
         return set_error(CS_EINVAL, "f and Q overlap");
     if (int rc = ensure_workspace(hd, ncells)) return rc;
+    if (int rc = launch_input_check(hd, f, (long long)ncells * hd.g.M, s)) return rc;
     return collide_combine(hd, f, ncells, eps, conserve ? 1 : 0, 0.0, nullptr, 0.0, nullptr, 1.0, Q, s);
 }
 
@@ -1194,7 +1217,10 @@ int cs_relax(cs_handle_t h, double *f, int ncells, double dt, double eps, int ns
     Handle &hd = h->h;
     if (int rc = ensure_workspace(hd, ncells)) return rc;
     Handle::GraphEntry key{2, f, nullptr, nullptr, ncells, 0.0, {0.0, 0.0, 0.0}, dt, eps, nullptr, 0, 1, 0.0};
-    return run_steps(hd, key, nsteps, s, [&](cudaStream_t st) { return heun_collision(hd, f, ncells, dt, eps, st); });
+    return run_steps(hd, key, nsteps, s, [&](cudaStream_t st) {
+        if (int rc = launch_input_check(hd, f, (long long)ncells * hd.g.M, st)) return rc;
+        return heun_collision(hd, f, ncells, dt, eps, st);
+    });
 }
 
 int cs_transport(cs_handle_t h, double *f, int ncells, const cs_domain *dom, double dt, cudaStream_t s)
@@ -1228,6 +1254,7 @@ int cs_step(cs_handle_t h, double *f, int ncells, const cs_domain *dom, double d
     Handle::GraphEntry key{1, f, d.dx, d.f_far, ncells, d.wall_T, {d.wall_V[0], d.wall_V[1], d.wall_V[2]},
                            dt, eps, nullptr, 0, 1, 0.0};
     return run_steps(hd, key, nsteps, s, [&](cudaStream_t st) {
+        if (int rc = launch_input_check(hd, f, (long long)ncells * hd.g.M, st)) return rc;
         if (int rc = launch_transport_prep(hd, ncells, d, st)) return rc;
         if (int rc = heun_transport(hd, f, ncells, d, 0.5 * dt, st)) return rc;
         if (int rc = heun_collision(hd, f, ncells, dt, eps, st)) return rc;
@@ -1332,6 +1359,7 @@ int cs_step2d(cs_handle_t h, double *f, int nx, const cs_domain2d *dom, double d
     Handle::GraphEntry key{3, f, d.dx, d.f_far, ncells, d.wall_T, {d.wall_V[0], d.wall_V[1], d.wall_V[2]},
                            dt, eps, nullptr, 0, ny, dy};
     return run_steps(hd, key, nsteps, s, [&](cudaStream_t st) {
+        if (int rc = launch_input_check(hd, f, (long long)ncells * hd.g.M, st)) return rc;
         if (int rc = launch_transport_prep(hd, nx, d, st)) return rc;
         if (int rc = heun_transport2d(hd, f, nx, ny, dy, d, 0.5 * dt, st)) return rc;
         if (int rc = heun_collision(hd, f, ncells, dt, eps, st)) return rc;

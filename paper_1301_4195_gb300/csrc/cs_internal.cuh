@@ -155,6 +155,14 @@ struct Handle {
     int tune_ctas = 0;    // resident CTAs per SM of the persistent strip kernel
     int tune_weights = 0; // 1 = stored tiles, 2 = tiles rebuilt from the radius tables
     int tune_split = 0;   // tile ranges per pencil at N = 16 (2 or 4; 0 = 2)
+    // checks (cs_tune): limit of the convolution's bounded waits (ns, 0 =
+    // 2 s), the stall that makes them run out in tests, the input scan
+    // (0 off, 1 non-finite, 2 non-finite or negative), and whether a Heun
+    // step's first inverse launch also transforms forward (2 = no)
+    unsigned long long wait_ns = 0;
+    int test_stall = 0;
+    int check_input = 0;
+    int tune_fwd_next = 0;
     // stage timing (cs_profile)
     bool prof = false;
     struct Rec {
@@ -265,6 +273,10 @@ int launch_conserve(const Handle &hd, const double *Qt, int ncells, int project,
                     double *moments, cudaStream_t s);
 int launch_moments(const Handle &hd, const double *f, int ncells, double *out, cudaStream_t s);
 int conserve_parts(int M);  // blocks per cell of the projection
+// the input scan of CS_TUNE_CHECK_INPUT: sets bit 1 of hd.err if one of the
+// ncells * N^3 values of f is not finite, bit 2 if one is negative (mode 2);
+// enqueues nothing when the handle's scan is off
+int launch_input_check(const Handle &hd, const double *f, long long count, cudaStream_t s);
 
 // ---- transport.cu
 // doubles of workspace the transport tables need; tables are filled by

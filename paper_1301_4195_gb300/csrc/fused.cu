@@ -517,7 +517,10 @@ int inverse_n(const Handle &hd, int ncells, double eps, int project, double a, c
 
 }  // namespace
 
-bool fused_forward_next(const Handle &hd) { return fused_available(hd) && hd.g.N != 32; }
+bool fused_forward_next(const Handle &hd)
+{
+    return fused_available(hd) && hd.g.N != 32 && hd.tune_fwd_next != 2;
+}
 
 bool fused_available(const Handle &hd)
 {

@@ -338,6 +338,10 @@ struct StripJob {
     const float *radA = nullptr, *radB = nullptr;
     const int *emap = nullptr;
     int bbn = 0;
+    // limit of the item's bounded waits, and the test stall (the launch's
+    // first CTA issues no copy for its first item, so its waits run out)
+    unsigned long long wait_ns = kWaitNs;
+    int stall = 0;
 };
 
 // A persistent CTA's stage ring: barriers and the abort word at the front of
@@ -485,12 +489,16 @@ __device__ __forceinline__ Ring ring_init(unsigned char *smem, int *err)
 }
 
 // after an abort: give the copies thread 0 issued a bounded time to land
-// before the CTA exits
+// before the CTA exits.  Only the last NST uses can be in flight (thread 0
+// issues use u after every warp released use u - NST, i.e. after it landed),
+// and those sit in distinct slots, each in its slot's latest phase.  The
+// limit is fixed (0.1 s), whatever the handle's wait limit.
 template <int NST>
 __device__ __forceinline__ void ring_drain(const Ring &r, bool ok)
 {
     if (threadIdx.x == 0 && (!ok || *r.abort_flag)) {
-        for (uint32_t u = r.tt; u < r.issued; ++u) {
+        const uint32_t from = r.issued > r.tt + NST ? r.issued - NST : r.tt;
+        for (uint32_t u = from; u < r.issued; ++u) {
             volatile int dummy = 0;
             wait_phase(&r.full[u % NST], (u / NST) & 1u, &dummy, r.err, kWaitNs / 20);
         }
@@ -536,7 +544,7 @@ __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &r
     auto issue_next = [&]() -> bool {
         const uint32_t u = rg.tt + pt;
         const int s = u % NST;
-        if (u >= NST && !wait_phase(&rg.empty[s], ((u / NST) + 1) & 1u, rg.abort_flag, rg.err, kWaitNs))
+        if (u >= NST && !wait_phase(&rg.empty[s], ((u / NST) + 1) & 1u, rg.abort_flag, rg.err, jb.wait_ns))
             return false;
         unsigned char *st = rg.stages + s * C::STAGE;
         mbar_arrive_expect_tx(&rg.full[s], 2 * GPC * C::ROWB + (RAD ? 0 : C::GB));
@@ -553,7 +561,9 @@ __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &r
         pw.next();
         return true;
     };
-    if (threadIdx.x == 0) {
+    // the test stall: the first CTA issues nothing for its first item
+    const bool stalled = jb.stall && blockIdx.x == 0 && rg.tt == 0;
+    if (threadIdx.x == 0 && !stalled) {
         pw.start(lo1, lo2, hi2, K1, K2);
         for (int i = 0; i < tb; ++i) pw.next();
         while (pt < NST && pt < T)
@@ -597,7 +607,7 @@ __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &r
                 radius_gather<N, EPL>(jb, s_emap, seg, nseg, radius_tile<N>(k1, k2, nw.m1, nw.m2), lane, pa);
             }
         }
-        if (!wait_phase(&rg.full[s], (u / NST) & 1u, rg.abort_flag, rg.err, kWaitNs)) {
+        if (!wait_phase(&rg.full[s], (u / NST) & 1u, rg.abort_flag, rg.err, jb.wait_ns)) {
             ok = false;
             break;
         }
@@ -620,7 +630,7 @@ __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &r
         cw.next();
         __syncwarp();
         if (lane == 0) mbar_arrive(&rg.empty[s]);
-        if (threadIdx.x == 0 && pt < T)
+        if (threadIdx.x == 0 && pt < T && !stalled)
             if (!issue_next()) ok = false;
         __syncwarp();
     }
@@ -747,6 +757,8 @@ int launch_cfg(const Handle &hd, int ncells, cudaStream_t s)
     StripJob jb{(const float *)hd.ghat, hd.pencil_tile0, hd.pencil_order, (const float2 *)hd.F,
                 (float2 *)hd.Qh, (float2 *)hd.Qh2, (float2 *)hd.Qh3, (float2 *)hd.Qh4, hd.done, hd.err, omega,
                 nblocks, N, 0};
+    jb.wait_ns = hd.wait_ns ? hd.wait_ns : kWaitNs;
+    jb.stall = hd.test_stall;
     if constexpr (RAD) {
         jb.radA = hd.radA;
         jb.radB = hd.radB;

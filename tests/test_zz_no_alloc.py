@@ -41,10 +41,17 @@ def _noalloc(api, h, f, Q, ncells):
     return api.lib().cs_collide_noalloc(h.ptr, f.data_ptr(), ncells, 1.0, Q.data_ptr(), 1, stream)
 
 
-@pytest.mark.parametrize("N,prec,tol,n1,n2", [(8, "fp64", 1e-12, 33, 5), (16, "fp32", 1e-5, 40, 64),
-                                              (32, "fp32", 1e-5, 64, 3)])
-def test_noalloc_matches_cs_collide_twice(cs, N, prec, tol, n1, n2):
+@pytest.mark.parametrize("N,prec,split,n1,n2", [(8, "fp64", 0, 33, 5), (16, "fp32", 0, 40, 64),
+                                                (16, "fp32", 4, 384, 7), (32, "fp32", 0, 64, 3)])
+def test_noalloc_matches_cs_collide_twice(cs, N, prec, split, n1, n2):
+    """Both entry points run the same kernels in the same order on the same
+    launch choices, so their results must agree bit for bit; any overlap of
+    the intermediate buffers inside the fixed array would break that.  The
+    four-way split at N = 16 (the only launch that writes all four partial
+    sums and the counters of finished ranges) is run at its 384-cell limit."""
     h = cs.Handle(N, L, 1.0, prec)
+    if split:
+        cs.cs_tune(h.ptr, cs.CS_TUNE_SPLIT, split)
     for ncells, first in ((n1, 0), (n2, 500)):
         f = torch.from_numpy(I.random_mixture_cells(N, L, ncells, first_id=first)).cuda()
         ref = torch.empty_like(f)
@@ -54,17 +61,18 @@ def test_noalloc_matches_cs_collide_twice(cs, N, prec, tol, n1, n2):
         torch.cuda.synchronize()
         g, r = got.cpu().numpy(), ref.cpu().numpy()
         assert np.isfinite(g).all()
-        assert np.abs(g - r).max() <= tol * np.abs(r).max()
+        assert np.array_equal(g, r)
+    cs.cs_status(h.ptr)
     h.close()
 
 
-def test_noalloc_refuses_more_cells_than_the_fixed_array_holds(cs):
-    N = 32
-    h = cs.Handle(N, L, 1.0, "fp64")
-    f = torch.zeros((33, N, N, N), dtype=torch.float64, device="cuda")
+@pytest.mark.parametrize("N,prec,limit", [(32, "fp64", 32), (16, "fp32", 384)])
+def test_noalloc_refuses_more_cells_than_the_fixed_array_holds(cs, N, prec, limit):
+    h = cs.Handle(N, L, 1.0, prec)
+    f = torch.zeros((limit + 1, N, N, N), dtype=torch.float64, device="cuda")
     Q = torch.empty_like(f)
-    rc = _noalloc(cs, h, f, Q, 33)  # 32 cells is the double-precision limit at N = 32
+    rc = _noalloc(cs, h, f, Q, limit + 1)
     assert rc == cs.CS_EINVAL
     msg = cs.lib().cs_last_error().decode()
-    assert "at most 32 cells" in msg
+    assert f"at most {limit} cells" in msg
     h.close()
