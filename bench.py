@@ -8,11 +8,14 @@ hot path.  The metric is nominal pair-updates per second,
     (collision evaluations) x (cells) x N^6 / time,
 the count the paper's N^6 cost model uses.
 
-Default workload (N=1): N = 16, L = 6, lambda = 1, 128 cells of width
+Default workload (N=1): N = 32, L = 6, lambda = 1, 256 cells of width
 min(dx0 1.05^j, 0.5), dx0 = 1/8, wall at T_w = 1.5 against a unit Maxwellian
 gas, dt = 0.01; transforms and convolution in float, weights, projection,
 transport and state in double.  Secondary objects in the same line: the same
-step in double precision ("fp64") and the N = 32, 256-cell workload ("n32").
+step in double precision ("fp64"); the N = 16, 128-cell workload ("wall16");
+the N = 32 run of 2000 steps with its error and moment drift ("config4"); the
+uneven batch ("batched"); the serving sweep ("serve"); N = 64 ("n64"); the
+wall problem in two space dimensions ("wall2d").
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun (N > 1) every rank runs its own replica (weak scaling).
@@ -47,8 +50,9 @@ WORKLOADS = {
 }
 MAX_SM_MHZ = 2070.0
 # DRAM bytes (read + write) per convolution launch from ncu captures of the
-# current kernel (profiles/), keyed by (N, cells); None where not captured
-TRAFFIC = {(16, 128): 18415616, (32, 256): 3028994304 + 67706112}
+# current kernel (profiles/), keyed by (N, cells); absent where not captured
+# since the kernel last changed
+TRAFFIC = {}
 SMS = 152
 FP32_LANES = 128
 
@@ -74,6 +78,55 @@ def tiles_total(N: int) -> int:
 def unique_pairs_per_cell(N: int) -> int:
     """Pairs the symmetrised half-tile convolution visits per cell per evaluation."""
     return tiles_total(N) * (3 * N * N // 4)
+
+
+def valid_pairs_per_cell(N: int) -> int:
+    """The valid (not dropped) pairs of the convolution per cell: (3 N^2 / 4)^3."""
+    return (3 * N * N // 4) ** 3
+
+
+PEAK_TOPS = SMS * FP32_LANES * MAX_SM_MHZ * 1e6 / 1e12        # FP32 FMA-pipe lane operations, T/s
+PEAK_TFLOPS = 2 * PEAK_TOPS                                   # one FMA = 2 flops
+
+
+def conv_roofline(N: int, ncells: int, avg_ms: float, probe=None) -> dict:
+    """Roofline of one convolution launch over ncells cells at grid N.  The
+    kernel visits P(N) symmetrised pairs per cell, 6 FP32 FMA-pipe lane
+    operations each (one packed FMUL2 + two FFMA2); frac_executed counts
+    those, frac_effective_pairs counts the 27 N^6 / 64 valid pairs the
+    unsymmetrised sum has, at the same 6 lane operations each (the work a
+    kernel without the symmetrisation would have to do)."""
+    ops = 6.0 * unique_pairs_per_cell(N) * ncells
+    ops_eff = 6.0 * valid_pairs_per_cell(N) * ncells
+    t = avg_ms * 1e-3
+    ach = ops / t / 1e12
+    out = {"bound": "alu", "achieved": ach, "peak": PEAK_TOPS, "unit": "T FP32 FMA-pipe lane-ops/s",
+           "frac": ach / PEAK_TOPS, "frac_executed": ach / PEAK_TOPS,
+           "frac_effective_pairs": ops_eff / t / 1e12 / PEAK_TOPS,
+           "traffic": TRAFFIC.get((N, ncells)), "avg_launch_ms": avg_ms,
+           "ops_per_launch": ops, "effective_ops_per_launch": ops_eff,
+           "tflops": 10.0 * unique_pairs_per_cell(N) * ncells / t / 1e12,
+           "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz (max SM clock), derived"}
+    out["flop_frac"] = out["tflops"] / PEAK_TFLOPS
+    if probe:
+        out["frac_of_best_fp32_probe"] = ach / max(probe["ffma_tlane_ops"], probe["ffma2_tlane_ops"])
+    return out
+
+
+def moment_rows(N: int) -> np.ndarray:
+    """The integration matrix C of the conservation step: rows dv^3 (1, v1, v2, v3, |v|^2)."""
+    from paper_1301_4195_gb300 import inputs
+    v = inputs.velocity_grid(N, L_BOX)
+    w = (2 * L_BOX / N) ** 3
+    return np.stack([np.ones_like(v[0]), v[0], v[1], v[2], v[0] ** 2 + v[1] ** 2 + v[2] ** 2]).reshape(5, -1) * w
+
+
+def drift_of(Q: np.ndarray, N: int) -> float:
+    """max over cells and rows of |C Q| / (|C| |Q|): the moment drift of a collision
+    term relative to the rounding scale of its moments."""
+    C = moment_rows(N)
+    q = Q.reshape(Q.shape[0], -1)
+    return float((np.abs(q @ C.T) / (np.abs(q) @ np.abs(C).T)).max())
 
 
 # ----------------------------------------------------------------- clocks
@@ -197,6 +250,275 @@ def time_steps(torch, h, fd, dxd, fard, K, W, flush, profile=False):
     return total, prof
 
 
+def step_workload(api, inputs, torch, device, N, ncells, K, W, flush, tune="", profile_stages=True):
+    """One Strang-step workload on a float handle: autotune (or fixed choices),
+    W warm-up steps, K timed steps (replayed graphs, events per step, L2
+    flushed before each), then the same K steps with per-stage events for
+    the convolution's average launch.  Returns the handle, its state and the
+    measurements."""
+    h = api.Handle(N, L_BOX, LAM, "fp32")
+    h.reserve(ncells)
+    if tune:  # fixed launch choices (profiling runs: timings under a profiler would mislead the autotuner)
+        for param, v in zip((api.CS_TUNE_GROUPS_PER_CTA, api.CS_TUNE_CTAS_PER_SM, api.CS_TUNE_SPLIT,
+                             api.CS_TUNE_WEIGHTS), (int(x) for x in tune.split(","))):
+            api.cs_tune(h.ptr, param, v)
+        tuned_ms = None
+    else:
+        tuned_ms = api.cs_autotune(h.ptr, ncells)  # launch shape of the convolution (outside the timed region)
+    f0, fd, dxd, fard = make_state(api, inputs, torch, N, ncells, device)
+    for _ in range(W):
+        h.step(fd, dxd, fard, WALL_T, (0.0, 0.0, 0.0), DT, nsteps=1)
+    torch.cuda.synchronize()
+    return h, f0, fd, dxd, fard, tuned_ms
+
+
+def launch_choice(api, h) -> dict:
+    return {"groups_per_cta": api.cs_tune_get(h.ptr, api.CS_TUNE_GROUPS_PER_CTA),
+            "ctas_per_sm": api.cs_tune_get(h.ptr, api.CS_TUNE_CTAS_PER_SM),
+            "tile_split": api.cs_tune_get(h.ptr, api.CS_TUNE_SPLIT),
+            "weights": WEIGHT_MODES[api.cs_tune_get(h.ptr, api.CS_TUNE_WEIGHTS)]}
+
+
+def q_eval_run(api, torch, h, fd, N, ncells, world=1):
+    """The operator alone (t_Q = forward transform + convolution + inverse +
+    projection, one cs_collide on the workload's state), direct launches."""
+    qd = torch.empty_like(fd)
+    for _ in range(3):
+        api.cs_collide(h.ptr, fd, ncells, 1.0, qd, 1)
+    torch.cuda.synchronize()
+    ta, tb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nq = 10
+    ta.record()
+    for _ in range(nq):
+        api.cs_collide(h.ptr, fd, ncells, 1.0, qd, 1)
+    tb.record()
+    tb.synchronize()
+    tq = ta.elapsed_time(tb) / nq
+    return {"ms_per_evaluation": tq, "value": world * ncells * N ** 6 / (tq * 1e-3), "unit": UNIT,
+            "note": "one collision evaluation Q(f) of the workload's cells (t_Q: transforms, convolution, "
+                    "projection), L2 not flushed between evaluations"}
+
+
+def fp64_step(api, inputs, torch, device, N, ncells, dxd, fard, flush, k64):
+    """The same Strang step in double precision (the plain FP64 GPU form)."""
+    h64 = api.Handle(N, L_BOX, LAM, "fp64")
+    h64.reserve(ncells)
+    _, fd64, _, _ = make_state(api, inputs, torch, N, ncells, device)
+    ms64, _ = time_steps(torch, h64, fd64, dxd, fard, k64, 1, flush)
+    return h64, {"value": 2 * ncells * N ** 6 / (ms64 / k64 * 1e-3), "ms_per_step": ms64 / k64, "steps": k64}
+
+
+def secondary_workload(api, inputs, torch, device, args, wl, flush, probe):
+    """A Strang-step workload beside the headline one: its rate, the
+    convolution's roofline, the operator alone, both weight modes and the
+    double-precision form of the same step."""
+    N, ncells = WORKLOADS[wl]["N"], WORKLOADS[wl]["ncells"]
+    h, f0, fd, dxd, fard, tuned = step_workload(api, inputs, torch, device, N, ncells, args.steps, 3, flush)
+    k = max(3, min(args.steps, 20))
+    ms, _ = time_steps(torch, h, fd, dxd, fard, k, 0, flush, profile=False)
+    _, prof = time_steps(torch, h, fd, dxd, fard, k, 0, flush, profile=True)
+    cavg = prof["convolve"][0] / max(prof["convolve"][1], 1)
+    out = {"workload": describe(wl), "value": 2 * ncells * N ** 6 / (ms / k * 1e-3), "unit": UNIT,
+           "ms_per_step": ms / k, "steps": k, "conv_ms": cavg,
+           "roofline": conv_roofline(N, ncells, cavg, probe), "launch": launch_choice(api, h),
+           "autotuned_ms": tuned, "stage_ms_per_step": {kk: v[0] / k for kk, v in prof.items()},
+           "q_eval": q_eval_run(api, torch, h, fd, N, ncells),
+           "weights": {"stored_conv_ms": conv_ms_in_mode(api, torch, h, fd, ncells, 1),
+                       "radius_conv_ms": conv_ms_in_mode(api, torch, h, fd, ncells, 2)}}
+    if not args.skip_fp64:
+        h64, fp = fp64_step(api, inputs, torch, device, N, ncells, dxd, fard, flush, max(2, min(args.steps, 5)))
+        h64.close()
+        out["fp64"] = fp
+        out["speedup_vs_fp64"] = fp["ms_per_step"] / out["ms_per_step"]
+    h.close()
+    return out
+
+
+def config4_run(api, inputs, torch, device, h32, args):
+    """The large-grid wall problem run whole: N = 32, 256 cells, 2000 Strang
+    steps of dt = 0.01 in float (convolution with compensated xi-sums,
+    projection in double), from the unit Maxwellian, on the headline's
+    handle.  Reported: the moment drift of the collision step at ten points
+    of the run (the moments of every cell before and after one Heun collision
+    step of its current state, relative to the largest moment of the cell),
+    |C Q| / (|C| |Q|) of the final state's collision term in every cell, the
+    final state's collision term on cells 0, 1, 64 and 255 (wall, next to it,
+    interior, far end) against the oracle, relative to its largest value and
+    to the rounding scale S of the float sum (cells where S / |Q| > 100 are
+    flagged), and the float state against the plain double form after the
+    first 10 steps."""
+    import oracle
+    oracle.build()
+    N, nc, total = 32, 256, args.config4_steps
+    _, f, dx, far = make_state(api, inputs, torch, N, nc, device)
+    chunk = max(1, total // 10)
+    drift_steps, drifts = [], []
+    ta, tb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f10 = None
+    run_ms, done = 0.0, 0
+    g = torch.empty_like(f)
+    m0 = torch.empty((nc, 5), dtype=torch.float64, device=device)
+    m1 = torch.empty_like(m0)
+    while done < total:
+        n = 10 if done == 0 else min(chunk, total - done)
+        ta.record()
+        h32.step(f, dx, far, WALL_T, (0.0, 0.0, 0.0), DT, nsteps=n)
+        tb.record()
+        tb.synchronize()
+        run_ms += ta.elapsed_time(tb)
+        done += n
+        if done == 10:
+            f10 = f.cpu().numpy()
+        # the collision step's moment drift on the current state
+        g.copy_(f)
+        api.cs_moments(h32.ptr, g, nc, m0)
+        api.cs_relax(h32.ptr, g, nc, DT, 1.0, 1)
+        api.cs_moments(h32.ptr, g, nc, m1)
+        a, b = m0.cpu().numpy(), m1.cpu().numpy()
+        drift_steps.append(done)
+        drifts.append(float((np.abs(b - a).max(axis=1) / np.abs(a).max(axis=1)).max()))
+    api.cs_status(h32.ptr)
+    fin = f.cpu().numpy()
+    q = torch.empty_like(f)
+    api.cs_collide(h32.ptr, f, nc, 1.0, q, 1)
+    Q = q.cpu().numpy()
+    sample = [0, 1, 64, 255]
+    cores = os.cpu_count() or 1
+    ref = oracle.collide(fin[sample], N, L_BOX, LAM, nthreads=cores)
+    S = oracle.rounding_scale(fin[sample], N, L_BOX, LAM, nthreads=cores)
+    cells = []
+    for i, c in enumerate(sample):
+        err = float(np.abs(Q[c] - ref[i]).max())
+        qmax = float(np.abs(ref[i]).max())
+        cells.append({"cell": c, "rel_err": err / qmax, "err_over_S": err / S[i], "S_over_Qmax": S[i] / qmax,
+                      "flagged": bool(S[i] / qmax > 100.0)})
+    out = {"workload": f"N=32, L=6, lambda=1, 256 cells of the wall grid, unit Maxwellian start, T_w=1.5, "
+                       f"{total} Strang steps of dt=0.01 (float transforms and convolution with compensated "
+                       f"xi-sums, double projection, transport and state)",
+           "steps": total, "ms_per_step": run_ms / total, "run_s": run_ms / 1e3,
+           "value": 2 * nc * N ** 6 / (run_ms / total * 1e-3), "unit": UNIT,
+           "finite": bool(np.isfinite(fin).all()),
+           "collision_step_drift": {"steps": drift_steps, "max_rel": max(drifts), "per_check": drifts},
+           "final_q_drift": drift_of(Q, N),
+           "oracle_err": {"cells": cells, "max_rel_err": max(c["rel_err"] for c in cells),
+                          "max_err_over_S": max(c["err_over_S"] for c in cells), "tolerance": 1e-5}}
+    # the plain double form over the first 10 steps
+    if not args.skip_fp64:
+        h64 = api.Handle(N, L_BOX, LAM, "fp64")
+        h64.reserve(nc)
+        _, f64, _, _ = make_state(api, inputs, torch, N, nc, device)
+        h64.step(f64, dx, far, WALL_T, (0.0, 0.0, 0.0), DT, nsteps=2)
+        torch.cuda.synchronize()
+        ta.record()
+        h64.step(f64, dx, far, WALL_T, (0.0, 0.0, 0.0), DT, nsteps=8)
+        tb.record()
+        tb.synchronize()
+        ms64 = ta.elapsed_time(tb) / 8
+        d = f64.cpu().numpy()
+        out["fp64_10_steps"] = {"state_rel_diff": float(np.abs(f10 - d).max() / np.abs(d).max()),
+                                "ms_per_step": ms64, "value": 2 * nc * N ** 6 / (ms64 * 1e-3)}
+        h64.close()
+    return out
+
+
+def serve_sweep(args):
+    """Config 5: Poisson arrivals of space-homogeneous relaxation requests,
+    N in {12, 16, 24, 32}, lambda in {0, 1}, 2-4 Maxwellian mixtures, horizons
+    U[1, 20] time units at dt = 0.01 (100 to 2000 Heun steps), every eighth
+    request a Maxwell-molecule one from BKW data checked against the closed
+    form.  First a saturating run measures the capacity (requests completed
+    per second with every request waiting at the start), then the rate is set
+    to 0.5x, 1x and 2x that capacity; each run has args.serve_requests
+    requests."""
+    from paper_1301_4195_gb300 import serve
+    n, hz = args.serve_requests, (1.0, 20.0)
+    sat = serve.serve_bench(n, 1e4, horizon=hz, bkw_every=8)
+    cap = sat["requests_per_s"]
+    out = {"load": f"{n} Poisson requests per rate, N in {{12,16,24,32}}, lambda in {{0,1}}, 2-4 Maxwellian "
+                   f"mixtures, horizon U[1,20] time units at dt=0.01, every 8th request BKW (lambda=0, K0=0.6), "
+                   f"weight tables resident, per-class streams, up to 8 Heun steps per iteration",
+           "capacity_requests_per_s": cap, "saturated": sat, "sweep": []}
+    for factor in (0.5, 1.0, 2.0):
+        r = serve.serve_bench(n, factor * cap, horizon=hz, bkw_every=8)
+        r["rate_vs_capacity"] = factor
+        out["sweep"].append(r)
+    one = out["sweep"][1]
+    out.update({"p50_s": one["p50_s"], "p99_s": one["p99_s"], "rate_per_s": one["rate_per_s"],
+                "throughput_pair_updates_per_s": one["throughput_pair_updates_per_s"]})
+    return out
+
+
+def n64_run(api, inputs, torch, device):
+    """N = 64 (a 58 GB float weight table): one collision evaluation of 32
+    random-mixture cells, its convolution's roofline, and the same from a
+    handle holding the radius tables only."""
+    N6, nc6 = 64, 32
+    t0 = time.perf_counter()
+    h6 = api.Handle(N6, L_BOX, LAM, "fp32")
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    h6.reserve(nc6)
+    f6 = torch.from_numpy(inputs.random_mixture_cells(N6, L_BOX, nc6, first_id=7000)).to(device)
+    q6 = torch.empty_like(f6)
+    api.cs_collide(h6.ptr, f6, nc6, 1.0, q6, 1)
+    torch.cuda.synchronize()
+    api.cs_profile(h6.ptr, True)
+    api.cs_profile_read(h6.ptr, reset=True)
+    reps6 = 2
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps6):
+        api.cs_collide(h6.ptr, f6, nc6, 1.0, q6, 1)
+    b.record()
+    b.synchronize()
+    p6 = api.cs_profile_read(h6.ptr, reset=True)
+    api.cs_profile(h6.ptr, False)
+    ms6 = a.elapsed_time(b) / reps6
+    c6 = p6["convolve"][0] / max(p6["convolve"][1], 1)
+    out = {"workload": f"one collision evaluation, N={N6}, {nc6} random-mixture cells (L=6, lambda=1)",
+           "ms_per_evaluation": ms6, "value": nc6 * N6 ** 6 / (ms6 * 1e-3), "unit": UNIT,
+           "weights_build_s": build_s, "weight_bytes": h6.weight_bytes(), "conv_ms": c6,
+           "roofline": conv_roofline(N6, nc6, c6), "drift": drift_of(q6.cpu().numpy(), N6)}
+    h6.close()
+    t0 = time.perf_counter()
+    h6 = api.Handle(N6, L_BOX, LAM, "fp32-radius")
+    torch.cuda.synchronize()
+    out["radius_only"] = {"weights_build_s": time.perf_counter() - t0, "weight_bytes": h6.weight_bytes(),
+                          "conv_ms": conv_ms_in_mode(api, torch, h6, f6, nc6, 2, 2)}
+    h6.close()
+    return out
+
+
+def wall2d_run(api, inputs, torch, device, args, flush):
+    """The wall problem in two space dimensions: 32 x-cells by 8 periodic
+    y-cells at N = 16, the same step with the 2-D transport."""
+    N2, nx, ny, Y = 16, 32, 8, 2.0
+    hw = api.Handle(N2, L_BOX, LAM, "fp32")
+    hw.reserve(nx * ny)
+    api.cs_autotune(hw.ptr, nx * ny)
+    dx2 = torch.from_numpy(inputs.wall_grid(nx)).to(device)
+    far2 = torch.from_numpy(inputs.maxwellian(N2, L_BOX, 1.0, (0.0, 0.0, 0.0), 1.0)).to(device)
+    f2 = torch.from_numpy(inputs.wall2d_initial(N2, L_BOX, nx, ny, Y)).to(device)
+    for _ in range(3):
+        hw.step2d(f2, dx2, far2, WALL_T, (0.0, 0.0, 0.0), ny, Y / ny, DT)
+    torch.cuda.synchronize()
+    k2, ms2 = max(2, min(args.steps, 10)), 0.0
+    for _ in range(k2):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        hw.step2d(f2, dx2, far2, WALL_T, (0.0, 0.0, 0.0), ny, Y / ny, DT)
+        b.record()
+        b.synchronize()
+        ms2 += a.elapsed_time(b)
+    hw.close()
+    return {"workload": f"wall problem in 2-D: N={N2}, {nx} x-cells (dx_j=min(0.125*1.05^j,0.5)) x {ny} "
+                        f"periodic y-cells (Y={Y}), density 1+0.2 sin(2 pi y/Y), one Strang step",
+            "ms_per_step": ms2 / k2, "value": 2 * nx * ny * N2 ** 6 / (ms2 / k2 * 1e-3), "unit": UNIT}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -221,20 +543,8 @@ def run_ours(args):
     N, ncells = wl["N"], (args.cells or wl["ncells"])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)  # > L2 (129 MB)
 
-    h32 = api.Handle(N, L_BOX, LAM, "fp32")
-    h32.reserve(ncells)
-    if args.tune:  # fixed launch choices (profiling runs: timings under a profiler would mislead the autotuner)
-        for param, v in zip((api.CS_TUNE_GROUPS_PER_CTA, api.CS_TUNE_CTAS_PER_SM, api.CS_TUNE_SPLIT,
-                             api.CS_TUNE_WEIGHTS), (int(x) for x in args.tune.split(","))):
-            api.cs_tune(h32.ptr, param, v)
-        tuned_ms = None
-    else:
-        tuned_ms = api.cs_autotune(h32.ptr, ncells)  # launch shape of the convolution (outside the timed region)
-    f0, fd, dxd, fard = make_state(api, inputs, torch, N, ncells, device)
-
-    # warm-up + timed region (barrier and synchronize on both sides, max over ranks)
-    for _ in range(args.warmup):
-        h32.step(fd, dxd, fard, WALL_T, (0.0, 0.0, 0.0), DT, nsteps=1)
+    h32, f0, fd, dxd, fard, tuned_ms = step_workload(api, inputs, torch, device, N, ncells, args.steps,
+                                                     args.warmup, flush, tune=args.tune)
 
     def barrier():
         torch.cuda.synchronize()
@@ -258,21 +568,9 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     ms_step = plain_ms / args.steps
-    evals_per_step = 2
-    pairs_step = evals_per_step * ncells * N ** 6
+    pairs_step = 2 * ncells * N ** 6
     value = world * pairs_step / (ms_step * 1e-3)
-
-    # roofline of the dominant kernel (the convolution), timed live above:
-    # FP32 FMA-pipe lane operations, 6 per (pair, cell) (one FMUL2 + two FFMA2), against
-    # 152 SMs x 128 lanes x 2070 MHz; flops (10 per pair) reported beside it
-    conv_ms, conv_n = prof["convolve"]
-    conv_avg = conv_ms / max(conv_n, 1)
-    pair_cells = unique_pairs_per_cell(N) * ncells
-    flops_launch = 10.0 * pair_cells
-    peak_tflops = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
-    peak_tops = SMS * FP32_LANES * MAX_SM_MHZ * 1e6 / 1e12
-    achieved_ops = 6.0 * pair_cells / (conv_avg * 1e-3) / 1e12
-    achieved = flops_launch / (conv_avg * 1e-3) / 1e12
+    conv_avg = prof["convolve"][0] / max(prof["convolve"][1], 1)
     step_stage_ms = {k: v[0] / args.steps for k, v in prof.items()}
 
     # e2e: host state in pinned memory, copied in and out around the public call every step
@@ -303,140 +601,9 @@ def run_ours(args):
     # measured pipe peaks beside the derived one (lane operations per second)
     probe = {"ffma_tlane_ops": api.cs_fma_probe(0) / 1e12, "ffma2_tlane_ops": api.cs_fma_probe(1) / 1e12,
              "dfma_tlane_ops": api.cs_fma_probe(2) / 1e12}
-    probe["frac_of_best_fp32_probe"] = achieved_ops / max(probe["ffma_tlane_ops"], probe["ffma2_tlane_ops"])
-
-    # the operator alone (t_Q = forward transform + convolution + inverse +
-    # projection, one cs_collide on the workload's state), graph-free direct launches
-    qd = torch.empty_like(fd)
-    for _ in range(3):
-        api.cs_collide(h32.ptr, fd, ncells, 1.0, qd, 1)
-    torch.cuda.synchronize()
-    ta, tb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    nq = 20
-    ta.record()
-    for _ in range(nq):
-        api.cs_collide(h32.ptr, fd, ncells, 1.0, qd, 1)
-    tb.record()
-    tb.synchronize()
-    tq = ta.elapsed_time(tb) / nq
-    q_eval = {"ms_per_evaluation": tq, "value": world * ncells * N ** 6 / (tq * 1e-3), "unit": UNIT,
-              "note": "one collision evaluation Q(f) of the workload's cells (t_Q: transforms, convolution, "
-                      "projection), L2 not flushed between evaluations"}
-
-    # store versus recompute: the convolution with stored weight tiles and with
-    # tiles rebuilt from the radius tables (the autotuner keeps the faster)
-    weights = {"chosen": WEIGHT_MODES[api.cs_tune_get(h32.ptr, api.CS_TUNE_WEIGHTS)],
-               "stored_conv_ms": conv_ms_in_mode(api, torch, h32, fd, ncells, 1),
-               "radius_conv_ms": conv_ms_in_mode(api, torch, h32, fd, ncells, 2)}
-
-    # the same step in double precision (the plain FP64 GPU form)
-    h64, fp64 = None, None
-    if not args.skip_fp64:
-        h64 = api.Handle(N, L_BOX, LAM, "fp64")
-        h64.reserve(ncells)
-        _, fd64, _, _ = make_state(api, inputs, torch, N, ncells, device)
-        k64 = max(2, min(args.steps, 5))
-        ms64, _ = time_steps(torch, h64, fd64, dxd, fard, k64, 1, flush)
-        fp64 = {"value": pairs_step / (ms64 / k64 * 1e-3), "ms_per_step": ms64 / k64}
-
-    # the N = 32, 256-cell workload (secondary)
-    n32 = None
-    if args.workload == "wall16" and not args.skip_n32:
-        N2, nc2 = WORKLOADS["wall32"]["N"], WORKLOADS["wall32"]["ncells"]
-        hb = api.Handle(N2, L_BOX, LAM, "fp32")
-        hb.reserve(nc2)
-        api.cs_autotune(hb.ptr, nc2)
-        _, fb, dxb, farb = make_state(api, inputs, torch, N2, nc2, device)
-        kb = max(2, min(args.steps, 4))
-        msb, profb = time_steps(torch, hb, fb, dxb, farb, kb, 1, flush, profile=True)
-        cms, cn = profb["convolve"]
-        cavg = cms / max(cn, 1)
-        fl2 = 10.0 * unique_pairs_per_cell(N2) * nc2
-        pc2 = unique_pairs_per_cell(N2) * nc2
-        n32 = {"workload": describe("wall32"), "value": 2 * nc2 * N2 ** 6 / (msb / kb * 1e-3),
-               "ms_per_step": msb / kb, "conv_ms": cavg,
-               "weights": {"chosen": WEIGHT_MODES[api.cs_tune_get(hb.ptr, api.CS_TUNE_WEIGHTS)],
-                           "stored_conv_ms": cavg, "radius_conv_ms": conv_ms_in_mode(api, torch, hb, fb, nc2, 2, 2)},
-               "roofline": {"bound": "alu", "achieved": 6.0 * pc2 / (cavg * 1e-3) / 1e12, "peak": peak_tops,
-                            "unit": "T FP32 FMA-pipe lane-ops/s",
-                            "frac": 6.0 * pc2 / (cavg * 1e-3) / 1e12 / peak_tops,
-                            "tflops": fl2 / (cavg * 1e-3) / 1e12,
-                            "flop_frac": fl2 / (cavg * 1e-3) / 1e12 / peak_tflops,
-                            "traffic": TRAFFIC.get((N2, nc2))}}
-        hb.close()
-
-    # N = 64 (the largest grid; a 40 GB float weight table): one collision
-    # evaluation of 32 random-mixture cells, and its convolution's roofline
-    n64 = None
-    if args.workload == "wall16" and not args.skip_n64:
-        N6, nc6 = 64, 32
-        t0 = time.perf_counter()
-        h6 = api.Handle(N6, L_BOX, LAM, "fp32")
-        torch.cuda.synchronize()
-        build_s = time.perf_counter() - t0
-        h6.reserve(nc6)
-        f6 = torch.from_numpy(inputs.random_mixture_cells(N6, L_BOX, nc6, first_id=7000)).to(device)
-        q6 = torch.empty_like(f6)
-        api.cs_collide(h6.ptr, f6, nc6, 1.0, q6, 1)
-        torch.cuda.synchronize()
-        api.cs_profile(h6.ptr, True)
-        api.cs_profile_read(h6.ptr, reset=True)
-        reps6 = 2
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        for _ in range(reps6):
-            api.cs_collide(h6.ptr, f6, nc6, 1.0, q6, 1)
-        b.record()
-        b.synchronize()
-        p6 = api.cs_profile_read(h6.ptr, reset=True)
-        api.cs_profile(h6.ptr, False)
-        ms6 = a.elapsed_time(b) / reps6
-        c6 = p6["convolve"][0] / max(p6["convolve"][1], 1)
-        pc6 = unique_pairs_per_cell(N6) * nc6
-        n64 = {"workload": f"one collision evaluation, N={N6}, {nc6} random-mixture cells (L=6, lambda=1)",
-               "ms_per_evaluation": ms6, "value": nc6 * N6 ** 6 / (ms6 * 1e-3), "unit": UNIT,
-               "weights_build_s": build_s, "weight_bytes": h6.weight_bytes(), "conv_ms": c6,
-               "roofline": {"bound": "alu", "achieved": 6.0 * pc6 / (c6 * 1e-3) / 1e12, "peak": peak_tops,
-                            "unit": "T FP32 FMA-pipe lane-ops/s",
-                            "frac": 6.0 * pc6 / (c6 * 1e-3) / 1e12 / peak_tops, "traffic": None}}
-        h6.close()
-        # the same evaluation from a handle holding the radius tables only
-        t0 = time.perf_counter()
-        h6 = api.Handle(N6, L_BOX, LAM, "fp32-radius")
-        torch.cuda.synchronize()
-        n64["radius_only"] = {"weights_build_s": time.perf_counter() - t0, "weight_bytes": h6.weight_bytes(),
-                              "conv_ms": conv_ms_in_mode(api, torch, h6, f6, nc6, 2, 2)}
-        h6.close()
-
-    # the wall problem in two space dimensions (secondary): 32 x-cells by 8
-    # periodic y-cells, the same step with the 2-D transport
-    wall2d = None
-    if args.workload == "wall16" and not args.skip_2d:
-        N2, nx, ny, Y = 16, 32, 8, 2.0
-        hw = api.Handle(N2, L_BOX, LAM, "fp32")
-        hw.reserve(nx * ny)
-        api.cs_autotune(hw.ptr, nx * ny)
-        dx2 = torch.from_numpy(inputs.wall_grid(nx)).to(device)
-        far2 = torch.from_numpy(inputs.maxwellian(N2, L_BOX, 1.0, (0.0, 0.0, 0.0), 1.0)).to(device)
-        f2 = torch.from_numpy(inputs.wall2d_initial(N2, L_BOX, nx, ny, Y)).to(device)
-        for _ in range(3):
-            hw.step2d(f2, dx2, far2, WALL_T, (0.0, 0.0, 0.0), ny, Y / ny, DT)
-        torch.cuda.synchronize()
-        k2, ms2 = max(2, min(args.steps, 10)), 0.0
-        for _ in range(k2):
-            flush.zero_()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record()
-            hw.step2d(f2, dx2, far2, WALL_T, (0.0, 0.0, 0.0), ny, Y / ny, DT)
-            b.record()
-            b.synchronize()
-            ms2 += a.elapsed_time(b)
-        wall2d = {"workload": f"wall problem in 2-D: N={N2}, {nx} x-cells (dx_j=min(0.125*1.05^j,0.5)) x {ny} "
-                              f"periodic y-cells (Y={Y}), density 1+0.2 sin(2 pi y/Y), one Strang step",
-                  "ms_per_step": ms2 / k2, "value": 2 * nx * ny * N2 ** 6 / (ms2 / k2 * 1e-3), "unit": UNIT}
-        hw.close()
+    roof = conv_roofline(N, ncells, conv_avg, probe)
+    roof.update({"kernel": "conv_strip_kernel (step a2)", "autotuned_ms": tuned_ms,
+                 "launch": launch_choice(api, h32), "probe": probe})
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -449,54 +616,38 @@ def run_ours(args):
         "clocks": clk,
         "e2e": e2e,
         "gpu_launches": launches,
+        "roofline": roof,
         # the same rate in valid pairs (27 N^6 / 64 per cell and evaluation) instead of the nominal N^6
         "effective": {"value": value * 27.0 / 64.0, "unit": "valid pair-updates/s (27 N^6/64 per cell)"},
         "gpu_launches_per_step": launches / args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved_ops, "peak": peak_tops,
-                     "unit": "T FP32 FMA-pipe lane-ops/s", "frac": achieved_ops / peak_tops,
-                     "traffic": TRAFFIC.get((N, ncells)),
-                     "kernel": "conv_strip_kernel (step a2)", "avg_launch_ms": conv_avg,
-                     "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz (max SM clock)",
-                     "ops_per_launch": 6.0 * pair_cells, "tflops": achieved,
-                     "flop_frac": achieved / peak_tflops, "autotuned_ms": tuned_ms,
-                     "launch": {"groups_per_cta": api.cs_tune_get(h32.ptr, api.CS_TUNE_GROUPS_PER_CTA),
-                                "ctas_per_sm": api.cs_tune_get(h32.ptr, api.CS_TUNE_CTAS_PER_SM),
-                                "tile_split": api.cs_tune_get(h32.ptr, api.CS_TUNE_SPLIT)},
-                     "probe": probe},
         "stage_ms_per_step": step_stage_ms,
-        "q_eval": q_eval,
-        "weights": weights,
-        "fp64": fp64,
-        "speedup_vs_fp64": fp64["ms_per_step"] / ms_step if fp64 else None,
+        "q_eval": q_eval_run(api, torch, h32, fd, N, ncells, world),
+        "weights": {"chosen": WEIGHT_MODES[api.cs_tune_get(h32.ptr, api.CS_TUNE_WEIGHTS)],
+                    "stored_conv_ms": conv_ms_in_mode(api, torch, h32, fd, ncells, 1),
+                    "radius_conv_ms": conv_ms_in_mode(api, torch, h32, fd, ncells, 2)},
     }
-    if n32:
-        out["n32"] = n32
-    if wall2d:
-        out["wall2d"] = wall2d
-    if n64:
-        out["n64"] = n64
-    if not args.skip_batched and world == 1:
-        out["batched"] = batched_run(api, inputs, torch, device, args)
-    if not args.skip_serve and world == 1:
-        from paper_1301_4195_gb300 import serve
-        torch.cuda.synchronize()
-        out["serve"] = serve.serve_bench(48, args.serve_rate, horizon=(0.1, 0.5))
-        out["serve"]["load"] = (f"48 Poisson requests at {args.serve_rate}/s, N in {{12,16,24,32}}, "
-                                f"lambda in {{0,1}}, 2-4 Maxwellian mixtures, horizon U[0.1,0.5] at dt=0.01, "
-                                f"weight tables resident")
-        # the same load with one cs_relax_batched call per iteration instead of one cs_relax per class
-        pc = serve.serve_bench(48, args.serve_rate, horizon=(0.1, 0.5), batched=True)
-        out["serve"]["batched_relax"] = {k: pc[k] for k in ("p50_s", "p99_s", "requests_per_s",
-                                                           "throughput_pair_updates_per_s")}
-        # the arrival rate swept around the measured capacity (requests completed per second)
-        cap = out["serve"]["requests_per_s"]
-        out["serve"]["sweep"] = []
-        for factor in (0.5, 2.0):
-            r = serve.serve_bench(48, factor * cap, horizon=(0.1, 0.5))
-            out["serve"]["sweep"].append({"rate_per_s": r["rate_per_s"], "rate_vs_capacity": factor,
-                                          "p50_s": r["p50_s"], "p99_s": r["p99_s"],
-                                          "requests_per_s": r["requests_per_s"],
-                                          "throughput_pair_updates_per_s": r["throughput_pair_updates_per_s"]})
+    # the plain FP64 GPU form of the same step
+    h64 = None
+    if not args.skip_fp64:
+        h64, fp = fp64_step(api, inputs, torch, device, N, ncells, dxd, fard, flush,
+                            2 if N >= 32 else max(2, min(args.steps, 5)))
+        out["fp64"] = fp
+        out["speedup_vs_fp64"] = fp["ms_per_step"] / ms_step
+    if world == 1:
+        other = "wall16" if args.workload == "wall32" else "wall32"
+        if not args.skip_secondary:
+            out[other] = secondary_workload(api, inputs, torch, device, args, other, flush, probe)
+        if N == 32 and ncells == 256 and args.config4_steps > 0:
+            out["config4"] = config4_run(api, inputs, torch, device, h32, args)
+        if not args.skip_batched:
+            out["batched"] = batched_run(api, inputs, torch, device, args)
+        if not args.skip_2d:
+            out["wall2d"] = wall2d_run(api, inputs, torch, device, args, flush)
+        if not args.skip_n64:
+            out["n64"] = n64_run(api, inputs, torch, device)
+        if not args.skip_serve:
+            torch.cuda.synchronize()
+            out["serve"] = serve_sweep(args)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"], out["error_vs_oracle"] = cpu_baseline(args, api, inputs, torch, device, h32, h64)
     h32.close()
@@ -511,9 +662,15 @@ def run_ours(args):
 def batched_run(api, inputs, torch, device, args):
     """Uneven cells in one replayed graph: 4096 cells at N = 16 and 1024 at
     N = 24, half lambda = 0 and half lambda = 1, random 2-3 Maxwellian
-    mixtures; one cs_collide_batched call = one collision evaluation of all."""
+    mixtures; one cs_collide_batched call = one collision evaluation of all.
+    The roofline counts the whole call's time (transforms and projections
+    included) against the convolutions' lane operations, so it is a lower
+    bound on the shared convolution launch's own fraction.  Two cells of
+    every entry (the first and the last) are checked against the oracle."""
+    import oracle
+    oracle.build()
     specs = [(16, 0.0, 2048), (16, 1.0, 2048), (24, 0.0, 512), (24, 1.0, 512)]
-    hs, fs, qs, first = [], [], [], 20000
+    hs, fs, qs, first, firsts = [], [], [], 20000, []
     for N, lam, n in specs:
         h = api.Handle(N, L_BOX, lam, "fp32")
         h.reserve(n)
@@ -521,6 +678,7 @@ def batched_run(api, inputs, torch, device, args):
         hs.append(h)
         fs.append(torch.from_numpy(inputs.random_mixture_cells(N, L_BOX, n, first_id=first)).to(device))
         qs.append(torch.empty_like(fs[-1]))
+        firsts.append(first)
         first += n
     entries = [(h.ptr, f, q, n) for h, f, q, (_, _, n) in zip(hs, fs, qs, specs)]
     for _ in range(2):
@@ -537,23 +695,44 @@ def batched_run(api, inputs, torch, device, args):
         total += a.elapsed_time(b)
     ms = total / reps
     pairs = sum(n * N ** 6 for N, _, n in specs)
+    ops = sum(6.0 * unique_pairs_per_cell(N) * n for N, _, n in specs)
+    ops_eff = sum(6.0 * valid_pairs_per_cell(N) * n for N, _, n in specs)
+    errs, drift = [], 0.0
+    cores = os.cpu_count() or 1
+    for (N, lam, n), f, q, fid in zip(specs, fs, qs, firsts):
+        Q = q.cpu().numpy()
+        drift = max(drift, drift_of(Q, N))
+        idx = [0, n - 1]
+        fc = np.concatenate([inputs.random_mixture_cells(N, L_BOX, 1, first_id=fid + c) for c in idx])
+        ref = oracle.collide(fc, N, L_BOX, lam, nthreads=cores)
+        for j, c in enumerate(idx):
+            errs.append(float(np.abs(Q[c] - ref[j]).max() / np.abs(ref[j]).max()))
     for h in hs:
         h.close()
+    t = ms * 1e-3
     return {"workload": "4096 cells N=16 + 1024 cells N=24, lambda 0/1 half each, random mixtures, "
                         "one graph replay per collision evaluation (cs_collide_batched), autotuned",
-            "ms_per_call": ms, "value": pairs / (ms * 1e-3), "unit": UNIT}
+            "ms_per_call": ms, "value": pairs / t, "unit": UNIT,
+            "roofline": {"bound": "alu", "achieved": ops / t / 1e12, "peak": PEAK_TOPS,
+                         "unit": "T FP32 FMA-pipe lane-ops/s", "frac": ops / t / 1e12 / PEAK_TOPS,
+                         "frac_executed": ops / t / 1e12 / PEAK_TOPS,
+                         "frac_effective_pairs": ops_eff / t / 1e12 / PEAK_TOPS, "traffic": None,
+                         "timed": "the whole call (transforms, shared convolution launch, projections)"},
+            "error_vs_oracle": {"max_rel": max(errs), "cells": "first and last cell of every entry"},
+            "drift": drift}
 
 
 def cpu_baseline(args, api, inputs, torch, device, h32, h64):
     """The oracle, as it stands, on this host's cores: one collision evaluation
-    (transform, convolution, inverse, projection) of a sample of the workload's
-    cells; also the GPU results' error against it on that sample."""
+    (transform, convolution, inverse, projection) of a sample of random-mixture
+    cells at the workload's N; also the GPU results' error against it on that
+    sample, relative to the largest value of Q and (float) to the rounding
+    scale S of the float sum."""
     import oracle
     oracle.build()
     wl = WORKLOADS[args.workload]
     N = wl["N"]
-    nsample = 16
-    # sample cells: the wall state after a few steps has non-trivial collisions
+    nsample = 8 if N >= 32 else 16
     f0 = inputs.random_mixture_cells(N, L_BOX, nsample, first_id=5000)
     cores = os.cpu_count() or 1
     reps, t_total = 0, 0.0
@@ -566,17 +745,11 @@ def cpu_baseline(args, api, inputs, torch, device, h32, h64):
     cpu = {"value": reps * nsample * N ** 6 / t_total, "unit": UNIT, "cores": cores, "kind": "oracle",
            "sample": f"{reps} x one collision evaluation of {nsample} random-mixture cells at N={N} "
                      f"(L=6, lambda=1), OpenMP over zeta outputs"}
-    # the same on one core, and one N = 32 cell on all cores (the paper's Tables 1-4
-    # time one evaluation on 1..16 cores)
+    # the same on one core (the paper's Tables 1-4 time one evaluation on 1..16 cores)
     t0 = time.perf_counter()
-    oracle.collide(f0[:4], N, L_BOX, LAM, nthreads=1)
-    cpu["single_thread"] = {"value": 4 * N ** 6 / (time.perf_counter() - t0), "cores": 1,
-                            "sample": f"one evaluation of 4 of the cells at N={N}"}
-    f32 = inputs.random_mixture_cells(32, L_BOX, 1, first_id=5000)
-    t0 = time.perf_counter()
-    oracle.collide(f32, 32, L_BOX, LAM, nthreads=cores)
-    cpu["n32_one_cell"] = {"value": 32 ** 6 / (time.perf_counter() - t0), "cores": cores,
-                           "sample": "one evaluation of one random-mixture cell at N=32"}
+    oracle.collide(f0[:1], N, L_BOX, LAM, nthreads=1)
+    cpu["single_thread"] = {"value": N ** 6 / (time.perf_counter() - t0), "cores": 1,
+                            "sample": f"one evaluation of one of the cells at N={N}"}
     # the space-homogeneous two-stream case whole: N = 8, one cell, 100 Heun steps
     # of dt = 0.01 (200 evaluations), one core, and the GPU's Heun steps beside it
     f8 = inputs.two_stream(8, L_BOX)[None]
@@ -591,20 +764,29 @@ def cpu_baseline(args, api, inputs, torch, device, h32, h64):
                             "sample": "N=8, one two-stream cell, 100 Heun steps of dt=0.01 (200 evaluations)",
                             "gpu_fp64_error": float(np.abs(g8.cpu().numpy() - r8).max() / np.abs(r8).max())}
     h8.close()
-    err = {}
+    err = {"cells": f"{nsample} random-mixture cells at N={N}"}
     fd = torch.from_numpy(f0).to(device)
     for name, h in (("fp32", h32), ("fp64", h64)):
         if h is None:
             continue
         q = h.collide(fd).cpu().numpy()
         err[name] = float(np.abs(q - ref).max() / np.abs(ref).max())
+        err[name + "_drift"] = drift_of(q, N)
+        if name == "fp32":
+            S = oracle.rounding_scale(f0, N, L_BOX, LAM, nthreads=cores)
+            qmax = np.abs(ref.reshape(nsample, -1)).max(axis=1)
+            e = np.abs(q - ref).reshape(nsample, -1).max(axis=1)
+            err["fp32_err_over_S"] = float((e / S).max())
+            err["S_over_Qmax_max"] = float((S / qmax).max())
+            err["flagged_cells"] = int((S / qmax > 100.0).sum())
     return cpu, err
 
 
 # ----------------------------------------------------------------- reference arm
 def run_reference(args):
     """The CPU oracle as the reference arm: each step is one Strang step of a
-    bounded sample (16 of the workload's cells) on this host's cores."""
+    bounded sample (the first cells of the workload's grid, a grid of their
+    own with the same boundaries) on this host's cores."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -612,7 +794,8 @@ def run_reference(args):
     from paper_1301_4195_gb300 import inputs
     oracle.build()
     wl = WORKLOADS[args.workload]
-    N, ncells = wl["N"], 16
+    N = wl["N"]
+    ncells = 2 if N >= 32 else 16
     dx = inputs.wall_grid(wl["ncells"])[:ncells]
     f = inputs.wall_initial(N, L_BOX, ncells)
     far = inputs.maxwellian(N, L_BOX, 1.0, (0, 0, 0), 1.0)
@@ -631,7 +814,7 @@ def run_reference(args):
            "config": {"workload": describe(args.workload), "N": N, "cells_per_step_sample": ncells,
                       "note": "reference = the FP64 CPU oracle (the paper has no code)"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": f"Strang steps of {ncells} of the {wl['ncells']} cells"},
+                            "sample": f"Strang steps of the first {ncells} of the {wl['ncells']} cells"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -639,21 +822,23 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="wall16")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="wall32")
     ap.add_argument("--cells", type=int, default=0, help="override the workload's cell count (profiling runs)")
     ap.add_argument("--tune", default="", help="fixed launch choices instead of the autotuner: "
                     "groups_per_cta,ctas_per_sm,tile_split,weights (profiling runs)")
-    ap.add_argument("--skip-n32", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true", help="omit the double-precision comparison")
-    ap.add_argument("--skip-serve", action="store_true", help="omit the serving run")
+    ap.add_argument("--skip-secondary", action="store_true", help="omit the other wall workload")
+    ap.add_argument("--skip-serve", action="store_true", help="omit the serving sweep")
     ap.add_argument("--skip-batched", action="store_true", help="omit the uneven-N batched run")
     ap.add_argument("--skip-2d", action="store_true", help="omit the two-dimensional wall problem")
     ap.add_argument("--skip-n64", action="store_true", help="omit the N = 64 collision evaluation")
-    ap.add_argument("--serve-rate", type=float, default=100.0, help="Poisson arrival rate of the serving run (1/s)")
+    ap.add_argument("--config4-steps", type=int, default=2000,
+                    help="Strang steps of the N = 32 run with error and drift (0: omit)")
+    ap.add_argument("--serve-requests", type=int, default=200, help="requests per rate of the serving sweep")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

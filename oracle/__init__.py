@@ -100,6 +100,8 @@ def _load():
                 "or_q_bruteforce": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp,
                                                    ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int,
                                                    ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int]),
+                "or_rounding_scale": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                                     ctypes.c_int, _dp, ctypes.c_double, _dp, ctypes.c_int]),
                 "or_max_threads": (ctypes.c_int, []),
             }
             for name, (res, args) in sigs.items():
@@ -215,6 +217,16 @@ def convolve_at(fhat: np.ndarray, N: int, L: float, lam: float, kflat, nthreads:
     out = np.zeros((fh.shape[0], ks.shape[0], 2))
     _load().or_convolve_at(N, L, lam, fh.shape[0], _d(fi), ks.shape[0], _i(ks), _d(out), nthreads)
     return out[..., 0] + 1j * out[..., 1]
+
+
+def rounding_scale(f: np.ndarray, N: int, L: float, lam: float, eps: float = 1.0, nthreads: int = 0) -> np.ndarray:
+    """Per cell S = (2 pi)^{-3/2} dzeta^3 sum_k Shat_k / eps with Shat the
+    convolution of Sec. 3.2 taken over the terms' magnitudes: a bound on
+    max_j |Qt(v_j)| and the scale of a float evaluation's rounding error."""
+    fc = _cells(f, N)
+    out = np.zeros(fc.shape[0])
+    _load().or_rounding_scale(N, L, lam, fc.shape[0], _d(fc), eps, _d(out), nthreads)
+    return out
 
 
 # ------------------------------------------------------ conservation (Sec. 3.3)

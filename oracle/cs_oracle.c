@@ -433,6 +433,59 @@ int or_convolve_at(int N, double L, double lambda, int ncells, const double *fha
     return 0;
 }
 
+/* The rounding scale of the convolution (an error yardstick for a float
+ * evaluation; not a step of the method): the same sum as Sec. 3.2 with every
+ * term replaced by its magnitude,
+ *   Shat_k = omega sum_m |Ghat(xi_m, zeta_k)| |fhat(xi_m)| |fhat(zeta_k - xi_m)|,
+ * carried through the inverse transform of Sec. 3.2 as the bound
+ *   S = (2 pi)^{-3/2} dzeta^3 sum_k Shat_k / eps  >=  max_j |Qt(v_j)|.
+ * A float sum of these terms has an error of order u S (u the unit
+ * roundoff), whatever |Qt| is: near equilibrium |Qt| << S.  S[c] per cell. */
+int or_rounding_scale(int N, double L, double lambda, int ncells, const double *f, double eps, double *S,
+                      int nthreads)
+{
+    int M = N * N * N;
+    int h = N / 2;
+    double dz = or_dzeta(L);
+    double omega = dz * dz * dz;
+    double *fh = (double *)malloc(sizeof(double) * 2 * (size_t)M * ncells);
+    or_dft_forward(N, L, ncells, f, fh);
+    for (int c = 0; c < ncells; ++c) S[c] = 0.0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    for (int c = 0; c < ncells; ++c) {
+        const double *F = fh + (size_t)2 * M * c;
+        double total = 0.0;
+#pragma omp parallel for schedule(dynamic, 4) reduction(+ : total)
+        for (int kf = 0; kf < M; ++kf) {
+            int k[3] = {kf / (N * N), (kf / N) % N, kf % N};
+            double acc = 0.0;
+            for (int m1 = 0; m1 < N; ++m1) {
+                int s1 = k[0] - m1 + h;
+                if (s1 < 0 || s1 > N - 1) continue;
+                for (int m2 = 0; m2 < N; ++m2) {
+                    int s2 = k[1] - m2 + h;
+                    if (s2 < 0 || s2 > N - 1) continue;
+                    for (int m3 = 0; m3 < N; ++m3) {
+                        int s3 = k[2] - m3 + h;
+                        if (s3 < 0 || s3 > N - 1) continue;
+                        int m[3] = {m1, m2, m3};
+                        int im = idx3(N, m1, m2, m3), is = idx3(N, s1, s2, s3);
+                        double a = hypot(F[2 * im], F[2 * im + 1]);
+                        double b = hypot(F[2 * is], F[2 * is + 1]);
+                        acc += fabs(or_ghat(N, L, lambda, k, m)) * a * b;
+                    }
+                }
+            }
+            total += omega * acc;
+        }
+        S[c] = pow(2.0 * OR_PI, -1.5) * omega * total / eps;
+    }
+    free(fh);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Moments and conservation, Sec. 2 ("moments") and Sec. 3.3.
  * Integration matrix C (5 x M): rows dv^3 * (1, v^1, v^2, v^3, |v|^2).      */

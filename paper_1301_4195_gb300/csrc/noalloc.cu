@@ -135,7 +135,8 @@ extern "C" int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, do
     }
     // Nothing in the array needs clearing: the forward passes write every
     // element of X, Y and F (zeros for the padding cells of the last group),
-    // the convolution every element of Qh, the inverse passes all of X', Y'.
+    // the convolution every element of Qh, the inverse passes (where the
+    // handle has no whole-cell inverse) all of X', Y'.
     void *base = nullptr;
     if (int rc = scratch_address(&base)) return rc;
     char *A = (char *)base;
@@ -161,6 +162,12 @@ extern "C" int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, do
     inv.part5 = (double *)(C + (nbuf - 2) * buffer_bytes(hd, ncells));
     if (int rc = launch_forward(fwd, f, ncells, stream)) return rc;
     if (int rc = launch_convolve(fwd, ncells, stream)) return rc;
+    // the steps after the convolution exactly as cs_collide takes them: the
+    // whole-cell inverse with the projection in the same launch where the
+    // handle has it (float, N <= 32), else the inverse passes and the
+    // projection kernels, so both entry points give the same bits
+    if (fused_available(inv))
+        return launch_inverse_project(inv, ncells, eps, conserve ? 1 : 0, 0.0, nullptr, 0.0, nullptr, 1.0, Q, stream);
     if (int rc = launch_inverse(inv, ncells, eps, Q, stream)) return rc;
     if (conserve) return launch_conserve(inv, Q, ncells, 1, 0.0, nullptr, 0.0, nullptr, 1.0, Q, nullptr, stream);
     return CS_OK;

@@ -12,8 +12,10 @@ a horizon t_end, in Heun steps of dt (cs_relax).  The server
   workspace), in arrival order; a float class whose table of every pair
   does not fit is built from the radius tables alone (CS_WEIGHTS_RADIUS:
   9 MB instead of 0.9 GB at N = 32), slower per step but admitted;
-* per iteration advances every active request of every class by one Heun
-  step: one cs_relax per class on its own stream (classes overlap on the
+* per iteration advances every active request of every class by a chunk of
+  Heun steps (at most max_chunk, and never past the end of any of the
+  class's requests, so each request takes exactly its own number of steps):
+  one cs_relax per class on its own stream (classes overlap on the
   device), or with batched=True one cs_relax_batched call over all active
   classes (a replayed graph with one branch per class and the float classes'
   convolutions as one persistent launch per evaluation); requests that
@@ -51,6 +53,7 @@ class Request:
     f0: np.ndarray            # [N, N, N] float64
     t_end: float              # horizon (time units)
     arrival: float = 0.0      # seconds on the server clock
+    bkw_K0: Optional[float] = None  # Maxwell-molecule request started from BKW data with this K
     # filled by the server
     steps_done: int = 0
     steps_total: int = 0
@@ -93,8 +96,9 @@ class Server:
 
     def __init__(self, L: float = 6.0, dt: float = 0.01, eps: float = 1.0, precision: str = "fp32",
                  mem_budget: Optional[int] = None, device=None, max_cells_per_class: int = 4096,
-                 radius_fallback: bool = True, batched: bool = False):
+                 radius_fallback: bool = True, batched: bool = False, max_chunk: int = 8):
         self.L, self.dt, self.eps, self.precision = L, dt, eps, precision
+        self.max_chunk = max(1, int(max_chunk))
         self.radius_fallback = radius_fallback
         self.batched = batched
         self.device = torch.device(device or "cuda")
@@ -208,25 +212,33 @@ class Server:
             else:
                 i += 1
 
+    def _chunk(self, reqs) -> int:
+        """Heun steps the next iteration may take without passing any request's end."""
+        return max(1, min([self.max_chunk] + [r.steps_total - r.steps_done for r in reqs]))
+
     def iterate(self) -> bool:
-        """One iteration: admit, one Heun step for every active request, retire.
-        Returns False when nothing is active or waiting."""
+        """One iteration: admit, a chunk of Heun steps for every active request,
+        retire.  Returns False when nothing is active or waiting."""
         self._admit()
         active = [c for c in self.classes.values() if c.reqs]
         if not active and not self.waiting:
             return False
+        steps = {}
         if self.batched and active:
-            for k in range(0, len(active), 16):  # at most 16 entries per batched call
-                part = active[k:k + 16]
+            k = self._chunk([r for c in active for r in c.reqs])  # one chunk for the shared graph
+            for j in range(0, len(active), 16):  # at most 16 entries per batched call
+                part = active[j:j + 16]
                 api.cs_relax_batched([(c.handle.ptr, c.buf[:len(c.reqs)], len(c.reqs)) for c in part], self.dt,
-                                     1, self.eps, stream=self.stream)
+                                     k, self.eps, stream=self.stream)
+            steps = {id(c): k for c in active}
         else:
             for c in active:
-                n = len(c.reqs)
-                api.cs_relax(c.handle.ptr, c.buf[:n], n, self.dt, self.eps, 1, stream=c.stream)
+                n, k = len(c.reqs), self._chunk(c.reqs)
+                api.cs_relax(c.handle.ptr, c.buf[:n], n, self.dt, self.eps, k, stream=c.stream)
+                steps[id(c)] = k
         for c in active:
             for r in c.reqs:
-                r.steps_done += 1
+                r.steps_done += steps[id(c)]
         for c in active:
             c.stream.synchronize()
             self._retire(c)
@@ -262,10 +274,13 @@ def percentile(xs, q):
 
 
 def poisson_requests(n: int, rate: float, seed: int = 13014195, Ns=(12, 16, 24, 32), lams=(0.0, 1.0),
-                     horizon=(0.1, 1.0), L: float = 6.0):
+                     horizon=(0.1, 1.0), L: float = 6.0, bkw_every: int = 0, bkw_K0: float = 0.6):
     """n requests with exponential inter-arrival times (mean 1/rate seconds),
     N and lambda uniform over the given sets, f0 a random 2-4 Maxwellian
-    mixture seeded per request id, horizon uniform in time units."""
+    mixture seeded per request id, horizon uniform in time units.  With
+    bkw_every = k > 0 every k-th request is a Maxwell-molecule one (lambda =
+    0) started from the BKW distribution with K = bkw_K0, whose exact
+    solution is known at every time."""
     from . import inputs
     rng = np.random.default_rng(seed)
     t, out = 0.0, []
@@ -273,15 +288,42 @@ def poisson_requests(n: int, rate: float, seed: int = 13014195, Ns=(12, 16, 24, 
         t += rng.exponential(1.0 / rate)
         N = int(rng.choice(Ns))
         lam = float(rng.choice(lams))
+        t_end = float(rng.uniform(*horizon))
+        if bkw_every and i % bkw_every == bkw_every - 1:
+            out.append(Request(rid=i, N=N, lam=0.0, f0=inputs.bkw(N, L, bkw_K0), t_end=t_end, arrival=t,
+                               bkw_K0=bkw_K0))
+            continue
         f0 = inputs.mixture(N, L, inputs.random_mixture_params(seed + i, 2, 4))
-        out.append(Request(rid=i, N=N, lam=lam, f0=f0, t_end=float(rng.uniform(*horizon)), arrival=t))
+        out.append(Request(rid=i, N=N, lam=lam, f0=f0, t_end=t_end, arrival=t))
     return out
 
 
-def serve_bench(n: int = 48, rate: float = 50.0, seed: int = 13014195, horizon=(0.1, 0.5), **kw) -> dict:
+def bkw_errors(done, L: float = 6.0, dt: float = 0.01) -> dict:
+    """Maxwell-molecule requests started from BKW data against the closed form
+    at their final time, K(t) = 1 - (1 - K0) exp(-t/6): the largest error
+    relative to the state's maximum and to the change of the exact solution
+    over the run."""
+    from . import inputs
+    out = {"requests": 0, "max_rel_to_state": 0.0, "max_rel_to_change": 0.0}
+    for r in done:
+        if r.bkw_K0 is None:
+            continue
+        t = r.steps_total * dt
+        K = 1.0 - (1.0 - r.bkw_K0) * np.exp(-t / 6.0)
+        ref = inputs.bkw(r.N, L, K)
+        err = float(np.abs(r.result - ref).max())
+        change = float(np.abs(ref - inputs.bkw(r.N, L, r.bkw_K0)).max())
+        out["requests"] += 1
+        out["max_rel_to_state"] = max(out["max_rel_to_state"], err / float(np.abs(ref).max()))
+        out["max_rel_to_change"] = max(out["max_rel_to_change"], err / change)
+    return out
+
+
+def serve_bench(n: int = 48, rate: float = 50.0, seed: int = 13014195, horizon=(0.1, 0.5), bkw_every: int = 0,
+                **kw) -> dict:
     """Run a Poisson workload through a fresh server; latency percentiles and
     throughput (nominal pair-updates/s = 2 N^6 per Heun step per request)."""
-    reqs = poisson_requests(n, rate, seed, horizon=horizon)
+    reqs = poisson_requests(n, rate, seed, horizon=horizon, bkw_every=bkw_every)
     srv = Server(**kw)
     srv.warm([(N, lam) for N in (12, 16, 24, 32) for lam in (0.0, 1.0)])  # resident tables, clock restarts
     t0 = time.perf_counter()
@@ -290,10 +332,13 @@ def serve_bench(n: int = 48, rate: float = 50.0, seed: int = 13014195, horizon=(
     srv.close()
     lat = [r.latency for r in done]
     pairs = sum(2 * r.steps_total * r.N ** 6 for r in done)
-    return {"requests": len(done), "rate_per_s": rate, "p50_s": percentile(lat, 50), "p99_s": percentile(lat, 99),
-            "mean_s": float(np.mean(lat)), "wall_s": wall, "iterations": srv.iterations,
-            "throughput_pair_updates_per_s": pairs / wall, "requests_per_s": len(done) / wall,
-            "horizon_time_units": list(horizon), "N_set": [12, 16, 24, 32], "lambda_set": [0, 1]}
+    out = {"requests": len(done), "rate_per_s": rate, "p50_s": percentile(lat, 50), "p99_s": percentile(lat, 99),
+           "mean_s": float(np.mean(lat)), "max_s": float(np.max(lat)), "wall_s": wall, "iterations": srv.iterations,
+           "throughput_pair_updates_per_s": pairs / wall, "requests_per_s": len(done) / wall,
+           "horizon_time_units": list(horizon), "N_set": [12, 16, 24, 32], "lambda_set": [0, 1]}
+    if bkw_every:
+        out["bkw"] = bkw_errors(done, srv.L, srv.dt)
+    return out
 
 
 if __name__ == "__main__":

@@ -57,3 +57,18 @@ def test_reference_arm_prints_one_complete_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"]
+
+
+def test_roofline_states_both_pair_counts():
+    """frac_executed counts the pairs the symmetrised kernel visits, P(N);
+    frac_effective_pairs the 27 N^6 / 64 valid pairs of the plain sum; both
+    at 6 FMA-pipe lane operations per pair and the same launch time."""
+    import bench
+    for N in (16, 32):
+        r = bench.conv_roofline(N, 256, 10.0)
+        ratio = r["frac_effective_pairs"] / r["frac_executed"]
+        assert abs(ratio - bench.valid_pairs_per_cell(N) / bench.unique_pairs_per_cell(N)) < 1e-12
+        assert 1.8 < ratio < 2.1  # the symmetrisation halves the work, up to the centre tiles
+        assert bench.valid_pairs_per_cell(N) == 27 * N ** 6 // 64
+        assert r["frac"] == r["frac_executed"]
+        assert abs(r["achieved"] - 6.0 * bench.unique_pairs_per_cell(N) * 256 / 10e-3 / 1e12) < 1e-9

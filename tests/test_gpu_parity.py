@@ -415,9 +415,9 @@ def test_launch_choices_give_identical_results(cs):
     best = cs.cs_autotune(h.ptr, nc)
     assert best > 0
     with pytest.raises(cs.CSError):
-        cs.cs_tune(h.ptr, 7, 1)
+        cs.cs_tune(h.ptr, 99, 1)
     with pytest.raises(cs.CSError):
-        cs.cs_tune_get(h.ptr, 7)
+        cs.cs_tune_get(h.ptr, 99)
     h.close()
 
 

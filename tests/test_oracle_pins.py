@@ -439,3 +439,37 @@ def test_sampled_convolution_equals_the_full_one(oracle_mod):
     ks = np.array([0, 5, 77, 200, 511, 256])
     part = oracle_mod.convolve_at(fh, N, L, 1.0, ks)
     assert np.array_equal(part, full[:, ks])
+
+
+# ------------------------------------------------- rounding scale (error yardstick)
+@pytest.mark.parametrize("lam", [0.0, 1.0])
+def test_rounding_scale_bruteforce_and_bound(oracle_mod, lam):
+    """S = (2 pi)^{-3/2} dzeta^3 sum_k omega sum_m |Ghat| |fhat_m| |fhat_{k-m}| / eps.
+    Brute force at N = 4 over the full weight table (every (k, m) pair, the
+    dropped ones masked by index arithmetic written here), and at N = 8 the
+    triangle inequality: every |Qt(v_j)| before the projection is at most S."""
+    N, L, eps = 4, 6.0, 0.7
+    f = I.random_mixture_cells(N, L, 2, first_id=77)
+    G = oracle_mod.ghat_table(N, L, lam)
+    fh = oracle_mod.dft_forward(f, N, L).reshape(2, -1)
+    h, M = N // 2, N ** 3
+    idx = np.arange(M)
+    k3 = np.stack([idx // (N * N), (idx // N) % N, idx % N], axis=1)
+    want = np.zeros(2)
+    dz = math.pi / L
+    for kf in range(M):
+        s = k3[kf][None, :] - k3 + h  # partner indices of every m
+        ok = np.all((s >= 0) & (s <= N - 1), axis=1)
+        sf = (s[:, 0] * N + s[:, 1]) * N + s[:, 2]
+        for c in range(2):
+            want[c] += dz ** 3 * np.sum(np.abs(G[kf, ok]) * np.abs(fh[c, ok]) * np.abs(fh[c, sf[ok]]))
+    want *= (2 * math.pi) ** -1.5 * dz ** 3 / eps
+    got = oracle_mod.rounding_scale(f, N, L, lam, eps=eps)
+    assert _rel(got, want) < 1e-13
+    N = 8
+    f = I.random_mixture_cells(N, L, 3, first_id=78)
+    S = oracle_mod.rounding_scale(f, N, L, lam)
+    qt = oracle_mod.collide(f, N, L, lam, conserve=False)
+    for c in range(3):
+        assert np.abs(qt[c]).max() <= S[c]
+        assert np.abs(qt[c]).max() > 1e-3 * S[c]  # a yardstick of the right size, not a loose bound
