@@ -102,6 +102,15 @@ def _load():
                                                    ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int]),
                 "or_rounding_scale": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                                      ctypes.c_int, _dp, ctypes.c_double, _dp, ctypes.c_int]),
+                "or_ghat_aniso": (ctypes.c_double, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                                    _dp, _ip, _ip]),
+                "or_convolve_b": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp,
+                                                 ctypes.c_int, _dp, _dp, ctypes.c_int]),
+                "or_collide_b": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp,
+                                                ctypes.c_int, _dp, ctypes.c_double, _dp, ctypes.c_int, ctypes.c_int]),
+                "or_q_bruteforce_b": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp,
+                                                     ctypes.c_int, _dp, ctypes.c_int, _dp, ctypes.c_int,
+                                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int]),
                 "or_max_threads": (ctypes.c_int, []),
             }
             for name, (res, args) in sigs.items():
@@ -227,6 +236,45 @@ def rounding_scale(f: np.ndarray, N: int, L: float, lam: float, eps: float = 1.0
     out = np.zeros(fc.shape[0])
     _load().or_rounding_scale(N, L, lam, fc.shape[0], _d(fc), eps, _d(out), nthreads)
     return out
+
+
+# --------------------------------------------- anisotropic scattering (Sec. 2, 2.2)
+def _moments(beta) -> np.ndarray:
+    b = np.ascontiguousarray(beta, dtype=np.float64).reshape(-1)
+    assert 1 <= b.shape[0] <= 16
+    return b
+
+
+def ghat_aniso(N: int, L: float, lam: float, beta, k, m) -> float:
+    """Ghat(xi_m, zeta_k) for B = |u|^lam b(cos theta), b given by its Legendre
+    moments beta_l = int_{S^2} b(sigma . u^) P_l(sigma . u^) dsigma (Funk-Hecke
+    reduction of the sphere integral, radial integrals of products of
+    spherical Bessel functions by quadrature)."""
+    b = _moments(beta)
+    kk = np.ascontiguousarray(k, dtype=np.int32)
+    mm = np.ascontiguousarray(m, dtype=np.int32)
+    return _load().or_ghat_aniso(N, L, lam, b.shape[0], _d(b), _i(kk), _i(mm))
+
+
+def convolve_b(fhat: np.ndarray, N: int, L: float, lam: float, beta, nthreads: int = 0) -> np.ndarray:
+    """The convolution of Sec. 3.2 with the anisotropic weights."""
+    b = _moments(beta)
+    fh = np.ascontiguousarray(fhat, dtype=np.complex128).reshape(-1, N ** 3)
+    fi = np.ascontiguousarray(np.stack([fh.real, fh.imag], axis=-1))
+    out = np.zeros_like(fi)
+    _load().or_convolve_b(N, L, lam, b.shape[0], _d(b), fh.shape[0], _d(fi), _d(out), nthreads)
+    return (out[..., 0] + 1j * out[..., 1]).reshape(fh.shape[0], N, N, N)
+
+
+def collide_b(f: np.ndarray, N: int, L: float, lam: float, beta, eps: float = 1.0,
+              conserve: bool = True, nthreads: int = 0) -> np.ndarray:
+    """P_N Qt(f) / eps with B = |u|^lam b(cos theta) (b by its Legendre moments)."""
+    b = _moments(beta)
+    fc = _cells(f, N)
+    out = np.zeros_like(fc)
+    _load().or_collide_b(N, L, lam, b.shape[0], _d(b), fc.shape[0], _d(fc), eps, _d(out), int(bool(conserve)),
+                         nthreads)
+    return out.reshape(-1, N, N, N)
 
 
 # ------------------------------------------------------ conservation (Sec. 3.3)
@@ -368,6 +416,18 @@ def strang_step2d(f: np.ndarray, N: int, L: float, lam: float, nx: int, ny: int,
 
 
 # ---------------------------------------------- direct collision integral (Sec. 2)
+def q_bruteforce_b(lam: float, r0: float, beta, mix, vpts, npan: int = 6, nr: int = 12,
+                   nth: int = 16, nph: int = 32, nthreads: int = 0) -> np.ndarray:
+    """q_bruteforce with B = |u|^lam b(cos theta), b(t) = sum_l (2l+1) beta_l P_l(t) / 4 pi."""
+    b = _moments(beta)
+    mx = np.ascontiguousarray(mix, dtype=np.float64).reshape(-1, 5)
+    vp = np.ascontiguousarray(vpts, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros(vp.shape[0])
+    _load().or_q_bruteforce_b(lam, r0, b.shape[0], _d(b), mx.shape[0], _d(mx), vp.shape[0], _d(vp), npan, nr,
+                              nth, nph, _d(out), nthreads)
+    return out
+
+
 def q_bruteforce(lam: float, r0: float, mix, vpts, npan: int = 6, nr: int = 12,
                  nth: int = 16, nph: int = 32, nthreads: int = 0) -> np.ndarray:
     """Quadrature of eq. (Q_general) with B = |u|^lam / 4 pi cut at |u| <= r0, for f a

@@ -307,6 +307,181 @@ double or_ghat(int N, double L, double lambda, const int *k, const int *m)
     return pref * or_ghat_radial_quad(a, b, c, r0, lambda, np, 24);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Anisotropic scattering, Sec. 2 (B = |u|^lambda b(cos theta)) with the
+ * weights of Sec. 2.2 left as integrals (the paper computes only b = 1/4pi;
+ * Sec. 4.2 notes the same convolution serves anisotropic b).  The sphere
+ * integral in G(u, zeta) is reduced with the Funk-Hecke theorem and the
+ * angular part of the Fourier transform in u with the addition theorem of
+ * Legendre polynomials:
+ *   Ghat(xi, zeta) = sqrt(2/pi) [ sum_l (2l+1) (-1)^l beta_l P_l(cos g) R_l
+ *                                 - beta_0 int_0^r0 r^{lambda+2} sinc(|xi| r) dr ],
+ *   R_l = int_0^r0 r^{lambda+2} j_l(|zeta| r / 2) j_l(|xi - zeta/2| r) dr,
+ * cos g the cosine between zeta and xi - zeta/2, j_l the spherical Bessel
+ * functions and beta_l = int_{S^2} b(sigma . u^) P_l(sigma . u^) dsigma the
+ * Legendre moments of b (beta_0 = 1 under the normalisation of Sec. 2;
+ * b(t) = sum_l (2l+1) beta_l P_l(t) / 4pi).  beta_0 = 1 and no other moment
+ * is the isotropic case.                                                    */
+
+/* Legendre polynomial P_l(t) by the three-term recurrence */
+static double legendre_p(int l, double t)
+{
+    double p0 = 1.0, p1 = t;
+    if (l == 0) return p0;
+    for (int n = 1; n < l; ++n) {
+        double p2 = ((2.0 * n + 1.0) * t * p1 - n * p0) / (n + 1.0);
+        p0 = p1;
+        p1 = p2;
+    }
+    return p1;
+}
+
+/* spherical Bessel function j_l(x), x >= 0: the power series
+ *   j_l(x) = x^l / (2l+1)!! sum_k (-x^2/2)^k / (k! (2l+3)(2l+5)...(2l+2k+1))
+ * below x = l + 1, the upward recurrence j_{n+1} = (2n+1)/x j_n - j_{n-1}
+ * from j_0 = sin x / x, j_1 = sin x / x^2 - cos x / x above (stable there) */
+static double sph_bessel(int l, double x)
+{
+    if (x < l + 1.0) {
+        double lead = 1.0;
+        for (int i = 1; i <= l; ++i) lead *= x / (2.0 * i + 1.0);
+        double term = 1.0, sum = 1.0;
+        for (int k = 1; k < 200; ++k) {
+            term *= -0.5 * x * x / (k * (2.0 * l + 2.0 * k + 1.0));
+            sum += term;
+            if (fabs(term) < 1e-18 * fabs(sum)) break;
+        }
+        return lead * sum;
+    }
+    double j0 = sin(x) / x;
+    if (l == 0) return j0;
+    double j1 = sin(x) / (x * x) - cos(x) / x;
+    for (int n = 1; n < l; ++n) {
+        double j2 = (2.0 * n + 1.0) / x * j1 - j0;
+        j0 = j1;
+        j1 = j2;
+    }
+    return j1;
+}
+
+/* R_l(a, b) and, with l < 0, the loss integral int r^{lambda+2} j_0(a r) dr,
+ * by composite Gauss-Legendre (first panel graded toward r = 0, as above) */
+static double radial_l_quad(int l, double a, double b, double r0, double lam)
+{
+    int nodes = 24;
+    double x[24], w[24];
+    or_gauss_legendre(nodes, x, w);
+    int npanel = (int)ceil((a + b) * r0 / 2.0) + 4;
+    double h = r0 / npanel;
+    double total = 0.0;
+    for (int p = 0; p < npanel; ++p) {
+        int nsub = (p == 0) ? 12 : 1;
+        for (int sidx = 0; sidx < nsub; ++sidx) {
+            double lo, hi;
+            if (p == 0) {
+                hi = h / pow(2.0, (double)(nsub - 1 - sidx));
+                lo = (sidx == 0) ? 0.0 : h / pow(2.0, (double)(nsub - sidx));
+            } else {
+                lo = p * h;
+                hi = (p + 1) * h;
+            }
+            double mid = 0.5 * (lo + hi), half = 0.5 * (hi - lo);
+            for (int i = 0; i < nodes; ++i) {
+                double r = mid + half * x[i];
+                double g = (l < 0) ? sph_bessel(0, a * r) : sph_bessel(l, a * r) * sph_bessel(l, b * r);
+                total += half * w[i] * pow(r, lam + 2.0) * g;
+            }
+        }
+    }
+    return total;
+}
+
+/* the weight of a collision model: isotropic (nl = 0) or given by the
+ * Legendre moments of b.  rtab / btab, when set, hold the radial integrals
+ * R_l(kk, bb) and the loss integrals of every integer squared radius of the
+ * grid (each the same radial_l_quad value the direct route computes), so a
+ * convolution evaluates each distinct integral once instead of once per pair. */
+struct or_model {
+    double lambda;
+    int nl;
+    const double *beta;
+    const double *rtab; /* [nl][nkk][nbb] */
+    const double *btab; /* [nkk] */
+    int nkk, nbb;
+};
+
+static double aniso_weight(const struct or_model *md, int N, double L, const int *k, const int *m)
+{
+    double dz = or_dzeta(L);
+    double r0 = L;
+    long kk = 0, mm = 0, bb = 0, kd = 0;
+    for (int d = 0; d < 3; ++d) {
+        long kp = k[d] - N / 2, mp = m[d] - N / 2, dd = 2 * mp - kp;
+        kk += kp * kp;
+        mm += mp * mp;
+        bb += dd * dd;
+        kd += kp * dd; /* zeta . (2 xi - zeta) in units of dzeta^2 */
+    }
+    if (kk == 0) return 0.0; /* G(u, 0) = 0 */
+    double a = 0.5 * dz * sqrt((double)kk); /* |zeta| / 2 */
+    double b = 0.5 * dz * sqrt((double)bb); /* |xi - zeta / 2| */
+    double c = dz * sqrt((double)mm);       /* |xi| */
+    double cg = (bb == 0) ? 0.0 : (double)kd / (sqrt((double)kk) * sqrt((double)bb));
+    double gain = 0.0;
+    for (int l = 0; l < md->nl; ++l) {
+        if (md->beta[l] == 0.0) continue;
+        if (l > 0 && bb == 0) continue; /* j_l(0) = 0 for l > 0 */
+        double sgn = (l % 2) ? -1.0 : 1.0;
+        double R = md->rtab ? md->rtab[((size_t)l * md->nkk + kk) * md->nbb + bb]
+                            : radial_l_quad(l, a, b, r0, md->lambda);
+        gain += (2.0 * l + 1.0) * sgn * md->beta[l] * legendre_p(l, cg) * R;
+    }
+    double lossint = md->btab ? md->btab[mm] : radial_l_quad(-1, c, 0.0, r0, md->lambda);
+    return sqrt(2.0 / OR_PI) * (gain - md->beta[0] * lossint);
+}
+
+double or_ghat_aniso(int N, double L, double lambda, int nl, const double *beta, const int *k, const int *m)
+{
+    struct or_model md = {lambda, nl, beta, NULL, NULL, 0, 0};
+    return aniso_weight(&md, N, L, k, m);
+}
+
+/* the radial integrals of every integer squared radius of an N-grid:
+ * |zeta|^2 / dzeta^2 = kk <= 3 (N/2)^2, |2 xi - zeta|^2 / dzeta^2 = bb <= 3 (N-1)^2,
+ * |xi|^2 / dzeta^2 = mm <= 3 (N/2)^2 */
+static void aniso_tables(struct or_model *md, int N, double L, double **rt, double **bt)
+{
+    double dz = or_dzeta(L);
+    int nkk = 3 * (N / 2) * (N / 2) + 1, nbb = 3 * (N - 1) * (N - 1) + 1;
+    double *R = (double *)calloc((size_t)md->nl * nkk * nbb, sizeof(double));
+    double *B = (double *)calloc((size_t)nkk, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int row = 0; row < md->nl * nkk; ++row) {
+        int l = row / nkk, kk = row % nkk;
+        if (md->beta[l] == 0.0 || kk == 0) continue;
+        double a = 0.5 * dz * sqrt((double)kk);
+        for (int bb = 0; bb < nbb; ++bb) {
+            if (l > 0 && bb == 0) continue;
+            double b = 0.5 * dz * sqrt((double)bb);
+            R[((size_t)l * nkk + kk) * nbb + bb] = radial_l_quad(l, a, b, L, md->lambda);
+        }
+    }
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int mm = 0; mm < nkk; ++mm) B[mm] = radial_l_quad(-1, dz * sqrt((double)mm), 0.0, L, md->lambda);
+    md->rtab = R;
+    md->btab = B;
+    md->nkk = nkk;
+    md->nbb = nbb;
+    *rt = R;
+    *bt = B;
+}
+
+static double model_ghat(const struct or_model *md, int N, double L, const int *k, const int *m)
+{
+    if (md->nl > 0) return aniso_weight(md, N, L, k, m);
+    return or_ghat(N, L, md->lambda, k, m);
+}
+
 /* Same, always through the quadrature route (independent check). */
 double or_ghat_quad(int N, double L, double lambda, const int *k, const int *m,
                     int nodes)
@@ -349,8 +524,8 @@ int or_ghat_table(int N, double L, double lambda, double *out)
  * the zeta_k outputs over threads, as in Sec. 4.1.                          */
 /* One output zeta_k of the convolution for ncells cells: acc[2c], acc[2c+1]
  * receive the real and imaginary sums (before the factor omega).            */
-static void convolve_one(int N, double L, double lambda, const int *k, int ncells, const double *fhat,
-                         double *acc)
+static void convolve_one(int N, double L, const struct or_model *md, const int *k, int ncells,
+                         const double *fhat, double *acc)
 {
     int M = N * N * N;
     int h = N / 2;
@@ -365,7 +540,7 @@ static void convolve_one(int N, double L, double lambda, const int *k, int ncell
                 int s3 = k[2] - m3 + h;
                 if (s3 < 0 || s3 > N - 1) continue;
                 int m[3] = {m1, m2, m3};
-                double g = or_ghat(N, L, lambda, k, m);
+                double g = model_ghat(md, N, L, k, m);
                 int im = idx3(N, m1, m2, m3), is = idx3(N, s1, s2, s3);
                 for (int c = 0; c < ncells; ++c) {
                     const double *F = fhat + (size_t)2 * M * c;
@@ -379,8 +554,8 @@ static void convolve_one(int N, double L, double lambda, const int *k, int ncell
     }
 }
 
-int or_convolve(int N, double L, double lambda, int ncells, const double *fhat,
-                double *qhat, int nthreads)
+static int convolve_model(int N, double L, const struct or_model *md, int ncells, const double *fhat,
+                          double *qhat, int nthreads)
 {
     int M = N * N * N;
     double dz = or_dzeta(L);
@@ -394,7 +569,7 @@ int or_convolve(int N, double L, double lambda, int ncells, const double *fhat,
 #pragma omp for schedule(dynamic, 4)
         for (int kf = 0; kf < M; ++kf) {
             int k[3] = {kf / (N * N), (kf / N) % N, kf % N};
-            convolve_one(N, L, lambda, k, ncells, fhat, acc);
+            convolve_one(N, L, md, k, ncells, fhat, acc);
             for (int c = 0; c < ncells; ++c) {
                 qhat[(size_t)2 * M * c + 2 * kf] = omega * acc[2 * c];
                 qhat[(size_t)2 * M * c + 2 * kf + 1] = omega * acc[2 * c + 1];
@@ -405,12 +580,35 @@ int or_convolve(int N, double L, double lambda, int ncells, const double *fhat,
     return 0;
 }
 
+int or_convolve(int N, double L, double lambda, int ncells, const double *fhat,
+                double *qhat, int nthreads)
+{
+    struct or_model md = {lambda, 0, NULL, NULL, NULL, 0, 0};
+    return convolve_model(N, L, &md, ncells, fhat, qhat, nthreads);
+}
+
+int or_convolve_b(int N, double L, double lambda, int nl, const double *beta, int ncells, const double *fhat,
+                  double *qhat, int nthreads)
+{
+    struct or_model md = {lambda, nl, beta, NULL, NULL, 0, 0};
+    double *rt, *bt;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    aniso_tables(&md, N, L, &rt, &bt);
+    int rc = convolve_model(N, L, &md, ncells, fhat, qhat, nthreads);
+    free(rt);
+    free(bt);
+    return rc;
+}
+
 /* The convolution at nk selected outputs kf[i] (flat indices) only, for
  * grids too large for the full sum: qhat [ncells][nk][2].  Each output is
  * the same sum as in or_convolve, bit for bit.                              */
 int or_convolve_at(int N, double L, double lambda, int ncells, const double *fhat, int nk, const int *kf,
                    double *qhat, int nthreads)
 {
+    struct or_model md = {lambda, 0, NULL, NULL, NULL, 0, 0};
     double dz = or_dzeta(L);
     double omega = dz * dz * dz;
 #ifdef _OPENMP
@@ -422,7 +620,7 @@ int or_convolve_at(int N, double L, double lambda, int ncells, const double *fha
 #pragma omp for schedule(dynamic, 1)
         for (int i = 0; i < nk; ++i) {
             int k[3] = {kf[i] / (N * N), (kf[i] / N) % N, kf[i] % N};
-            convolve_one(N, L, lambda, k, ncells, fhat, acc);
+            convolve_one(N, L, &md, k, ncells, fhat, acc);
             for (int c = 0; c < ncells; ++c) {
                 qhat[(size_t)2 * nk * c + 2 * i] = omega * acc[2 * c];
                 qhat[(size_t)2 * nk * c + 2 * i + 1] = omega * acc[2 * c + 1];
@@ -587,19 +785,42 @@ int or_conserve(int N, double L, int ncells, double *Q)
 /* ------------------------------------------------------------------------ */
 /* The whole collision evaluation: forward transform, weighted convolution,
  * inverse transform (real part, / eps) and, if conserve != 0, the projection. */
-int or_collide(int N, double L, double lambda, int ncells, const double *f,
-               double eps, double *Q, int conserve, int nthreads)
+static int collide_model(int N, double L, const struct or_model *md, int ncells, const double *f,
+                         double eps, double *Q, int conserve, int nthreads)
 {
     int M = N * N * N;
     double *fh = (double *)malloc(sizeof(double) * 2 * (size_t)M * ncells);
     double *qh = (double *)malloc(sizeof(double) * 2 * (size_t)M * ncells);
     or_dft_forward(N, L, ncells, f, fh);
-    or_convolve(N, L, lambda, ncells, fh, qh, nthreads);
+    convolve_model(N, L, md, ncells, fh, qh, nthreads);
     or_dft_inverse(N, L, ncells, qh, eps, Q, NULL);
     if (conserve) or_conserve(N, L, ncells, Q);
     free(fh);
     free(qh);
     return 0;
+}
+
+int or_collide(int N, double L, double lambda, int ncells, const double *f,
+               double eps, double *Q, int conserve, int nthreads)
+{
+    struct or_model md = {lambda, 0, NULL, NULL, NULL, 0, 0};
+    return collide_model(N, L, &md, ncells, f, eps, Q, conserve, nthreads);
+}
+
+/* the collision evaluation with an anisotropic b (Legendre moments beta) */
+int or_collide_b(int N, double L, double lambda, int nl, const double *beta, int ncells, const double *f,
+                 double eps, double *Q, int conserve, int nthreads)
+{
+    struct or_model md = {lambda, nl, beta, NULL, NULL, 0, 0};
+    double *rt, *bt;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    aniso_tables(&md, N, L, &rt, &bt);
+    int rc = collide_model(N, L, &md, ncells, f, eps, Q, conserve, nthreads);
+    free(rt);
+    free(bt);
+    return rc;
 }
 
 /* Space-homogeneous second-order Runge-Kutta (Heun), Sec. 3.1, on
@@ -955,10 +1176,20 @@ static double maxw_mix(int nmix, const double *mix, const double *v)
     return s;
 }
 
-int or_q_bruteforce(double lambda, double r0, int nmix, const double *mix, int nv,
-                    const double *vpts, int npan, int nr, int nth, int nph, double *out,
-                    int nthreads)
+/* b(t) from its Legendre moments, b(t) = sum_l (2l+1) beta_l P_l(t) / 4pi;
+ * nl = 0 is the isotropic 1/4pi */
+static double b_of(int nl, const double *beta, double t)
 {
+    if (nl == 0) return 1.0 / (4.0 * OR_PI);
+    double s = 0.0;
+    for (int l = 0; l < nl; ++l) s += (2.0 * l + 1.0) * beta[l] * legendre_p(l, t);
+    return s / (4.0 * OR_PI);
+}
+
+int or_q_bruteforce_b(double lambda, double r0, int nl, const double *beta, int nmix, const double *mix, int nv,
+                      const double *vpts, int npan, int nr, int nth, int nph, double *out, int nthreads)
+{
+    double b0 = nl == 0 ? 1.0 : beta[0]; /* int b dsigma */
     double *xr = (double *)malloc(sizeof(double) * nr), *wr = (double *)malloc(sizeof(double) * nr);
     double *xt = (double *)malloc(sizeof(double) * nth), *wt = (double *)malloc(sizeof(double) * nth);
     or_gauss_legendre(nr, xr, wr);
@@ -991,7 +1222,7 @@ int or_q_bruteforce(double lambda, double r0, int nmix, const double *mix, int n
                 for (int io = 0; io < nsph; ++io) {
                     double u[3] = {r * dir[3 * io], r * dir[3 * io + 1], r * dir[3 * io + 2]};
                     double vs[3] = {v[0] - u[0], v[1] - u[1], v[2] - u[2]};
-                    double loss = fv * maxw_mix(nmix, mix, vs);
+                    double loss = b0 * fv * maxw_mix(nmix, mix, vs);
                     double gain = 0.0;
                     for (int is = 0; is < nsph; ++is) {
                         double rs[3] = {r * dir[3 * is], r * dir[3 * is + 1], r * dir[3 * is + 2]};
@@ -1000,15 +1231,25 @@ int or_q_bruteforce(double lambda, double r0, int nmix, const double *mix, int n
                             vp[d] = v[d] + 0.5 * (rs[d] - u[d]);
                             vps[d] = v[d] - 0.5 * (u[d] + rs[d]);
                         }
-                        gain += dw[is] * maxw_mix(nmix, mix, vp) * maxw_mix(nmix, mix, vps);
+                        double ct = dir[3 * is] * dir[3 * io] + dir[3 * is + 1] * dir[3 * io + 1] +
+                                    dir[3 * is + 2] * dir[3 * io + 2]; /* cos theta = sigma . u^ */
+                        gain += dw[is] * b_of(nl, beta, ct) * maxw_mix(nmix, mix, vp) * maxw_mix(nmix, mix, vps);
                     }
-                    total += wrr * dw[io] * (gain / (4.0 * OR_PI) - loss);
+                    total += wrr * dw[io] * (gain - loss);
                 }
             }
         out[iv] = total;
     }
     free(xr); free(wr); free(xt); free(wt); free(dir); free(dw);
     return 0;
+}
+
+/* the isotropic case, B = |u|^lambda / 4pi */
+int or_q_bruteforce(double lambda, double r0, int nmix, const double *mix, int nv,
+                    const double *vpts, int npan, int nr, int nth, int nph, double *out,
+                    int nthreads)
+{
+    return or_q_bruteforce_b(lambda, r0, 0, NULL, nmix, mix, nv, vpts, npan, nr, nth, nph, out, nthreads);
 }
 
 int or_max_threads(void)
