@@ -17,10 +17,11 @@
  *     [-L, L]^3, v_k = dv (k - N/2), dv = 2L/N, zeta_k = dzeta (k - N/2),
  *     dzeta = pi/L.  A cell's distribution is N^3 doubles in C order, flat
  *     index (k1*N + k2)*N + k3.  A batch of cells is [ncells][N^3].
- *   - Collision kernel B = |u|^lambda / (4 pi) (isotropic, Sec. 2.2),
- *     -3 < lambda <= 1 (soft potentials, Maxwell molecules, variable hard
- *     potentials, hard spheres; Sec. 2), weight integral cut at r0 = L,
- *     beta = 1.
+ *   - Collision kernel B = |u|^lambda / (4 pi) (isotropic, Sec. 2.2), or
+ *     |u|^lambda b(cos theta) with b given by its Legendre moments
+ *     (cs_weights_build_aniso), -3 < lambda <= 1 (soft potentials, Maxwell
+ *     molecules, variable hard potentials, hard spheres; Sec. 2), weight
+ *     integral cut at r0 = L, beta = 1.
  *   - Pointers marked "device" are CUDA device pointers owned by the caller
  *     (e.g. allocated by PyTorch); "host" pointers are ordinary memory.
  *     Device arrays must be 8-byte aligned and must not overlap unless a
@@ -111,6 +112,30 @@ int cs_tile_layout(int N, int precision, int *map, int cap, int *entries);
  * Errors: CS_EINVAL, CS_ENOMEM, CS_ECUDA. */
 int cs_weights_build(int N, double L, double lambda, int precision, cudaStream_t stream,
                      cs_handle_t *out);
+
+/* cs_weights_build for an anisotropic scattering kernel B = |u|^lambda
+ * b(cos theta) (Sec. 2; the paper computes the weights of Sec. 2.2 only for
+ * the isotropic b = 1/4pi, and notes in Sec. 4.2 that the same weighted
+ * convolution serves anisotropic scattering).  b is given by its Legendre
+ * moments
+ *   moments[l] = int_{S^2} b(sigma . u^) P_l(sigma . u^) dsigma,  l < nmom,
+ * i.e. b(t) = sum_l (2l + 1) moments[l] P_l(t) / 4pi; moments[0] is the total
+ * integral of b (1 under the normalisation of Sec. 2), and {1} alone is the
+ * isotropic case.  The weights are
+ *   Ghat(xi, zeta) = sqrt(2/pi) [ sum_l (2l+1) (-1)^l moments[l] P_l(cos g) R_l
+ *                                 - moments[0] int_0^r0 r^{lambda+2} sinc(|xi| r) dr ]
+ * with R_l = int_0^r0 r^{lambda+2} j_l(|zeta| r/2) j_l(|xi - zeta/2| r) dr and
+ * cos g the cosine between zeta and xi - zeta/2 (the Funk-Hecke reduction of
+ * the sphere integral in G, Sec. 2.2).  Odd moments do not change Q (for
+ * identical particles only b(t) + b(-t) enters the convolution); the table
+ * keeps the symmetrised weights as for isotropic handles, so every other call
+ * works unchanged.  Radius tables are not built (CS_TUNE_WEIGHTS = 2 is
+ * refused); cs_weights_sample returns the unsymmetrised Ghat with every moment.
+ *   moments (host) [nmom], 1 <= nmom <= 16, finite, moments[0] > 0
+ *   precision CS_FP64 or CS_FP32 (not CS_WEIGHTS_RADIUS)
+ *   other arguments and errors as cs_weights_build. */
+int cs_weights_build_aniso(int N, double L, double lambda, const double *moments, int nmom, int precision,
+                           cudaStream_t stream, cs_handle_t *out);
 
 /* Free the handle, its weight table and its workspace.  NULL is a no-op.
  * The caller must make sure no work using the handle is still in flight. */

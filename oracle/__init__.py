@@ -111,6 +111,16 @@ def _load():
                 "or_q_bruteforce_b": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp,
                                                      ctypes.c_int, _dp, ctypes.c_int, _dp, ctypes.c_int,
                                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int]),
+                "or_transport3d_rhs": (ctypes.c_int, [ctypes.c_int, ctypes.c_double] + [ctypes.c_int] * 3 +
+                                       [_dp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _dp,
+                                        _dp]),
+                "or_transport3d_rk2": (ctypes.c_int, [ctypes.c_int, ctypes.c_double] + [ctypes.c_int] * 3 +
+                                       [_dp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _dp,
+                                        ctypes.c_double]),
+                "or_strang_step3d": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double] +
+                                     [ctypes.c_int] * 3 + [_dp, _dp, ctypes.c_double, ctypes.c_double,
+                                                           ctypes.c_double, _dp, _dp, ctypes.c_double,
+                                                           ctypes.c_double, ctypes.c_int]),
                 "or_max_threads": (ctypes.c_int, []),
             }
             for name, (res, args) in sigs.items():
@@ -413,6 +423,48 @@ def strang_step2d(f: np.ndarray, N: int, L: float, lam: float, nx: int, ny: int,
     ff = np.ascontiguousarray(ffar, dtype=np.float64).reshape(-1)
     _load().or_strang_step2d(N, L, lam, nx, ny, _d(fc), _d(dxa), dy, Tw, _d(vw), _d(ff), dt, eps, nthreads)
     return fc.reshape(nx, ny, N, N, N)
+
+
+# ---------------------------------------------- three space dimensions
+def transport3d_rhs(f: np.ndarray, N: int, L: float, nx: int, ny: int, nz: int, dx: np.ndarray, dy: float,
+                    dz: float, Tw: float, Vw, ffar: np.ndarray) -> np.ndarray:
+    """Right-hand side of the 3-D transport, f [nx][ny][nz][N,N,N] (x: the wall
+    problem's grid and boundaries; y, z: periodic, uniform dy, dz)."""
+    fc = np.ascontiguousarray(f, dtype=np.float64).reshape(nx * ny * nz, N ** 3).copy()
+    dxa = np.ascontiguousarray(dx, dtype=np.float64)
+    vw = np.ascontiguousarray(Vw, dtype=np.float64)
+    ff = np.ascontiguousarray(ffar, dtype=np.float64).reshape(-1)
+    out = np.empty_like(fc)
+    rc = _load().or_transport3d_rhs(N, L, nx, ny, nz, _d(fc), _d(dxa), dy, dz, Tw, _d(vw), _d(ff), _d(out))
+    if rc != 0:
+        raise ValueError("bad 3-D grid")
+    return out.reshape(nx, ny, nz, N, N, N)
+
+
+def transport3d_rk2(f: np.ndarray, N: int, L: float, nx: int, ny: int, nz: int, dx: np.ndarray, dy: float,
+                    dz: float, Tw: float, Vw, ffar: np.ndarray, dt: float) -> np.ndarray:
+    """One Heun step of the 3-D transport."""
+    fc = np.ascontiguousarray(f, dtype=np.float64).reshape(nx * ny * nz, N ** 3).copy()
+    dxa = np.ascontiguousarray(dx, dtype=np.float64)
+    vw = np.ascontiguousarray(Vw, dtype=np.float64)
+    ff = np.ascontiguousarray(ffar, dtype=np.float64).reshape(-1)
+    if _load().or_transport3d_rk2(N, L, nx, ny, nz, _d(fc), _d(dxa), dy, dz, Tw, _d(vw), _d(ff), dt) != 0:
+        raise ValueError("bad 3-D grid")
+    return fc.reshape(nx, ny, nz, N, N, N)
+
+
+def strang_step3d(f: np.ndarray, N: int, L: float, lam: float, nx: int, ny: int, nz: int, dx: np.ndarray,
+                  dy: float, dz: float, Tw: float, Vw, ffar: np.ndarray, dt: float, eps: float = 1.0,
+                  nthreads: int = 0) -> np.ndarray:
+    """Strang step T(dt/2) C(dt) T(dt/2) with the 3-D transport."""
+    fc = np.ascontiguousarray(f, dtype=np.float64).reshape(nx * ny * nz, N ** 3).copy()
+    dxa = np.ascontiguousarray(dx, dtype=np.float64)
+    vw = np.ascontiguousarray(Vw, dtype=np.float64)
+    ff = np.ascontiguousarray(ffar, dtype=np.float64).reshape(-1)
+    if _load().or_strang_step3d(N, L, lam, nx, ny, nz, _d(fc), _d(dxa), dy, dz, Tw, _d(vw), _d(ff), dt, eps,
+                                nthreads) != 0:
+        raise ValueError("bad 3-D grid")
+    return fc.reshape(nx, ny, nz, N, N, N)
 
 
 # ---------------------------------------------- direct collision integral (Sec. 2)

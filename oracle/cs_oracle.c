@@ -1155,6 +1155,122 @@ int or_strang_step2d(int N, double L, double lambda, int nx, int ny, double *f, 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Transport in three space dimensions (Sec. 3.4: the scheme carries over to
+ * higher dimensions): x is the wall direction of the 1-D problem, y and z are
+ * periodic with uniform cells dy, dz.  Cell (i, j, l) is stored at
+ * ((i ny + j) nz + l) N^3.  The semi-discrete scheme adds the three
+ * directions' flux differences (no splitting):
+ *   d f/dt = -(F_{i+1/2} - F_{i-1/2})/dx_i - (H_{j+1/2} - H_{j-1/2})/dy
+ *            - (K_{l+1/2} - K_{l-1/2})/dz,
+ * F the 1-D flux on each x-row, H and K the second-order upwind fluxes with
+ * velocity components v2 and v3 and the three-argument minmod slope.         */
+static void periodic_rhs(size_t M, int n, double h, double vel, const double *col, double *r)
+{
+    /* col[j] for j = 0 .. n-1 of one periodic line at one velocity; r[j] -= (P_{j+1/2} - P_{j-1/2}) / h */
+    for (int j = 0; j < n; ++j) {
+#define FP(jj) col[(((jj) % n) + n) % n]
+#define SLP(jj) minmod3((FP((jj) + 1) - FP(jj)) / h, (FP(jj) - FP((jj) - 1)) / h, \
+                        (FP((jj) + 1) - FP((jj) - 1)) / (2.0 * h))
+        double pp, pm; /* P_{j+1/2}, P_{j-1/2} */
+        if (vel >= 0) {
+            pp = vel * (FP(j) + 0.5 * h * SLP(j));
+            pm = vel * (FP(j - 1) + 0.5 * h * SLP(j - 1));
+        } else {
+            pp = vel * (FP(j + 1) - 0.5 * h * SLP(j + 1));
+            pm = vel * (FP(j) - 0.5 * h * SLP(j));
+        }
+#undef SLP
+#undef FP
+        r[j] -= (pp - pm) / h;
+    }
+    (void)M;
+}
+
+static void transport_rhs_3d(int N, double L, int nx, int ny, int nz, const double *f, const double *dx,
+                             double dy, double dzs, double Tw, const double *Vw, const double *ffar, double *rhs)
+{
+    size_t M = (size_t)N * N * N;
+    double dv = or_dv(N, L);
+    int nl = ny > nz ? ny : nz;
+    double *row = (double *)malloc(sizeof(double) * M * nx);
+    double *rr = (double *)malloc(sizeof(double) * M * nx);
+    double *col = (double *)malloc(sizeof(double) * nl);
+    double *rc = (double *)malloc(sizeof(double) * nl);
+#define IDX(i, j, l) (M * (((size_t)(i) * ny + (j)) * nz + (l)))
+    /* x: the 1-D right-hand side of every (j, l) row */
+    for (int j = 0; j < ny; ++j)
+        for (int l = 0; l < nz; ++l) {
+            for (int i = 0; i < nx; ++i) memcpy(row + M * i, f + IDX(i, j, l), sizeof(double) * M);
+            transport_rhs(N, L, nx, row, dx, Tw, Vw, ffar, rr);
+            for (int i = 0; i < nx; ++i) memcpy(rhs + IDX(i, j, l), rr + M * i, sizeof(double) * M);
+        }
+    for (size_t v = 0; v < M; ++v) {
+        double v2 = dv * ((int)((v / N) % N) - N / 2);
+        double v3 = dv * ((int)(v % N) - N / 2);
+        for (int i = 0; i < nx; ++i) {
+            /* y: periodic lines over j at fixed (i, l) */
+            for (int l = 0; l < nz; ++l) {
+                for (int j = 0; j < ny; ++j) {
+                    col[j] = f[IDX(i, j, l) + v];
+                    rc[j] = rhs[IDX(i, j, l) + v];
+                }
+                periodic_rhs(M, ny, dy, v2, col, rc);
+                for (int j = 0; j < ny; ++j) rhs[IDX(i, j, l) + v] = rc[j];
+            }
+            /* z: periodic lines over l at fixed (i, j) */
+            for (int j = 0; j < ny; ++j) {
+                for (int l = 0; l < nz; ++l) {
+                    col[l] = f[IDX(i, j, l) + v];
+                    rc[l] = rhs[IDX(i, j, l) + v];
+                }
+                periodic_rhs(M, nz, dzs, v3, col, rc);
+                for (int l = 0; l < nz; ++l) rhs[IDX(i, j, l) + v] = rc[l];
+            }
+        }
+    }
+#undef IDX
+    free(row);
+    free(rr);
+    free(col);
+    free(rc);
+}
+
+int or_transport3d_rhs(int N, double L, int nx, int ny, int nz, const double *f, const double *dx, double dy,
+                       double dzs, double Tw, const double *Vw, const double *ffar, double *rhs)
+{
+    if (nx < 2 || ny < 1 || nz < 1 || !(dy > 0) || !(dzs > 0)) return -1;
+    transport_rhs_3d(N, L, nx, ny, nz, f, dx, dy, dzs, Tw, Vw, ffar, rhs);
+    return 0;
+}
+
+/* one Heun step of length dt of the 3-D transport */
+int or_transport3d_rk2(int N, double L, int nx, int ny, int nz, double *f, const double *dx, double dy,
+                       double dzs, double Tw, const double *Vw, const double *ffar, double dt)
+{
+    if (nx < 2 || ny < 1 || nz < 1 || !(dy > 0) || !(dzs > 0)) return -1;
+    size_t n = (size_t)N * N * N * nx * ny * nz;
+    double *r = (double *)malloc(sizeof(double) * n);
+    double *f1 = (double *)malloc(sizeof(double) * n);
+    transport_rhs_3d(N, L, nx, ny, nz, f, dx, dy, dzs, Tw, Vw, ffar, r);
+    for (size_t i = 0; i < n; ++i) f1[i] = f[i] + dt * r[i];
+    transport_rhs_3d(N, L, nx, ny, nz, f1, dx, dy, dzs, Tw, Vw, ffar, r);
+    for (size_t i = 0; i < n; ++i) f[i] = 0.5 * (f[i] + f1[i] + dt * r[i]);
+    free(r);
+    free(f1);
+    return 0;
+}
+
+/* Strang step T(dt/2) C(dt) T(dt/2) with the 3-D transport */
+int or_strang_step3d(int N, double L, double lambda, int nx, int ny, int nz, double *f, const double *dx,
+                     double dy, double dzs, double Tw, const double *Vw, const double *ffar, double dt, double eps,
+                     int nthreads)
+{
+    if (or_transport3d_rk2(N, L, nx, ny, nz, f, dx, dy, dzs, Tw, Vw, ffar, 0.5 * dt)) return -1;
+    or_rk2_homogeneous(N, L, lambda, nx * ny * nz, f, dt, 1, eps, 1, nthreads);
+    return or_transport3d_rk2(N, L, nx, ny, nz, f, dx, dy, dzs, Tw, Vw, ffar, 0.5 * dt);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Direct quadrature of the collision integral, Sec. 2 ("Q_general") with
  * the collision law "velocity_interact", B = |u|^lambda / (4 pi) and the
  * same cut |u| <= r0 as the weights, for f a sum of Maxwellians

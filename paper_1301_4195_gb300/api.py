@@ -65,6 +65,7 @@ _SIGS = {
     "cs_last_error": (ctypes.c_char_p, []),
     "cs_weights_bytes": (_i, [_i, _i, ctypes.POINTER(ctypes.c_size_t)]),
     "cs_weights_build": (_i, [_i, _d, _d, _i, _vp, ctypes.POINTER(_vp)]),
+    "cs_weights_build_aniso": (_i, [_i, _d, _d, ctypes.POINTER(_d), _i, _i, _vp, ctypes.POINTER(_vp)]),
     "cs_handle_destroy": (_i, [_vp]),
     "cs_handle_info": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_d), ctypes.POINTER(_d),
                             ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_size_t)]),
@@ -175,6 +176,16 @@ def cs_status(h: int):
 def cs_weights_build(N: int, L: float, lam: float, precision: int = CS_FP64, stream=None) -> int:
     h = _vp()
     _check(lib().cs_weights_build(N, L, lam, precision, _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def cs_weights_build_aniso(N: int, L: float, lam: float, moments, precision: int = CS_FP64, stream=None) -> int:
+    """Weights of B = |u|^lam b(cos theta), b by its Legendre moments
+    moments[l] = int_{S^2} b P_l dsigma (see include/cs.h)."""
+    m = [float(x) for x in moments]
+    arr = (_d * max(1, len(m)))(*m)
+    h = _vp()
+    _check(lib().cs_weights_build_aniso(N, L, lam, arr, len(m), precision, _stream(stream), ctypes.byref(h)))
     return h.value
 
 
@@ -350,11 +361,16 @@ def cs_collide_noalloc(h, f, ncells, eps, Q, conserve=1, stream=None):
 class Handle:
     """Owns one cs_handle_t (weights for one (N, L, lambda, precision))."""
 
-    def __init__(self, N: int, L: float, lam: float, precision: str | int = "fp64", stream=None):
+    def __init__(self, N: int, L: float, lam: float, precision: str | int = "fp64", stream=None, moments=None):
+        """moments: Legendre moments of an anisotropic b(cos theta) (None: isotropic)."""
         p = precision if isinstance(precision, int) else {
             "fp64": CS_FP64, "fp32": CS_FP32, "fp32-radius": CS_FP32 | CS_WEIGHTS_RADIUS}[precision]
         self.N, self.L, self.lam, self.precision = int(N), float(L), float(lam), p
-        self._h = cs_weights_build(self.N, self.L, self.lam, p, stream)
+        self._h = None
+        if moments is None:
+            self._h = cs_weights_build(self.N, self.L, self.lam, p, stream)
+        else:
+            self._h = cs_weights_build_aniso(self.N, self.L, self.lam, moments, p, stream)
 
     @property
     def ptr(self) -> int:

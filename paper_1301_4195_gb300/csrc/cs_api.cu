@@ -97,6 +97,7 @@ void fill_geom(Geom &g, int N, double L, double lambda, int precision)
     g.dv = 2.0 * L / N;
     g.dz = M_PI / L;
     g.lambda = lambda;
+    g.nleg = 0;  // isotropic unless cs_weights_build_aniso sets moments
     // ROWS layout: rows of a tile (one per m3) padded to a multiple of 4 entries
     g.off[0] = 0;
     g.TS = 0;
@@ -800,7 +801,35 @@ int cs_tile_layout(int N, int precision, int *map, int cap, int *entries)
     return CS_OK;
 }
 
+namespace {
+int build_handle(int N, double L, double lambda, int precision, const double *moments, int nmom,
+                 cudaStream_t stream, cs_handle_t *out);
+}
+
 int cs_weights_build(int N, double L, double lambda, int precision, cudaStream_t stream, cs_handle_t *out)
+{
+    return build_handle(N, L, lambda, precision, nullptr, 0, stream, out);
+}
+
+int cs_weights_build_aniso(int N, double L, double lambda, const double *moments, int nmom, int precision,
+                           cudaStream_t stream, cs_handle_t *out)
+{
+    if (!moments || nmom < 1 || nmom > kMaxLeg)
+        return set_error(CS_EINVAL, "anisotropic b: 1 to 16 Legendre moments");
+    for (int l = 0; l < nmom; ++l)
+        if (!is_finite(moments[l])) return set_error(CS_EINVAL, "anisotropic b: moments must be finite");
+    if (!(moments[0] > 0)) return set_error(CS_EINVAL, "anisotropic b: moment 0 (int b dsigma) must be > 0");
+    if (precision & CS_WEIGHTS_RADIUS)
+        return set_error(CS_EINVAL, "anisotropic b: the radius tables describe isotropic weights only");
+    return build_handle(N, L, lambda, precision, moments, nmom, stream, out);
+}
+
+}  // extern "C"
+
+namespace {
+
+int build_handle(int N, double L, double lambda, int precision, const double *moments, int nmom,
+                 cudaStream_t stream, cs_handle_t *out)
 {
     const bool radius_only = (precision & CS_WEIGHTS_RADIUS) != 0;
     precision &= ~CS_WEIGHTS_RADIUS;
@@ -818,6 +847,8 @@ int cs_weights_build(int N, double L, double lambda, int precision, cudaStream_t
     hd.precision = precision;
     hd.has_table = !radius_only;
     fill_geom(hd.g, N, L, lambda, precision);
+    hd.g.nleg = nmom;
+    for (int l = 0; l < nmom; ++l) hd.g.bl[l] = moments[l];
     // twiddles exp(-i 2 pi ((k-h)(j-h) mod N) / N)
     std::vector<double2> t64(N * N);
     std::vector<float2> t32(N * N);
@@ -864,7 +895,7 @@ int cs_weights_build(int N, double L, double lambda, int precision, cudaStream_t
         return rc;
     }
     int rc = build_weights(hd, stream);
-    if (rc == CS_OK && hd.g.layout == LAYOUT_STRIP) rc = build_radius_tables(hd, stream);
+    if (rc == CS_OK && hd.g.layout == LAYOUT_STRIP && hd.g.nleg == 0) rc = build_radius_tables(hd, stream);
     if (rc == CS_OK) {
         // host vectors above must outlive the async copies
         e = cudaStreamSynchronize(stream);
@@ -879,6 +910,10 @@ int cs_weights_build(int N, double L, double lambda, int precision, cudaStream_t
     *out = hs;
     return CS_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 int cs_tune(cs_handle_t h, int param, int value)
 {

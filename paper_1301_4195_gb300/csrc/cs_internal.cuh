@@ -22,6 +22,7 @@ namespace cs {
 
 constexpr int kGroup = 32;  // cells per group (= warp lanes)
 constexpr int kMaxN = 64;
+constexpr int kMaxLeg = 16;  // Legendre moments of an anisotropic b(cos theta)
 
 template <typename T> struct C2;
 template <> struct C2<double> { using type = double2; };
@@ -44,6 +45,10 @@ struct Geom {
     double L, dv, dz;     // half-width, velocity and Fourier spacings
     double lambda;
     int off[kMaxN + 1];   // ROWS layout: off[m3] = first entry of row m3 inside a tile
+    // anisotropic scattering: b(cos theta) by its Legendre moments
+    // bl[l] = int_{S^2} b(t) P_l(t) dsigma, l < nleg (nleg = 0: isotropic 1/4pi)
+    int nleg;
+    double bl[kMaxLeg];
 };
 
 __host__ __device__ inline int kmin_of(int m3, int h) { return m3 - h > 0 ? m3 - h : 0; }

@@ -206,9 +206,182 @@ __device__ double ghat_centered(const Geom &g, const QuadRule &q, int kp1, int k
     return pref * radial_bracket_quad(a, b, c, r0, lam, q);
 }
 
+// ---- anisotropic scattering (Sec. 2: B = |u|^lambda b(cos theta)).  With the
+// Legendre moments bl[l] = int_{S^2} b P_l dsigma, the Funk-Hecke theorem turns
+// the sphere integral of G(u, zeta) into a Legendre series in cos(u^, zeta^),
+// and the Fourier transform in u keeps one Bessel product per degree:
+//   Ghat(xi, zeta) = sqrt(2/pi) [ sum_l (2l+1) (-1)^l bl[l] P_l(cos g) R_l(a, b)
+//                                 - bl[0] int_0^r0 r^{lambda+2} sinc(c r) dr ],
+//   R_l(a, b) = int_0^r0 r^{lambda+2} j_l(a r) j_l(b r) dr,
+// a = |zeta|/2, b = |xi - zeta/2|, c = |xi|, cos g = zeta^ . (xi - zeta/2)^.
+// The mirror partner xi' = zeta - xi flips the sign of cos g, so in the
+// symmetrised table entry Ghat(xi) + Ghat(zeta - xi) the odd degrees cancel
+// exactly (P_l(-t) = (-1)^l P_l(t) holds bit for bit in the recurrence) and
+// only the even ones are tabulated.
+
+// spherical Bessel function j_l(x), x >= 0: power series below x = 1/2;
+// Miller's downward recurrence up to x = l, normalised by the larger of the
+// exact j_0 and j_1; the upward recurrence (stable there) above
+__device__ double sph_bessel_j(int l, double x)
+{
+    if (x < 0.5) {
+        double lead = 1.0;
+        for (int i = 1; i <= l; ++i) lead *= x / (2.0 * i + 1.0);
+        double term = 1.0, sum = 1.0;
+        for (int k = 1; k < 30; ++k) {
+            term *= -0.5 * x * x / (k * (2.0 * l + 2.0 * k + 1.0));
+            sum += term;
+            if (fabs(term) < 1e-17 * fabs(sum)) break;
+        }
+        return lead * sum;
+    }
+    double sx, cx;
+    sincos(x, &sx, &cx);
+    const double j0 = sx / x, j1 = sx / (x * x) - cx / x;
+    if (l == 0) return j0;
+    if (l == 1) return j1;
+    if (x > l) {
+        double jm = j0, jc = j1;
+        for (int n = 1; n < l; ++n) {
+            const double jn = (2.0 * n + 1.0) / x * jc - jm;
+            jm = jc;
+            jc = jn;
+        }
+        return jc;
+    }
+    const int top = l + 24 + (int)x;
+    double jp = 0.0, jc = 1e-200, jl = 0.0, f0 = 1.0, f1 = 1.0;
+    for (int n = top; n >= 1; --n) {  // j_{n-1} from j_n and j_{n+1}
+        const double jm = (2.0 * n + 1.0) / x * jc - jp;
+        jp = jc;
+        jc = jm;
+        if (n - 1 == l) jl = jc;
+        if (n - 1 == 1) f1 = jc;
+    }
+    f0 = jc;
+    return fabs(j0) > fabs(j1) ? jl * (j0 / f0) : jl * (j1 / f1);
+}
+
+__device__ double legendre_poly(int l, double t)
+{
+    double p0 = 1.0, p1 = t;
+    if (l == 0) return 1.0;
+    for (int n = 1; n < l; ++n) {
+        const double p2 = ((2.0 * n + 1.0) * t * p1 - n * p0) / (n + 1.0);
+        p0 = p1;
+        p1 = p2;
+    }
+    return p1;
+}
+
+// R_l(a, b) by composite Gauss-Legendre, the panels as in radial_bracket_quad
+__device__ double aniso_radial(int l, double a, double b, double r0, double lam, const QuadRule &q)
+{
+    const int np = (int)ceil((a + b) * r0 / 3.0) + 2;
+    const double hw = r0 / np;
+    double total = 0.0;
+    for (int p = 0; p < np; ++p) {
+        const int nsub = (p == 0) ? 12 : 1;
+        for (int sidx = 0; sidx < nsub; ++sidx) {
+            double lo, hi;
+            if (p == 0) {
+                hi = hw * exp2(-(double)(nsub - 1 - sidx));
+                lo = (sidx == 0) ? 0.0 : hw * exp2(-(double)(nsub - sidx));
+            } else {
+                lo = p * hw;
+                hi = (p + 1) * hw;
+            }
+            const double mid = 0.5 * (lo + hi), half = 0.5 * (hi - lo);
+            for (int i = 0; i < kQuadNodes; ++i) {
+                const double r = mid + half * q.x[i];
+                total += half * q.w[i] * pow(r, lam + 2.0) * sph_bessel_j(l, a * r) * sph_bessel_j(l, b * r);
+            }
+        }
+    }
+    return total;
+}
+
+__device__ double radial_pair_quad(double a, double b, double r0, double lam, const QuadRule &q);
+
+// int_0^r0 r^{lambda+2} sinc(c r) dr: closed forms at lambda = 0, 1, else quadrature
+__device__ double loss_integral(double c, double r0, double lam, const QuadRule &q)
+{
+    if (lam == 0.0 || lam == 1.0) return sinc_moment(c, r0, (int)lam);
+    return radial_pair_quad(c, 0.0, r0, lam, q);
+}
+
+// The tabulated integrals of an anisotropic handle: R_l(kk, bb) for the even
+// degrees l = ls[s] of the slots s, and the loss integral of every |xi|^2
+struct AnisoTables {
+    const double *R;  // [nslot][nkk][nbb]
+    const double *B;  // [nkk]
+    int nslot, nkk, nbb;
+    int ls[kMaxLeg / 2];
+};
+
+// Ghat (unsymmetrised) from the tables, even degrees only: the half of the
+// weight that survives the symmetrisation
+__device__ double ghat_aniso_tab(const Geom &g, const AnisoTables &t, long kk, long bb, long mm, long kd)
+{
+    if (kk == 0) return 0.0;
+    const double cg = bb == 0 ? 0.0 : (double)kd / (sqrt((double)kk) * sqrt((double)bb));
+    double gain = 0.0;
+    for (int s = 0; s < t.nslot; ++s) {
+        const int l = t.ls[s];
+        if (l > 0 && bb == 0) continue;
+        gain += (2.0 * l + 1.0) * g.bl[l] * legendre_poly(l, cg) * t.R[((size_t)s * t.nkk + kk) * t.nbb + bb];
+    }
+    return 0.79788456080286535588 * (gain - g.bl[0] * t.B[mm]);
+}
+
+// Ghat (unsymmetrised, every degree) computed directly: cs_weights_sample
+__device__ double ghat_aniso_direct(const Geom &g, const QuadRule &q, long kk, long bb, long mm, long kd)
+{
+    if (kk == 0) return 0.0;
+    const double a = 0.5 * g.dz * sqrt((double)kk), b = 0.5 * g.dz * sqrt((double)bb), c = g.dz * sqrt((double)mm);
+    const double cg = bb == 0 ? 0.0 : (double)kd / (sqrt((double)kk) * sqrt((double)bb));
+    double gain = 0.0;
+    for (int l = 0; l < g.nleg; ++l) {
+        if (g.bl[l] == 0.0 || (l > 0 && bb == 0)) continue;
+        const double sgn = (l & 1) ? -1.0 : 1.0;
+        gain += (2.0 * l + 1.0) * sgn * g.bl[l] * legendre_poly(l, cg) * aniso_radial(l, a, b, g.L, g.lambda, q);
+    }
+    return 0.79788456080286535588 * (gain - g.bl[0] * loss_integral(c, g.L, g.lambda, q));
+}
+
+__device__ void aniso_radii(int kp1, int kp2, int kp3, int mp1, int mp2, int mp3, long &kk, long &bb, long &mm,
+                            long &kd)
+{
+    const long d1 = 2 * mp1 - kp1, d2 = 2 * mp2 - kp2, d3 = 2 * mp3 - kp3;
+    kk = (long)kp1 * kp1 + (long)kp2 * kp2 + (long)kp3 * kp3;
+    mm = (long)mp1 * mp1 + (long)mp2 * mp2 + (long)mp3 * mp3;
+    bb = d1 * d1 + d2 * d2 + d3 * d3;
+    kd = kp1 * d1 + kp2 * d2 + kp3 * d3;
+}
+
+__global__ void aniso_radial_kernel(Geom g, QuadRule q, AnisoTables t, double *__restrict__ R, double *__restrict__ B)
+{
+    const long long n = (long long)t.nslot * t.nkk * t.nbb;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n + t.nkk;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (i >= n) {  // the loss integrals
+            const int mm = (int)(i - n);
+            B[mm] = loss_integral(g.dz * sqrt((double)mm), g.L, g.lambda, q);
+            continue;
+        }
+        const int s = (int)(i / ((long long)t.nkk * t.nbb));
+        const int kk = (int)((i / t.nbb) % t.nkk), bb = (int)(i % t.nbb);
+        const int l = t.ls[s];
+        double v = 0.0;
+        if (kk > 0 && !(l > 0 && bb == 0))
+            v = aniso_radial(l, 0.5 * g.dz * sqrt((double)kk), 0.5 * g.dz * sqrt((double)bb), g.L, g.lambda, q);
+        R[i] = v;
+    }
+}
+
 template <typename T>
 __global__ void build_table_kernel(Geom g, QuadRule q, const int *__restrict__ tile0, long long total,
-                                   const int *__restrict__ emap, T *__restrict__ out)
+                                   const int *__restrict__ emap, T *__restrict__ out, AnisoTables at)
 {
     const long long tile = blockIdx.x;
     if (tile >= total) return;
@@ -246,8 +419,19 @@ __global__ void build_table_kernel(Geom g, QuadRule q, const int *__restrict__ t
         }
         const int m3 = e >> 8, k3 = e & 255;
         const int s3 = k3 + h - m3;
-        double w = ghat_centered(g, q, k1 - h, k2 - h, k3 - h, m1 - h, m2 - h, m3 - h);
-        if (!centre) w += ghat_centered(g, q, k1 - h, k2 - h, k3 - h, s1 - h, s2 - h, s3 - h);
+        double w;
+        if (g.nleg > 0) {
+            long kk, bb, mm, kd;
+            aniso_radii(k1 - h, k2 - h, k3 - h, m1 - h, m2 - h, m3 - h, kk, bb, mm, kd);
+            w = ghat_aniso_tab(g, at, kk, bb, mm, kd);
+            if (!centre) {
+                aniso_radii(k1 - h, k2 - h, k3 - h, s1 - h, s2 - h, s3 - h, kk, bb, mm, kd);
+                w += ghat_aniso_tab(g, at, kk, bb, mm, kd);
+            }
+        } else {
+            w = ghat_centered(g, q, k1 - h, k2 - h, k3 - h, m1 - h, m2 - h, m3 - h);
+            if (!centre) w += ghat_centered(g, q, k1 - h, k2 - h, k3 - h, s1 - h, s2 - h, s3 - h);
+        }
         dst[p] = (T)w;
     }
 }
@@ -330,6 +514,12 @@ __global__ void sample_kernel(Geom g, QuadRule q, const int *__restrict__ km, in
     if (i >= n) return;
     const int *e = km + 6 * i;
     const int h = g.h;
+    if (g.nleg > 0) {
+        long kk, bb, mm, kd;
+        aniso_radii(e[0] - h, e[1] - h, e[2] - h, e[3] - h, e[4] - h, e[5] - h, kk, bb, mm, kd);
+        out[i] = ghat_aniso_direct(g, q, kk, bb, mm, kd);
+        return;
+    }
     out[i] = ghat_centered(g, q, e[0] - h, e[1] - h, e[2] - h, e[3] - h, e[4] - h, e[5] - h);
 }
 
@@ -446,19 +636,48 @@ int build_weights(Handle &hd, cudaStream_t s)
     }
     e = cudaMemcpyAsync(demap, emap.data(), sizeof(int) * emap.size(), cudaMemcpyHostToDevice, s);
     const QuadRule q = make_rule();
+    // anisotropic b: the radial integrals of the even degrees and the loss
+    // integrals, tabulated over the grid's integer squared radii first
+    AnisoTables at{};
+    double *aR = nullptr, *aB = nullptr;
+    if (e == cudaSuccess && g.nleg > 0) {
+        int KK, BB, MM;
+        radius_dims(g.N, &KK, &BB, &MM);
+        at.nkk = KK;
+        at.nbb = BB;
+        for (int l = 0; l < g.nleg; l += 2)
+            if (l == 0 || g.bl[l] != 0.0) at.ls[at.nslot++] = l;
+        e = cudaMalloc(&aR, sizeof(double) * (size_t)at.nslot * KK * BB);
+        if (e == cudaSuccess) e = cudaMalloc(&aB, sizeof(double) * (size_t)KK);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(aR);
+            cudaFree(demap);
+            return set_error(CS_ENOMEM, "cudaMalloc of the anisotropic radial tables failed");
+        }
+        at.R = aR;
+        at.B = aB;
+        const long long n = (long long)at.nslot * KK * BB + KK;
+        aniso_radial_kernel<<<(unsigned)std::min<long long>((n + 127) / 128, 1 << 20), 128, 0, s>>>(g, q, at, aR, aB);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) note_kernels(s, 1);
+    }
     if (e == cudaSuccess) {
         if (hd.precision == CS_FP32)
-            build_table_kernel<float><<<(unsigned)hd.total_tiles, 128, 0, s>>>(g, q, hd.pencil_tile0,
-                                                                                hd.total_tiles, demap, (float *)hd.ghat);
+            build_table_kernel<float><<<(unsigned)hd.total_tiles, 128, 0, s>>>(g, q, hd.pencil_tile0, hd.total_tiles,
+                                                                                demap, (float *)hd.ghat, at);
         else
             build_table_kernel<double><<<(unsigned)hd.total_tiles, 128, 0, s>>>(g, q, hd.pencil_tile0,
-                                                                                 hd.total_tiles, demap, (double *)hd.ghat);
+                                                                                 hd.total_tiles, demap,
+                                                                                 (double *)hd.ghat, at);
         e = cudaGetLastError();
         if (e == cudaSuccess) note_kernels(s, 1);
     }
     // the map (and the host vector behind the async copy) must outlive the kernel
     const cudaError_t e2 = cudaStreamSynchronize(s);
     cudaFree(demap);
+    cudaFree(aR);
+    cudaFree(aB);
     if (e != cudaSuccess) return cuda_error(e, "weight table build");
     if (e2 != cudaSuccess) return cuda_error(e2, "weight table build");
     return CS_OK;

@@ -128,3 +128,19 @@ def test_tile_layout_covers_every_valid_pair_once(libcs, N, prec):
     want = sorted(m3 * 256 + k3 for m3 in range(N) for k3 in range(N) if 0 <= k3 - m3 + N // 2 <= N - 1)
     assert got == want
     assert len(want) == 3 * N * N // 4
+
+
+def test_aniso_build_checks_its_moments_on_the_host(libcs):
+    lib = libcs.lib()
+    h = libcs._vp()
+    good = (libcs._d * 3)(1.0, 0.0, 0.3)
+    bad0 = (libcs._d * 2)(0.0, 0.1)
+    nan = (libcs._d * 2)(1.0, float("nan"))
+    assert lib.cs_weights_build_aniso(16, 6.0, 1.0, None, 1, 0, None, libcs.ctypes.byref(h)) == libcs.CS_EINVAL
+    assert lib.cs_weights_build_aniso(16, 6.0, 1.0, good, 0, 0, None, libcs.ctypes.byref(h)) == libcs.CS_EINVAL
+    assert lib.cs_weights_build_aniso(16, 6.0, 1.0, good, 17, 0, None, libcs.ctypes.byref(h)) == libcs.CS_EINVAL
+    assert lib.cs_weights_build_aniso(16, 6.0, 1.0, bad0, 2, 0, None, libcs.ctypes.byref(h)) == libcs.CS_EINVAL
+    assert lib.cs_weights_build_aniso(16, 6.0, 1.0, nan, 2, 0, None, libcs.ctypes.byref(h)) == libcs.CS_EINVAL
+    assert lib.cs_weights_build_aniso(16, 6.0, 1.0, good, 3, libcs.CS_FP32 | libcs.CS_WEIGHTS_RADIUS, None,
+                                      libcs.ctypes.byref(h)) == libcs.CS_EINVAL
+    assert lib.cs_weights_build_aniso(5, 6.0, 1.0, good, 3, 0, None, libcs.ctypes.byref(h)) == libcs.CS_EINVAL
