@@ -8,7 +8,7 @@
  * transform of f on an N^3 velocity grid, the weighted Fourier convolution
  * with the precomputed weights Ghat, an inverse transform and the
  * conservation projection; plus Heun time stepping and a finite-volume
- * transport step (one space dimension, or two with a periodic second one)
+ * transport step (one space dimension, or two or three with periodic further ones)
  * combined by Strang splitting, sharded transport stages for domain
  * decomposition, and batched calls over handles of different N.
  *
@@ -309,6 +309,40 @@ int cs_transport2d(cs_handle_t h, double *f, int nx, const cs_domain2d *dom, dou
  * Errors: CS_EINVAL, CS_ENOMEM, CS_ECUDA. */
 int cs_step2d(cs_handle_t h, double *f, int nx, const cs_domain2d *dom, double dt, double eps,
               int nsteps, cudaStream_t stream);
+
+/* Transport in three space dimensions (Sec. 3.4): x is the wall-normal
+ * direction of the 1-D problem (cells of width dx, diffusely reflecting wall
+ * at x = 0, far-field gas at the end), y and z periodic directions of ny and
+ * nz cells of uniform widths dy and dz.  The state is [nx][ny][nz][N^3]
+ * (cell (i, j, l) at index (i ny + j) nz + l).  A stage adds the flux
+ * differences of all three directions (no splitting):
+ *   d f/dt = -(F_{i+1/2} - F_{i-1/2})/dx_i - (H_{j+1/2} - H_{j-1/2})/dy
+ *            - (K_{l+1/2} - K_{l-1/2})/dz,
+ * F the x-flux of cs_transport on each x-row, H and K the second-order upwind
+ * fluxes with velocity components v2 and v3.  nz = 1 is the 2-D problem of
+ * cs_transport2d (bit for bit). */
+typedef struct {
+    const double *dx;    /* device, [nx] cell widths across x */
+    const double *f_far; /* device, [N^3] far-field distribution (x end), used for v1 < 0 */
+    double wall_T;       /* wall temperature T_w > 0 */
+    double wall_V[3];    /* wall velocity V_w */
+    int ny;              /* cells across the periodic y direction, >= 1 */
+    double dy;           /* their width, > 0 */
+    int nz;              /* cells across the periodic z direction, >= 1 (ny * nz <= 65535) */
+    double dz;           /* their width, > 0 */
+} cs_domain3d;
+
+/* One Heun step of length dt of the 3-D transport, in place.
+ *   f (device, in/out) [nx][ny][nz][N^3].  nx >= 2.
+ * Errors: CS_EINVAL, CS_ENOMEM, CS_ECUDA. */
+int cs_transport3d(cs_handle_t h, double *f, int nx, const cs_domain3d *dom, double dt, cudaStream_t stream);
+
+/* nsteps Strang-split steps with the 3-D transport: transport dt/2,
+ * collision dt (Heun on P_N Qt / eps, every cell), transport dt/2, in place;
+ * captured once as a CUDA graph and replayed like cs_step.
+ * Errors: CS_EINVAL, CS_ENOMEM, CS_ECUDA. */
+int cs_step3d(cs_handle_t h, double *f, int nx, const cs_domain3d *dom, double dt, double eps, int nsteps,
+              cudaStream_t stream);
 
 /* Sharded transport (Sec. 4.2, distributed memory): the x-grid of
  * total_cells cells is split into contiguous shards, one per process (or

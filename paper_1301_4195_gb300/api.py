@@ -50,6 +50,12 @@ class Domain2D(ctypes.Structure):
     _fields_ = [("dx", _vp), ("f_far", _vp), ("wall_T", _d), ("wall_V", _d * 3), ("ny", _i), ("dy", _d)]
 
 
+class Domain3D(ctypes.Structure):
+    """cs_domain3d: dx (device), f_far (device), wall_T, wall_V[3], ny, dy, nz, dz."""
+    _fields_ = [("dx", _vp), ("f_far", _vp), ("wall_T", _d), ("wall_V", _d * 3), ("ny", _i), ("dy", _d),
+                ("nz", _i), ("dz", _d)]
+
+
 class BatchEntry(ctypes.Structure):
     """cs_batch_entry: handle, f (device), Q (device), ncells."""
     _fields_ = [("handle", _vp), ("f", _vp), ("Q", _vp), ("ncells", _i)]
@@ -93,6 +99,8 @@ _SIGS = {
     "cs_launch_count": (_i, [ctypes.POINTER(ctypes.c_longlong), _i]),
     "cs_transport2d": (_i, [_vp, _vp, _i, ctypes.POINTER(Domain2D), _d, _vp]),
     "cs_step2d": (_i, [_vp, _vp, _i, ctypes.POINTER(Domain2D), _d, _d, _i, _vp]),
+    "cs_transport3d": (_i, [_vp, _vp, _i, ctypes.POINTER(Domain3D), _d, _vp]),
+    "cs_step3d": (_i, [_vp, _vp, _i, ctypes.POINTER(Domain3D), _d, _d, _i, _vp]),
     "cs_transport_shard_prepare": (_i, [_vp, _i, _i, _i, ctypes.POINTER(Domain), _vp]),
     "cs_transport_shard_stage": (_i, [_vp, _vp, _i, _i, _i, ctypes.POINTER(Domain), _d, _vp, _d, _vp, _d, _vp,
                                       _vp]),
@@ -282,6 +290,19 @@ def cs_step2d(h, f, nx, dom: Domain2D, dt, eps, nsteps, stream=None):
     _check(lib().cs_step2d(h, _dptr(f, "f"), nx, ctypes.byref(dom), dt, eps, nsteps, _stream(stream)))
 
 
+def _domain3d(dx, f_far, wall_T, wall_V, ny, dy, nz, dz):
+    return Domain3D(_dptr(dx, "dx"), _dptr(f_far, "f_far"), float(wall_T), (_d * 3)(*[float(v) for v in wall_V]),
+                    int(ny), float(dy), int(nz), float(dz))
+
+
+def cs_transport3d(h, f, nx, dom: Domain3D, dt, stream=None):
+    _check(lib().cs_transport3d(h, _dptr(f, "f"), nx, ctypes.byref(dom), dt, _stream(stream)))
+
+
+def cs_step3d(h, f, nx, dom: Domain3D, dt, eps, nsteps, stream=None):
+    _check(lib().cs_step3d(h, _dptr(f, "f"), nx, ctypes.byref(dom), dt, eps, nsteps, _stream(stream)))
+
+
 def cs_transport_shard_prepare(h, ncells, first_cell, total_cells, dom: Domain, stream=None):
     _check(lib().cs_transport_shard_prepare(h, ncells, first_cell, total_cells, ctypes.byref(dom), _stream(stream)))
 
@@ -462,6 +483,17 @@ class Handle:
     def step2d(self, f, dx, f_far, wall_T, wall_V, ny, dy, dt, nsteps=1, eps=1.0, stream=None):
         nx = _ncells(f, self.N) // int(ny)
         cs_step2d(self._h, f, nx, _domain2d(dx, f_far, wall_T, wall_V, ny, dy), dt, eps, nsteps, stream)
+        return f
+
+    def transport3d(self, f, dx, f_far, wall_T, wall_V, ny, dy, nz, dz, dt, stream=None):
+        """f: [nx][ny][nz][N][N][N] float64 CUDA tensor (x wall-normal, y and z periodic)."""
+        nx = _ncells(f, self.N) // (int(ny) * int(nz))
+        cs_transport3d(self._h, f, nx, _domain3d(dx, f_far, wall_T, wall_V, ny, dy, nz, dz), dt, stream)
+        return f
+
+    def step3d(self, f, dx, f_far, wall_T, wall_V, ny, dy, nz, dz, dt, nsteps=1, eps=1.0, stream=None):
+        nx = _ncells(f, self.N) // (int(ny) * int(nz))
+        cs_step3d(self._h, f, nx, _domain3d(dx, f_far, wall_T, wall_V, ny, dy, nz, dz), dt, eps, nsteps, stream)
         return f
 
     def sample_weights(self, km):

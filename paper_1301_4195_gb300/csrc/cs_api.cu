@@ -323,6 +323,20 @@ int heun_transport2d(Handle &hd, double *f, int nx, int ny, double dy, const cs_
     return launch_transport_stage2d(hd, hd.f1, nx, ny, dy, dom, 0.5, f, 0.5, hd.f1, 0.5 * dt, f, s);
 }
 
+// one Heun step of the transport in three space dimensions, f [nx][ny][nz][N^3]
+int heun_transport3d(Handle &hd, double *f, int nx, int ny, int nz, double dy, double dz, const cs_domain &dom,
+                     double dt, cudaStream_t s)
+{
+    int rc;
+    {
+        StageTimer t(hd, CS_K_TRANSPORT, s);
+        rc = launch_transport_stage3d(hd, f, nx, ny, nz, dy, dz, dom, 1.0, f, 0.0, nullptr, dt, hd.f1, s);
+    }
+    if (rc) return rc;
+    StageTimer t(hd, CS_K_TRANSPORT, s);
+    return launch_transport_stage3d(hd, hd.f1, nx, ny, nz, dy, dz, dom, 0.5, f, 0.5, hd.f1, 0.5 * dt, f, s);
+}
+
 int heun_transport(Handle &hd, double *f, int ncells, const cs_domain &dom, double dt, cudaStream_t s)
 {
     int rc = timed_transport(hd, f, ncells, dom, 1.0, f, 0.0, nullptr, dt, hd.f1, s);
@@ -349,7 +363,7 @@ int run_steps(Handle &hd, Handle::GraphEntry key, int nsteps, cudaStream_t s, Bo
         if (g.kind == key.kind && g.f == key.f && g.dx == key.dx && g.ffar == key.ffar && g.ncells == key.ncells &&
             g.wall_T == key.wall_T && g.wall_V[0] == key.wall_V[0] && g.wall_V[1] == key.wall_V[1] &&
             g.wall_V[2] == key.wall_V[2] && g.dt == key.dt && g.eps == key.eps && g.ny == key.ny &&
-            g.dy == key.dy) {
+            g.dy == key.dy && g.nz == key.nz && g.dz == key.dz) {
             exec = g.exec;
             key.kernels = g.kernels;
         }
@@ -1399,6 +1413,64 @@ int cs_step2d(cs_handle_t h, double *f, int nx, const cs_domain2d *dom, double d
         if (int rc = heun_transport2d(hd, f, nx, ny, dy, d, 0.5 * dt, st)) return rc;
         if (int rc = heun_collision(hd, f, ncells, dt, eps, st)) return rc;
         return heun_transport2d(hd, f, nx, ny, dy, d, 0.5 * dt, st);
+    });
+}
+
+// ---- three space dimensions
+static int check_domain3d(const Handle &hd, const cs_domain3d *dom, int nx, cs_domain *d1)
+{
+    if (dom == nullptr) return set_error(CS_EINVAL, "domain is NULL");
+    if (dom->ny < 1 || dom->nz < 1) return set_error(CS_EINVAL, "ny and nz must be >= 1");
+    if (!(dom->dy > 0) || !is_finite(dom->dy) || !(dom->dz > 0) || !is_finite(dom->dz))
+        return set_error(CS_EINVAL, "dy and dz must be finite and > 0");
+    if ((long long)dom->ny * dom->nz > 65535) return set_error(CS_EINVAL, "ny * nz must be at most 65535");
+    if ((long long)nx * dom->ny * dom->nz > (1ll << 30)) return set_error(CS_EINVAL, "too many cells");
+    d1->dx = dom->dx;
+    d1->f_far = dom->f_far;
+    d1->wall_T = dom->wall_T;
+    for (int i = 0; i < 3; ++i) d1->wall_V[i] = dom->wall_V[i];
+    return check_domain(hd, d1, nx);
+}
+
+int cs_transport3d(cs_handle_t h, double *f, int nx, const cs_domain3d *dom, double dt, cudaStream_t s)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (int rc = check_cells(nx)) return rc;
+    if (!is_finite(dt)) return set_error(CS_EINVAL, "dt must be finite");
+    Handle &hd = h->h;
+    cs_domain d;
+    if (int rc = check_domain3d(hd, dom, nx, &d)) return rc;
+    if (int rc = check_device_ptr(f, "f")) return rc;
+    if (int rc = ensure_workspace(hd, nx * dom->ny * dom->nz, nx)) return rc;
+    hd.shard_tables.total_cells = -1;
+    if (int rc = launch_transport_prep(hd, nx, d, s)) return rc;
+    return heun_transport3d(hd, f, nx, dom->ny, dom->nz, dom->dy, dom->dz, d, dt, s);
+}
+
+int cs_step3d(cs_handle_t h, double *f, int nx, const cs_domain3d *dom, double dt, double eps, int nsteps,
+              cudaStream_t s)
+{
+    if (int rc = check_handle(h)) return rc;
+    if (int rc = check_cells(nx)) return rc;
+    if (!is_finite(dt)) return set_error(CS_EINVAL, "dt must be finite");
+    if (!(eps > 0) || !is_finite(eps)) return set_error(CS_EINVAL, "eps must be finite and > 0");
+    if (nsteps < 0) return set_error(CS_EINVAL, "nsteps < 0");
+    Handle &hd = h->h;
+    cs_domain d;
+    if (int rc = check_domain3d(hd, dom, nx, &d)) return rc;
+    if (int rc = check_device_ptr(f, "f")) return rc;
+    const int ny = dom->ny, nz = dom->nz, ncells = nx * ny * nz;
+    const double dy = dom->dy, dz = dom->dz;
+    if (int rc = ensure_workspace(hd, ncells, nx)) return rc;
+    hd.shard_tables.total_cells = -1;
+    Handle::GraphEntry key{4, f, d.dx, d.f_far, ncells, d.wall_T, {d.wall_V[0], d.wall_V[1], d.wall_V[2]},
+                           dt, eps, nullptr, 0, ny, dy, nz, dz};
+    return run_steps(hd, key, nsteps, s, [&](cudaStream_t st) {
+        if (int rc = launch_input_check(hd, f, (long long)ncells * hd.g.M, st)) return rc;
+        if (int rc = launch_transport_prep(hd, nx, d, st)) return rc;
+        if (int rc = heun_transport3d(hd, f, nx, ny, nz, dy, dz, d, 0.5 * dt, st)) return rc;
+        if (int rc = heun_collision(hd, f, ncells, dt, eps, st)) return rc;
+        return heun_transport3d(hd, f, nx, ny, nz, dy, dz, d, 0.5 * dt, st);
     });
 }
 

@@ -143,14 +143,16 @@ struct Handle {
     double *part5 = nullptr;  // per-block partial moments of the projection
     // replayable steps (cs_step, cs_relax): one captured step per argument set
     struct GraphEntry {
-        int kind;  // 1 = Strang step, 2 = homogeneous Heun step, 3 = Strang step in 2-D
+        int kind;  // 1 = Strang step, 2 = homogeneous Heun step, 3 = Strang step in 2-D, 4 = in 3-D
         const void *f, *dx, *ffar;
         int ncells;
         double wall_T, wall_V[3], dt, eps;
         cudaGraphExec_t exec;
         int kernels;  // kernel nodes of the captured step
-        int ny;       // 2-D: cells across y, and their width
+        int ny;       // 2-D, 3-D: cells across y, and their width
         double dy;
+        int nz;       // 3-D: cells across z, and their width
+        double dz;
     };
     std::vector<GraphEntry> graphs;
     cudaStream_t cap_stream = nullptr;
@@ -294,6 +296,11 @@ int launch_transport_prep(const Handle &hd, int total_cells, const cs_domain &do
 int launch_transport_stage2d(const Handle &hd, const double *fin, int nx, int ny, double dy, const cs_domain &dom,
                              double a, const double *x, double b, const double *y, double c, double *out,
                              cudaStream_t s);
+// a stage in three space dimensions: fin, out [nx][ny][nz][N^3], y and z
+// periodic with ny, nz cells of widths dy, dz
+int launch_transport_stage3d(const Handle &hd, const double *fin, int nx, int ny, int nz, double dy, double dz,
+                             const cs_domain &dom, double a, const double *x, double b, const double *y, double c,
+                             double *out, cudaStream_t s);
 // one transport stage, out = a x + b y + c rhs(fin), rhs the finite-volume
 // operator, for cells first .. first+ncells-1, read from fin with `ghost`
 // leading ghost cells (0: fin holds exactly the cells; 2: a window); out must

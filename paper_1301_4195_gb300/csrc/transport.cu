@@ -130,23 +130,46 @@ constexpr int kStageCells = 4;      // cells per block: their 5 faces from 8 loa
 // hold the same value.  Reads fin only, writes out only: out must not overlap
 // fin (it may alias x or y, read and written by the same thread).
 //
-// Two space dimensions (Y2D): cell (i, j) of an x-grid of nc cells and a
-// periodic y-row of ny cells is stored at index i ny + j; blockIdx.z = j.  The
-// x-part is the 1-D stage applied to row j (the same arithmetic); the y-part
-// adds -(H_{j+1/2} - H_{j-1/2}) / dy, H the second-order upwind flux on the
-// uniform periodic y-grid with the two-argument minmod (equal to the
-// three-argument one: on a uniform grid the central quotient is the mean of
-// the other two).  Both rows of a y-face evaluate its flux with the same
-// operations on the same values, so the y-fluxes telescope exactly.
+// More space dimensions (PD periodic directions): cell (i, j, l) of an x-grid
+// of nc cells, ny periodic y-cells and nz periodic z-cells (nz = 1 when
+// PD = 1) is stored at index (i ny + j) nz + l; blockIdx.z = j nz + l.  The
+// x-part is the 1-D stage applied to that x-row (the same arithmetic); each
+// periodic direction adds -(H_{j+1/2} - H_{j-1/2}) / dy, H the second-order
+// upwind flux on the uniform periodic grid with the two-argument minmod
+// (equal to the three-argument one: on a uniform grid the central quotient is
+// the mean of the other two), with velocity component v2 along y and v3 along
+// z.  Both cells of a periodic face evaluate its flux with the same
+// operations on the same values, so the periodic fluxes telescope exactly; a
+// single z-layer adds exactly zero, so PD = 2 with nz = 1 is PD = 1 bit for bit.
 __device__ __forceinline__ double yface(double fu, double hs, double s) { return fma(hs, s, fu); }
 
-template <bool Y2D>
+// (H_{j-1/2} - H_{j+1/2}) vco of one periodic direction from the values of
+// the cell's line at offsets -2, -1, +1, +2 (in elements from `cell`) and its
+// own value f0; vco = c v_dir / h, idh = 1/h, hh = h/2
+__device__ __forceinline__ double periodic_part(const double *cell, const size_t (&o)[4], double f0, double vel,
+                                                double vco, double idh, double hh)
+{
+    const double fm2 = cell[o[0]], fm1 = cell[o[1]], fp1 = cell[o[2]], fp2 = cell[o[3]];
+    double hp, hm;
+    if (vel >= 0) {  // faces j+1/2 and j-1/2 from cells j and j-1
+        const double e_2 = (fm1 - fm2) * idh, e_1 = (f0 - fm1) * idh, e0 = (fp1 - f0) * idh;
+        hp = yface(f0, hh, minmod2(e0, e_1));
+        hm = yface(fm1, hh, minmod2(e_1, e_2));
+    } else {  // from cells j+1 and j
+        const double e_1 = (f0 - fm1) * idh, e0 = (fp1 - f0) * idh, e1 = (fp2 - fp1) * idh;
+        hp = yface(fp1, -hh, minmod2(e1, e0));
+        hm = yface(f0, -hh, minmod2(e0, e_1));
+    }
+    return (hm - hp) * vco;
+}
+
+template <int PD>
 __global__ void __launch_bounds__(kStageThreads) stage_kernel(Geom g, const double *__restrict__ fin, int first,
                                                               int ncl, int nc, int G, const double *__restrict__ dx,
                                                               const double *__restrict__ ffar,
                                                               const double *__restrict__ scal, double a, const double *x,
                                                               double b, const double *y, double c, double *out, int ny,
-                                                              double idy, double hdy)
+                                                              double idy, double hdy, int nz, double idz, double hdz)
 {
     __shared__ double sh[kStageThreads / 32];
     __shared__ double s_coef[kStageCells];  // c / dx_j of the block's cells
@@ -156,9 +179,9 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(Geom g, const doub
     const int ncb = min(kStageCells, ncl - cl0);  // cells of this block
     const int v = blockIdx.x * kStageThreads + threadIdx.x;
     const int c0 = first + cl0;                   // grid index of the block's first cell and face
-    const int row = Y2D ? (int)blockIdx.z : 0;    // y-row j
-    const size_t XS = (size_t)(Y2D ? ny : 1) * M;  // stride between x-neighbours
-    const size_t R0 = (size_t)row * M;             // offset of the row
+    const int row = PD ? (int)blockIdx.z : 0;          // the x-row (j, l): j nz + l
+    const size_t XS = (size_t)(PD ? ny * nz : 1) * M;  // stride between x-neighbours
+    const size_t R0 = (size_t)row * M;                 // offset of the row
 
     // sigma_w enters the wall face of velocities with v1 > 0 only, i.e. index
     // k1 > N/2, v >= (N/2 + 1) N^2 (block-uniform test)
@@ -214,31 +237,33 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(Geom g, const doub
 #pragma unroll
     for (int i = 0; i < kStageCells; ++i) vco[i] = v1 * s_coef[i];
     const bool plain = a == 1.0 && y == nullptr;  // out = x + c R(f): one fused multiply-add per point
-    // y-part of the block's cells: (H_{j-1/2} - H_{j+1/2}) c v2 / dy
+    // periodic parts of the block's cells: (H_{j-1/2} - H_{j+1/2}) c v2 / dy
+    // (+ the same along z with v3)
     double ry[kStageCells];
-    if constexpr (Y2D) {
+    if constexpr (PD >= 1) {
+        const int j = row / nz, l = row % nz;
         const double v2 = t.v1[(v / g.N) % g.N];
         const double vy = c * v2 * idy;
-        const int jm2 = (row + 2 * ny - 2) % ny, jm1 = (row + ny - 1) % ny;
-        const int jp1 = (row + 1) % ny, jp2 = (row + 2) % ny;
+        size_t oy[4], oz[4];
+        const int dk[4] = {-2, -1, 1, 2};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            oy[k] = ((size_t)((j + dk[k] + 2 * ny) % ny) * nz + l) * M;
+            oz[k] = ((size_t)j * nz + (l + dk[k] + 2 * nz) % nz) * M;
+        }
+        double v3 = 0.0, vz = 0.0;
+        if constexpr (PD == 2) {
+            v3 = t.v1[v % g.N];
+            vz = c * v3 * idz;
+        }
 #pragma unroll
         for (int i = 0; i < kStageCells; ++i) {
             ry[i] = 0.0;
             if (i < ncb) {
+                // the cell's x-slice (every row of it) at this velocity
                 const double *cell = fin + (ptrdiff_t)(c0 + i - first + G) * XS + v;
-                const double fm2 = cell[(size_t)jm2 * M], fm1 = cell[(size_t)jm1 * M], f0 = fv[i + 2];
-                const double fp1 = cell[(size_t)jp1 * M], fp2 = cell[(size_t)jp2 * M];
-                double hp, hm;
-                if (v2 >= 0) {  // faces j+1/2 and j-1/2 from cells j and j-1
-                    const double e_2 = (fm1 - fm2) * idy, e_1 = (f0 - fm1) * idy, e0 = (fp1 - f0) * idy;
-                    hp = yface(f0, hdy, minmod2(e0, e_1));
-                    hm = yface(fm1, hdy, minmod2(e_1, e_2));
-                } else {  // from cells j+1 and j
-                    const double e_1 = (f0 - fm1) * idy, e0 = (fp1 - f0) * idy, e1 = (fp2 - fp1) * idy;
-                    hp = yface(fp1, -hdy, minmod2(e1, e0));
-                    hm = yface(f0, -hdy, minmod2(e0, e_1));
-                }
-                ry[i] = (hm - hp) * vy;
+                ry[i] = periodic_part(cell, oy, fv[i + 2], v2, vy, idy, hdy);
+                if constexpr (PD == 2) ry[i] += periodic_part(cell, oz, fv[i + 2], v3, vz, idz, hdz);
             }
         }
     }
@@ -266,7 +291,7 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(Geom g, const doub
         if (i > 0) {  // cell cf-1 = local cl0 + i - 1
             const size_t idx = (size_t)(cl0 + i - 1) * XS + R0 + v;
             double o;
-            if constexpr (Y2D) {
+            if constexpr (PD >= 1) {
                 o = fma(Gprev - G, vco[i - 1], ry[i - 1]);
                 if (x) o = fma(a, x[idx], o);
                 if (y) o = fma(b, y[idx], o);
@@ -319,8 +344,8 @@ int launch_transport_stage(const Handle &hd, const double *fin, int ghost, int f
 {
     const dim3 grid((unsigned)((hd.g.M + kStageThreads - 1) / kStageThreads),
                     (unsigned)((ncells + kStageCells - 1) / kStageCells));
-    stage_kernel<false><<<grid, kStageThreads, 0, s>>>(hd.g, fin, first, ncells, total_cells, ghost, dom.dx,
-                                                       dom.f_far, hd.scal, a, x, b, y, c, out, 1, 0.0, 0.0);
+    stage_kernel<0><<<grid, kStageThreads, 0, s>>>(hd.g, fin, first, ncells, total_cells, ghost, dom.dx, dom.f_far,
+                                                   hd.scal, a, x, b, y, c, out, 1, 0.0, 0.0, 1, 0.0, 0.0);
     CS_LAUNCHED(1, s, "transport stage");
     return CS_OK;
 }
@@ -331,9 +356,21 @@ int launch_transport_stage2d(const Handle &hd, const double *fin, int nx, int ny
 {
     const dim3 grid((unsigned)((hd.g.M + kStageThreads - 1) / kStageThreads),
                     (unsigned)((nx + kStageCells - 1) / kStageCells), (unsigned)ny);
-    stage_kernel<true><<<grid, kStageThreads, 0, s>>>(hd.g, fin, 0, nx, nx, 0, dom.dx, dom.f_far, hd.scal, a, x,
-                                                      b, y, c, out, ny, 1.0 / dy, 0.5 * dy);
+    stage_kernel<1><<<grid, kStageThreads, 0, s>>>(hd.g, fin, 0, nx, nx, 0, dom.dx, dom.f_far, hd.scal, a, x, b, y,
+                                                   c, out, ny, 1.0 / dy, 0.5 * dy, 1, 0.0, 0.0);
     CS_LAUNCHED(1, s, "transport stage (2-D)");
+    return CS_OK;
+}
+
+int launch_transport_stage3d(const Handle &hd, const double *fin, int nx, int ny, int nz, double dy, double dz,
+                             const cs_domain &dom, double a, const double *x, double b, const double *y, double c,
+                             double *out, cudaStream_t s)
+{
+    const dim3 grid((unsigned)((hd.g.M + kStageThreads - 1) / kStageThreads),
+                    (unsigned)((nx + kStageCells - 1) / kStageCells), (unsigned)(ny * nz));
+    stage_kernel<2><<<grid, kStageThreads, 0, s>>>(hd.g, fin, 0, nx, nx, 0, dom.dx, dom.f_far, hd.scal, a, x, b, y,
+                                                   c, out, ny, 1.0 / dy, 0.5 * dy, nz, 1.0 / dz, 0.5 * dz);
+    CS_LAUNCHED(1, s, "transport stage (3-D)");
     return CS_OK;
 }
 

@@ -144,3 +144,9 @@ def test_aniso_build_checks_its_moments_on_the_host(libcs):
     assert lib.cs_weights_build_aniso(16, 6.0, 1.0, good, 3, libcs.CS_FP32 | libcs.CS_WEIGHTS_RADIUS, None,
                                       libcs.ctypes.byref(h)) == libcs.CS_EINVAL
     assert lib.cs_weights_build_aniso(5, 6.0, 1.0, good, 3, 0, None, libcs.ctypes.byref(h)) == libcs.CS_EINVAL
+
+
+def test_transport3d_checks_its_domain_on_the_host(libcs):
+    lib = libcs.lib()
+    assert lib.cs_transport3d(None, None, 4, None, 0.01, None) == libcs.CS_EINVAL
+    assert lib.cs_step3d(None, None, 4, None, 0.01, 1.0, 1, None) == libcs.CS_EINVAL
