@@ -260,7 +260,7 @@ def step_workload(api, inputs, torch, device, N, ncells, K, W, flush, tune="", p
     h.reserve(ncells)
     if tune:  # fixed launch choices (profiling runs: timings under a profiler would mislead the autotuner)
         for param, v in zip((api.CS_TUNE_GROUPS_PER_CTA, api.CS_TUNE_CTAS_PER_SM, api.CS_TUNE_SPLIT,
-                             api.CS_TUNE_WEIGHTS), (int(x) for x in tune.split(","))):
+                             api.CS_TUNE_WEIGHTS, api.CS_TUNE_L2_HINT), (int(x) for x in tune.split(","))):
             api.cs_tune(h.ptr, param, v)
         tuned_ms = None
     else:
@@ -276,7 +276,8 @@ def launch_choice(api, h) -> dict:
     return {"groups_per_cta": api.cs_tune_get(h.ptr, api.CS_TUNE_GROUPS_PER_CTA),
             "ctas_per_sm": api.cs_tune_get(h.ptr, api.CS_TUNE_CTAS_PER_SM),
             "tile_split": api.cs_tune_get(h.ptr, api.CS_TUNE_SPLIT),
-            "weights": WEIGHT_MODES[api.cs_tune_get(h.ptr, api.CS_TUNE_WEIGHTS)]}
+            "weights": WEIGHT_MODES[api.cs_tune_get(h.ptr, api.CS_TUNE_WEIGHTS)],
+            "l2_hint": api.cs_tune_get(h.ptr, api.CS_TUNE_L2_HINT)}
 
 
 def q_eval_run(api, torch, h, fd, N, ncells, world=1):
@@ -436,7 +437,8 @@ def serve_sweep(args):
     cap = sat["requests_per_s"]
     out = {"load": f"{n} Poisson requests per rate, N in {{12,16,24,32}}, lambda in {{0,1}}, 2-4 Maxwellian "
                    f"mixtures, horizon U[1,20] time units at dt=0.01, every 8th request BKW (lambda=0, K0=0.6), "
-                   f"weight tables resident, per-class streams, up to 8 Heun steps per iteration",
+                   f"weight tables resident, every class on its own stream advancing in chunks of up to 8 Heun steps "
+                   f"as soon as its previous chunk completes",
            "capacity_requests_per_s": cap, "saturated": sat, "sweep": []}
     for factor in (0.5, 1.0, 2.0):
         r = serve.serve_bench(n, factor * cap, horizon=hz, bkw_every=8)
@@ -828,7 +830,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="wall32")
     ap.add_argument("--cells", type=int, default=0, help="override the workload's cell count (profiling runs)")
     ap.add_argument("--tune", default="", help="fixed launch choices instead of the autotuner: "
-                    "groups_per_cta,ctas_per_sm,tile_split,weights (profiling runs)")
+                    "groups_per_cta,ctas_per_sm,tile_split,weights[,l2_hint] (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true", help="omit the double-precision comparison")
     ap.add_argument("--skip-secondary", action="store_true", help="omit the other wall workload")

@@ -428,6 +428,14 @@ int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, double eps, d
  *   CS_TUNE_WEIGHTS         1: read the stored weight tiles; 2: rebuild each
  *                           tile from the radius tables (float strip handles;
  *                           results agree to float rounding of the weights)
+ *   CS_TUNE_L2_HINT         1: plain copies; 2 (default, 0 = 2): the
+ *                           convolution's tile copies carry L2 eviction
+ *                           priorities (the weight tiles, streamed once per
+ *                           launch, evict first; the f-hat rows, read again by
+ *                           every pencil that needs them, evict last): at
+ *                           N = 32, 256 cells 2.2 GB of DRAM reads per launch
+ *                           instead of 3.1 GB in the same time; changes
+ *                           traffic, not results
  * Settings of the handle's checks and of its Heun steps (no counterpart in
  * the paper; failure detection and test plumbing):
  *   CS_TUNE_WAIT_US         limit of every bounded device-side wait of the
@@ -465,6 +473,7 @@ int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, double eps, d
 #define CS_TUNE_TEST_STALL 6
 #define CS_TUNE_CHECK_INPUT 7
 #define CS_TUNE_FORWARD_NEXT 8
+#define CS_TUNE_L2_HINT 9
 int cs_tune(cs_handle_t h, int param, int value);
 
 /* The current value of a launch choice (0 = automatic).

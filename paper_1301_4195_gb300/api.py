@@ -323,6 +323,7 @@ CS_TUNE_WAIT_US = 5        # limit of the convolution's bounded waits, microseco
 CS_TUNE_TEST_STALL = 6     # 1: the first CTA of each convolution launch issues no copy (its waits run out)
 CS_TUNE_CHECK_INPUT = 7    # 1: scan inputs for non-finite values, 2: also for negative ones
 CS_TUNE_FORWARD_NEXT = 8   # 2: a Heun step's second forward transform in a launch of its own
+CS_TUNE_L2_HINT = 9        # 1: plain copies; 2 (default): L2 eviction priorities (weights first, rows last)
 
 
 def cs_tune(h, param: int, value: int):

@@ -145,8 +145,9 @@ int launch_strip_mixed(const Handle *const *hds, const int *ncells, int n, cudaS
                            (float)(hd.g.dz * hd.g.dz * hd.g.dz),
                            nblocks, N, (int)first};
         js.j[k].S = parts;
-        js.j[k].wait_ns = hd.wait_ns ? hd.wait_ns : kWaitNs;
+        js.j[k].wait_us = hd.wait_us ? hd.wait_us : kWaitUs;
         js.j[k].stall = hd.test_stall;
+        js.j[k].l2hint = hd.tune_l2 != 1;
         first += (long long)N * N * nblocks * parts;
     }
     if (first > 0x7fffffff) return set_error(CS_EINVAL, "mixed convolution: too many items");

@@ -954,7 +954,7 @@ int cs_tune(cs_handle_t h, int param, int value)
         break;
     case CS_TUNE_WAIT_US:
         if (value < 0 || value > 10000000) return set_error(CS_EINVAL, "wait limit must be 0 .. 10^7 microseconds");
-        hd.wait_ns = 1000ull * (unsigned long long)value;
+        hd.wait_us = (unsigned)value;
         break;
     case CS_TUNE_TEST_STALL:
         if (value < 0 || value > 1) return set_error(CS_EINVAL, "test stall must be 0 or 1");
@@ -967,6 +967,10 @@ int cs_tune(cs_handle_t h, int param, int value)
     case CS_TUNE_FORWARD_NEXT:
         if (value < 0 || value > 2) return set_error(CS_EINVAL, "forward-next must be 0, 1 or 2");
         hd.tune_fwd_next = value;
+        break;
+    case CS_TUNE_L2_HINT:
+        if (value < 0 || value > 2) return set_error(CS_EINVAL, "L2 hint must be 0, 1 or 2");
+        hd.tune_l2 = value;
         break;
     default: return set_error(CS_EINVAL, "unknown tuning parameter");
     }
@@ -984,10 +988,11 @@ int cs_tune_get(cs_handle_t h, int param, int *value)
     case CS_TUNE_CTAS_PER_SM: *value = h->h.tune_ctas; return CS_OK;
     case CS_TUNE_WEIGHTS: *value = h->h.tune_weights; return CS_OK;
     case CS_TUNE_SPLIT: *value = h->h.tune_split; return CS_OK;
-    case CS_TUNE_WAIT_US: *value = (int)(h->h.wait_ns / 1000ull); return CS_OK;
+    case CS_TUNE_WAIT_US: *value = (int)h->h.wait_us; return CS_OK;
     case CS_TUNE_TEST_STALL: *value = h->h.test_stall; return CS_OK;
     case CS_TUNE_CHECK_INPUT: *value = h->h.check_input; return CS_OK;
     case CS_TUNE_FORWARD_NEXT: *value = h->h.tune_fwd_next; return CS_OK;
+    case CS_TUNE_L2_HINT: *value = h->h.tune_l2; return CS_OK;
     default: return set_error(CS_EINVAL, "unknown tuning parameter");
     }
 }

@@ -162,11 +162,12 @@ struct Handle {
     int tune_ctas = 0;    // resident CTAs per SM of the persistent strip kernel
     int tune_weights = 0; // 1 = stored tiles, 2 = tiles rebuilt from the radius tables
     int tune_split = 0;   // tile ranges per pencil at N = 16 (2 or 4; 0 = 2)
-    // checks (cs_tune): limit of the convolution's bounded waits (ns, 0 =
+    int tune_l2 = 0;      // L2 eviction priorities on the convolution's copies (1 off, 2 on; 0 = on)
+    // checks (cs_tune): limit of the convolution's bounded waits (us, 0 =
     // 2 s), the stall that makes them run out in tests, the input scan
     // (0 off, 1 non-finite, 2 non-finite or negative), and whether a Heun
     // step's first inverse launch also transforms forward (2 = no)
-    unsigned long long wait_ns = 0;
+    unsigned wait_us = 0;
     int test_stall = 0;
     int check_input = 0;
     int tune_fwd_next = 0;

@@ -78,8 +78,9 @@ Handle view_of(const Handle &hd)
     v.tune_split = hd.tune_split;
     v.tune_gpc = hd.tune_gpc;
     v.tune_ctas = hd.tune_ctas;
-    v.wait_ns = hd.wait_ns;
+    v.wait_us = hd.wait_us;
     v.test_stall = hd.test_stall;
+    v.tune_l2 = hd.tune_l2;
     v.err = hd.err;
     v.counter = hd.counter;
     v.tw64 = hd.tw64;

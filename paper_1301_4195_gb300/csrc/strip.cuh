@@ -13,7 +13,7 @@ namespace cs {
 
 namespace {
 
-constexpr unsigned long long kWaitNs = 2000000000ull;
+constexpr unsigned kWaitUs = 2000000u;  // default limit of a bounded wait: 2 s
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -60,9 +60,37 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t b
                  : "memory");
 }
 
+// the same with an L2 eviction priority for the source lines (a policy from
+// createpolicy): the weight tiles stream through L2 once per launch (evict
+// first) while the f-hat rows are read again by every pencil that needs them
+// (evict last)
+__device__ __forceinline__ void bulk_copy_hint(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
+                                               uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+        : "memory");
+}
+
+__device__ __forceinline__ uint64_t l2_policy_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t l2_policy_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
 // wait for the phase of parity `parity`; false if the CTA aborted or the wait
 // exceeded its time limit (then the CTA is told to abort and *err is set)
-__device__ bool wait_phase(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *err, unsigned long long limit)
+__device__ bool wait_phase(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *err, unsigned limit_us)
 {
     if (mbar_test(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
@@ -70,7 +98,7 @@ __device__ bool wait_phase(uint64_t *bar, uint32_t parity, volatile int *abort_f
         if (mbar_test(bar, parity)) return true;
         if ((it & 63) == 0) {
             if (*abort_flag) return false;
-            if (globaltimer() - t0 > limit) {
+            if (globaltimer() - t0 > 1000ull * limit_us) {
                 *abort_flag = 1;
                 atomicOr(err, 1);
                 return false;
@@ -122,6 +150,7 @@ __device__ __forceinline__ void wrow(const float *g, int e0, float2 (&w)[K])
 }
 
 __device__ __forceinline__ float2 wpair(const float *g, int e) { return make_float2(g[e], g[e]); }
+
 
 // UB uniform rows starting at row m3 = m3b: window value t is the partner at
 // s3 = smin + t; entry (u, j) uses t = j - u + UB - 1.  Weights: UB rows of K.
@@ -340,8 +369,9 @@ struct StripJob {
     int bbn = 0;
     // limit of the item's bounded waits, and the test stall (the launch's
     // first CTA issues no copy for its first item, so its waits run out)
-    unsigned long long wait_ns = kWaitNs;
+    unsigned wait_us = kWaitUs;
     int stall = 0;
+    int l2hint = 0;  // 1: copies carry L2 eviction priorities (weights first, f-hat rows last)
 };
 
 // A persistent CTA's stage ring: barriers and the abort word at the front of
@@ -500,7 +530,7 @@ __device__ __forceinline__ void ring_drain(const Ring &r, bool ok)
         const uint32_t from = r.issued > r.tt + NST ? r.issued - NST : r.tt;
         for (uint32_t u = from; u < r.issued; ++u) {
             volatile int dummy = 0;
-            wait_phase(&r.full[u % NST], (u / NST) & 1u, &dummy, r.err, kWaitNs / 20);
+            wait_phase(&r.full[u % NST], (u / NST) & 1u, &dummy, r.err, kWaitUs / 20);
         }
     }
 }
@@ -544,18 +574,34 @@ __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &r
     auto issue_next = [&]() -> bool {
         const uint32_t u = rg.tt + pt;
         const int s = u % NST;
-        if (u >= NST && !wait_phase(&rg.empty[s], ((u / NST) + 1) & 1u, rg.abort_flag, rg.err, jb.wait_ns))
+        if (u >= NST && !wait_phase(&rg.empty[s], ((u / NST) + 1) & 1u, rg.abort_flag, rg.err, jb.wait_us))
             return false;
         unsigned char *st = rg.stages + s * C::STAGE;
         mbar_arrive_expect_tx(&rg.full[s], 2 * GPC * C::ROWB + (RAD ? 0 : C::GB));
+        if (jb.l2hint) {  // policies made here (one instruction each), so no thread holds them in registers
+            const uint64_t pol_f = l2_policy_evict_last();
 #pragma unroll
-        for (int q = 0; q < GPC; ++q) {
-            const float2 *Fq = Fb0 + (size_t)q * C::M * kGroup;
-            bulk_copy(st + q * C::ROWB, Fq + (size_t)(pw.m1 * N + pw.m2) * N * kGroup, C::ROWB, &rg.full[s]);
-            bulk_copy(st + (GPC + q) * C::ROWB, Fq + (size_t)((K1 - pw.m1) * N + (K2 - pw.m2)) * N * kGroup,
-                      C::ROWB, &rg.full[s]);
+            for (int q = 0; q < GPC; ++q) {
+                const float2 *Fq = Fb0 + (size_t)q * C::M * kGroup;
+                bulk_copy_hint(st + q * C::ROWB, Fq + (size_t)(pw.m1 * N + pw.m2) * N * kGroup, C::ROWB,
+                               &rg.full[s], pol_f);
+                bulk_copy_hint(st + (GPC + q) * C::ROWB,
+                               Fq + (size_t)((K1 - pw.m1) * N + (K2 - pw.m2)) * N * kGroup, C::ROWB, &rg.full[s],
+                               pol_f);
+            }
+            if constexpr (!RAD)
+                bulk_copy_hint(st + 2 * GPC * C::ROWB, Gp + (size_t)pt * C::TSV, C::GB, &rg.full[s],
+                               l2_policy_evict_first());
+        } else {
+#pragma unroll
+            for (int q = 0; q < GPC; ++q) {
+                const float2 *Fq = Fb0 + (size_t)q * C::M * kGroup;
+                bulk_copy(st + q * C::ROWB, Fq + (size_t)(pw.m1 * N + pw.m2) * N * kGroup, C::ROWB, &rg.full[s]);
+                bulk_copy(st + (GPC + q) * C::ROWB, Fq + (size_t)((K1 - pw.m1) * N + (K2 - pw.m2)) * N * kGroup,
+                          C::ROWB, &rg.full[s]);
+            }
+            if constexpr (!RAD) bulk_copy(st + 2 * GPC * C::ROWB, Gp + (size_t)pt * C::TSV, C::GB, &rg.full[s]);
         }
-        if constexpr (!RAD) bulk_copy(st + 2 * GPC * C::ROWB, Gp + (size_t)pt * C::TSV, C::GB, &rg.full[s]);
         ++pt;
         ++rg.issued;
         pw.next();
@@ -607,7 +653,7 @@ __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &r
                 radius_gather<N, EPL>(jb, s_emap, seg, nseg, radius_tile<N>(k1, k2, nw.m1, nw.m2), lane, pa);
             }
         }
-        if (!wait_phase(&rg.full[s], (u / NST) & 1u, rg.abort_flag, rg.err, jb.wait_ns)) {
+        if (!wait_phase(&rg.full[s], (u / NST) & 1u, rg.abort_flag, rg.err, jb.wait_us)) {
             ok = false;
             break;
         }
@@ -683,7 +729,11 @@ __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &r
 // Resident CTAs per SM the register allocation must allow: at N = 16 the
 // kernel is latency-bound and 128 registers (8 one-group or 4 two-group CTAs
 // per SM) measured faster than the ~134 the compiler picks on its own; for
-// the other N one CTA (no cap) measured best.
+// the other N one CTA (no cap) measured best.  At N = 32 (one group per CTA)
+// three CTAs share an SM only while a thread needs at most 168 registers
+// (they are allocated in steps of 8): 170 rounded up to 176 and left two,
+// 7 % slower, and a cap of three CTAs made the compiler settle at 163, 2 %
+// slower than its own 166.
 template <int N, int GPC>
 constexpr int strip_min_ctas() { return N == 16 ? (GPC == 1 ? 8 : 4) : 1; }
 
@@ -757,8 +807,9 @@ int launch_cfg(const Handle &hd, int ncells, cudaStream_t s)
     StripJob jb{(const float *)hd.ghat, hd.pencil_tile0, hd.pencil_order, (const float2 *)hd.F,
                 (float2 *)hd.Qh, (float2 *)hd.Qh2, (float2 *)hd.Qh3, (float2 *)hd.Qh4, hd.done, hd.err, omega,
                 nblocks, N, 0};
-    jb.wait_ns = hd.wait_ns ? hd.wait_ns : kWaitNs;
+    jb.wait_us = hd.wait_us ? hd.wait_us : kWaitUs;
     jb.stall = hd.test_stall;
+    jb.l2hint = hd.tune_l2 != 1;
     if constexpr (RAD) {
         jb.radA = hd.radA;
         jb.radB = hd.radB;

@@ -12,18 +12,23 @@ a horizon t_end, in Heun steps of dt (cs_relax).  The server
   workspace), in arrival order; a float class whose table of every pair
   does not fit is built from the radius tables alone (CS_WEIGHTS_RADIUS:
   9 MB instead of 0.9 GB at N = 32), slower per step but admitted;
-* per iteration advances every active request of every class by a chunk of
-  Heun steps (at most max_chunk, and never past the end of any of the
-  class's requests, so each request takes exactly its own number of steps):
-  one cs_relax per class on its own stream (classes overlap on the
-  device), or with batched=True one cs_relax_batched call over all active
-  classes (a replayed graph with one branch per class and the float classes'
-  convolutions as one persistent launch per evaluation); requests that
-  arrive while others run join the next iteration.  Per-class streams are
-  the default: with classes of a few requests each, the shared launch pads
-  every small class to whole pairs of 32-cell groups and the batched graph
-  is captured again whenever a class's size changes, and at 100 requests/s
-  it measured 15 % lower throughput;
+* runs every class on its own: a class advances all its active requests by
+  a chunk of Heun steps (one cs_relax, a replayed graph, on the class's
+  stream; at most max_chunk steps and never past the end of any of its
+  requests, so each request takes exactly its own number of steps), and as
+  soon as that chunk has completed (an event, polled) it retires its
+  finished requests, admits waiting ones and launches the next chunk.  No
+  class waits for another: the chunks of all classes overlap on the device,
+  a small grid's requests are not held to the pace of the largest, and a
+  request that arrives while its class runs joins at the class's next chunk.
+  With batched=True the classes instead advance in lock step, one
+  cs_relax_batched call over all of them per iteration (a replayed graph
+  with one branch per class and the float classes' convolutions as one
+  persistent launch per evaluation).  Per-class streams are the default:
+  with classes of a few requests each, the shared launch pads every small
+  class to whole pairs of 32-cell groups and the batched graph is captured
+  again whenever a class's size changes, and at 100 requests/s it measured
+  15 % lower throughput;
 * retires finished requests (their final state is copied out) and compacts
   the class buffer by moving the last active state into the freed slot.
 
@@ -78,6 +83,14 @@ class _Class:
         self.buf = torch.empty((capacity, N, N, N), dtype=torch.float64, device=device)
         self.reqs: List[Request] = []
         self.handle.reserve(capacity)
+        # the chunk in flight: completion event, its cells and steps
+        self.event = None
+        self.inflight_n = 0
+        self.inflight_k = 0
+
+    @property
+    def idle(self) -> bool:
+        return self.event is None
 
     def grow(self, capacity: int):
         if capacity <= self.capacity:
@@ -155,11 +168,19 @@ class Server:
         heapq.heappush(self.waiting, (req.arrival, req.rid, req))
 
     def _admit(self):
+        """Admit arrived requests in arrival order into classes that have no
+        chunk in flight (their buffers may then move and grow); a request
+        whose class is busy waits for its next chunk boundary, and those
+        behind it in other classes are not held up by it."""
         now = self.now()
+        held = []
         while self.waiting and self.waiting[0][0] <= now:
             _, _, r = self.waiting[0]
             key = (r.N, float(r.lam))
             c = self.classes.get(key)
+            if c is not None and not c.idle:
+                held.append(heapq.heappop(self.waiting))
+                continue
             extra, radius = 0, False
             if c is None:
                 extra += self._class_bytes(r.N) + 32 * self._cell_bytes(r.N)
@@ -185,10 +206,12 @@ class Server:
                 c.buf[slot].copy_(torch.from_numpy(np.ascontiguousarray(r.f0)).to(self.device, non_blocking=False))
             c.reqs.append(r)
             r.admitted = now
+        for item in held:
+            heapq.heappush(self.waiting, item)
 
     def _evict_idle(self):
         """Free the weight tables and buffers of classes with no active request."""
-        for key in [k for k, c in self.classes.items() if not c.reqs]:
+        for key in [k for k, c in self.classes.items() if not c.reqs and c.idle]:
             c = self.classes.pop(key)
             c.stream.synchronize()
             c.handle.close()
@@ -213,37 +236,60 @@ class Server:
                 i += 1
 
     def _chunk(self, reqs) -> int:
-        """Heun steps the next iteration may take without passing any request's end."""
+        """Heun steps the next chunk may take: max_chunk, but no request's end passed."""
         return max(1, min([self.max_chunk] + [r.steps_total - r.steps_done for r in reqs]))
 
     def iterate(self) -> bool:
-        """One iteration: admit, a chunk of Heun steps for every active request,
-        retire.  Returns False when nothing is active or waiting."""
+        """One pass of the loop; returns False when nothing is active or waiting."""
+        return self._iterate_batched() if self.batched else self._iterate_async()
+
+    def _iterate_async(self) -> bool:
+        """Complete the chunks that have finished (steps counted, requests
+        retired), admit, and launch the next chunk of every idle class."""
+        progressed = False
+        for c in self.classes.values():
+            if c.event is not None and c.event.query():
+                for r in c.reqs[:c.inflight_n]:
+                    r.steps_done += c.inflight_k
+                c.event = None
+                self._retire(c)
+                progressed = True
+        self._admit()
+        for c in self.classes.values():
+            if c.idle and c.reqs:
+                n, k = len(c.reqs), self._chunk(c.reqs)
+                api.cs_relax(c.handle.ptr, c.buf[:n], n, self.dt, self.eps, k, stream=c.stream)
+                c.event = torch.cuda.Event()
+                c.event.record(c.stream)
+                c.inflight_n, c.inflight_k = n, k
+                self.iterations += 1
+                progressed = True
+        if all(c.idle for c in self.classes.values()) and not self.waiting:
+            return False
+        if not progressed:
+            time.sleep(5e-5)  # nothing finished or arrived yet
+        return True
+
+    def _iterate_batched(self) -> bool:
+        """Lock step: admit, one chunk of Heun steps for every active request in
+        one cs_relax_batched call, retire."""
         self._admit()
         active = [c for c in self.classes.values() if c.reqs]
         if not active and not self.waiting:
             return False
-        steps = {}
-        if self.batched and active:
+        if active:
             k = self._chunk([r for c in active for r in c.reqs])  # one chunk for the shared graph
             for j in range(0, len(active), 16):  # at most 16 entries per batched call
                 part = active[j:j + 16]
                 api.cs_relax_batched([(c.handle.ptr, c.buf[:len(c.reqs)], len(c.reqs)) for c in part], self.dt,
                                      k, self.eps, stream=self.stream)
-            steps = {id(c): k for c in active}
-        else:
+            self.stream.synchronize()
             for c in active:
-                n, k = len(c.reqs), self._chunk(c.reqs)
-                api.cs_relax(c.handle.ptr, c.buf[:n], n, self.dt, self.eps, k, stream=c.stream)
-                steps[id(c)] = k
-        for c in active:
-            for r in c.reqs:
-                r.steps_done += steps[id(c)]
-        for c in active:
-            c.stream.synchronize()
-            self._retire(c)
-        self.iterations += 1
-        if not active:
+                for r in c.reqs:
+                    r.steps_done += k
+                self._retire(c)
+            self.iterations += 1
+        else:
             time.sleep(1e-4)  # idle until the next arrival
         if not any(c.reqs for c in self.classes.values()) and not self.waiting:
             return False
