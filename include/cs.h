@@ -434,7 +434,8 @@ int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, double eps, d
  *                           launch, evict first; the f-hat rows, read again by
  *                           every pencil that needs them, evict last): at
  *                           N = 32, 256 cells 2.2 GB of DRAM reads per launch
- *                           instead of 3.1 GB in the same time; changes
+ *                           instead of 3.1 GB in the same time; 3: the weight
+ *                           tiles' priority only; 4: the rows' only; changes
  *                           traffic, not results
  * Settings of the handle's checks and of its Heun steps (no counterpart in
  * the paper; failure detection and test plumbing):

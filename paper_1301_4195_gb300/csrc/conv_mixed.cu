@@ -147,7 +147,7 @@ int launch_strip_mixed(const Handle *const *hds, const int *ncells, int n, cudaS
         js.j[k].S = parts;
         js.j[k].wait_us = hd.wait_us ? hd.wait_us : kWaitUs;
         js.j[k].stall = hd.test_stall;
-        js.j[k].l2hint = hd.tune_l2 != 1;
+        js.j[k].l2hint = l2_hint_bits(hd.tune_l2);
         first += (long long)N * N * nblocks * parts;
     }
     if (first > 0x7fffffff) return set_error(CS_EINVAL, "mixed convolution: too many items");

@@ -969,7 +969,7 @@ int cs_tune(cs_handle_t h, int param, int value)
         hd.tune_fwd_next = value;
         break;
     case CS_TUNE_L2_HINT:
-        if (value < 0 || value > 2) return set_error(CS_EINVAL, "L2 hint must be 0, 1 or 2");
+        if (value < 0 || value > 4) return set_error(CS_EINVAL, "L2 hint must be 0 .. 4");
         hd.tune_l2 = value;
         break;
     default: return set_error(CS_EINVAL, "unknown tuning parameter");

@@ -371,7 +371,7 @@ struct StripJob {
     // first CTA issues no copy for its first item, so its waits run out)
     unsigned wait_us = kWaitUs;
     int stall = 0;
-    int l2hint = 0;  // 1: copies carry L2 eviction priorities (weights first, f-hat rows last)
+    int l2hint = 0;  // L2 eviction priorities: bit 0 weight tiles evict first, bit 1 f-hat rows evict last
 };
 
 // A persistent CTA's stage ring: barriers and the abort word at the front of
@@ -397,6 +397,10 @@ __host__ __device__ constexpr int strip_seg_max(int N, int K)
     for (int w = 0; w < N / K; ++w) m = strip_seg_size(N, K, w) > m ? strip_seg_size(N, K, w) : m;
     return m;
 }
+
+// the L2 eviction priorities of a handle's setting (CS_TUNE_L2_HINT): 1 none,
+// 0 or 2 both, 3 the weight tiles only, 4 the f-hat rows only
+__host__ __device__ inline int l2_hint_bits(int tune) { return tune == 1 ? 0 : tune == 3 ? 1 : tune == 4 ? 2 : 3; }
 
 // Shared memory of a strip CTA: the ring head, NST stages (two f-hat rows per
 // group, plus the weight tile unless RAD), and with RAD one weight segment
@@ -535,81 +539,12 @@ __device__ __forceinline__ void ring_drain(const Ring &r, bool ok)
     }
 }
 
-// The geometry of one work item of job jb (item numbered within the job): a
-// (pencil, group block) pair, or the part-th of S ranges of its tiles.
-struct ItemPlan {
-    int pencil, gblk, part, rest, tb, T, K1, K2, lo1, lo2, hi2;
-};
-
-template <int N, int S>
-__device__ __forceinline__ ItemPlan plan_item(const StripJob &jb, int item)
-{
-    constexpr int H = N / 2;
-    ItemPlan p;
-    p.part = item % S;
-    p.rest = item / S;
-    p.pencil = jb.order[p.rest / jb.nblocks];
-    p.gblk = p.rest % jb.nblocks;
-    p.K1 = p.pencil / N + H;
-    p.K2 = p.pencil % N + H;
-    p.lo1 = max(0, p.K1 - N + 1);
-    p.lo2 = max(0, p.K2 - N + 1);
-    p.hi2 = min(N - 1, p.K2);
-    const int Tall = jb.tile0[p.pencil + 1] - jb.tile0[p.pencil];
-    p.tb = (p.part * Tall + S - 1) / S;  // this part's tiles: tb .. tb+T-1
-    p.T = ((p.part + 1) * Tall + S - 1) / S - p.tb;
-    return p;
-}
-
-// Thread 0: stage tile pt of item ip (walk position pw) into the ring's next
-// use (rg.issued), after every warp has released that slot's previous use.
-// False if that wait expired or the CTA aborted.
-template <int N, int K, int U, int NST, int GPC, bool RAD>
-__device__ __forceinline__ bool issue_tile(const StripJob &jb, const ItemPlan &ip, const TileWalk &pw, int pt,
-                                           Ring &rg)
-{
-    using C = StripCfg<N, K, U, NST, GPC, RAD>;
-    const uint32_t u = rg.issued;
-    const int s = u % NST;
-    if (u >= NST && !wait_phase(&rg.empty[s], ((u / NST) + 1) & 1u, rg.abort_flag, rg.err, jb.wait_us))
-        return false;
-    const float2 *Fb0 = jb.F + (size_t)ip.gblk * GPC * C::M * kGroup;
-    const float *Gt = jb.ghat + (size_t)(jb.tile0[ip.pencil] + ip.tb + pt) * C::TSV;
-    const size_t ra = (size_t)(pw.m1 * N + pw.m2) * N * kGroup;
-    const size_t rb = (size_t)((ip.K1 - pw.m1) * N + (ip.K2 - pw.m2)) * N * kGroup;
-    unsigned char *st = rg.stages + s * C::STAGE;
-    mbar_arrive_expect_tx(&rg.full[s], 2 * GPC * C::ROWB + (RAD ? 0 : C::GB));
-    if (jb.l2hint) {  // policies made here (one instruction each), so no thread holds them in registers
-        const uint64_t pol_f = l2_policy_evict_last();
-#pragma unroll
-        for (int q = 0; q < GPC; ++q) {
-            const float2 *Fq = Fb0 + (size_t)q * C::M * kGroup;
-            bulk_copy_hint(st + q * C::ROWB, Fq + ra, C::ROWB, &rg.full[s], pol_f);
-            bulk_copy_hint(st + (GPC + q) * C::ROWB, Fq + rb, C::ROWB, &rg.full[s], pol_f);
-        }
-        if constexpr (!RAD) bulk_copy_hint(st + 2 * GPC * C::ROWB, Gt, C::GB, &rg.full[s], l2_policy_evict_first());
-    } else {
-#pragma unroll
-        for (int q = 0; q < GPC; ++q) {
-            const float2 *Fq = Fb0 + (size_t)q * C::M * kGroup;
-            bulk_copy(st + q * C::ROWB, Fq + ra, C::ROWB, &rg.full[s]);
-            bulk_copy(st + (GPC + q) * C::ROWB, Fq + rb, C::ROWB, &rg.full[s]);
-        }
-        if constexpr (!RAD) bulk_copy(st + 2 * GPC * C::ROWB, Gt, C::GB, &rg.full[s]);
-    }
-    ++rg.issued;
-    return true;
-}
-
-// The warps' side of one work item: every warp sums its strip over the
-// item's tiles as they land in the ring (ring uses rg.tt .. rg.tt+T-1);
-// after each tile thread 0 calls produce() to stage a further one.  Then the
-// outputs, and with S > 1 the adding of the partial sums.  ok0 is thread 0's
-// state after staging the first tiles.  Returns false (CTA-uniform) if a
-// wait expired or the CTA aborted.
-template <int N, int K, int U, int NST, int GPC, int S, bool RAD, typename Produce>
-__device__ __forceinline__ bool strip_consume(const StripJob &jb, const ItemPlan &ip, Ring &rg, Produce &&produce,
-                                              bool ok0)
+// One work item of job jb (item numbered within the job): a (pencil, group
+// block) pair, or the part-th of S ranges of its tiles.  Thread 0 produces the
+// pencil's tiles into the ring, NST ahead of the warps; every warp sums its
+// strip.  Returns false (CTA-uniform) if a wait expired or the CTA aborted.
+template <int N, int K, int U, int NST, int GPC, int S, bool RAD = false>
+__device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &rg)
 {
     using C = StripCfg<N, K, U, NST, GPC, RAD>;
     constexpr int H = N / 2;
@@ -618,11 +553,77 @@ __device__ __forceinline__ bool strip_consume(const StripJob &jb, const ItemPlan
     const int k0 = warp * K;
     const bool kind_a = k0 < H;
     const int seg = strip_seg_off(N, K, warp);
-    const int pencil = ip.pencil, T = ip.T;
-    const int grp = ip.gblk * GPC + gl;
+    const int nblocks = jb.nblocks;
+    rg.err = jb.err;
+
+    const int part = item % S, rest = item / S;
+    const int pencil = jb.order[rest / nblocks];
+    const int gblk = rest % nblocks;
+    const int grp = gblk * GPC + gl;
     const int k1 = pencil / N, k2 = pencil % N;
-    float2 *Qout = ip.part == 0 ? jb.Qh : ip.part == 1 ? jb.Qh2 : ip.part == 2 ? jb.Qh3 : jb.Qh4;
-    bool ok = ok0;
+    const int K1 = k1 + H, K2 = k2 + H;
+    const int lo1 = max(0, K1 - N + 1);
+    const int lo2 = max(0, K2 - N + 1), hi2 = min(N - 1, K2);
+    const int Tall = jb.tile0[pencil + 1] - jb.tile0[pencil];
+    const int tb = (part * Tall + S - 1) / S;  // this part's tiles: tb .. te-1
+    const int te = ((part + 1) * Tall + S - 1) / S;
+    const int T = te - tb;
+    const float2 *Fb0 = jb.F + (size_t)gblk * GPC * C::M * kGroup;
+    const float *Gp = jb.ghat + (size_t)(jb.tile0[pencil] + tb) * C::TSV;
+    float2 *Qout = part == 0 ? jb.Qh : part == 1 ? jb.Qh2 : part == 2 ? jb.Qh3 : jb.Qh4;
+    bool ok = true;
+
+    TileWalk pw;  // producer's walk (thread 0), NST tiles ahead of the consumers
+    int pt = 0;
+    auto issue_next = [&]() -> bool {
+        const uint32_t u = rg.tt + pt;
+        const int s = u % NST;
+        if (u >= NST && !wait_phase(&rg.empty[s], ((u / NST) + 1) & 1u, rg.abort_flag, rg.err, jb.wait_us))
+            return false;
+        unsigned char *st = rg.stages + s * C::STAGE;
+        mbar_arrive_expect_tx(&rg.full[s], 2 * GPC * C::ROWB + (RAD ? 0 : C::GB));
+        const size_t ra = (size_t)(pw.m1 * N + pw.m2) * N * kGroup;
+        const size_t rb = (size_t)((K1 - pw.m1) * N + (K2 - pw.m2)) * N * kGroup;
+        // policies made here (one instruction each), so no thread holds them in registers
+        if (jb.l2hint & 2) {
+            const uint64_t pol_f = l2_policy_evict_last();
+#pragma unroll
+            for (int q = 0; q < GPC; ++q) {
+                const float2 *Fq = Fb0 + (size_t)q * C::M * kGroup;
+                bulk_copy_hint(st + q * C::ROWB, Fq + ra, C::ROWB, &rg.full[s], pol_f);
+                bulk_copy_hint(st + (GPC + q) * C::ROWB, Fq + rb, C::ROWB, &rg.full[s], pol_f);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < GPC; ++q) {
+                const float2 *Fq = Fb0 + (size_t)q * C::M * kGroup;
+                bulk_copy(st + q * C::ROWB, Fq + ra, C::ROWB, &rg.full[s]);
+                bulk_copy(st + (GPC + q) * C::ROWB, Fq + rb, C::ROWB, &rg.full[s]);
+            }
+        }
+        if constexpr (!RAD) {
+            if (jb.l2hint & 1)
+                bulk_copy_hint(st + 2 * GPC * C::ROWB, Gp + (size_t)pt * C::TSV, C::GB, &rg.full[s],
+                               l2_policy_evict_first());
+            else
+                bulk_copy(st + 2 * GPC * C::ROWB, Gp + (size_t)pt * C::TSV, C::GB, &rg.full[s]);
+        }
+        ++pt;
+        ++rg.issued;
+        pw.next();
+        return true;
+    };
+    // the test stall: the first CTA issues nothing for its first item
+    const bool stalled = jb.stall && blockIdx.x == 0 && rg.tt == 0;
+    if (threadIdx.x == 0 && !stalled) {
+        pw.start(lo1, lo2, hi2, K1, K2);
+        for (int i = 0; i < tb; ++i) pw.next();
+        while (pt < NST && pt < T)
+            if (!issue_next()) {
+                ok = false;
+                break;
+            }
+    }
 
     float2 acc[K];
     CompSum<K, strip_comp_local<N>()> cs;
@@ -630,8 +631,8 @@ __device__ __forceinline__ bool strip_consume(const StripJob &jb, const ItemPlan
     for (int j = 0; j < K; ++j) acc[j] = make_float2(0.f, 0.f);
     cs.zero();
     TileWalk cw;
-    cw.start(ip.lo1, ip.lo2, ip.hi2, ip.K1, ip.K2);
-    for (int i = 0; i < ip.tb; ++i) cw.next();
+    cw.start(lo1, lo2, hi2, K1, K2);
+    for (int i = 0; i < tb; ++i) cw.next();
     int cur_m1 = cw.m1;
     float *wb = nullptr;  // RAD: this warp's weight segment, the entry map and B
     const int *s_emap = nullptr;
@@ -681,7 +682,8 @@ __device__ __forceinline__ bool strip_consume(const StripJob &jb, const ItemPlan
         cw.next();
         __syncwarp();
         if (lane == 0) mbar_arrive(&rg.empty[s]);
-        if (threadIdx.x == 0 && !produce()) ok = false;
+        if (threadIdx.x == 0 && pt < T && !stalled)
+            if (!issue_next()) ok = false;
         __syncwarp();
     }
     if (__syncthreads_or(!ok || *rg.abort_flag)) return false;  // CTA-uniform
@@ -704,7 +706,7 @@ __device__ __forceinline__ bool strip_consume(const StripJob &jb, const ItemPlan
         __syncthreads();
         if (threadIdx.x == 0) {
             int old;
-            asm volatile("atom.add.acq_rel.gpu.s32 %0, [%1], 1;" : "=r"(old) : "l"(jb.done + ip.rest) : "memory");
+            asm volatile("atom.add.acq_rel.gpu.s32 %0, [%1], 1;" : "=r"(old) : "l"(jb.done + rest) : "memory");
             s_last = old == S - 1;
         }
         __syncthreads();
@@ -726,37 +728,6 @@ __device__ __forceinline__ bool strip_consume(const StripJob &jb, const ItemPlan
     return true;
 }
 
-// One work item with its own producer (the mixed kernel, whose items may
-// differ in stage size, so the ring is empty between them): thread 0 stages
-// the item's first NST tiles, then one more after each consumed tile.
-template <int N, int K, int U, int NST, int GPC, int S, bool RAD = false>
-__device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &rg)
-{
-    rg.err = jb.err;
-    const ItemPlan ip = plan_item<N, S>(jb, item);
-    // the test stall: the first CTA issues nothing for its first item
-    const bool stalled = jb.stall && blockIdx.x == 0 && rg.tt == 0;
-    TileWalk pw;  // producer's walk (thread 0), NST tiles ahead of the consumers
-    int pt = 0;
-    bool ok = true;
-    auto produce = [&]() -> bool {
-        if (stalled || pt >= ip.T) return true;
-        if (!issue_tile<N, K, U, NST, GPC, RAD>(jb, ip, pw, pt, rg)) return false;
-        ++pt;
-        pw.next();
-        return true;
-    };
-    if (threadIdx.x == 0 && !stalled) {
-        pw.start(ip.lo1, ip.lo2, ip.hi2, ip.K1, ip.K2);
-        for (int i = 0; i < ip.tb; ++i) pw.next();
-        while (pt < NST && pt < ip.T)
-            if (!produce()) {
-                ok = false;
-                break;
-            }
-    }
-    return strip_consume<N, K, U, NST, GPC, S, RAD>(jb, ip, rg, produce, ok);
-}
 
 // Persistent kernel: CTAs take (pencil, group block) items from an atomic
 // counter, heaviest pencils first, so the tail of the launch holds only the
@@ -778,6 +749,7 @@ __global__ void __launch_bounds__(32 * (N / K) * GPC, strip_min_ctas<N, GPC>())
 {
     using C = StripCfg<N, K, U, NST, GPC, RAD>;
     extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int s_item;
     Ring rg = ring_init<NST, C::WARPS>(smem, jb.err);
     if constexpr (RAD) {  // the entry map and B into shared memory, once per CTA
         float *r = reinterpret_cast<float *>(rg.stages + NST * C::STAGE) + C::WARPS * C::WBUF;
@@ -787,54 +759,15 @@ __global__ void __launch_bounds__(32 * (N / K) * GPC, strip_min_ctas<N, GPC>())
         __syncthreads();
     }
     const int nitems = N * N * jb.nblocks * S;
-    // Thread 0 is the producer and runs ahead of the warps across items: when
-    // it has staged every tile of its item it takes the next item from the
-    // counter and goes on staging that one's tiles, so the ring stays full
-    // while the warps finish an item and add its partial sums, and the next
-    // item starts on landed tiles.  Items go through a small queue of their
-    // numbers in shared memory (the producer is at most NST tiles, hence at
-    // most NST + 1 items, ahead).
-    __shared__ int s_items[8];
-    ItemPlan pp{};  // producer's item, walk and next tile
-    TileWalk pw{};
-    int ppt = 0, pord = 0;
-    bool plive = false;
-    auto fetch = [&]() -> bool {  // the next item for the producer; false when the counter is spent
-        const int it = *rg.abort_flag ? nitems : atomicAdd(counter, 1);
-        s_items[pord++ & 7] = it;
-        if (it >= nitems) return false;
-        pp = plan_item<N, S>(jb, it);
-        pw.start(pp.lo1, pp.lo2, pp.hi2, pp.K1, pp.K2);
-        for (int i = 0; i < pp.tb; ++i) pw.next();
-        ppt = 0;
-        return true;
-    };
-    auto produce = [&]() -> bool {
-        if (*rg.abort_flag) return false;
-        while (plive && ppt >= pp.T) plive = fetch();
-        if (!plive) return true;
-        if (!issue_tile<N, K, U, NST, GPC, RAD>(jb, pp, pw, ppt, rg)) return false;
-        ++ppt;
-        pw.next();
-        return true;
-    };
     bool ok = true;
-    if (threadIdx.x == 0) {
-        plive = fetch();
-        // the test stall: the first CTA issues no copy at all
-        if (jb.stall && blockIdx.x == 0) plive = false;
-        while (plive && rg.issued < NST)
-            if (!produce()) {
-                ok = false;
-                break;
-            }
-    }
-    for (int ci = 0;; ++ci) {
-        __syncthreads();  // thread 0 wrote item ci's number before this barrier
-        const int item = s_items[ci & 7];
+    for (;;) {
+        // thread 0 decides for the whole CTA, so every thread leaves the loop together
+        if (threadIdx.x == 0) s_item = *rg.abort_flag ? nitems : atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
         if (item >= nitems) break;
-        if (!strip_consume<N, K, U, NST, GPC, S, RAD>(jb, plan_item<N, S>(jb, item), rg, produce,
-                                                      threadIdx.x == 0 ? ok : true)) {
+        if (!strip_item<N, K, U, NST, GPC, S, RAD>(jb, item, rg)) {
             ok = false;
             break;
         }
@@ -882,7 +815,7 @@ int launch_cfg(const Handle &hd, int ncells, cudaStream_t s)
                 nblocks, N, 0};
     jb.wait_us = hd.wait_us ? hd.wait_us : kWaitUs;
     jb.stall = hd.test_stall;
-    jb.l2hint = hd.tune_l2 != 1;
+    jb.l2hint = l2_hint_bits(hd.tune_l2);
     if constexpr (RAD) {
         jb.radA = hd.radA;
         jb.radB = hd.radB;
