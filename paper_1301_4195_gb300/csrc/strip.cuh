@@ -406,10 +406,14 @@ __host__ __device__ inline int l2_hint_bits(int tune) { return tune == 1 ? 0 : t
 // group, plus the weight tile unless RAD), and with RAD one weight segment
 // per warp rebuilt from the radius tables, the tile entry map and the table
 // B (both copied in once per CTA).
-template <int N, int K, int U, int NST, int GPC, bool RAD = false>
+// HS = 2 (few cells): a warp sums two strips of the same kind for 16 cells
+// of one group, lanes 0-15 the first strip, lanes 16-31 the second; every
+// (cell, output) runs the same operations in the same order as with HS = 1,
+// so results are the same bit for bit.
+template <int N, int K, int U, int NST, int GPC, bool RAD = false, int HS = 1>
 struct StripCfg {
     static constexpr int W = N / K;
-    static constexpr int WARPS = W * GPC;
+    static constexpr int WARPS = W * GPC / HS;
     static constexpr int M = N * N * N;
     static constexpr int TSV = strip_stride(N, K);
     static constexpr uint32_t ROWB = N * kGroup * sizeof(float2);
@@ -543,13 +547,18 @@ __device__ __forceinline__ void ring_drain(const Ring &r, bool ok)
 // block) pair, or the part-th of S ranges of its tiles.  Thread 0 produces the
 // pencil's tiles into the ring, NST ahead of the warps; every warp sums its
 // strip.  Returns false (CTA-uniform) if a wait expired or the CTA aborted.
-template <int N, int K, int U, int NST, int GPC, int S, bool RAD = false>
+template <int N, int K, int U, int NST, int GPC, int S, bool RAD = false, int HS = 1>
 __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &rg)
 {
-    using C = StripCfg<N, K, U, NST, GPC, RAD>;
+    using C = StripCfg<N, K, U, NST, GPC, RAD, HS>;
     constexpr int H = N / 2;
+    static_assert(HS == 1 || (HS == 2 && GPC == 1 && !RAD && (C::W / 2) % 2 == 0),
+                  "two strips per warp: one group, stored tiles, pairs of strips of one kind");
     const int warp_id = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gl = warp_id / C::W, warp = warp_id % C::W;  // group within the CTA, strip
+    // group within the CTA, strip, and the cell's lane in the group
+    const int gl = HS == 1 ? warp_id / C::W : 0;
+    const int warp = HS == 1 ? warp_id % C::W : 2 * warp_id + (lane >> 4);
+    const int cl = HS == 1 ? lane : (lane & 15);
     const int k0 = warp * K;
     const bool kind_a = k0 < H;
     const int seg = strip_seg_off(N, K, warp);
@@ -676,9 +685,9 @@ __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &r
         const float2 *brow = reinterpret_cast<const float2 *>(st + (GPC + gl) * C::ROWB);
         const float *gt = RAD ? wb : reinterpret_cast<const float *>(st + 2 * GPC * C::ROWB) + seg;
         if (kind_a)
-            strip_a<N, K, U>(arow, brow, gt, k0, lane, acc);
+            strip_a<N, K, U>(arow, brow, gt, k0, cl, acc);
         else
-            strip_b<N, K, U>(arow, brow, gt, k0, lane, acc);
+            strip_b<N, K, U>(arow, brow, gt, k0, cl, acc);
         cw.next();
         __syncwarp();
         if (lane == 0) mbar_arrive(&rg.empty[s]);
@@ -691,7 +700,7 @@ __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &r
     for (int j = 0; j < K; ++j) {
         cs.add(j, acc[j]);
         const float2 v = cs.value(j);
-        Qout[((size_t)grp * C::M + (size_t)pencil * N + k0 + j) * kGroup + lane] =
+        Qout[((size_t)grp * C::M + (size_t)pencil * N + k0 + j) * kGroup + cl] =
             make_float2(jb.omega * v.x, jb.omega * v.y);
     }
     rg.tt += T;
@@ -714,7 +723,7 @@ __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &r
             const float2 *more[3] = {jb.Qh2, jb.Qh3, jb.Qh4};
 #pragma unroll
             for (int j = 0; j < K; ++j) {
-                const size_t idx = ((size_t)grp * C::M + (size_t)pencil * N + k0 + j) * kGroup + lane;
+                const size_t idx = ((size_t)grp * C::M + (size_t)pencil * N + k0 + j) * kGroup + cl;
                 float2 v = __ldcg(jb.Qh + idx);
 #pragma unroll
                 for (int m = 0; m < S - 1; ++m) {
@@ -743,11 +752,11 @@ __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &r
 template <int N, int GPC>
 constexpr int strip_min_ctas() { return N == 16 ? (GPC == 1 ? 8 : 4) : 1; }
 
-template <int N, int K, int U, int NST, int GPC, int S, bool RAD>
-__global__ void __launch_bounds__(32 * (N / K) * GPC, strip_min_ctas<N, GPC>())
+template <int N, int K, int U, int NST, int GPC, int S, bool RAD, int HS = 1>
+__global__ void __launch_bounds__(32 * (N / K) * GPC / HS, strip_min_ctas<N, GPC>())
     conv_strip_kernel(StripJob jb, int *counter)
 {
-    using C = StripCfg<N, K, U, NST, GPC, RAD>;
+    using C = StripCfg<N, K, U, NST, GPC, RAD, HS>;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int s_item;
     Ring rg = ring_init<NST, C::WARPS>(smem, jb.err);
@@ -767,7 +776,7 @@ __global__ void __launch_bounds__(32 * (N / K) * GPC, strip_min_ctas<N, GPC>())
         const int item = s_item;
         __syncthreads();
         if (item >= nitems) break;
-        if (!strip_item<N, K, U, NST, GPC, S, RAD>(jb, item, rg)) {
+        if (!strip_item<N, K, U, NST, GPC, S, RAD, HS>(jb, item, rg)) {
             ok = false;
             break;
         }
@@ -775,13 +784,13 @@ __global__ void __launch_bounds__(32 * (N / K) * GPC, strip_min_ctas<N, GPC>())
     ring_drain<NST>(rg, ok);
 }
 
-template <int N, int K, int U, int NST, int GPC, int S, bool RAD>
+template <int N, int K, int U, int NST, int GPC, int S, bool RAD, int HS = 1>
 int launch_cfg(const Handle &hd, int ncells, cudaStream_t s)
 {
-    using C = StripCfg<N, K, U, NST, GPC, RAD>;
+    using C = StripCfg<N, K, U, NST, GPC, RAD, HS>;
     static_assert(K % 4 == 0 && (N / 2) % K == 0, "strip width must divide N/2 and be a multiple of 4");
     static_assert(C::STAGE % 16 == 0 && C::ROWB % 16 == 0 && C::GB % 16 == 0, "bulk copies need 16-byte units");
-    auto kern = conv_strip_kernel<N, K, U, NST, GPC, S, RAD>;
+    auto kern = conv_strip_kernel<N, K, U, NST, GPC, S, RAD, HS>;
     if (C::SMEM > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         if (e != cudaSuccess) return cuda_error(e, "strip kernel shared-memory attribute");
@@ -789,8 +798,7 @@ int launch_cfg(const Handle &hd, int ncells, cudaStream_t s)
     const int ng = ngroups_of(ncells);
     const int nblocks = ng / GPC;  // callers pick GPC dividing ng
     const int nitems = N * N * nblocks * S;
-    static int per_sm[2] = {0, 0};  // resident CTAs per SM, per GPC variant
-    int &occ = per_sm[GPC - 1];
+    static int occ = 0;  // resident CTAs per SM of this instantiation
     if (occ == 0) {
         int v = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, 32 * C::WARPS, C::SMEM) != cudaSuccess || v < 1) {
@@ -833,6 +841,9 @@ int launch_n(const Handle &hd, int ncells, cudaStream_t s)
     const bool even = ngroups_of(ncells) % 2 == 0;
     const bool two = hd.tune_gpc == 2 || (hd.tune_gpc == 0 && N <= 16);  // measured: 1 group per CTA wins at N = 32
     if (even && two) return launch_cfg<N, K, U, NST2, 2, S, RAD>(hd, ncells, s);
+    // at most 16 cells: two strips per warp, 16 lanes each, so no lane holds padding
+    if constexpr (!RAD && (N == 32 || N == 64))
+        if (ncells <= 16 && hd.tune_gpc != 1) return launch_cfg<N, K, U, NST1, 1, S, RAD, 2>(hd, ncells, s);
     return launch_cfg<N, K, U, NST1, 1, S, RAD>(hd, ncells, s);
 }
 

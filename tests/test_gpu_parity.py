@@ -430,3 +430,25 @@ def test_fma_probe_rates_are_plausible(cs):
     assert 0.1 < dfma < 1.5, dfma
     with pytest.raises(cs.CSError):
         cs.cs_fma_probe(3)
+
+
+@pytest.mark.parametrize("N", [32])
+def test_few_cells_two_strips_per_warp_is_exact(cs, orc, N):
+    """At most 16 cells: the convolution puts two strips in each warp (16
+    lanes each) instead of leaving half the lanes on padding.  Every (cell,
+    output) runs the same operations in the same order, so the result is the
+    same bit for bit as with one strip per warp (forced by one group per
+    CTA), and matches the oracle."""
+    f = I.random_mixture_cells(N, L, 16, first_id=1500)
+    h = cs.Handle(N, L, 1.0, "fp32")
+    fd = dev(f)
+    few = host(h.collide(fd))  # automatic: two strips per warp
+    cs.cs_tune(h.ptr, cs.CS_TUNE_GROUPS_PER_CTA, 1)
+    one = host(h.collide(fd))
+    assert np.array_equal(few, one)
+    cs.cs_tune(h.ptr, cs.CS_TUNE_GROUPS_PER_CTA, 0)
+    assert np.array_equal(host(h.collide(dev(f[:5]))), few[:5])
+    ref = orc.collide(f[[0, 15]], N, L, 1.0)
+    assert rel(few[0], ref[0]) < 1e-5 and rel(few[15], ref[1]) < 1e-5
+    cs.cs_status(h.ptr)
+    h.close()
