@@ -260,7 +260,8 @@ def step_workload(api, inputs, torch, device, N, ncells, K, W, flush, tune="", p
     h.reserve(ncells)
     if tune:  # fixed launch choices (profiling runs: timings under a profiler would mislead the autotuner)
         for param, v in zip((api.CS_TUNE_GROUPS_PER_CTA, api.CS_TUNE_CTAS_PER_SM, api.CS_TUNE_SPLIT,
-                             api.CS_TUNE_WEIGHTS, api.CS_TUNE_L2_HINT), (int(x) for x in tune.split(","))):
+                             api.CS_TUNE_WEIGHTS, api.CS_TUNE_L2_HINT, api.CS_TUNE_TILE),
+                            (int(x) for x in tune.split(","))):
             api.cs_tune(h.ptr, param, v)
         tuned_ms = None
     else:
@@ -277,7 +278,8 @@ def launch_choice(api, h) -> dict:
             "ctas_per_sm": api.cs_tune_get(h.ptr, api.CS_TUNE_CTAS_PER_SM),
             "tile_split": api.cs_tune_get(h.ptr, api.CS_TUNE_SPLIT),
             "weights": WEIGHT_MODES[api.cs_tune_get(h.ptr, api.CS_TUNE_WEIGHTS)],
-            "l2_hint": api.cs_tune_get(h.ptr, api.CS_TUNE_L2_HINT)}
+            "l2_hint": api.cs_tune_get(h.ptr, api.CS_TUNE_L2_HINT),
+            "tile": api.cs_tune_get(h.ptr, api.CS_TUNE_TILE)}
 
 
 def q_eval_run(api, torch, h, fd, N, ncells, world=1):
@@ -830,7 +832,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="wall32")
     ap.add_argument("--cells", type=int, default=0, help="override the workload's cell count (profiling runs)")
     ap.add_argument("--tune", default="", help="fixed launch choices instead of the autotuner: "
-                    "groups_per_cta,ctas_per_sm,tile_split,weights[,l2_hint] (profiling runs)")
+                    "groups_per_cta,ctas_per_sm,tile_split,weights[,l2_hint[,tile]] (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true", help="omit the double-precision comparison")
     ap.add_argument("--skip-secondary", action="store_true", help="omit the other wall workload")

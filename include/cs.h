@@ -437,6 +437,13 @@ int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, double eps, d
  *                           instead of 3.1 GB in the same time; 3: the weight
  *                           tiles' priority only; 4: the rows' only; changes
  *                           traffic, not results
+ *   CS_TUNE_TILE            float handles at N = 16 and 32 with stored tiles:
+ *                           the xi-tile and the ring depth, 1 (default, 0 =
+ *                           1): blocks of 8 uniform rows, 3 stages; 2: blocks
+ *                           of 4 rows; 3: 4 stages; 4: 2 stages.  Every output
+ *                           adds its terms in the same order in all of them
+ *                           (results bit for bit equal); cs_autotune times
+ *                           them at the best launch shape
  * Settings of the handle's checks and of its Heun steps (no counterpart in
  * the paper; failure detection and test plumbing):
  *   CS_TUNE_WAIT_US         limit of every bounded device-side wait of the
@@ -475,6 +482,7 @@ int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, double eps, d
 #define CS_TUNE_CHECK_INPUT 7
 #define CS_TUNE_FORWARD_NEXT 8
 #define CS_TUNE_L2_HINT 9
+#define CS_TUNE_TILE 10
 int cs_tune(cs_handle_t h, int param, int value);
 
 /* The current value of a launch choice (0 = automatic).
@@ -492,10 +500,11 @@ int cs_fma_probe(int kind, cudaStream_t stream, double *lane_ops_per_s);
 /* Time the convolution's launch choices on ncells synthetic cells on
  * `stream` (synchronising), keep the fastest in the handle and return its
  * time per launch in *ms (may be NULL).  The choices are the launch shapes
- * times the weight modes the handle has (stored tiles, radius tables): the
- * store-versus-recompute choice of the weights is timed, not assumed; at
- * N = 16 in float times the two splits as well.  Uses
- * the workspace (cs_reserve).
+ * (cell groups per CTA, CTAs per SM) times the weight modes the handle has
+ * (stored tiles, radius tables): the store-versus-recompute choice of the
+ * weights is timed, not assumed; at N = 16 in float it times the two splits
+ * as well; then, at the best of those, the tile shapes of CS_TUNE_TILE
+ * (N = 16 and 32 with stored tiles).  Uses the workspace (cs_reserve).
  * Errors: CS_EINVAL, CS_ENOMEM, CS_ECUDA. */
 int cs_autotune(cs_handle_t h, int ncells, cudaStream_t stream, double *ms);
 

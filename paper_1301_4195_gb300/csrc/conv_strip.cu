@@ -66,9 +66,16 @@ bool strip_uses_radius(const Handle &hd)
     return hd.radA && (!hd.has_table || hd.tune_weights == 2);
 }
 
+bool tile_shapes_available(const Handle &hd)
+{
+    return hd.precision == CS_FP32 && hd.g.layout == LAYOUT_STRIP && (hd.g.N == 16 || hd.g.N == 32) &&
+           !strip_uses_radius(hd);
+}
+
 int launch_strip(const Handle &hd, int ncells, cudaStream_t s)
 {
     if (strip_uses_radius(hd)) return launch_strip_radius(hd, ncells, s);
+    if (hd.tune_tile >= 2 && tile_shapes_available(hd)) return launch_strip_tiles(hd, ncells, s);
     return launch_strip_mode<false>(hd, ncells, s);
 }
 

@@ -972,6 +972,12 @@ int cs_tune(cs_handle_t h, int param, int value)
         if (value < 0 || value > 4) return set_error(CS_EINVAL, "L2 hint must be 0 .. 4");
         hd.tune_l2 = value;
         break;
+    case CS_TUNE_TILE:
+        if (value < 0 || value > 4) return set_error(CS_EINVAL, "tile shape must be 0 .. 4");
+        if (value >= 2 && !tile_shapes_available(hd))
+            return set_error(CS_ENOTSUP, "other tile shapes: float handles at N = 16 and 32 with stored tiles");
+        hd.tune_tile = value;
+        break;
     default: return set_error(CS_EINVAL, "unknown tuning parameter");
     }
     drop_graphs(hd);  // captured steps and batches hold the old launch configuration
@@ -993,6 +999,7 @@ int cs_tune_get(cs_handle_t h, int param, int *value)
     case CS_TUNE_CHECK_INPUT: *value = h->h.check_input; return CS_OK;
     case CS_TUNE_FORWARD_NEXT: *value = h->h.tune_fwd_next; return CS_OK;
     case CS_TUNE_L2_HINT: *value = h->h.tune_l2; return CS_OK;
+    case CS_TUNE_TILE: *value = h->h.tune_tile; return CS_OK;
     default: return set_error(CS_EINVAL, "unknown tuning parameter");
     }
 }
@@ -1022,34 +1029,59 @@ int cs_autotune(cs_handle_t h, int ncells, cudaStream_t s, double *ms)
     std::vector<int> splits = conv_split_max(hd) > 1 ? std::vector<int>{4, 2} : std::vector<int>{0};
     const size_t nc = sizeof(cand) / sizeof(cand[0]);
     double best = 1e300;
-    int bg = 0, bc = 0, bw = 0, bs = 0;
-    const int keep_g = hd.tune_gpc, keep_c = hd.tune_ctas, keep_w = hd.tune_weights, keep_s = hd.tune_split;
+    int bg = 0, bc = 0, bw = 0, bs = 0, bt = 0;
+    const int keep_g = hd.tune_gpc, keep_c = hd.tune_ctas, keep_w = hd.tune_weights, keep_s = hd.tune_split,
+              keep_t = hd.tune_tile;
     int rc = CS_OK;
+    // the average time of three launches in the current choices (one more first, untimed)
+    auto time_it = [&](double *out) -> int {
+        int r = launch_convolve(hd, ncells, s);
+        if (r != CS_OK) return r;
+        cudaEventRecord(a, s);
+        for (int k = 0; k < 3 && r == CS_OK; ++k) r = launch_convolve(hd, ncells, s);
+        cudaEventRecord(b, s);
+        if (r != CS_OK) return r;
+        cudaError_t err = cudaEventSynchronize(b);
+        float t = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&t, a, b);
+        if (err != cudaSuccess) return cuda_error(err, "cs_autotune: timing");
+        *out = t / 3.0;
+        return CS_OK;
+    };
+    // launch shapes x weight modes x splits, with the default tile shape
+    hd.tune_tile = 0;
     for (size_t ci = 0; ci < splits.size() * modes.size() * nc && rc == CS_OK; ++ci) {
         const auto &c = cand[ci % nc];
         hd.tune_weights = modes[(ci / nc) % modes.size()];
         hd.tune_split = splits[ci / (nc * modes.size())];
         hd.tune_gpc = c[0];
         hd.tune_ctas = c[1];
-        if ((rc = launch_convolve(hd, ncells, s)) != CS_OK) break;  // warm-up
-        cudaEventRecord(a, s);
-        for (int r = 0; r < 3 && rc == CS_OK; ++r) rc = launch_convolve(hd, ncells, s);
-        cudaEventRecord(b, s);
-        if (rc != CS_OK) break;
-        e = cudaEventSynchronize(b);
-        float t = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
-        if (e != cudaSuccess) {
-            rc = cuda_error(e, "cs_autotune: timing");
-            break;
-        }
-        if (t / 3.0 < best) {
-            best = t / 3.0;
+        double t = 0.0;
+        if ((rc = time_it(&t)) != CS_OK) break;
+        if (t < best) {
+            best = t;
             bg = c[0];
             bc = c[1];
             bw = hd.tune_weights;
             bs = hd.tune_split;
         }
+    }
+    // then the tile shapes (xi-tile U, ring depth) at the best of those
+    if (rc == CS_OK) {
+        hd.tune_gpc = bg;
+        hd.tune_ctas = bc;
+        hd.tune_weights = bw;
+        hd.tune_split = bs;
+        if (tile_shapes_available(hd))
+            for (int tile = 2; tile <= 4 && rc == CS_OK; ++tile) {
+                hd.tune_tile = tile;
+                double t = 0.0;
+                if ((rc = time_it(&t)) != CS_OK) break;
+                if (t < best) {
+                    best = t;
+                    bt = tile;
+                }
+            }
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
@@ -1058,16 +1090,19 @@ int cs_autotune(cs_handle_t h, int ncells, cudaStream_t s, double *ms)
         hd.tune_ctas = keep_c;
         hd.tune_weights = keep_w;
         hd.tune_split = keep_s;
+        hd.tune_tile = keep_t;
         return rc;
     }
     hd.tune_gpc = bg;
     hd.tune_ctas = bc;
     hd.tune_weights = bw;
     hd.tune_split = bs;
+    hd.tune_tile = bt;
     drop_graphs(hd);
     drop_batch_graphs_of(h);
     if (ms) *ms = best;
     (void)sms;
+    (void)e;
     return CS_OK;
 }
 

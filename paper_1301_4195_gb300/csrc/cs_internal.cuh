@@ -163,6 +163,7 @@ struct Handle {
     int tune_weights = 0; // 1 = stored tiles, 2 = tiles rebuilt from the radius tables
     int tune_split = 0;   // tile ranges per pencil at N = 16 (2 or 4; 0 = 2)
     int tune_l2 = 0;      // L2 eviction priorities on the convolution's copies (1 off, 2 on; 0 = on)
+    int tune_tile = 0;    // xi-tile and ring depth (1 = U 8 with 3 stages, the default; 2 .. 4 see conv_tiles.cu)
     // checks (cs_tune): limit of the convolution's bounded waits (us, 0 =
     // 2 s), the stall that makes them run out in tests, the input scan
     // (0 off, 1 non-finite, 2 non-finite or negative), and whether a Heun
@@ -266,6 +267,10 @@ int conv_split(const Handle &hd);
 int conv_split_max(const Handle &hd);  // the largest split the handle's workspace must hold
 int launch_strip(const Handle &hd, int ncells, cudaStream_t s);     // float, LAYOUT_STRIP
 int launch_strip_radius(const Handle &hd, int ncells, cudaStream_t s);  // conv_radius.cu
+// conv_tiles.cu: the strip launch with the tile shape hd.tune_tile (2: U = 4;
+// 3: a 4-stage ring; 4: a 2-stage ring) at N = 16 and 32, stored tiles
+int launch_strip_tiles(const Handle &hd, int ncells, cudaStream_t s);
+bool tile_shapes_available(const Handle &hd);
 bool strip_uses_radius(const Handle &hd);  // the handle's strip launches rebuild tiles from the radius tables
 
 // ---- conv_mixed.cu: the convolutions of several float strip handles in one launch

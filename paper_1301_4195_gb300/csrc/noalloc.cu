@@ -81,6 +81,7 @@ Handle view_of(const Handle &hd)
     v.wait_us = hd.wait_us;
     v.test_stall = hd.test_stall;
     v.tune_l2 = hd.tune_l2;
+    v.tune_tile = hd.tune_tile;
     v.err = hd.err;
     v.counter = hd.counter;
     v.tw64 = hd.tw64;

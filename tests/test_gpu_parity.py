@@ -452,3 +452,32 @@ def test_few_cells_two_strips_per_warp_is_exact(cs, orc, N):
     assert rel(few[0], ref[0]) < 1e-5 and rel(few[15], ref[1]) < 1e-5
     cs.cs_status(h.ptr)
     h.close()
+
+
+@pytest.mark.parametrize("N,nc,split", [(16, 64, 2), (16, 40, 4), (32, 40, 0)])
+def test_tile_shapes_give_identical_results(cs, N, nc, split):
+    """The xi-tile (blocks of 8 or 4 uniform rows) and the ring depth (2, 3 or
+    4 stages) change neither the terms nor the order each output adds them
+    in: every tile shape gives the same bits, and unsupported requests are
+    refused."""
+    h = cs.Handle(N, L, 1.0, "fp32")
+    if split:
+        cs.cs_tune(h.ptr, cs.CS_TUNE_SPLIT, split)
+    f = dev(I.random_mixture_cells(N, L, nc, first_id=1700))
+    outs = []
+    for tile in (1, 2, 3, 4):
+        cs.cs_tune(h.ptr, cs.CS_TUNE_TILE, tile)
+        assert cs.cs_tune_get(h.ptr, cs.CS_TUNE_TILE) == tile
+        outs.append(host(h.collide(f)))
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    cs.cs_tune(h.ptr, cs.CS_TUNE_TILE, 0)
+    assert cs.cs_autotune(h.ptr, nc) > 0
+    assert np.array_equal(host(h.collide(f)), outs[0])
+    cs.cs_status(h.ptr)
+    h.close()
+    h8 = cs.Handle(8, L, 1.0, "fp32")
+    with pytest.raises(cs.CSError) as e:
+        cs.cs_tune(h8.ptr, cs.CS_TUNE_TILE, 2)
+    assert e.value.code == cs.CS_ENOTSUP
+    h8.close()
