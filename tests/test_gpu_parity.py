@@ -473,7 +473,11 @@ def test_tile_shapes_give_identical_results(cs, N, nc, split):
         assert np.array_equal(o, outs[0])
     cs.cs_tune(h.ptr, cs.CS_TUNE_TILE, 0)
     assert cs.cs_autotune(h.ptr, nc) > 0
-    assert np.array_equal(host(h.collide(f)), outs[0])
+    tuned = host(h.collide(f))
+    if cs.cs_tune_get(h.ptr, cs.CS_TUNE_SPLIT) in (0, split):
+        assert np.array_equal(tuned, outs[0])
+    else:  # the autotuner also picks the split, which groups the terms differently
+        assert rel(tuned, outs[0]) < 1e-6
     cs.cs_status(h.ptr)
     h.close()
     h8 = cs.Handle(8, L, 1.0, "fp32")
