@@ -555,9 +555,17 @@ __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &r
     static_assert(HS == 1 || (HS == 2 && GPC == 1 && !RAD && (C::W / 2) % 2 == 0),
                   "two strips per warp: one group, stored tiles, pairs of strips of one kind");
     const int warp_id = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // group within the CTA, strip, and the cell's lane in the group
+    // group within the CTA, strip, and the cell's lane in the group.
+    // Warps issue from the SM's four sub-partitions by warp slot mod 4, and
+    // the strips of a tile carry unequal work (N = 32: 164, 228, 220 and 156
+    // pairs for strips 0 .. 3), so with two groups the second takes the
+    // strips shifted by W/2: the two warps of a CTA that share a
+    // sub-partition then hold a light and a heavy strip (164 + 220 and
+    // 228 + 156 at N = 32) instead of the same one twice.  Which warp sums
+    // which strip moves no arithmetic.
     const int gl = HS == 1 ? warp_id / C::W : 0;
-    const int warp = HS == 1 ? warp_id % C::W : 2 * warp_id + (lane >> 4);
+    const int warp = HS == 1 ? (GPC == 2 ? (warp_id % C::W + gl * (C::W / 2)) % C::W : warp_id % C::W)
+                             : 2 * warp_id + (lane >> 4);
     const int cl = HS == 1 ? lane : (lane & 15);
     const int k0 = warp * K;
     const bool kind_a = k0 < H;
@@ -789,6 +797,7 @@ int launch_cfg(const Handle &hd, int ncells, cudaStream_t s)
 {
     using C = StripCfg<N, K, U, NST, GPC, RAD, HS>;
     static_assert(K % 4 == 0 && (N / 2) % K == 0, "strip width must divide N/2 and be a multiple of 4");
+    static_assert(K % U == 0, "the row block must divide the strip width (the strip bodies' remainders assume it)");
     static_assert(C::STAGE % 16 == 0 && C::ROWB % 16 == 0 && C::GB % 16 == 0, "bulk copies need 16-byte units");
     auto kern = conv_strip_kernel<N, K, U, NST, GPC, S, RAD, HS>;
     if (C::SMEM > 48 * 1024) {
@@ -839,7 +848,9 @@ template <int N, int K, int U, int NST1, int NST2, int S, bool RAD>
 int launch_n(const Handle &hd, int ncells, cudaStream_t s)
 {
     const bool even = ngroups_of(ncells) % 2 == 0;
-    const bool two = hd.tune_gpc == 2 || (hd.tune_gpc == 0 && N <= 16);  // measured: 1 group per CTA wins at N = 32
+    // two groups per CTA by default up to N = 32 (N = 32, 256 cells: 13.27 ms against 13.44 ms with one
+    // group, and 1.6 GB of DRAM reads instead of 2.2 GB); at N = 48 and 64 one group fills a CTA
+    const bool two = hd.tune_gpc == 2 || (hd.tune_gpc == 0 && N <= 32);
     if (even && two) return launch_cfg<N, K, U, NST2, 2, S, RAD>(hd, ncells, s);
     // at most 16 cells: two strips per warp, 16 lanes each, so no lane holds padding
     if constexpr (!RAD && (N == 32 || N == 64))
