@@ -494,6 +494,46 @@ def n64_run(api, inputs, torch, device):
     return out
 
 
+def few_cells_run(api, inputs, torch, device, h):
+    """Convolutions over a few cells at N = 32 (the serving case): the
+    few-cell kernel (one warp per cell, a pencil's outputs over its lanes)
+    against the strip kernels (two strips per warp), same bits.  At one cell
+    the launch must at least stream the weight table, so its roofline is HBM:
+    the table's bytes per launch against the measured copy bandwidth."""
+    N = 32
+    f_all = torch.from_numpy(inputs.random_mixture_cells(N, L_BOX, 8, first_id=7600)).to(device)
+    keep = api.cs_tune_get(h.ptr, api.CS_TUNE_FEW_CELLS)
+    rows = []
+    for n in (1, 2, 4, 6):
+        f = f_all[:n].contiguous()
+        q = torch.empty_like(f)
+        r = {"cells": n}
+        outs = []
+        for key, mode in (("few_cell_ms", 16), ("strip_ms", -1)):
+            api.cs_tune(h.ptr, api.CS_TUNE_FEW_CELLS, mode)
+            r[key] = conv_ms_in_mode(api, torch, h, f, n, 1)
+            api.cs_collide(h.ptr, f, n, 1.0, q, 1)
+            outs.append(q.cpu().numpy())
+        r["identical"] = bool(np.array_equal(outs[0], outs[1]))
+        rows.append(r)
+    api.cs_tune(h.ptr, api.CS_TUNE_FEW_CELLS, keep)
+    table = h.weight_bytes()
+    ms1 = rows[0]["few_cell_ms"]
+    peak = None
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fp:
+            peak = json.load(fp)["hbm_gbs"]
+    except (OSError, KeyError, ValueError):
+        pass
+    achieved = table / (ms1 * 1e-3) / 1e9
+    return {"workload": f"the convolution of one collision evaluation, N={N}, 1-6 random-mixture cells "
+                        "(L=6, lambda=1), few-cell kernel against strip kernels",
+            "rows": rows,
+            "roofline_one_cell": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                  "frac": achieved / peak if peak else None, "traffic": None, "bytes": table,
+                                  "note": "the weight table once per launch, against the measured HBM copy bandwidth"}}
+
+
 def wall2d_run(api, inputs, torch, device, args, flush):
     """The wall problem in two space dimensions: 32 x-cells by 8 periodic
     y-cells at N = 16, the same step with the 2-D transport."""
@@ -649,6 +689,8 @@ def run_ours(args):
             out["wall2d"] = wall2d_run(api, inputs, torch, device, args, flush)
         if not args.skip_n64:
             out["n64"] = n64_run(api, inputs, torch, device)
+        if N == 32 and not args.skip_few:
+            out["few_cells"] = few_cells_run(api, inputs, torch, device, h32)
         if not args.skip_serve:
             torch.cuda.synchronize()
             out["serve"] = serve_sweep(args)
@@ -840,6 +882,7 @@ def main():
     ap.add_argument("--skip-batched", action="store_true", help="omit the uneven-N batched run")
     ap.add_argument("--skip-2d", action="store_true", help="omit the two-dimensional wall problem")
     ap.add_argument("--skip-n64", action="store_true", help="omit the N = 64 collision evaluation")
+    ap.add_argument("--skip-few", action="store_true", help="omit the few-cell convolutions")
     ap.add_argument("--config4-steps", type=int, default=2000,
                     help="Strang steps of the N = 32 run with error and drift (0: omit)")
     ap.add_argument("--serve-requests", type=int, default=200, help="requests per rate of the serving sweep")

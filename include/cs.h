@@ -422,7 +422,8 @@ int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, double eps, d
  *                           split 4 ways stay out of cs_collide_batched's
  *                           shared convolution launch
  *   CS_TUNE_GROUPS_PER_CTA  1 or 2 groups of 32 cells share each weight tile
- *                           in shared memory (2 needs an even group count)
+ *                           in shared memory (2 needs an even group count;
+ *                           0: 2 where the count is even at N <= 32, else 1)
  *   CS_TUNE_CTAS_PER_SM     resident CTAs per SM of the persistent kernel
  *                           (capped by what fits)
  *   CS_TUNE_WEIGHTS         1: read the stored weight tiles; 2: rebuild each
@@ -433,8 +434,9 @@ int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, double eps, d
  *                           priorities (the weight tiles, streamed once per
  *                           launch, evict first; the f-hat rows, read again by
  *                           every pencil that needs them, evict last): at
- *                           N = 32, 256 cells 2.2 GB of DRAM reads per launch
- *                           instead of 3.1 GB in the same time; 3: the weight
+ *                           N = 32, 256 cells and one group per CTA 2.2 GB of
+ *                           DRAM reads per launch instead of 3.1 GB in the
+ *                           same time; 3: the weight
  *                           tiles' priority only; 4: the rows' only; changes
  *                           traffic, not results
  *   CS_TUNE_TILE            float handles at N = 16 and 32 with stored tiles:
@@ -444,6 +446,14 @@ int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, double eps, d
  *                           adds its terms in the same order in all of them
  *                           (results bit for bit equal); cs_autotune times
  *                           them at the best launch shape
+ *   CS_TUNE_FEW_CELLS       float handles at N = 24 and 32 with stored tiles:
+ *                           the most cells a convolution launch gives to the
+ *                           few-cell kernel (one warp per cell, a pencil's
+ *                           outputs over its lanes) instead of the strip
+ *                           kernels; 0 (default): 6 at N = 32, 9 at N = 24,
+ *                           where it stops being faster; 1 .. 16 that many;
+ *                           -1 never.  Both kernels add every output's terms
+ *                           in the same order (results bit for bit equal)
  * Settings of the handle's checks and of its Heun steps (no counterpart in
  * the paper; failure detection and test plumbing):
  *   CS_TUNE_WAIT_US         limit of every bounded device-side wait of the
@@ -483,6 +493,7 @@ int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, double eps, d
 #define CS_TUNE_FORWARD_NEXT 8
 #define CS_TUNE_L2_HINT 9
 #define CS_TUNE_TILE 10
+#define CS_TUNE_FEW_CELLS 11
 int cs_tune(cs_handle_t h, int param, int value);
 
 /* The current value of a launch choice (0 = automatic).

@@ -74,6 +74,7 @@ bool tile_shapes_available(const Handle &hd)
 
 int launch_strip(const Handle &hd, int ncells, cudaStream_t s)
 {
+    if (lane_conv_applies(hd, ncells)) return launch_strip_lane(hd, ncells, s);
     if (strip_uses_radius(hd)) return launch_strip_radius(hd, ncells, s);
     if (hd.tune_tile >= 2 && tile_shapes_available(hd)) return launch_strip_tiles(hd, ncells, s);
     return launch_strip_mode<false>(hd, ncells, s);

@@ -978,6 +978,10 @@ int cs_tune(cs_handle_t h, int param, int value)
             return set_error(CS_ENOTSUP, "other tile shapes: float handles at N = 16 and 32 with stored tiles");
         hd.tune_tile = value;
         break;
+    case CS_TUNE_FEW_CELLS:
+        if (value < -1 || value > 16) return set_error(CS_EINVAL, "few-cell limit must be -1 .. 16");
+        hd.tune_few = value;
+        break;
     default: return set_error(CS_EINVAL, "unknown tuning parameter");
     }
     drop_graphs(hd);  // captured steps and batches hold the old launch configuration
@@ -1000,6 +1004,7 @@ int cs_tune_get(cs_handle_t h, int param, int *value)
     case CS_TUNE_FORWARD_NEXT: *value = h->h.tune_fwd_next; return CS_OK;
     case CS_TUNE_L2_HINT: *value = h->h.tune_l2; return CS_OK;
     case CS_TUNE_TILE: *value = h->h.tune_tile; return CS_OK;
+    case CS_TUNE_FEW_CELLS: *value = h->h.tune_few; return CS_OK;
     default: return set_error(CS_EINVAL, "unknown tuning parameter");
     }
 }

@@ -164,6 +164,7 @@ struct Handle {
     int tune_split = 0;   // tile ranges per pencil at N = 16 (2 or 4; 0 = 2)
     int tune_l2 = 0;      // L2 eviction priorities on the convolution's copies (1 off, 2 on; 0 = on)
     int tune_tile = 0;    // xi-tile and ring depth (1 = U 8 with 3 stages, the default; 2 .. 4 see conv_tiles.cu)
+    int tune_few = 0;     // most cells the few-cell kernel serves (0 = its default, -1 = never; conv_lane.cu)
     // checks (cs_tune): limit of the convolution's bounded waits (us, 0 =
     // 2 s), the stall that makes them run out in tests, the input scan
     // (0 off, 1 non-finite, 2 non-finite or negative), and whether a Heun
@@ -270,6 +271,8 @@ int launch_strip_radius(const Handle &hd, int ncells, cudaStream_t s);  // conv_
 // conv_tiles.cu: the strip launch with the tile shape hd.tune_tile (2: U = 4;
 // 3: a 4-stage ring; 4: a 2-stage ring) at N = 16 and 32, stored tiles
 int launch_strip_tiles(const Handle &hd, int ncells, cudaStream_t s);
+bool lane_conv_applies(const Handle &hd, int ncells);               // conv_lane.cu: the few-cell kernel serves the call
+int launch_strip_lane(const Handle &hd, int ncells, cudaStream_t s);  // its transpose and convolution launches
 bool tile_shapes_available(const Handle &hd);
 bool strip_uses_radius(const Handle &hd);  // the handle's strip launches rebuild tiles from the radius tables
 

@@ -82,6 +82,7 @@ Handle view_of(const Handle &hd)
     v.test_stall = hd.test_stall;
     v.tune_l2 = hd.tune_l2;
     v.tune_tile = hd.tune_tile;
+    v.tune_few = hd.tune_few;
     v.err = hd.err;
     v.counter = hd.counter;
     v.tw64 = hd.tw64;

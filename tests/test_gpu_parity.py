@@ -322,8 +322,12 @@ def test_collide_batched_matches_individual_calls(cs):
             q.fill_(float("nan"))
         cs.cs_launch_count(reset=True)
         cs.cs_collide_batched(entries)
-        # five strip convolutions became one launch
-        assert cs.cs_launch_count(reset=True) == alone - 4
+        # five strip convolutions became one launch; alone, the entries of a
+        # few cells at N = 24 and 32 took the few-cell kernel (two launches:
+        # the transpose of f-hat and the convolution)
+        few = sum(1 for N, _, n, prec in specs if prec == "fp32" and n <= {24: 9, 32: 6}.get(N, 0))
+        assert few == 2
+        assert cs.cs_launch_count(reset=True) == alone - 4 - few
         for q, r in zip(qs, refs):
             assert np.array_equal(host(q), r)
     # a launch choice changed after the capture holds at the next call: entry 0
@@ -333,7 +337,7 @@ def test_collide_batched_matches_individual_calls(cs):
     cs.cs_collide(hs[0].ptr, fs[0], specs[0][2], 1.0, q0, 1)
     cs.cs_launch_count(reset=True)
     cs.cs_collide_batched(entries)
-    assert cs.cs_launch_count(reset=True) == alone - 3
+    assert cs.cs_launch_count(reset=True) == alone - 3 - few
     assert np.array_equal(host(qs[0]), host(q0))
     for q, r in zip(qs[1:], refs[1:]):
         assert np.array_equal(host(q), r)
@@ -363,7 +367,10 @@ def test_relax_batched_matches_individual_calls(cs):
         fs = [dev(f) for f in f0]
         cs.cs_launch_count(reset=True)
         cs.cs_relax_batched([(h.ptr, f, n) for h, f, (_, _, n, _) in zip(hs, fs, specs)], 0.01, nsteps=3)
-        assert cs.cs_launch_count(reset=True) == alone - 3 * 2 * 3
+        # four convolutions per evaluation became one; alone, the N = 24 (9
+        # cells) and N = 32 (2 cells) entries took the few-cell kernel, two
+        # launches per evaluation
+        assert cs.cs_launch_count(reset=True) == alone - 3 * 2 * 3 - 2 * 2 * 3
         for f, r in zip(fs, refs):
             assert np.array_equal(host(f), r)
     with pytest.raises(cs.CSError):  # the same state twice
@@ -441,6 +448,7 @@ def test_few_cells_two_strips_per_warp_is_exact(cs, orc, N):
     CTA), and matches the oracle."""
     f = I.random_mixture_cells(N, L, 16, first_id=1500)
     h = cs.Handle(N, L, 1.0, "fp32")
+    cs.cs_tune(h.ptr, cs.CS_TUNE_FEW_CELLS, -1)  # the strip kernels only
     fd = dev(f)
     few = host(h.collide(fd))  # automatic: two strips per warp
     cs.cs_tune(h.ptr, cs.CS_TUNE_GROUPS_PER_CTA, 1)
@@ -450,6 +458,37 @@ def test_few_cells_two_strips_per_warp_is_exact(cs, orc, N):
     assert np.array_equal(host(h.collide(dev(f[:5]))), few[:5])
     ref = orc.collide(f[[0, 15]], N, L, 1.0)
     assert rel(few[0], ref[0]) < 1e-5 and rel(few[15], ref[1]) < 1e-5
+    cs.cs_status(h.ptr)
+    h.close()
+
+
+@pytest.mark.parametrize("N", [24, 32])
+def test_few_cell_kernel_is_exact(cs, orc, N):
+    """At most 16 cells (N = 24, 32) a warp can hold one cell and its lanes
+    the outputs of a pencil.  Each output adds the same terms in the same
+    order as in the strip kernels, so every cell count from 1 to 16 gives the
+    same bits either way (and the same bits as the cell inside a larger
+    launch); the oracle checks two of the cells."""
+    f = I.random_mixture_cells(N, L, 40, first_id=1900)
+    h = cs.Handle(N, L, 1.0, "fp32")
+    assert cs.cs_tune_get(h.ptr, cs.CS_TUNE_FEW_CELLS) == 0  # its default limit (6 cells at N = 32, 9 at 24)
+    big = host(h.collide(dev(f)))  # 40 cells: the strip kernel
+    for nc in (1, 3, 16):
+        fd = dev(f[:nc])
+        cs.cs_tune(h.ptr, cs.CS_TUNE_FEW_CELLS, 16)
+        lane = host(h.collide(fd))
+        cs.cs_tune(h.ptr, cs.CS_TUNE_FEW_CELLS, -1)
+        strip = host(h.collide(fd))
+        assert np.array_equal(lane, strip), nc
+        assert np.array_equal(lane, big[:nc]), nc
+    cs.cs_tune(h.ptr, cs.CS_TUNE_FEW_CELLS, 2)  # at most 2 cells: 3 take the strip kernel
+    assert np.array_equal(host(h.collide(dev(f[:3]))), big[:3])
+    for bad in (-2, 17):
+        with pytest.raises(cs.CSError):
+            cs.cs_tune(h.ptr, cs.CS_TUNE_FEW_CELLS, bad)
+    cs.cs_tune(h.ptr, cs.CS_TUNE_FEW_CELLS, 0)
+    ref = orc.collide(f[[0, 2]], N, L, 1.0)
+    assert rel(big[0], ref[0]) < 1e-5 and rel(big[2], ref[1]) < 1e-5
     cs.cs_status(h.ptr)
     h.close()
 
