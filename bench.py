@@ -503,22 +503,26 @@ def few_cells_run(api, inputs, torch, device, h):
     N = 32
     f_all = torch.from_numpy(inputs.random_mixture_cells(N, L_BOX, 8, first_id=7600)).to(device)
     keep = api.cs_tune_get(h.ptr, api.CS_TUNE_FEW_CELLS)
+    keep_split = api.cs_tune_get(h.ptr, api.CS_TUNE_SPLIT)
     rows = []
-    for n in (1, 2, 4, 6):
-        f = f_all[:n].contiguous()
-        q = torch.empty_like(f)
-        r = {"cells": n}
-        outs = []
-        for key, mode in (("few_cell_ms", 16), ("strip_ms", -1)):
-            api.cs_tune(h.ptr, api.CS_TUNE_FEW_CELLS, mode)
-            r[key] = conv_ms_in_mode(api, torch, h, f, n, 1)
-            api.cs_collide(h.ptr, f, n, 1.0, q, 1)
-            outs.append(q.cpu().numpy())
-        r["identical"] = bool(np.array_equal(outs[0], outs[1]))
-        rows.append(r)
+    for split in (0, 2):  # whole pencils; two tile ranges per pencil (the serving loop's choice)
+        api.cs_tune(h.ptr, api.CS_TUNE_SPLIT, split)
+        for n in (1, 2, 4, 6):
+            f = f_all[:n].contiguous()
+            q = torch.empty_like(f)
+            r = {"cells": n, "tile_ranges": max(split, 1)}
+            outs = []
+            for key, mode in (("few_cell_ms", 16), ("strip_ms", -1)):
+                api.cs_tune(h.ptr, api.CS_TUNE_FEW_CELLS, mode)
+                r[key] = conv_ms_in_mode(api, torch, h, f, n, 1)
+                api.cs_collide(h.ptr, f, n, 1.0, q, 1)
+                outs.append(q.cpu().numpy())
+            r["identical"] = bool(np.array_equal(outs[0], outs[1]))
+            rows.append(r)
     api.cs_tune(h.ptr, api.CS_TUNE_FEW_CELLS, keep)
+    api.cs_tune(h.ptr, api.CS_TUNE_SPLIT, keep_split)
     table = h.weight_bytes()
-    ms1 = rows[0]["few_cell_ms"]
+    ms1 = min(r["few_cell_ms"] for r in rows if r["cells"] == 1)
     peak = None
     try:
         with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fp:

@@ -396,9 +396,10 @@ int cs_step(cs_handle_t h, double *f, int ncells, const cs_domain *dom, double d
  * cudaFree or other allocating routine.
  *   Arguments, layouts and results are those of cs_collide (same kernels).
  *   Size limit: the three spectral intermediates must fit in 64 MiB, i.e.
- *   at most 64 cells at N = 32 in CS_FP32, 32 cells at N = 32 in CS_FP64,
- *   384 cells at N = 16 in CS_FP32; larger ncells returns CS_EINVAL and a
- *   message with the limit for the handle's N and precision.
+ *   at most 64 cells at N = 32 in CS_FP32 (32 split four ways), 32 cells at
+ *   N = 32 in CS_FP64, 672 cells at N = 16 in CS_FP32 (384 split four ways);
+ *   larger ncells returns CS_EINVAL and a message with the limit for the
+ *   handle's N, precision and split.
  *   Every GPU that loads the library holds the 64 MiB array until the
  *   process exits.  All calls on a device share it and it keeps the last
  *   call's contents (each call writes every element it later reads, so
@@ -413,14 +414,16 @@ int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, double eps, d
                        cudaStream_t stream);
 
 /* Launch choices of the convolution (autotuner parameters).
- *   CS_TUNE_SPLIT           float handles at N = 16: 2 (default) or 4 tile
- *                           ranges per output pencil (4 shortens the tail of
- *                           a launch over few cells); the ranges' partial
- *                           sums are added in a fixed order, so a choice
- *                           changes the rounding of the sum, not its terms,
- *                           and holds for every call on the handle; handles
- *                           split 4 ways stay out of cs_collide_batched's
- *                           shared convolution launch
+ *   CS_TUNE_SPLIT           float handles at N = 16: 2 (default, 0 = 2) or 4
+ *                           tile ranges per output pencil (4 shortens the
+ *                           tail of a launch over few cells); at N = 32: 1
+ *                           (default, 0 = 1), 2 or 4 (shorter launches over
+ *                           one or two cells).  The ranges' partial sums are
+ *                           added in a fixed order, so a choice changes the
+ *                           rounding of the sum, not its terms, and holds for
+ *                           every call on the handle; handles split other
+ *                           than 2 ways at N = 16 or whole at N = 32 stay out
+ *                           of cs_collide_batched's shared convolution launch
  *   CS_TUNE_GROUPS_PER_CTA  1 or 2 groups of 32 cells share each weight tile
  *                           in shared memory (2 needs an even group count;
  *                           0: 2 where the count is even at N <= 32, else 1)

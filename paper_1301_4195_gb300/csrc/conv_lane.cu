@@ -29,8 +29,14 @@
 // (m1, m2) row the C cells' N values one after another, so one bulk copy
 // stages a row of all cells and lane k3 reads partner m3' = k3 + N/2 - m3 of
 // its cell from consecutive words (no bank conflicts).  The transpose writes
-// into the handle's per-axis transform scratch (Y), unused by whole-cell
-// float transforms and by unsplit convolutions.
+// into a workspace region of its own (16 cells' f-hat at most); where a
+// handle has none (cs_collide_noalloc's view) the strip kernels serve.
+//
+// Tile split.  With S > 1 (CS_TUNE_SPLIT at N = 32) a work item is one of S
+// consecutive ranges of a pencil's tiles, summed into its own partial buffer
+// and added in range order by the last range to finish, the strip kernel's
+// cut and order, so the two kernels stay bit-identical; the shorter items
+// shorten the launch at one or two cells, which the heaviest pencils set.
 //
 // Per lane the tile offsets of its weights (the STRIP layout of its strip,
 // see cs_internal.cuh) are fixed for the whole launch and sit in registers,
@@ -55,8 +61,10 @@ constexpr int lane_default(int N) { return N == 32 ? 6 : 9; }
 struct LaneJob {
     const float *ghat;
     const int *tile0, *order;
-    const float2 *Fc;  // f-hat, row-major by cell: [(m1 N + m2) C + c] N + m3
-    float2 *Qh;        // grouped layout, as the strip kernel writes it
+    const float2 *Fc;              // f-hat, row-major by cell: [(m1 N + m2) C + c] N + m3
+    float2 *Qh, *Qh2, *Qh3, *Qh4;  // grouped layout, as the strip kernel writes them (partial sums of S ranges)
+    int *done;                     // S > 1: finished ranges per pencil, zero at the launch
+    int S;
     int *err;
     float omega;
     int ncells;
@@ -161,7 +169,8 @@ __global__ void __launch_bounds__(32 * kLaneMaxCells, 1) conv_lane_kernel(LaneJo
         takes |= (o >= 0 ? 1u : 0u) << m3;
     }
 
-    const int nitems = N * N;
+    const int S = jb.S;
+    const int nitems = N * N * S;
     uint32_t tt = 0, issued = 0;  // ring uses consumed before the current item; uses issued (thread 0)
     bool ok = true;
     for (;;) {
@@ -171,13 +180,19 @@ __global__ void __launch_bounds__(32 * kLaneMaxCells, 1) conv_lane_kernel(LaneJo
         __syncthreads();
         if (item >= nitems) break;
 
-        const int pencil = jb.order[item];
+        // a pencil, or with S > 1 the part-th of S consecutive ranges of its
+        // tiles, exactly as the strip kernel cuts them
+        const int part = item % S, rest = item / S;
+        const int pencil = jb.order[rest];
         const int k1 = pencil / N, k2 = pencil % N;
         const int K1 = k1 + H, K2 = k2 + H;
         const int lo1 = max(0, K1 - N + 1);
         const int lo2 = max(0, K2 - N + 1), hi2 = min(N - 1, K2);
-        const int T = jb.tile0[pencil + 1] - jb.tile0[pencil];
-        const float *Gp = jb.ghat + (size_t)jb.tile0[pencil] * L::TSV;
+        const int Tall = jb.tile0[pencil + 1] - jb.tile0[pencil];
+        const int tb = (part * Tall + S - 1) / S, te = ((part + 1) * Tall + S - 1) / S;
+        const int T = te - tb;
+        const float *Gp = jb.ghat + (size_t)(jb.tile0[pencil] + tb) * L::TSV;
+        float2 *Qout = part == 0 ? jb.Qh : part == 1 ? jb.Qh2 : part == 2 ? jb.Qh3 : jb.Qh4;
 
         TileWalk pw;  // producer's walk (thread 0), NST tiles ahead
         int pt = 0;
@@ -210,6 +225,7 @@ __global__ void __launch_bounds__(32 * kLaneMaxCells, 1) conv_lane_kernel(LaneJo
         const bool stalled = jb.stall && blockIdx.x == 0 && tt == 0;  // the test stall
         if (threadIdx.x == 0 && !stalled) {
             pw.start(lo1, lo2, hi2, K1, K2);
+            for (int i = 0; i < tb; ++i) pw.next();
             while (pt < NST && pt < T)
                 if (!issue_next()) {
                     ok = false;
@@ -220,6 +236,7 @@ __global__ void __launch_bounds__(32 * kLaneMaxCells, 1) conv_lane_kernel(LaneJo
         float2 acc = make_float2(0.f, 0.f), hi = acc, lo = acc;
         TileWalk cw;
         cw.start(lo1, lo2, hi2, K1, K2);
+        for (int i = 0; i < tb; ++i) cw.next();
         int cur_m1 = cw.m1;
         for (int t = 0; t < T && ok; ++t) {
             const uint32_t u = tt + t;
@@ -261,11 +278,34 @@ __global__ void __launch_bounds__(32 * kLaneMaxCells, 1) conv_lane_kernel(LaneJo
         }
         two_sum(hi.x, lo.x, acc.x);
         two_sum(hi.y, lo.y, acc.y);
+        const size_t qi = ((size_t)pencil * N + k3) * kGroup + warp_id;
         if (lane < N && warp_id < C) {
             const float2 v = make_float2(hi.x + lo.x, hi.y + lo.y);
-            jb.Qh[((size_t)pencil * N + k3) * kGroup + warp_id] = make_float2(jb.omega * v.x, jb.omega * v.y);
+            Qout[qi] = make_float2(jb.omega * v.x, jb.omega * v.y);
         }
         tt += T;
+        if (S > 1) {
+            // the last of a pencil's S ranges adds the partial sums into Qh in
+            // range order, as the strip kernel does (same release / acquire
+            // count, same order of additions, loads that bypass L1)
+            __shared__ int s_last;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int old;
+                asm volatile("atom.add.acq_rel.gpu.s32 %0, [%1], 1;" : "=r"(old) : "l"(jb.done + rest) : "memory");
+                s_last = old == S - 1;
+            }
+            __syncthreads();
+            if (s_last && lane < N && warp_id < C) {
+                const float2 *more[3] = {jb.Qh2, jb.Qh3, jb.Qh4};
+                float2 v = __ldcg(jb.Qh + qi);
+                for (int m = 0; m < S - 1; ++m) {
+                    const float2 w = __ldcg(more[m] + qi);
+                    v = make_float2(v.x + w.x, v.y + w.y);
+                }
+                jb.Qh[qi] = v;
+            }
+        }
     }
     // after an abort: the copies thread 0 issued get a bounded time to land
     if (threadIdx.x == 0 && (!ok || *abort_flag)) {
@@ -299,13 +339,28 @@ int launch_lane_n(const Handle &hd, int ncells, cudaStream_t s)
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, hd.device);
     const int grid = std::min(N * N, std::max(1, sms) * occ);
-    float2 *Fc = (float2 *)hd.Y;
+    float2 *Fc = (float2 *)hd.Fc;
+    const int S = conv_split(hd);
     lane_transpose_kernel<N><<<N * N, N * ncells, 0, s>>>((const float2 *)hd.F, ncells, Fc);
     CS_LAUNCHED(1, s, "few-cell convolution: f-hat by cell");
     cudaError_t e = cudaMemsetAsync(hd.counter, 0, sizeof(int), s);
-    if (e != cudaSuccess) return cuda_error(e, "few-cell kernel work counter");
-    LaneJob jb{(const float *)hd.ghat, hd.pencil_tile0, hd.pencil_order, Fc, (float2 *)hd.Qh, hd.err,
-               (float)(hd.g.dz * hd.g.dz * hd.g.dz), ncells, hd.wait_us ? hd.wait_us : kWaitUs, hd.test_stall,
+    if (e == cudaSuccess && S > 1) e = cudaMemsetAsync(hd.done, 0, sizeof(int) * N * N, s);
+    if (e != cudaSuccess) return cuda_error(e, "few-cell kernel work counters");
+    LaneJob jb{(const float *)hd.ghat,
+               hd.pencil_tile0,
+               hd.pencil_order,
+               Fc,
+               (float2 *)hd.Qh,
+               (float2 *)hd.Qh2,
+               (float2 *)hd.Qh3,
+               (float2 *)hd.Qh4,
+               hd.done,
+               S,
+               hd.err,
+               (float)(hd.g.dz * hd.g.dz * hd.g.dz),
+               ncells,
+               hd.wait_us ? hd.wait_us : kWaitUs,
+               hd.test_stall,
                l2_hint_bits(hd.tune_l2)};
     kern<<<grid, threads, smem, s>>>(jb, hd.counter);
     CS_LAUNCHED(1, s, "few-cell convolution (one cell per warp, outputs over lanes)");
@@ -314,13 +369,17 @@ int launch_lane_n(const Handle &hd, int ncells, cudaStream_t s)
 
 }  // namespace
 
+bool lane_conv_capable(const Handle &hd)
+{
+    return hd.precision == CS_FP32 && hd.g.layout == LAYOUT_STRIP && (hd.g.N == 24 || hd.g.N == 32);
+}
+
 bool lane_conv_applies(const Handle &hd, int ncells)
 {
     const int most = hd.tune_few < 0   ? 0
                      : hd.tune_few > 0 ? std::min(hd.tune_few, kLaneMaxCells)
                                        : lane_default(hd.g.N);
-    return hd.precision == CS_FP32 && hd.g.layout == LAYOUT_STRIP && (hd.g.N == 24 || hd.g.N == 32) &&
-           !strip_uses_radius(hd) && conv_split(hd) == 1 && hd.Y != nullptr && ncells >= 1 && ncells <= most;
+    return lane_conv_capable(hd) && !strip_uses_radius(hd) && hd.Fc != nullptr && ncells >= 1 && ncells <= most;
 }
 
 int launch_strip_lane(const Handle &hd, int ncells, cudaStream_t s)

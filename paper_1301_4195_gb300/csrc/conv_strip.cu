@@ -13,7 +13,8 @@
 // into Qh in that fixed order.  At N = 16 S is 4 or 2, a handle's tuning
 // choice (CS_TUNE_SPLIT): smaller items shorten the tail of a launch over
 // few cells (128 cells: 3 % less time with 4), fewer save the combining at
-// many (2048 cells: 5 % less with 2).  The split belongs to the handle, not
+// many (2048 cells: 5 % less with 2).  At N = 32 S is 1 (default), 2 or 4
+// (conv_split32.cu); the few-cell kernel splits the same way.  The split belongs to the handle, not
 // to a call, so a cell's result never depends on how many cells share the
 // launch.  The pencil's k3 range is cut
 // into N/K strips of K outputs; warp (group g, strip w) keeps only its K
@@ -52,12 +53,13 @@ namespace cs {
 
 int conv_split_max(const Handle &hd)
 {
-    return (hd.precision == CS_FP32 && hd.g.layout == LAYOUT_STRIP && hd.g.N == 16) ? 4 : 1;
+    return (hd.precision == CS_FP32 && hd.g.layout == LAYOUT_STRIP && (hd.g.N == 16 || hd.g.N == 32)) ? 4 : 1;
 }
 
 int conv_split(const Handle &hd)
 {
     if (conv_split_max(hd) == 1) return 1;
+    if (hd.g.N == 32) return hd.tune_split == 4 ? 4 : hd.tune_split == 2 ? 2 : 1;  // default: whole pencils
     return hd.tune_split == 4 ? 4 : 2;
 }
 
@@ -68,8 +70,8 @@ bool strip_uses_radius(const Handle &hd)
 
 bool tile_shapes_available(const Handle &hd)
 {
-    return hd.precision == CS_FP32 && hd.g.layout == LAYOUT_STRIP && (hd.g.N == 16 || hd.g.N == 32) &&
-           !strip_uses_radius(hd);
+    return hd.precision == CS_FP32 && hd.g.layout == LAYOUT_STRIP &&
+           (hd.g.N == 16 || (hd.g.N == 32 && conv_split(hd) == 1)) && !strip_uses_radius(hd);
 }
 
 int launch_strip(const Handle &hd, int ncells, cudaStream_t s)

@@ -152,9 +152,10 @@ size_t spectral_bytes(const Handle &hd, int ncells)
 }
 
 // Carve the workspace: F, Qh, X, Y (spectral), Qt, f1 (state), scal
-// (transport tables), part5 (projection partials), and for a split
-// convolution one more spectral buffer (its fourth partial sum) and the
-// counters of finished tile ranges per (pencil, block).
+// (transport tables), part5 (projection partials), for a split convolution
+// one more spectral buffer (its fourth partial sum) and the counters of
+// finished tile ranges per (pencil, block), and for the few-cell kernel the
+// f-hat of up to 16 cells in its own layout.
 size_t workspace_bytes(const Handle &hd, int ncells, int geo_cells, size_t *offs)
 {
     const size_t sb = align_up(spectral_bytes(hd, ncells), 256);
@@ -178,6 +179,8 @@ size_t workspace_bytes(const Handle &hd, int ncells, int geo_cells, size_t *offs
     if (conv_split_max(hd) > 3) o += sb;  // Qh4
     if (offs) offs[9] = o;
     if (conv_split_max(hd) > 1) o += align_up(sizeof(int) * (size_t)hd.g.N * hd.g.N * ngroups_of(ncells), 256);
+    if (offs) offs[10] = o;
+    if (lane_conv_capable(hd)) o += align_up((size_t)std::min(ncells, 16) * hd.g.M * sizeof(float2), 256);
     return o;
 }
 
@@ -196,7 +199,7 @@ int ensure_workspace(Handle &hd, int ncells, int geo_cells = 0)
     if (ncells < hd.ws_cells) ncells = hd.ws_cells;
     if (geo_cells < hd.ws_geo_cells) geo_cells = hd.ws_geo_cells;
     drop_graphs(hd);  // captured steps point into the old workspace
-    size_t offs[10];
+    size_t offs[11];
     const size_t bytes = workspace_bytes(hd, ncells, geo_cells, offs);
     if (hd.ws) {
         cudaError_t e = cudaDeviceSynchronize();
@@ -224,6 +227,7 @@ int ensure_workspace(Handle &hd, int ncells, int geo_cells = 0)
     hd.Qh3 = b + offs[3];
     hd.Qh4 = conv_split_max(hd) > 3 ? b + offs[8] : nullptr;
     hd.done = conv_split_max(hd) > 1 ? (int *)(b + offs[9]) : nullptr;
+    hd.Fc = lane_conv_capable(hd) ? b + offs[10] : nullptr;
     hd.X = b + offs[2];
     hd.Y = b + offs[3];
     hd.Qt = (double *)(b + offs[4]);
@@ -1030,8 +1034,10 @@ int cs_autotune(cs_handle_t h, int ncells, cudaStream_t s, double *ms)
     if (hd.has_table) modes.push_back(1);
     if (hd.radA) modes.push_back(2);
     if (modes.empty()) modes.push_back(0);
-    // and the tile split where the handle has one (float, N = 16)
-    std::vector<int> splits = conv_split_max(hd) > 1 ? std::vector<int>{4, 2} : std::vector<int>{0};
+    // and the tile split where the handle has one (float, N = 16: 2 or 4; N = 32: 1, 2 or 4)
+    std::vector<int> splits = conv_split_max(hd) == 1 ? std::vector<int>{0}
+                              : hd.g.N == 32         ? std::vector<int>{0, 2, 4}
+                                                     : std::vector<int>{4, 2};
     const size_t nc = sizeof(cand) / sizeof(cand[0]);
     double best = 1e300;
     int bg = 0, bc = 0, bw = 0, bs = 0, bt = 0;

@@ -133,6 +133,7 @@ struct Handle {
     unsigned ws_generation = 0;  // bumped whenever the workspace moves
     // pieces of the workspace (set by layout_workspace)
     void *F = nullptr, *Qh = nullptr, *X = nullptr, *Y = nullptr;
+    void *Fc = nullptr;  // the few-cell kernel's f-hat of up to 16 cells (conv_lane.cu), or none
     // partial sums 2-4 of a split convolution (conv_split > 1; the kernel's
     // last part adds them into Qh): Qh2 aliases X, Qh3 aliases Y (scratch of
     // the per-axis transforms, which split handles do not use), Qh4 and the
@@ -271,6 +272,8 @@ int launch_strip_radius(const Handle &hd, int ncells, cudaStream_t s);  // conv_
 // conv_tiles.cu: the strip launch with the tile shape hd.tune_tile (2: U = 4;
 // 3: a 4-stage ring; 4: a 2-stage ring) at N = 16 and 32, stored tiles
 int launch_strip_tiles(const Handle &hd, int ncells, cudaStream_t s);
+int launch_strip_split32(const Handle &hd, int ncells, cudaStream_t s, bool rad);  // conv_split32.cu: N = 32, S = 2, 4
+bool lane_conv_capable(const Handle &hd);                           // conv_lane.cu: the handle's kind has a few-cell kernel
 bool lane_conv_applies(const Handle &hd, int ncells);               // conv_lane.cu: the few-cell kernel serves the call
 int launch_strip_lane(const Handle &hd, int ncells, cudaStream_t s);  // its transpose and convolution launches
 bool tile_shapes_available(const Handle &hd);

@@ -121,7 +121,7 @@ extern "C" int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, do
     // third and fourth, and the split's counters); inverse Qh -> X', Y'
     // (reusing Y's and F's space); then the per-block partial moments of the
     // projection
-    const int split = conv_split_max(hd);
+    const int split = conv_split(hd);
     const int nbuf = 3 + (split > 2 ? split - 2 : 0);
     const size_t part_bytes = (sizeof(double) * 5 * (size_t)ncells * conserve_parts(hd.g.M) + 255) / 256 * 256;
     const size_t done_bytes =

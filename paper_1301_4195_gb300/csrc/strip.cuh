@@ -870,7 +870,8 @@ int launch_strip_mode(const Handle &hd, int ncells, cudaStream_t s)
         return conv_split(hd) == 2 ? launch_n<16, 8, 8, 3, 3, 2, RAD>(hd, ncells, s)
                                    : launch_n<16, 8, 8, 3, 3, 4, RAD>(hd, ncells, s);
     case 24: return launch_n<24, 12, 4, 3, 2, 1, RAD>(hd, ncells, s);
-    case 32: return launch_n<32, 8, 8, 3, 3, 1, RAD>(hd, ncells, s);
+    case 32:  // tile split (CS_TUNE_SPLIT) in a translation unit of its own
+        return conv_split(hd) > 1 ? launch_strip_split32(hd, ncells, s, RAD) : launch_n<32, 8, 8, 3, 3, 1, RAD>(hd, ncells, s);
     case 48: return launch_n<48, 8, 8, 3, 2, 1, RAD>(hd, ncells, s);
     case 64: return launch_n<64, 8, 8, 3, 2, 1, RAD>(hd, ncells, s);
     default: return set_error(CS_ENOTSUP, "strip kernel: unsupported N");

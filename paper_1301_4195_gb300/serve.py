@@ -78,6 +78,12 @@ class _Class:
                  stream=None):
         self.N, self.lam, self.radius = N, lam, radius
         self.handle = api.Handle(N, L, lam, "fp32-radius" if radius else precision)
+        if N == 32 and precision == "fp32" and not radius:
+            # classes hold a handful of requests: two tile ranges per pencil
+            # make those launches shorter (one request 0.43 -> 0.30 ms, 7 to 16
+            # requests 1.37 -> 1.26 ms) at the cost of 1-2 % from 64 cells up;
+            # a request's result still does not depend on its class's size
+            api.cs_tune(self.handle.ptr, api.CS_TUNE_SPLIT, 2)
         self.stream = stream if stream is not None else torch.cuda.Stream(device=device)
         self.capacity = capacity
         self.buf = torch.empty((capacity, N, N, N), dtype=torch.float64, device=device)

@@ -462,17 +462,23 @@ def test_few_cells_two_strips_per_warp_is_exact(cs, orc, N):
     h.close()
 
 
-@pytest.mark.parametrize("N", [24, 32])
-def test_few_cell_kernel_is_exact(cs, orc, N):
+@pytest.mark.parametrize("N,split", [(24, 0), (32, 0), (32, 2), (32, 4)])
+def test_few_cell_kernel_is_exact(cs, orc, N, split):
     """At most 16 cells (N = 24, 32) a warp can hold one cell and its lanes
     the outputs of a pencil.  Each output adds the same terms in the same
-    order as in the strip kernels, so every cell count from 1 to 16 gives the
-    same bits either way (and the same bits as the cell inside a larger
-    launch); the oracle checks two of the cells."""
+    order as in the strip kernels, also with a pencil's tiles split into 2 or
+    4 ranges (N = 32), so every cell count from 1 to 16 gives the same bits
+    either way (and the same bits as the cell inside a larger launch); the
+    oracle checks two of the cells, and a split changes only the rounding."""
     f = I.random_mixture_cells(N, L, 40, first_id=1900)
     h = cs.Handle(N, L, 1.0, "fp32")
     assert cs.cs_tune_get(h.ptr, cs.CS_TUNE_FEW_CELLS) == 0  # its default limit (6 cells at N = 32, 9 at 24)
+    if split:
+        whole = host(h.collide(dev(f)))
+        cs.cs_tune(h.ptr, cs.CS_TUNE_SPLIT, split)
     big = host(h.collide(dev(f)))  # 40 cells: the strip kernel
+    if split:
+        assert 0 < np.max(np.abs(big - whole)) <= 1e-6 * np.max(np.abs(whole))
     for nc in (1, 3, 16):
         fd = dev(f[:nc])
         cs.cs_tune(h.ptr, cs.CS_TUNE_FEW_CELLS, 16)

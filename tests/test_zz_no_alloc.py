@@ -42,13 +42,15 @@ def _noalloc(api, h, f, Q, ncells):
 
 
 @pytest.mark.parametrize("N,prec,split,n1,n2", [(8, "fp64", 0, 33, 5), (16, "fp32", 0, 40, 64),
-                                                (16, "fp32", 4, 384, 7), (32, "fp32", 0, 64, 3)])
+                                                (16, "fp32", 4, 384, 7), (32, "fp32", 0, 64, 3),
+                                                (32, "fp32", 4, 32, 5)])
 def test_noalloc_matches_cs_collide_twice(cs, N, prec, split, n1, n2):
     """Both entry points run the same kernels in the same order on the same
     launch choices, so their results must agree bit for bit; any overlap of
     the intermediate buffers inside the fixed array would break that.  The
-    four-way split at N = 16 (the only launch that writes all four partial
-    sums and the counters of finished ranges) is run at its 384-cell limit."""
+    four-way split (the launches that write all four partial sums and the
+    counters of finished ranges) is run at its limits: 384 cells at N = 16,
+    32 at N = 32."""
     h = cs.Handle(N, L, 1.0, prec)
     if split:
         cs.cs_tune(h.ptr, cs.CS_TUNE_SPLIT, split)
@@ -66,9 +68,14 @@ def test_noalloc_matches_cs_collide_twice(cs, N, prec, split, n1, n2):
     h.close()
 
 
-@pytest.mark.parametrize("N,prec,limit", [(32, "fp64", 32), (16, "fp32", 384)])
-def test_noalloc_refuses_more_cells_than_the_fixed_array_holds(cs, N, prec, limit):
+@pytest.mark.parametrize("N,prec,split,limit", [(32, "fp64", 0, 32), (16, "fp32", 4, 384), (16, "fp32", 0, 672),
+                                                (32, "fp32", 0, 64), (32, "fp32", 4, 32)])
+def test_noalloc_refuses_more_cells_than_the_fixed_array_holds(cs, N, prec, split, limit):
+    """The limit follows from the buffers a call needs: three spectral
+    arrays, two more for a four-way split."""
     h = cs.Handle(N, L, 1.0, prec)
+    if split:
+        cs.cs_tune(h.ptr, cs.CS_TUNE_SPLIT, split)
     f = torch.zeros((limit + 1, N, N, N), dtype=torch.float64, device="cuda")
     Q = torch.empty_like(f)
     rc = _noalloc(cs, h, f, Q, limit + 1)
