@@ -345,9 +345,11 @@ struct CompSum<K, true> {
 };
 
 // where a strip keeps its compensated sums (measured: local memory wins at
-// N = 24 only; at N = 16 and 32 it cost 1-2 %)
-template <int N>
-constexpr bool strip_comp_local() { return N == 24; }
+// N = 24, and at N = 32 with two groups per CTA, where the freed registers
+// (166 -> 113) let two 8-warp CTAs share an SM: 13.27 -> 12.66 ms for 256
+// cells; at N = 16, and at N = 32 with one group, it cost 1-2 %)
+template <int N, int GPC = 1>
+constexpr bool strip_comp_local() { return N == 24 || (N == 32 && GPC == 2); }
 
 // One problem of a strip launch: a handle's weights, tile tables and
 // workspace.  A mixed launch carries several (of different N), each owning
@@ -643,7 +645,7 @@ __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &r
     }
 
     float2 acc[K];
-    CompSum<K, strip_comp_local<N>()> cs;
+    CompSum<K, strip_comp_local<N, GPC>()> cs;
 #pragma unroll
     for (int j = 0; j < K; ++j) acc[j] = make_float2(0.f, 0.f);
     cs.zero();
@@ -752,13 +754,14 @@ __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &r
 // Resident CTAs per SM the register allocation must allow: at N = 16 the
 // kernel is latency-bound and 128 registers (8 one-group or 4 two-group CTAs
 // per SM) measured faster than the ~134 the compiler picks on its own; for
-// the other N one CTA (no cap) measured best.  At N = 32 (one group per CTA)
-// three CTAs share an SM only while a thread needs at most 168 registers
-// (they are allocated in steps of 8): 170 rounded up to 176 and left two,
-// 7 % slower, and a cap of three CTAs made the compiler settle at 163, 2 %
-// slower than its own 166.
+// the other N one CTA (no cap) measured best, except N = 32 with two groups
+// per CTA (compensated sums in local memory, 113 registers, two CTAs of 8
+// warps per SM).  At N = 32 with one group per CTA three CTAs share an SM
+// only while a thread needs at most 168 registers (they are allocated in
+// steps of 8): 170 rounded up to 176 and left two, 7 % slower, and a cap of
+// three CTAs made the compiler settle at 163, 2 % slower than its own 166.
 template <int N, int GPC>
-constexpr int strip_min_ctas() { return N == 16 ? (GPC == 1 ? 8 : 4) : 1; }
+constexpr int strip_min_ctas() { return N == 16 ? (GPC == 1 ? 8 : 4) : (N == 32 && GPC == 2) ? 2 : 1; }
 
 template <int N, int K, int U, int NST, int GPC, int S, bool RAD, int HS = 1>
 __global__ void __launch_bounds__(32 * (N / K) * GPC / HS, strip_min_ctas<N, GPC>())
