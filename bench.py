@@ -52,7 +52,7 @@ MAX_SM_MHZ = 2070.0
 # DRAM bytes (read + write) per convolution launch from ncu captures of the
 # current kernel (profiles/), keyed by (N, cells); absent where not captured
 # since the kernel last changed
-TRAFFIC = {(16, 128): 18435584}
+TRAFFIC = {(32, 256): 2499984640 + 66020608, (16, 128): 18435584}
 SMS = 152
 FP32_LANES = 128
 

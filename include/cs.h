@@ -444,8 +444,9 @@ int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, double eps, d
  *                           traffic, not results
  *   CS_TUNE_TILE            float handles at N = 16 and 32 with stored tiles:
  *                           the xi-tile and the ring depth, 1 (default, 0 =
- *                           1): blocks of 8 uniform rows, 3 stages; 2: blocks
- *                           of 4 rows; 3: 4 stages; 4: 2 stages.  Every output
+ *                           1): blocks of 8 uniform rows, 3 stages (2 for two
+ *                           groups per CTA at N = 32); 2: blocks of 4 rows;
+ *                           3: 4 stages; 4: 2 stages.  Every output
  *                           adds its terms in the same order in all of them
  *                           (results bit for bit equal); cs_autotune times
  *                           them at the best launch shape

@@ -324,7 +324,7 @@ CS_TUNE_TEST_STALL = 6     # 1: the first CTA of each convolution launch issues 
 CS_TUNE_CHECK_INPUT = 7    # 1: scan inputs for non-finite values, 2: also for negative ones
 CS_TUNE_FORWARD_NEXT = 8   # 2: a Heun step's second forward transform in a launch of its own
 CS_TUNE_L2_HINT = 9        # 1: plain copies; 2 (default): L2 eviction priorities (weights first, rows last)
-CS_TUNE_TILE = 10          # xi-tile and ring depth at N = 16, 32: 1 (default) U 8 / 3 stages, 2 U 4, 3 4 stages, 4 2
+CS_TUNE_TILE = 10          # xi-tile and ring depth at N = 16, 32: 1 (default) U 8 / 3 stages (2: two groups at 32), 2 U 4, 3 4 stages, 4 2
 CS_TUNE_FEW_CELLS = 11     # most cells the few-cell kernel (N = 24, 32) serves: 0 its default, -1 never, 1 .. 16
 
 

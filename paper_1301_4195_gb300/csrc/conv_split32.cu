@@ -17,7 +17,7 @@ int launch_strip_split32(const Handle &hd, int ncells, cudaStream_t s, bool rad)
     const int S = conv_split(hd);
     if (rad)
         return S == 4 ? launch_n<32, 8, 8, 3, 3, 4, true>(hd, ncells, s) : launch_n<32, 8, 8, 3, 3, 2, true>(hd, ncells, s);
-    return S == 4 ? launch_n<32, 8, 8, 3, 3, 4, false>(hd, ncells, s) : launch_n<32, 8, 8, 3, 3, 2, false>(hd, ncells, s);
+    return S == 4 ? launch_n<32, 8, 8, 3, 2, 4, false>(hd, ncells, s) : launch_n<32, 8, 8, 3, 2, 2, false>(hd, ncells, s);
 }
 
 }  // namespace cs

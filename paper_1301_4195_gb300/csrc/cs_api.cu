@@ -1069,7 +1069,11 @@ int cs_autotune(cs_handle_t h, int ncells, cudaStream_t s, double *ms)
         hd.tune_ctas = c[1];
         double t = 0.0;
         if ((rc = time_it(&t)) != CS_OK) break;
-        if (t < best) {
+        // at N = 32 a tile split must win by 1 %: it reads the weight tiles
+        // in shorter runs (0.5 GB more DRAM traffic at 256 cells) and changes
+        // the rounding, for a gain within the noise of a few launches
+        const double bar = (hd.g.N == 32 && hd.tune_split > 1 && bs <= 1) ? 0.99 : 1.0;
+        if (t < best * bar) {
             best = t;
             bg = c[0];
             bc = c[1];

@@ -294,15 +294,19 @@ struct TileWalk {
 };
 
 // The compensated sums (hi, lo) of a strip's K outputs, folded once per m1
-// slab: in registers, or (LOCAL) in local memory, where the volatile array
-// keeps them out of the register file; at N = 24 that frees 48 registers a
-// thread and lets three CTAs share an SM instead of two.  Both forms run the
-// same operations in the same order.
-template <int K, bool LOCAL>
+// slab: in registers (WHERE 0), in local memory (1), where the volatile
+// array keeps them out of the register file, or in shared memory (2), value
+// i of thread t at i * stride + t (no bank conflicts).  At N = 24 local
+// memory frees 48 registers a thread and lets three CTAs share an SM instead
+// of two; at N = 32 with two groups per CTA shared memory frees 53 and lets
+// two 8-warp CTAs share one, where local memory would spill to L2 and DRAM
+// once two rings fill the SM's shared memory.  All forms run the same
+// operations in the same order.
+template <int K, int WHERE>
 struct CompSum;
 
 template <int K>
-struct CompSum<K, false> {
+struct CompSum<K, 0> {
     float2 hi[K], lo[K];
     __device__ __forceinline__ void zero()
     {
@@ -321,7 +325,7 @@ struct CompSum<K, false> {
 };
 
 template <int K>
-struct CompSum<K, true> {
+struct CompSum<K, 1> {
     volatile float v[4 * K];  // (hi.x, hi.y, lo.x, lo.y) per output
     __device__ __forceinline__ void zero()
     {
@@ -344,12 +348,39 @@ struct CompSum<K, true> {
     }
 };
 
+template <int K>
+struct CompSum<K, 2> {
+    float *v;    // this thread's first value
+    int stride;  // threads of the CTA
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int i = 0; i < 4 * K; ++i) v[i * stride] = 0.f;
+    }
+    __device__ __forceinline__ void add(int j, float2 p)
+    {
+        float hx = v[(4 * j) * stride], hy = v[(4 * j + 1) * stride], lx = v[(4 * j + 2) * stride],
+              ly = v[(4 * j + 3) * stride];
+        two_sum(hx, lx, p.x);
+        two_sum(hy, ly, p.y);
+        v[(4 * j) * stride] = hx;
+        v[(4 * j + 1) * stride] = hy;
+        v[(4 * j + 2) * stride] = lx;
+        v[(4 * j + 3) * stride] = ly;
+    }
+    __device__ __forceinline__ float2 value(int j) const
+    {
+        return make_float2(v[(4 * j) * stride] + v[(4 * j + 2) * stride],
+                           v[(4 * j + 1) * stride] + v[(4 * j + 3) * stride]);
+    }
+};
+
 // where a strip keeps its compensated sums (measured: local memory wins at
-// N = 24, and at N = 32 with two groups per CTA, where the freed registers
-// (166 -> 113) let two 8-warp CTAs share an SM: 13.27 -> 12.66 ms for 256
-// cells; at N = 16, and at N = 32 with one group, it cost 1-2 %)
-template <int N, int GPC = 1>
-constexpr bool strip_comp_local() { return N == 24 || (N == 32 && GPC == 2); }
+// N = 24; at N = 32 with two groups per CTA shared memory, whose freed
+// registers (166 -> ~113) let two 8-warp CTAs share an SM; at N = 16, and at
+// N = 32 with one group, leaving the registers measured 1-2 % slower)
+template <int N, int GPC = 1, bool RAD = false>
+constexpr int strip_comp_where() { return N == 24 ? 1 : (N == 32 && GPC == 2 && !RAD) ? 2 : 0; }
 
 // One problem of a strip launch: a handle's weights, tile tables and
 // workspace.  A mixed launch carries several (of different N), each owning
@@ -423,8 +454,9 @@ struct StripCfg {
     static constexpr uint32_t STAGE = (2 * GPC * ROWB + (RAD ? 0 : GB) + 127) / 128 * 128;
     static constexpr int WBUF = RAD ? strip_round4(strip_seg_max(N, K)) : 0;  // floats per warp
     static constexpr int NB = RAD ? 3 * (N / 2) * (N / 2) + 1 : 0;              // entries of B
+    static constexpr int COMPF = strip_comp_where<N, GPC, RAD>() == 2 ? 4 * K * 32 * WARPS : 0;  // compensated sums
     static constexpr size_t SMEM = kRingHead + (size_t)NST * STAGE +
-                                   sizeof(float) * ((size_t)WARPS * WBUF + (RAD ? TSV : 0) + strip_round4(NB));
+                                   sizeof(float) * ((size_t)WARPS * WBUF + (RAD ? TSV : 0) + strip_round4(NB) + COMPF);
 };
 
 // RAD: the per-CTA copies of the tile entry map and of B, after the warps'
@@ -645,7 +677,12 @@ __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &r
     }
 
     float2 acc[K];
-    CompSum<K, strip_comp_local<N, GPC>()> cs;
+    CompSum<K, strip_comp_where<N, GPC, RAD>()> cs;
+    if constexpr (strip_comp_where<N, GPC, RAD>() == 2) {
+        cs.v = reinterpret_cast<float *>(rg.stages + NST * C::STAGE) + C::WARPS * C::WBUF + (RAD ? C::TSV : 0) +
+               strip_round4(C::NB) + threadIdx.x;
+        cs.stride = 32 * C::WARPS;
+    }
 #pragma unroll
     for (int j = 0; j < K; ++j) acc[j] = make_float2(0.f, 0.f);
     cs.zero();
@@ -760,11 +797,11 @@ __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &r
 // only while a thread needs at most 168 registers (they are allocated in
 // steps of 8): 170 rounded up to 176 and left two, 7 % slower, and a cap of
 // three CTAs made the compiler settle at 163, 2 % slower than its own 166.
-template <int N, int GPC>
-constexpr int strip_min_ctas() { return N == 16 ? (GPC == 1 ? 8 : 4) : (N == 32 && GPC == 2) ? 2 : 1; }
+template <int N, int GPC, bool RAD = false>
+constexpr int strip_min_ctas() { return N == 16 ? (GPC == 1 ? 8 : 4) : (N == 32 && GPC == 2 && !RAD) ? 2 : 1; }
 
 template <int N, int K, int U, int NST, int GPC, int S, bool RAD, int HS = 1>
-__global__ void __launch_bounds__(32 * (N / K) * GPC / HS, strip_min_ctas<N, GPC>())
+__global__ void __launch_bounds__(32 * (N / K) * GPC / HS, strip_min_ctas<N, GPC, RAD>())
     conv_strip_kernel(StripJob jb, int *counter)
 {
     using C = StripCfg<N, K, U, NST, GPC, RAD, HS>;
@@ -874,7 +911,8 @@ int launch_strip_mode(const Handle &hd, int ncells, cudaStream_t s)
                                    : launch_n<16, 8, 8, 3, 3, 4, RAD>(hd, ncells, s);
     case 24: return launch_n<24, 12, 4, 3, 2, 1, RAD>(hd, ncells, s);
     case 32:  // tile split (CS_TUNE_SPLIT) in a translation unit of its own
-        return conv_split(hd) > 1 ? launch_strip_split32(hd, ncells, s, RAD) : launch_n<32, 8, 8, 3, 3, 1, RAD>(hd, ncells, s);
+        return conv_split(hd) > 1 ? launch_strip_split32(hd, ncells, s, RAD)
+                                  : launch_n<32, 8, 8, 3, RAD ? 3 : 2, 1, RAD>(hd, ncells, s);
     case 48: return launch_n<48, 8, 8, 3, 2, 1, RAD>(hd, ncells, s);
     case 64: return launch_n<64, 8, 8, 3, 2, 1, RAD>(hd, ncells, s);
     default: return set_error(CS_ENOTSUP, "strip kernel: unsupported N");
