@@ -323,13 +323,8 @@ int launch_lane_n(const Handle &hd, int ncells, cudaStream_t s)
     using L = LaneCfg<N>;
     static_assert(2 * L::nst(1) * sizeof(uint64_t) + sizeof(int) <= kRingHead, "ring head");
     auto kern = conv_lane_kernel<N>;
-    const size_t smem = L::smem(ncells);
-    static size_t smem_set = 0;  // largest dynamic shared memory granted so far
-    if (smem > 48 * 1024 && smem > smem_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_error(e, "few-cell kernel shared-memory attribute");
-        smem_set = smem;
-    }
+    const size_t smem = L::smem(ncells);  // 45 KB at most (16 cells at N = 32)
+    static_assert(L::smem(kLaneMaxCells) <= 48 * 1024, "the few-cell kernel needs no shared-memory opt-in");
     const int threads = 32 * ncells;
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem) != cudaSuccess || occ < 1) {
