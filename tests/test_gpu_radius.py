@@ -84,6 +84,34 @@ def test_radius_convolution_matches_oracle(cs, orc, N, ncells, lam):
     h.close()
 
 
+def test_radius_tiles_with_the_tile_split_at_n32(cs, orc):
+    """At N = 32 a handle may split each pencil's tiles into 2 or 4 ranges,
+    also when it rebuilds the weight tiles from the radius tables: the
+    ranges' sums agree with the stored tiles' to the weights' float rounding,
+    with the whole-pencil sums to the sums' rounding, and with the oracle.
+    40 cells: two 32-cell groups, the two-group launch."""
+    N, nc = 32, 40
+    f = I.random_mixture_cells(N, L, nc, first_id=1750)
+    fh = orc.dft_forward(f, N, L)
+    fd = dev(rinterleave(fh))
+    ref = orc.convolve(fh[:2], N, L, 1.0)
+    h = cs.Handle(N, L, 1.0, "fp32")
+    cs.cs_tune(h.ptr, cs.CS_TUNE_WEIGHTS, 2)
+    whole = cplx(host(h.convolve(fd)))
+    for split in (2, 4):
+        cs.cs_tune(h.ptr, cs.CS_TUNE_SPLIT, split)
+        cs.cs_tune(h.ptr, cs.CS_TUNE_WEIGHTS, 2)
+        got = cplx(host(h.convolve(fd)))
+        cs.cs_tune(h.ptr, cs.CS_TUNE_WEIGHTS, 1)
+        stored = cplx(host(h.convolve(fd)))
+        assert rel(got, stored) < 2e-6, split
+        assert rel(got, whole) < 1e-6, split
+        for c in range(2):
+            assert rel(got[c], ref[c]) < 1e-5, (split, c)
+    cs.cs_status(h.ptr)
+    h.close()
+
+
 def test_radius_only_handle_runs_the_operator(cs, orc):
     N = 16
     f = I.random_mixture_cells(N, L, 5, first_id=1800)
