@@ -43,7 +43,7 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
-@pytest.mark.parametrize("N,nc", [(16, 64), (32, 32)])
+@pytest.mark.parametrize("N,nc", [(16, 64), (32, 32), (32, 3), (24, 5)])  # the last two: the few-cell kernel
 def test_expired_wait_reports_timeout_and_the_handle_recovers(cs, N, nc):
     f = dev(I.random_mixture_cells(N, L, nc, first_id=8100))
     clean = cs.Handle(N, L, 1.0, "fp32")
