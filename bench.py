@@ -50,9 +50,29 @@ WORKLOADS = {
 }
 MAX_SM_MHZ = 2070.0
 # DRAM bytes (read + write) per convolution launch from ncu captures of the
-# current kernel (profiles/), keyed by (N, cells); absent where not captured
-# since the kernel last changed
-TRAFFIC = {(32, 256): 2499984640 + 66020608, (16, 128): 18435584}
+# current kernels (profiles/), keyed by (N, cells, groups per CTA, tile
+# ranges per pencil) with the default tile, stored weights and L2
+# priorities; absent (reported as null) where that launch was not captured
+TRAFFIC = {
+    (32, 256, 4, 1): 1491404544 + 67005696,
+    (32, 256, 2, 1): 2499984640 + 66020608,
+    (32, 256, 2, 2): 3038963968 + 138928896,
+    (16, 128, 2, 4): 18435584,
+}
+
+
+def traffic_key(N: int, ncells: int, launch: dict):
+    """The TRAFFIC key of the launch the handle's choices select, or None when
+    the choices are not the captured defaults (tile, weights, L2 priorities)."""
+    if launch is None or launch.get("tile") not in (0, 1) or launch.get("weights") != "stored tiles" or \
+            launch.get("l2_hint") not in (0, 2):
+        return None
+    groups = -(-ncells // 32)
+    g = launch["groups_per_cta"] or (2 if N <= 32 and groups % 2 == 0 else 1)
+    if g == 4 and (N != 32 or groups % 4):
+        g = 2 if groups % 2 == 0 else 1
+    split = launch["tile_split"] or (2 if N == 16 else 1)
+    return (N, ncells, g, split)
 SMS = 152
 FP32_LANES = 128
 
@@ -89,7 +109,7 @@ PEAK_TOPS = SMS * FP32_LANES * MAX_SM_MHZ * 1e6 / 1e12        # FP32 FMA-pipe la
 PEAK_TFLOPS = 2 * PEAK_TOPS                                   # one FMA = 2 flops
 
 
-def conv_roofline(N: int, ncells: int, avg_ms: float, probe=None) -> dict:
+def conv_roofline(N: int, ncells: int, avg_ms: float, probe=None, launch=None) -> dict:
     """Roofline of one convolution launch over ncells cells at grid N.  The
     kernel visits P(N) symmetrised pairs per cell, 6 FP32 FMA-pipe lane
     operations each (one packed FMUL2 + two FFMA2); frac_executed counts
@@ -103,7 +123,7 @@ def conv_roofline(N: int, ncells: int, avg_ms: float, probe=None) -> dict:
     out = {"bound": "alu", "achieved": ach, "peak": PEAK_TOPS, "unit": "T FP32 FMA-pipe lane-ops/s",
            "frac": ach / PEAK_TOPS, "frac_executed": ach / PEAK_TOPS,
            "frac_effective_pairs": ops_eff / t / 1e12 / PEAK_TOPS,
-           "traffic": TRAFFIC.get((N, ncells)), "avg_launch_ms": avg_ms,
+           "traffic": TRAFFIC.get(traffic_key(N, ncells, launch)), "avg_launch_ms": avg_ms,
            "ops_per_launch": ops, "effective_ops_per_launch": ops_eff,
            "tflops": 10.0 * unique_pairs_per_cell(N) * ncells / t / 1e12,
            "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz (max SM clock), derived"}
@@ -323,7 +343,7 @@ def secondary_workload(api, inputs, torch, device, args, wl, flush, probe):
     cavg = prof["convolve"][0] / max(prof["convolve"][1], 1)
     out = {"workload": describe(wl), "value": 2 * ncells * N ** 6 / (ms / k * 1e-3), "unit": UNIT,
            "ms_per_step": ms / k, "steps": k, "conv_ms": cavg,
-           "roofline": conv_roofline(N, ncells, cavg, probe), "launch": launch_choice(api, h),
+           "roofline": conv_roofline(N, ncells, cavg, probe, launch_choice(api, h)), "launch": launch_choice(api, h),
            "autotuned_ms": tuned, "stage_ms_per_step": {kk: v[0] / k for kk, v in prof.items()},
            "q_eval": q_eval_run(api, torch, h, fd, N, ncells),
            "weights": {"stored_conv_ms": conv_ms_in_mode(api, torch, h, fd, ncells, 1),
@@ -649,7 +669,7 @@ def run_ours(args):
     # measured pipe peaks beside the derived one (lane operations per second)
     probe = {"ffma_tlane_ops": api.cs_fma_probe(0) / 1e12, "ffma2_tlane_ops": api.cs_fma_probe(1) / 1e12,
              "dfma_tlane_ops": api.cs_fma_probe(2) / 1e12}
-    roof = conv_roofline(N, ncells, conv_avg, probe)
+    roof = conv_roofline(N, ncells, conv_avg, probe, launch_choice(api, h32))
     roof.update({"kernel": "conv_strip_kernel (step a2)", "autotuned_ms": tuned_ms,
                  "launch": launch_choice(api, h32), "probe": probe})
 

@@ -424,8 +424,10 @@ int cs_collide_noalloc(cs_handle_t h, const double *f, int ncells, double eps, d
  *                           every call on the handle; handles split other
  *                           than 2 ways at N = 16 or whole at N = 32 stay out
  *                           of cs_collide_batched's shared convolution launch
- *   CS_TUNE_GROUPS_PER_CTA  1 or 2 groups of 32 cells share each weight tile
- *                           in shared memory (2 needs an even group count;
+ *   CS_TUNE_GROUPS_PER_CTA  1, 2 or 4 groups of 32 cells share each weight
+ *                           tile in shared memory (2 needs an even group
+ *                           count; 4 float handles at N = 32 with stored
+ *                           tiles and a group count divisible by 4, else 2;
  *                           0: 2 where the count is even at N <= 32, else 1)
  *   CS_TUNE_CTAS_PER_SM     resident CTAs per SM of the persistent kernel
  *                           (capped by what fits)

@@ -380,7 +380,7 @@ struct CompSum<K, 2> {
 // registers (166 -> ~113) let two 8-warp CTAs share an SM; at N = 16, and at
 // N = 32 with one group, leaving the registers measured 1-2 % slower)
 template <int N, int GPC = 1, bool RAD = false>
-constexpr int strip_comp_where() { return N == 24 ? 1 : (N == 32 && GPC == 2 && !RAD) ? 2 : 0; }
+constexpr int strip_comp_where() { return N == 24 ? 1 : (N == 32 && GPC >= 2 && !RAD) ? 2 : 0; }
 
 // One problem of a strip launch: a handle's weights, tile tables and
 // workspace.  A mixed launch carries several (of different N), each owning
@@ -598,7 +598,12 @@ __device__ __forceinline__ bool strip_item(const StripJob &jb, int item, Ring &r
     // 228 + 156 at N = 32) instead of the same one twice.  Which warp sums
     // which strip moves no arithmetic.
     const int gl = HS == 1 ? warp_id / C::W : 0;
-    const int warp = HS == 1 ? (GPC == 2 ? (warp_id % C::W + gl * (C::W / 2)) % C::W : warp_id % C::W)
+    // (with four groups the shifts are 0, W/2, W/4, 3W/4: every sub-partition
+    // holds each of four strips once)
+    static_assert(GPC != 4 || C::W % 4 == 0, "four groups per CTA need a multiple of four strips");
+    const int warp = HS == 1 ? (GPC == 2   ? (warp_id % C::W + gl * (C::W / 2)) % C::W
+                                : GPC == 4 ? (warp_id % C::W + ((gl & 1) * 2 + (gl >> 1)) * (C::W / 4)) % C::W
+                                           : warp_id % C::W)
                              : 2 * warp_id + (lane >> 4);
     const int cl = HS == 1 ? lane : (lane & 15);
     const int k0 = warp * K;
@@ -891,7 +896,11 @@ int launch_n(const Handle &hd, int ncells, cudaStream_t s)
     // two groups per CTA by default up to N = 32 (N = 32, 256 cells: 13.27 ms against 13.44 ms with one
     // group, and 1.6 GB of DRAM reads instead of 2.2 GB); at N = 48 and 64 one group fills a CTA
     const bool two = hd.tune_gpc == 2 || (hd.tune_gpc == 0 && N <= 32);
-    if (even && two) return launch_cfg<N, K, U, NST2, 2, S, RAD>(hd, ncells, s);
+    // four groups per CTA (N = 32, stored tiles, a launch choice): one CTA of
+    // 16 warps per SM, each weight tile staged once for 128 cells
+    if constexpr (!RAD && N == 32 && StripCfg<N, K, U, NST2, 4>::SMEM <= 227 * 1024)
+        if (hd.tune_gpc == 4 && ngroups_of(ncells) % 4 == 0) return launch_cfg<N, K, U, NST2, 4, S, RAD>(hd, ncells, s);
+    if (even && (two || hd.tune_gpc == 4)) return launch_cfg<N, K, U, NST2, 2, S, RAD>(hd, ncells, s);
     // at most 16 cells: two strips per warp, 16 lanes each, so no lane holds padding
     if constexpr (!RAD && (N == 32 || N == 64))
         if (ncells <= 16 && hd.tune_gpc != 1) return launch_cfg<N, K, U, NST1, 1, S, RAD, 2>(hd, ncells, s);

@@ -428,6 +428,29 @@ def test_launch_choices_give_identical_results(cs):
     h.close()
 
 
+def test_launch_choices_at_n32_give_identical_results(cs):
+    """At N = 32 one, two or four 32-cell groups share a CTA (each group's
+    strips rotated differently among the warps): only scheduling and shared
+    weight tiles change, never a sum's order; four groups need a group count
+    divisible by four and fall back to two otherwise."""
+    N, nc = 32, 128
+    h = cs.Handle(N, L, 1.0, "fp32")
+    f = dev(I.random_mixture_cells(N, L, nc, first_id=950))
+    outs = []
+    for gpc in (1, 2, 4, 0):
+        cs.cs_tune(h.ptr, cs.CS_TUNE_GROUPS_PER_CTA, gpc)
+        assert cs.cs_tune_get(h.ptr, cs.CS_TUNE_GROUPS_PER_CTA) == gpc
+        outs.append(host(h.collide(f)))
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    cs.cs_tune(h.ptr, cs.CS_TUNE_GROUPS_PER_CTA, 4)
+    assert np.array_equal(host(h.collide(dev(host(f)[:96]))), outs[0][:96])  # three groups: two per CTA
+    with pytest.raises(cs.CSError):
+        cs.cs_tune(h.ptr, cs.CS_TUNE_GROUPS_PER_CTA, 3)
+    cs.cs_status(h.ptr)
+    h.close()
+
+
 def test_fma_probe_rates_are_plausible(cs):
     """The pipe probes land between a quarter of and just above the rates the
     unit counts give at the maximum clock (152 SMs x 128 FP32 lanes x 2.07 GHz
