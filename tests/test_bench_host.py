@@ -72,3 +72,26 @@ def test_roofline_states_both_pair_counts():
         assert bench.valid_pairs_per_cell(N) == 27 * N ** 6 // 64
         assert r["frac"] == r["frac_executed"]
         assert abs(r["achieved"] - 6.0 * bench.unique_pairs_per_cell(N) * 256 / 10e-3 / 1e12) < 1e-9
+
+
+def test_traffic_is_reported_only_for_the_captured_launch_shape():
+    """The roofline's DRAM traffic belongs to one launch shape: the default
+    and explicit choices that select a captured kernel map to its entry,
+    anything else (another tile shape, rebuilt weights, no L2 priorities, a
+    shape the group count cannot take) is reported as null."""
+    import bench
+    base = {"groups_per_cta": 0, "ctas_per_sm": 0, "tile_split": 0, "weights": "stored tiles", "l2_hint": 0,
+            "tile": 0}
+    assert bench.traffic_key(32, 256, base) == (32, 256, 2, 1)
+    assert bench.traffic_key(32, 256, dict(base, groups_per_cta=4)) == (32, 256, 4, 1)
+    assert bench.traffic_key(32, 256, dict(base, groups_per_cta=2, tile_split=2)) == (32, 256, 2, 2)
+    assert bench.traffic_key(16, 128, dict(base, groups_per_cta=2, tile_split=4)) == (16, 128, 2, 4)
+    assert bench.traffic_key(32, 96, dict(base, groups_per_cta=4)) == (32, 96, 1, 1)  # three groups: one per CTA
+    assert bench.traffic_key(32, 256, dict(base, tile=3)) is None
+    assert bench.traffic_key(32, 256, dict(base, weights="radius tables")) is None
+    assert bench.traffic_key(32, 256, dict(base, l2_hint=1)) is None
+    for key in ((32, 256, 4, 1), (32, 256, 2, 1), (32, 256, 2, 2), (16, 128, 2, 4)):
+        assert bench.TRAFFIC[key] > 0
+    r = bench.conv_roofline(32, 256, 12.5, None, dict(base, groups_per_cta=4))
+    assert r["traffic"] == bench.TRAFFIC[(32, 256, 4, 1)]
+    assert bench.conv_roofline(32, 256, 12.5, None, dict(base, tile=2))["traffic"] is None
