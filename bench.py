@@ -59,6 +59,8 @@ TRAFFIC = {
     (32, 256, 2, 2): 3038963968 + 138928896,
     (16, 128, 2, 4): 18435584,
 }
+# the same for the few-cell kernel, keyed by (N, cells, tile ranges per pencil)
+LANE_TRAFFIC = {(32, 1, 2): 915300864 + 3899648}
 
 
 def traffic_key(N: int, ncells: int, launch: dict):
@@ -542,7 +544,8 @@ def few_cells_run(api, inputs, torch, device, h):
     api.cs_tune(h.ptr, api.CS_TUNE_FEW_CELLS, keep)
     api.cs_tune(h.ptr, api.CS_TUNE_SPLIT, keep_split)
     table = h.weight_bytes()
-    ms1 = min(r["few_cell_ms"] for r in rows if r["cells"] == 1)
+    one = min((r for r in rows if r["cells"] == 1), key=lambda r: r["few_cell_ms"])
+    ms1 = one["few_cell_ms"]
     peak = None
     try:
         with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fp:
@@ -554,7 +557,9 @@ def few_cells_run(api, inputs, torch, device, h):
                         "(L=6, lambda=1), few-cell kernel against strip kernels",
             "rows": rows,
             "roofline_one_cell": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                                  "frac": achieved / peak if peak else None, "traffic": None, "bytes": table,
+                                  "frac": achieved / peak if peak else None,
+                                  "traffic": LANE_TRAFFIC.get((N, 1, one["tile_ranges"])), "bytes": table,
+                                  "tile_ranges": one["tile_ranges"],
                                   "note": "the weight table once per launch, against the measured HBM copy bandwidth"}}
 
 
